@@ -1,0 +1,371 @@
+"""Benchmark: extrinsic lnL evaluations per second and lnL_marg per second on one GB300.
+
+Workload (N = 1): the full-size plain ILE point -- 3 detectors (H1/L1/V1), all 21
+modes with 2 <= l <= 4, Q over +-0.1 s at 16384 Hz, SNR 30 -- marginalised over
+1e7 prior samples drawn on the device.  One step = one rift_ile_marginalize call
+(Philox draw, response, harmonics, Q gather/interpolation, quadratic forms,
+log-sum-exp, stopping rule) with Q/U/V already resident on the device.
+
+Under torchrun (N > 1) every rank marginalises its own point (independent points:
+weak scaling, no data-path collective); the barrier and the max over ranks use
+torch.distributed.  --impl reference times the FP64 oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+N_SAMPLES = 10_000_000
+WORKLOAD = "plain ILE full size: K=3 (H1,L1,V1), M=21 (2<=l<=4), Q +-0.1 s @ 16384 Hz (T=3277), SNR 30, N=1e7"
+
+
+def flops_per_sample(K: int, M: int, taps: int) -> int:
+    """Algorithmic FP32 flops of one likelihood evaluation (FMA = 2).
+
+    quadratic forms over pairs a <= b: products conj(ya) yb and ya yb (12), then per
+    detector Re(P U) (4) and R V (8); linear term per (k, lm): F conj(Y) (6) and per tap
+    Re(c q) + weight (5); harmonics ~14 M; response + delay ~60 + 40 K; transforms,
+    combine and log-sum-exp ~60."""
+    npair = M * (M + 1) // 2
+    quad = npair * (12 + 12 * K) + 10 * K
+    lin = K * M * (6 + 5 * taps) + 8 * K
+    return quad + lin + 14 * M + 60 + 40 * K + 60
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text())
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        if torch.cuda.is_available():
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda") if (torch.cuda.is_available() and dist.get_backend() == "nccl") else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def point_seed(rank: int) -> int:
+    """Rank r marginalises its own independent point (weak scaling over points)."""
+    return 2 + 1000 * rank
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+_ORACLE_PT = None
+
+
+def _oracle_init():
+    global _ORACLE_PT
+    import workload as W
+    _ORACLE_PT = W.make_point(W.cfg_full(), 2)
+
+
+def _oracle_chunk(args):
+    """One chunk of the oracle's plain marginalisation: draw, FP64 lnL, log-sum-exp state."""
+    seed, start, n = args
+    import numpy as np
+    from oracle import mc
+    pt = _ORACLE_PT
+    pr = mc.Prior(pt["t_lo"], pt["t_hi"])
+    t0 = time.perf_counter()
+    th, _, lpq = mc.draw(seed, 0, 0, np.arange(start, start + n, dtype=np.uint64), pr)
+    ell = mc.lnL_samples(pt, th) + lpq
+    acc = mc.Accum.of(ell)
+    return time.perf_counter() - t0, n, (acc.m, acc.s1, acc.s2, acc.n)
+
+
+class OraclePool:
+    """The FP64 oracle on the host cores: one spawned worker process per core, each holding the
+    full-size point; timed on bounded samples of the same workload."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init)
+        cal = self.pool.map(_oracle_chunk, [(31, i * 2000, 2000) for i in range(self.cores)])
+        self.per_sample = max(c[0] / c[1] for c in cal)
+
+    def run(self, target_s: float, start: int = 0):
+        chunk = 20000
+        n_chunks = max(self.cores, int(target_s / (self.per_sample * chunk)) * self.cores)
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_chunk, [(31, start + i * chunk, chunk) for i in range(n_chunks)])
+        wall = time.perf_counter() - t0
+        n = sum(r[1] for r in res)
+        return n / wall, n, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_throughput(target_s: float = 12.0):
+    op = OraclePool()
+    v, n, wall = op.run(target_s)
+    op.close()
+    return v, op.cores, f"{n} prior samples of the full-size point (indices 0..{n - 1}, seed 31)", wall
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_1902_04934_gb300 as rift
+    import workload as W
+
+    torch.cuda.set_device(local)
+    pt = W.make_point(W.cfg_full(), point_seed(rank))
+    K, M, T = pt["Q"].shape
+    h = rift.rift_ile_create(pt)
+    opts = dict(seed=1234 + rank, n_per_round=N_SAMPLES, max_evals=N_SAMPLES)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+
+    for _ in range(args.warmup):
+        rift.rift_ile_marginalize(h, **opts)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, kern_ms, launches = [], [], 0
+    results = []
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()                      # L2 flushed between timed steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = rift.rift_ile_marginalize(h, timing=1, **opts)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(r["kernel_ms"])
+        launches += r["kernel_launches"]
+        results.append(r)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+
+    total_ms = max_over_ranks(world, sum(step_ms))
+    ms_per_step = total_ms / args.steps
+    evals = N_SAMPLES * world
+    value = evals / (ms_per_step * 1e-3)
+
+    # roofline of the likelihood kernel (FP32 ALU bound)
+    taps = 4
+    fl = flops_per_sample(K, M, taps) * N_SAMPLES
+    kmean = statistics.mean(kern_ms)
+    achieved = fl / (kmean * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    f_mhz = clk["sm_mhz"] or 1455.0
+    peak = 2 * 128 * sms * f_mhz * 1e6 / 1e12
+
+    # end to end through the public API with host buffers: create (host Q/U/V -> device)
+    # + marginalise + result back, every step
+    e2e = None
+    if not args.no_e2e:
+        h2d = K * T * ((M + 1) // 2 * 2) * 8 + (M * (M + 1) // 2) * K * 16 + 2048
+        rift.rift_ile_destroy(h)
+        torch.cuda.synchronize()
+        times = []
+        rounds = 0
+        for s in range(max(1, min(args.steps, 5))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h2 = rift.rift_ile_create(pt)
+            r = rift.rift_ile_marginalize(h2, **opts)
+            rift.rift_ile_destroy(h2)
+            times.append(time.perf_counter() - t0)
+            rounds = r["rounds"]
+        e2e_s = max_over_ranks(world, statistics.mean(times))
+        e2e = {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 64 * rounds + 4,
+               "includes": "rift_ile_create from host FP64 arrays + rift_ile_marginalize + result read + destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sample, wall = cpu_oracle_throughput(args.cpu_seconds)
+        cpu = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "wall_s": round(wall, 2)}
+
+    r0 = results[-1]
+    out = {
+        "metric": "extrinsic lnL evals/sec (and lnL_marg/sec) per GB300",
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (double-float time index; f64 accumulators)",
+        "data": "synthetic: seeded chirp-like modes, analytic aLIGO PSD, Gaussian noise; samples drawn on device",
+        "config": {"workload": WORKLOAD, "global_batch": N_SAMPLES * world, "samples_per_point": N_SAMPLES,
+                   "points": world, "parallelism": f"independent points x{world}", "l2": "flushed between steps"},
+        "lnL_marg_per_s": world / (ms_per_step * 1e-3),
+        "lnL_marg": r0["lnL_marg"], "n_eff": r0["n_eff"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "mc_round_kernel<3> (fused draw + likelihood + block log-sum-exp)",
+                     "kernel_ms": kmean, "flops_per_sample": flops_per_sample(K, M, taps),
+                     "peak_basis": f"FP32 FMA: 128 lanes/SM x {sms} SMs x 2 flop x median SM clock {f_mhz} MHz "
+                                   "sampled during the run"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "wall_s": t_wall,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    rift.rift_ile_destroy(h)
+
+
+def run_reference(args, world, rank):
+    """The FP64 oracle timed as the reference arm on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    op = OraclePool()
+    per_step, desc = [], None
+    for s in range(args.warmup + args.steps):
+        v, n, wall = op.run(args.ref_seconds)
+        if s >= args.warmup:
+            per_step.append(v)
+            desc = f"{n} prior samples of the full-size point per step (seed 31), {op.cores} worker processes"
+    op.close()
+    v = statistics.mean(per_step)
+    out = {
+        "impl": "reference",
+        "metric": "extrinsic lnL evals/sec (and lnL_marg/sec) per GB300",
+        "value": v, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": N_SAMPLES / v * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (same workload generator)",
+        "config": {"workload": WORKLOAD, "global_batch": N_SAMPLES, "points": 1,
+                   "parallelism": "host cores (spawned processes)"},
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": op.cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=6.0)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * rift_ile.h -- C ABI of the GB300 extrinsic-likelihood library.
+ *
+ * The library evaluates, for one or many intrinsic points lambda, the extrinsic
+ * log-likelihood of Eq. (def:lnL:Decomposed) (Sec. II.A) from precomputed mode
+ * inner products Q, U, V (Eq. QUV), and reduces it to the marginalised
+ * likelihood of Eq. (lnLmarg) by importance-sampled Monte Carlo (Sec. II.A, II.C).
+ *
+ * Conventions shared by every entry point
+ *  - No exception crosses the ABI.  Every call returns a rift_status; details of the
+ *    last failure on a handle are in rift_ile_last_error().
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *    memory of the current device.  The caller keeps ownership of everything it
+ *    passes; the library copies what it needs at create time.
+ *  - Complex arrays are interleaved (re, im) float64.
+ *  - Angles in radians, times in seconds, distances in Mpc.
+ *  - Work is issued on the handle's stream (desc.cuda_stream, NULL = legacy default).
+ *    Entry points that return host results synchronise that stream; rift_ile_lnL
+ *    (device buffers) does not.
+ *  - The likelihood is, with F_k = F_+ - i F_x and x = D_ref / D,
+ *      lnL = x Re sum_k sum_lm F_k conj(Y_lm) Q_{k,lm}(t + delay_k)
+ *            - x^2/4 sum_k [ |F_k|^2 conj(Y)^T U_k Y + Re( conj(F_k)^2 Y^T V_k Y ) ],
+ *    Y_lm = -2Y_lm(incl, phi), delay_k = -(x_k . n)/c.  This is Eq. (def:lnL:Decomposed)
+ *    with the conjugations that follow from h_k = Re(conj(F_k) h), h = h_+ - i h_x.
+ */
+#ifndef RIFT_ILE_H
+#define RIFT_ILE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rift_ile rift_ile; /* opaque; owns all device buffers of one or many points */
+
+typedef enum {
+  RIFT_OK = 0,
+  RIFT_EINVAL = 1,        /* bad argument (sizes, null pointers, non-Hermitian U, ...) */
+  RIFT_EWINDOW = 2,       /* Q window does not cover t-range + time of flight + taps   */
+  RIFT_ENOMEM = 3,        /* device or host allocation failed                          */
+  RIFT_ECUDA = 4,         /* a CUDA runtime call failed                                */
+  RIFT_ETIMEOUT = 5,      /* a bounded device wait expired                             */
+  RIFT_ENONFINITE = 6,    /* a NaN/Inf likelihood was produced                         */
+  RIFT_ENOTCONVERGED = 7, /* max_evals reached before n_eff_target (results are valid) */
+  RIFT_EUNSUPPORTED = 8   /* valid request outside what this build implements          */
+} rift_status;
+
+/* Maximum sizes accepted by rift_ile_create. */
+#define RIFT_MAX_DET 4
+#define RIFT_MAX_MODES 21 /* all (l, m) with 2 <= l <= 4 */
+
+/*
+ * One intrinsic point: everything Eq. (def:lnL:Decomposed) needs that does not
+ * depend on the extrinsic sample (Sec. II.A, "multidimensional arrays").
+ * All pointers are host pointers, read during rift_ile_create only.
+ */
+typedef struct {
+  int n_det;                /* K, 1..RIFT_MAX_DET                                          */
+  const double *det_tensor; /* [K][3][3] response tensors (symmetric), Earth-fixed frame      */
+  const double *det_pos;    /* [K][3] vertex positions, metres, Earth-fixed frame             */
+  int n_modes;              /* M, 1..RIFT_MAX_MODES                                          */
+  const int *lm;            /* [M][2] (l, m), 2 <= l <= 4, |m| <= l, no duplicates            */
+  int n_t;                  /* T, samples of each Q_{k,lm} time series (>= 4)                */
+  const double *Q;          /* [K][M][T] complex: Q_{k,lm}(tau_j), tau_j = q_t0_gps[k] + j/fs */
+  const double *q_t0_gps;   /* [K] GPS time of Q[k][*][0]                                    */
+  double fs;                /* Q sampling rate, Hz                                           */
+  const double *U;          /* [K][M][M] complex, Hermitian: U_{k,lm,l'm'} = <h_lm|h_l'm'>   */
+  const double *V;          /* [K][M][M] complex, symmetric: V_{k,lm,l'm'} = <h*_lm|h_l'm'>  */
+  double t_ref_gps;         /* geocentre reference time; sample t is measured from it        */
+  double d_ref_mpc;         /* D_ref of Eq. (strain_mode)                                    */
+  double t_lo, t_hi;        /* time prior of the point, relative to t_ref (t_lo < t_hi)       */
+  int interp;               /* Q interpolation: 0 nearest, 1 linear, 3 cubic Lagrange         */
+  void *cuda_stream;        /* cudaStream_t, or NULL                                         */
+} rift_ile_desc;
+
+/*
+ * Create a handle for one point (Sec. II.B: Q, U, V are shipped to the device once).
+ * Validates sizes, U Hermitian and V symmetric (1e-10 relative), and that the Q
+ * window of every detector covers [t_lo - |x_k|/c - taps/fs, t_hi + |x_k|/c + taps/fs]
+ * (else RIFT_EWINDOW).  Computes GMST(t_ref) and all per-point constants in FP64 on
+ * the host (the sidereal angle is held fixed over the window, Sec. II.A).
+ * On failure *out is NULL.
+ */
+rift_status rift_ile_create(const rift_ile_desc *desc, rift_ile **out);
+
+/* Many points in one handle (the batched workload).  descs[i] as above; all points
+ * must share n_det and the stream of descs[0] is used. */
+rift_status rift_ile_batch_create(const rift_ile_desc *descs, int n_points, rift_ile **out);
+
+void rift_ile_destroy(rift_ile *h);
+const char *rift_status_str(rift_status s);
+const char *rift_ile_last_error(const rift_ile *h);
+int rift_ile_n_points(const rift_ile *h);
+
+/*
+ * Per-sample log-likelihood, Eq. (def:lnL:Decomposed), at caller-supplied samples
+ * (point 0 of the handle).  Device pointers, float32, each of length n:
+ * right ascension, declination, t (geocentre, relative to t_ref), polarisation psi,
+ * reference phase phi, inclination, distance D (Mpc).  lnL_out: device, length n.
+ * Asynchronous on the handle's stream.  A sample whose interpolation taps leave the
+ * Q window is clamped, flagged, and reported as RIFT_EWINDOW by the next call of
+ * rift_ile_check().
+ */
+rift_status rift_ile_lnL(rift_ile *h, size_t n, const float *ra, const float *dec, const float *t,
+                         const float *psi, const float *phi, const float *incl, const float *dist,
+                         float *lnL_out);
+
+/* Same with host pointers: the library copies the samples to the device, evaluates,
+ * copies lnL back and synchronises.  Staging buffers are owned by the handle. */
+rift_status rift_ile_lnL_host(rift_ile *h, size_t n, const float *ra, const float *dec, const float *t,
+                              const float *psi, const float *phi, const float *incl, const float *dist,
+                              float *lnL_out);
+
+/* Reads and clears the device status word (out-of-window taps, non-finite lnL). */
+rift_status rift_ile_check(rift_ile *h);
+
+/* Proposal kinds for rift_mc_opts.proposal. */
+#define RIFT_PROPOSAL_PRIOR 0
+#define RIFT_PROPOSAL_ADAPTIVE 1
+#define RIFT_PROPOSAL_LEARNED 2
+
+/*
+ * Monte Carlo options (Sec. II.C: fixed n_eff threshold; Sec. III.B: adaptive
+ * sampling prior regenerated from the most recent chunk).
+ * Prior: ra ~ U[0,2pi), sin dec ~ U[-1,1], t ~ U[t_lo,t_hi] of the point, psi ~ U[0,pi),
+ * phi ~ U[0,2pi), cos incl ~ U[-1,1], p(D) ~ D^2 on [d_lo, d_hi].
+ * Uniforms: Philox4x32-10, key = (seed lo32, seed hi32), counter = (sample index,
+ * round, block, point id); block b gives uniforms 4b..4b+3; u = ((x >> 9) + 1/2) 2^-23.
+ */
+typedef struct {
+  uint64_t seed;
+  uint32_t point_id;     /* counter word 3 (single-point handles); batches use the point index */
+  uint32_t n_per_round;  /* samples per round (chunk)                                   */
+  uint64_t max_evals;    /* stop after this many samples                                 */
+  double n_eff_target;   /* stop once sum w / max w reaches this                         */
+  double d_lo, d_hi;     /* distance prior bounds, Mpc                                   */
+  int proposal;          /* RIFT_PROPOSAL_*                                              */
+  int n_bins;            /* adaptive: bins per adapted coordinate (ra, sin dec, t), <= 256 */
+  double beta;           /* adaptive: tempering exponent on the weights                 */
+  double floor_eps;      /* adaptive: mixture weight of the prior in the new proposal   */
+  int adapt_rounds;      /* adaptive: rebuild tables after rounds 0..adapt_rounds-1 (<0: always) */
+  const float *tables;   /* adaptive: host [3][n_bins+1] float32 CDF tables of round 0, or NULL = prior */
+  const void *mdn;       /* learned proposal: a rift_mdn handle (RIFT_PROPOSAL_LEARNED)  */
+  float *dbg_ell;        /* optional device [max_evals]: log weight of sample (round r, i) at r*n_per_round+i */
+  float *dbg_tables;     /* optional device [rounds][3][n_bins+1]: tables used in each round */
+  int max_rounds;        /* optional cap on rounds (0 = none)                            */
+  int timing;            /* nonzero: time every likelihood-kernel launch with CUDA events */
+} rift_mc_opts;
+
+typedef struct {
+  double lnL_marg;   /* log( sum_i w_i / N ), w = L p / q                                */
+  double n_eff;      /* sum w / max w                                                    */
+  double n_eff_kish; /* (sum w)^2 / sum w^2                                              */
+  double sigma;      /* standard error of lnL_marg                                        */
+  uint64_t n_evals;  /* likelihood evaluations used                                       */
+  int rounds;
+  int status;        /* rift_status of this point                                          */
+  double acc_max, acc_s1, acc_s2; /* mergeable state: max l, sum e^{l-max}, sum e^{2(l-max)} */
+  double kernel_ms;  /* with opts.timing: summed duration of the likelihood-kernel launches */
+  int kernel_launches; /* likelihood + reduction + adaptive kernels launched by this call   */
+} rift_mc_result;
+
+/*
+ * Marginalised likelihood of point 0, Eq. (lnLmarg), by rounds of n_per_round
+ * samples drawn on the device, until n_eff >= n_eff_target or max_evals.
+ * Returns RIFT_ENOTCONVERGED (with a valid *res) if max_evals was reached first.
+ * Synchronises the handle's stream.
+ */
+rift_status rift_ile_marginalize(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
+
+/*
+ * Batched marginalisation of every point of a batch handle in one persistent launch
+ * per round group, replayed as a CUDA graph.  res: host array of n_points.
+ * Per point the same estimator and stopping rule as rift_ile_marginalize; the uniforms
+ * of point i use counter word 3 = i.
+ */
+rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
+
+/*
+ * Draw the samples of one round (prior or tables) without evaluating them: theta_out is
+ * device [7][n] float32 rows (ra, sin dec, t, psi, phi, cos incl, D); lpq_out device [n]
+ * (ln p - ln q), bins_out device [3][n] int32 or NULL.  tables: device [3][n_bins+1] or NULL.
+ */
+rift_status rift_ile_draw(rift_ile *h, const rift_mc_opts *opts, uint32_t round, const float *tables,
+                          size_t n, float *theta_out, float *lpq_out, int *bins_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIFT_ILE_H */

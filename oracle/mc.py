@@ -160,13 +160,13 @@ def rebuild_tables(ell, bins, n_bins, beta, floor_eps):
 
 
 def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_target,
-                adaptive=False, n_bins=100, beta=0.8, floor_eps=0.1, tables=None, interp=3,
-                max_rounds=None, keep=False):
+                adaptive=False, n_bins=100, beta=0.3, floor_eps=0.1, tables=None, interp=3,
+                max_rounds=None, keep=False, adapt_rounds=-1):
     """Round loop of Eq. (lnLmarg) with the n_eff stopping rule of Sec. II.C.
 
     adaptive=False: plain prior sampling.  adaptive=True: round 0 uses `tables`
-    (default: the prior's own uniform tables), later rounds use tables rebuilt from
-    the previous round.  Returns a dict with lnL_marg, n_eff, kish, sigma, n_evals,
+    (default: the prior's own uniform tables); after round r < adapt_rounds (all rounds
+    if adapt_rounds < 0) the tables are rebuilt from that round, otherwise kept.  Returns a dict with lnL_marg, n_eff, kish, sigma, n_evals,
     rounds (and per-round data if keep)."""
     acc = Accum()
     rnd = 0
@@ -174,17 +174,17 @@ def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_tar
     if adaptive and tables is None:
         tables = uniform_tables(n_bins)
     while True:
-        idx = np.arange(n_per_round, dtype=np.uint64)
+        idx = np.arange(min(n_per_round, max_evals - acc.n), dtype=np.uint64)
         th, bins, lpq = draw(seed, point, rnd, idx, prior, tables if adaptive else None)
         ell = lnL_samples(pt, th, interp) + lpq
         acc = acc.merge(Accum.of(ell))
         lnm, n_eff, kish, sig = acc.result()
         if keep:
-            hist.append(dict(ell=ell, tables=None if tables is None else tables.copy()))
+            hist.append(dict(ell=ell, bins=bins, tables=None if tables is None else tables.copy()))
         rnd += 1
         if n_eff >= n_eff_target or acc.n >= max_evals or (max_rounds and rnd >= max_rounds):
             break
-        if adaptive:
+        if adaptive and (adapt_rounds < 0 or rnd - 1 < adapt_rounds):
             tables, _ = rebuild_tables(ell, bins, n_bins, beta, floor_eps)
     lnm, n_eff, kish, sig = acc.result()
     out = dict(lnL_marg=lnm, n_eff=n_eff, kish=kish, sigma=sig, n_evals=acc.n, rounds=rnd, acc=acc)

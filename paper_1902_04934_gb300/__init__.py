@@ -1,0 +1,279 @@
+"""Python binding of the GB300 extrinsic-likelihood library (argument marshalling only).
+
+Every computation runs in the CUDA library built from ``csrc/`` (``_lib/librift_ile.so``);
+this module only converts Python/numpy/torch arguments to the C ABI declared in
+``include/rift_ile.h`` and back.  Importing it fails loudly when the library is
+missing: there is no CPU fallback.
+
+Functions carry the names of the C entry points:
+
+* rift_ile_create(point) / rift_ile_batch_create(points) -> handle
+* rift_ile_lnL(h, ra, dec, t, psi, phi, incl, dist, out=None)   (CUDA tensors)
+* rift_ile_lnL_host(h, ...)                                       (numpy arrays)
+* rift_ile_marginalize(h, **opts) -> dict
+* rift_ile_batch_marginalize(h, **opts) -> list of dicts
+* rift_ile_draw(h, round, n, tables=None, **opts) -> (theta, lpq, bins)
+* rift_ile_destroy(h)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+_LIBPATH = _PKG / "_lib" / "librift_ile.so"
+
+STATUS = {0: "RIFT_OK", 1: "RIFT_EINVAL", 2: "RIFT_EWINDOW", 3: "RIFT_ENOMEM", 4: "RIFT_ECUDA",
+          5: "RIFT_ETIMEOUT", 6: "RIFT_ENONFINITE", 7: "RIFT_ENOTCONVERGED", 8: "RIFT_EUNSUPPORTED"}
+PROPOSAL = {"prior": 0, "adaptive": 1, "learned": 2}
+
+
+class RiftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Desc(C.Structure):
+    _fields_ = [("n_det", C.c_int), ("det_tensor", C.c_void_p), ("det_pos", C.c_void_p),
+                ("n_modes", C.c_int), ("lm", C.c_void_p), ("n_t", C.c_int), ("Q", C.c_void_p),
+                ("q_t0_gps", C.c_void_p), ("fs", C.c_double), ("U", C.c_void_p), ("V", C.c_void_p),
+                ("t_ref_gps", C.c_double), ("d_ref_mpc", C.c_double), ("t_lo", C.c_double),
+                ("t_hi", C.c_double), ("interp", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class McOpts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("point_id", C.c_uint32), ("n_per_round", C.c_uint32),
+                ("max_evals", C.c_uint64), ("n_eff_target", C.c_double), ("d_lo", C.c_double),
+                ("d_hi", C.c_double), ("proposal", C.c_int), ("n_bins", C.c_int), ("beta", C.c_double),
+                ("floor_eps", C.c_double), ("adapt_rounds", C.c_int), ("tables", C.c_void_p),
+                ("mdn", C.c_void_p), ("dbg_ell", C.c_void_p), ("dbg_tables", C.c_void_p),
+                ("max_rounds", C.c_int), ("timing", C.c_int)]
+
+
+class McResult(C.Structure):
+    _fields_ = [("lnL_marg", C.c_double), ("n_eff", C.c_double), ("n_eff_kish", C.c_double),
+                ("sigma", C.c_double), ("n_evals", C.c_uint64), ("rounds", C.c_int), ("status", C.c_int),
+                ("acc_max", C.c_double), ("acc_s1", C.c_double), ("acc_s2", C.c_double),
+                ("kernel_ms", C.c_double), ("kernel_launches", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not _LIBPATH.exists():
+        raise ImportError(f"CUDA library {_LIBPATH} is not built; run __graft_entry__.build() "
+                          "(paper_1902_04934_gb300._build.build()) first")
+    lib = C.CDLL(str(_LIBPATH))
+    P, S, I, U32, U64, D = C.c_void_p, C.c_size_t, C.c_int, C.c_uint32, C.c_uint64, C.c_double
+    sig = {
+        "rift_ile_create": (I, [C.POINTER(Desc), C.POINTER(P)]),
+        "rift_ile_batch_create": (I, [C.POINTER(Desc), I, C.POINTER(P)]),
+        "rift_ile_destroy": (None, [P]),
+        "rift_status_str": (C.c_char_p, [I]),
+        "rift_ile_last_error": (C.c_char_p, [P]),
+        "rift_ile_n_points": (I, [P]),
+        "rift_ile_lnL": (I, [P, S] + [P] * 8),
+        "rift_ile_lnL_host": (I, [P, S] + [P] * 8),
+        "rift_ile_check": (I, [P]),
+        "rift_ile_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
+        "rift_ile_batch_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
+        "rift_ile_draw": (I, [P, C.POINTER(McOpts), U32, P, S, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIB_PATH = str(_LIBPATH)
+
+
+class Handle:
+    """Owns a rift_ile* and keeps the host arrays of its descriptor alive during create."""
+
+    def __init__(self, ptr, n_points):
+        self.ptr = C.c_void_p(ptr)
+        self.n_points = n_points
+
+    def __del__(self):
+        try:
+            rift_ile_destroy(self)
+        except Exception:
+            pass
+
+
+def _check(h, status):
+    if status not in (0,):
+        msg = _lib.rift_ile_last_error(h.ptr if h is not None else None)
+        raise RiftError(status, (msg or b"").decode())
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.float64)
+
+
+def _desc(pt, interp=3, stream=None, keep=None):
+    K = int(np.asarray(pt["det_tensor"]).shape[0])
+    lm = np.ascontiguousarray(np.asarray(pt["lm"], dtype=np.int32).reshape(-1, 2))
+    Q = np.asarray(pt["Q"])
+    M, T = Q.shape[1], Q.shape[2]
+    arrs = dict(det_tensor=_f64(pt["det_tensor"]), det_pos=_f64(pt["det_pos"]), lm=lm,
+                Q=np.ascontiguousarray(Q.astype(np.complex128)).view(np.float64),
+                q_t0_gps=_f64(pt["q_t0_gps"]),
+                U=np.ascontiguousarray(np.asarray(pt["U"]).astype(np.complex128)).view(np.float64),
+                V=np.ascontiguousarray(np.asarray(pt["V"]).astype(np.complex128)).view(np.float64))
+    if keep is not None:
+        keep.append(arrs)
+    d = Desc()
+    d.n_det = K
+    d.det_tensor = arrs["det_tensor"].ctypes.data
+    d.det_pos = arrs["det_pos"].ctypes.data
+    d.n_modes = M
+    d.lm = arrs["lm"].ctypes.data
+    d.n_t = T
+    d.Q = arrs["Q"].ctypes.data
+    d.q_t0_gps = arrs["q_t0_gps"].ctypes.data
+    d.fs = float(pt["fs"])
+    d.U = arrs["U"].ctypes.data
+    d.V = arrs["V"].ctypes.data
+    d.t_ref_gps = float(pt["t_ref_gps"])
+    d.d_ref_mpc = float(pt["d_ref_mpc"])
+    d.t_lo = float(pt["t_lo"])
+    d.t_hi = float(pt["t_hi"])
+    d.interp = int(interp)
+    d.cuda_stream = stream
+    return d
+
+
+def rift_ile_create(pt, interp=3, stream=None):
+    keep = []
+    d = _desc(pt, interp, stream, keep)
+    out = C.c_void_p()
+    st = _lib.rift_ile_create(C.byref(d), C.byref(out))
+    if st != 0:
+        raise RiftError(st, "rift_ile_create failed (see stderr)")
+    return Handle(out.value, 1)
+
+
+def rift_ile_batch_create(points, interp=3, stream=None):
+    keep = []
+    arr = (Desc * len(points))(*[_desc(p, interp, stream, keep) for p in points])
+    out = C.c_void_p()
+    st = _lib.rift_ile_batch_create(arr, len(points), C.byref(out))
+    if st != 0:
+        raise RiftError(st, "rift_ile_batch_create failed (see stderr)")
+    return Handle(out.value, len(points))
+
+
+def rift_ile_destroy(h):
+    if h is not None and h.ptr:
+        _lib.rift_ile_destroy(h.ptr)
+        h.ptr = C.c_void_p(None)
+
+
+def _dptr(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError("sample arrays differ in length")
+    return t.data_ptr()
+
+
+def rift_ile_lnL(h, ra, dec, t, psi, phi, incl, dist, out=None):
+    """Device-buffer call: CUDA float32 tensors in, CUDA float32 tensor out (asynchronous)."""
+    import torch
+    n = ra.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=ra.device)
+    ptrs = [_dptr(a, n) for a in (ra, dec, t, psi, phi, incl, dist, out)]
+    _check(h, _lib.rift_ile_lnL(h.ptr, n, *ptrs))
+    return out
+
+
+def rift_ile_lnL_host(h, ra, dec, t, psi, phi, incl, dist):
+    """Host-buffer call: numpy float32 in, numpy float32 out (copies inside the library)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (ra, dec, t, psi, phi, incl, dist)]
+    n = arrs[0].shape[0]
+    out = np.empty(n, dtype=np.float32)
+    _check(h, _lib.rift_ile_lnL_host(h.ptr, n, *[a.ctypes.data for a in arrs], out.ctypes.data))
+    return out
+
+
+def rift_ile_check(h):
+    _check(h, _lib.rift_ile_check(h.ptr))
+
+
+def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target=1e300, d_lo=1.0,
+          d_hi=1000.0, proposal="prior", n_bins=100, beta=0.3, floor_eps=0.1, adapt_rounds=-1,
+          tables=None, mdn=None, dbg_ell=None, dbg_tables=None, max_rounds=0, timing=0, keep=None):
+    o = McOpts()
+    o.seed = int(seed)
+    o.point_id = int(point_id)
+    o.n_per_round = int(n_per_round)
+    o.max_evals = int(max_evals)
+    o.n_eff_target = float(n_eff_target)
+    o.d_lo = float(d_lo)
+    o.d_hi = float(d_hi)
+    o.proposal = PROPOSAL[proposal] if isinstance(proposal, str) else int(proposal)
+    o.n_bins = int(n_bins)
+    o.beta = float(beta)
+    o.floor_eps = float(floor_eps)
+    o.adapt_rounds = int(adapt_rounds)
+    if tables is not None:
+        tb = np.ascontiguousarray(tables, dtype=np.float32)
+        if keep is not None:
+            keep.append(tb)
+        o.tables = tb.ctypes.data
+    o.mdn = mdn.ptr.value if mdn is not None else None
+    o.dbg_ell = dbg_ell.data_ptr() if dbg_ell is not None else None
+    o.dbg_tables = dbg_tables.data_ptr() if dbg_tables is not None else None
+    o.max_rounds = int(max_rounds)
+    o.timing = int(timing)
+    return o
+
+
+def rift_ile_marginalize(h, **kw):
+    keep = []
+    o = _opts(keep=keep, **kw)
+    r = McResult()
+    st = _lib.rift_ile_marginalize(h.ptr, C.byref(o), C.byref(r))
+    if st not in (0, 7):
+        _check(h, st)
+    return r.as_dict()
+
+
+def rift_ile_batch_marginalize(h, **kw):
+    keep = []
+    o = _opts(keep=keep, **kw)
+    res = (McResult * h.n_points)()
+    st = _lib.rift_ile_batch_marginalize(h.ptr, C.byref(o), res)
+    if st not in (0, 7):
+        _check(h, st)
+    return [r.as_dict() for r in res]
+
+
+def rift_ile_draw(h, rnd, n, tables=None, **kw):
+    """Samples of one round on the device: theta (7, n), ln p - ln q (n,), bins (3, n)."""
+    import torch
+    keep = []
+    o = _opts(keep=keep, **kw)
+    dev = torch.device("cuda")
+    theta = torch.empty((7, n), dtype=torch.float32, device=dev)
+    lpq = torch.empty(n, dtype=torch.float32, device=dev)
+    bins = torch.empty((3, n), dtype=torch.int32, device=dev)
+    tptr = None
+    if tables is not None:
+        tt = torch.as_tensor(np.asarray(tables, dtype=np.float32), device=dev).contiguous()
+        keep.append(tt)
+        tptr = tt.data_ptr()
+    _check(h, _lib.rift_ile_draw(h.ptr, C.byref(o), int(rnd), tptr, n, theta.data_ptr(), lpq.data_ptr(),
+                                 bins.data_ptr()))
+    return theta, lpq, bins

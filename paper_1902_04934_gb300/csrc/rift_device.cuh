@@ -1,0 +1,292 @@
+// Device-side data layout and per-sample arithmetic of the extrinsic likelihood.
+//
+// Eq. (def:lnL:Decomposed), evaluated per sample in FP32 with the time index,
+// the sidereal angle offset and the time of flight kept in double-float (pairs of
+// FP32, error-free transformations), which the sample-to-sample precision needs:
+// Q oscillates at ~100 Hz, so 1e-9 s of time error is ~1e-4 in lnL at SNR 30.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define RIFT_MAXK 4
+#define RIFT_MAXM 21
+#define RIFT_MAXPAIR (RIFT_MAXM * (RIFT_MAXM + 1) / 2)
+#define RIFT_MAXTERM 5
+#define RIFT_MAXBINS 256
+
+// status bits written by kernels
+#define RIFT_FLAG_WINDOW 1u
+#define RIFT_FLAG_NONFINITE 2u
+
+struct DetC {
+  float d[6];         // response tensor xx xy xz yy yz zz
+  float P[3], Plo[3]; // fs * x_k / c, samples (double-float)
+  float c0, c0lo;     // (t_lo - tau0_k) fs: Q index of the prior's lower edge (double-float)
+  float ct, ctlo;     // -tau0_k fs: Q index of t = 0 (double-float)
+};
+
+struct ModeC {
+  int l, m, nterm, pad;
+  float coef[RIFT_MAXTERM]; // -2Y_lm = e^{i m phi} sum_j coef_j c^{kc_j} s^{2l-kc_j}
+  int kc[RIFT_MAXTERM];
+};
+
+// One intrinsic point.  Lives in device memory (array over points); kernels copy
+// it into shared memory.
+struct PointC {
+  int K, M, T, Mp;    // detectors, modes, Q samples, Q row stride (M rounded up to even)
+  int npair, interp, pad0, pad1;
+  long long q_off;    // offset of this point's Q in the Q arena (float2 units), 16-byte aligned
+  long long uv_off;   // offset of this point's pair coefficients (float4 units)
+  float fs, dref;     // Q rate (Hz), D_ref (Mpc)
+  float g_hi, g_lo;   // GMST / 2pi (turns), double-float
+  float A, Alo;       // (t_hi - t_lo) fs, samples (double-float)
+  float t_lo, t_span; // time prior (s)
+  float tmin_idx, tmax_idx; // first/last admissible interpolation base index (window check)
+  DetC det[RIFT_MAXK];
+  ModeC mode[RIFT_MAXM];
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), written from the published round function.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// u = ((x >> 9) + 1/2) 2^-23: 24 significant bits, exact in FP32 and FP64, in (0, 1).
+__device__ __forceinline__ float bits_to_u(uint32_t x) {
+  return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float helpers (Knuth two-sum, FMA two-product).
+// ---------------------------------------------------------------------------
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  df s = two_sum(a.hi, b);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+
+// Split a double-float index into integer base and fraction in [0, 1).
+__device__ __forceinline__ void df_floor(df s, int &i, float &f) {
+  float fl = floorf(s.hi);
+  f = __fadd_rn(__fsub_rn(s.hi, fl), s.lo);
+  i = (int)fl;
+  if (f < 0.f) { f += 1.f; i -= 1; }
+  else if (f >= 1.f) { f -= 1.f; i += 1; }
+}
+
+// ---------------------------------------------------------------------------
+// Per-sample geometry: everything but the Q gather and quadratic forms.
+// ---------------------------------------------------------------------------
+struct SampleGeo {
+  float2 F[RIFT_MAXK];  // F_k = F_+ - i F_x
+  df s[RIFT_MAXK];      // Q index of t + delay_k (double-float, samples)
+  float x;              // D_ref / D
+};
+
+// Antenna pattern at psi = 0 and the delay from the source direction.
+// e_ra = (-sin a, cos a, 0), e_dec = (-sd cos a, -sd sin a, cd); at psi = 0 the axes are
+// X0 = -e_ra, Y0 = e_dec and F(psi) = e^{2 i psi} F(0) for F = F_+ - i F_x.
+template <int K>
+__device__ __forceinline__ void response_delay(const PointC &P, float ca, float sa, df sd, float cd,
+                                               float c2p, float s2p, SampleGeo &g, const df base_rel[]) {
+  const float ex = -sa, ey = ca;                   // e_ra (z = 0)
+  const float fx = -sd.hi * ca, fy = -sd.hi * sa, fz = cd; // e_dec
+  const float nx = cd * ca, ny = cd * sa;                // source direction (z = sin dec)
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float *d = P.det[k].d;
+    // e_ra^T d e_ra, e_dec^T d e_dec, e_ra^T d e_dec
+    const float dex = d[0] * ex + d[1] * ey;
+    const float dey = d[1] * ex + d[3] * ey;
+    const float dez = d[2] * ex + d[4] * ey;
+    const float ee = ex * dex + ey * dey;
+    const float ff = fx * (d[0] * fx + d[1] * fy + d[2] * fz) + fy * (d[1] * fx + d[3] * fy + d[4] * fz) +
+                     fz * (d[2] * fx + d[4] * fy + d[5] * fz);
+    const float ef = fx * dex + fy * dey + fz * dez;
+    // X0 = -e_ra, Y0 = e_dec: F+0 = ee - ff, Fx0 = -2 ef; F0 = F+0 - i Fx0 = (ee - ff) + 2 i ef
+    const float fr = ee - ff, fi = 2.f * ef;
+    g.F[k] = make_float2(c2p * fr - s2p * fi, s2p * fr + c2p * fi);
+    // delay_k fs = -(P . n) fs-scaled; double-float accumulation of the three products
+    const DetC &D = P.det[k];
+    df acc = df_mul_f(df{D.P[0], D.Plo[0]}, nx);
+    acc = df_add(acc, df_mul_f(df{D.P[1], D.Plo[1]}, ny));
+    acc = df_add(acc, df_mul(df{D.P[2], D.Plo[2]}, sd));
+    g.s[k] = df_add(base_rel[k], df{-acc.hi, -acc.lo});
+  }
+}
+
+// -2Y_lm for all modes of the point into smem column Ys[a * stride] (float2).
+__device__ __forceinline__ void swsh_modes(const PointC &P, float c, float s, float cphi, float sphi,
+                                           float2 *Ys, int stride) {
+  float cp[9], sp[9];
+  cp[0] = 1.f; sp[0] = 1.f;
+#pragma unroll
+  for (int j = 1; j < 9; ++j) { cp[j] = cp[j - 1] * c; sp[j] = sp[j - 1] * s; }
+  // e^{i m phi}, m = 0..4
+  float2 e[5];
+  e[0] = make_float2(1.f, 0.f);
+  e[1] = make_float2(cphi, sphi);
+  e[2] = make_float2(cphi * cphi - sphi * sphi, 2.f * cphi * sphi);
+  e[3] = make_float2(e[2].x * cphi - e[2].y * sphi, e[2].x * sphi + e[2].y * cphi);
+  e[4] = make_float2(e[2].x * e[2].x - e[2].y * e[2].y, 2.f * e[2].x * e[2].y);
+  for (int a = 0; a < P.M; ++a) {
+    const ModeC &md = P.mode[a];
+    float v = 0.f;
+    for (int j = 0; j < md.nterm; ++j) {
+      // indices are bounded by construction (0 <= kc <= 2l <= 8); select from the
+      // unrolled register arrays without dynamic indexing
+      const int kc = md.kc[j], ks = 2 * md.l - kc;
+      float pc = 1.f, ps = 1.f;
+#pragma unroll
+      for (int q = 1; q < 9; ++q) { if (q == kc) pc = cp[q]; if (q == ks) ps = sp[q]; }
+      v = fmaf(md.coef[j], pc * ps, v);
+    }
+    const int am = md.m < 0 ? -md.m : md.m;
+    float2 em = e[0];
+#pragma unroll
+    for (int q = 1; q < 5; ++q) if (q == am) em = e[q];
+    if (md.m < 0) em.y = -em.y;
+    Ys[a * stride] = make_float2(v * em.x, v * em.y);
+  }
+}
+
+// Lagrange interpolation weights: taps i-1..i+2 (cubic), i..i+1 (linear), i (nearest).
+__device__ __forceinline__ int interp_weights(int interp, float mu, float w[4], int &first) {
+  if (interp == 3) {
+    const float a = mu + 1.f, b = mu - 1.f, c = mu - 2.f;
+    w[0] = -mu * b * c * (1.f / 6.f);
+    w[1] = a * b * c * 0.5f;
+    w[2] = -a * mu * c * 0.5f;
+    w[3] = a * mu * b * (1.f / 6.f);
+    first = -1;
+    return 4;
+  }
+  if (interp == 1) { w[0] = 1.f - mu; w[1] = mu; first = 0; return 2; }
+  w[0] = 1.f; first = 0; return 1;
+}
+
+// Linear term: Re sum_k sum_lm F_k conj(Y_lm) Q_{k,lm}(t_k), taps gathered from
+// the point's Q rows [K][T][Mp] (modes contiguous, so the taps of one detector are
+// one contiguous block of ntap * Mp complex values).
+template <int K>
+__device__ __forceinline__ float linear_term(const PointC &P, const float2 *__restrict__ Q, const SampleGeo &g,
+                                             const float2 *Ys, int ystride, uint32_t &flags) {
+  float lin = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int i; float mu;
+    df s = g.s[k];
+    if (P.interp == 0) s = df_add_f(s, 0.5f);
+    df_floor(s, i, mu);
+    if (P.interp == 0) mu = 0.f;
+    float w[4]; int first;
+    const int ntap = interp_weights(P.interp, mu, w, first);
+    int i0 = i + first;
+    if (i0 < 0 || i0 + ntap > P.T) {
+      flags |= RIFT_FLAG_WINDOW;
+      i0 = min(max(i0, 0), P.T - ntap);
+    }
+    const float2 *row = Q + ((long long)k * P.T + i0) * P.Mp;
+    const float2 Fk = g.F[k];
+    float lk = 0.f;
+    for (int a = 0; a < P.M; a += 2) {
+      const float2 y0 = Ys[a * ystride];
+      const float2 y1 = (a + 1 < P.M) ? Ys[(a + 1) * ystride] : make_float2(0.f, 0.f);
+      // c = F_k conj(Y)
+      const float c0r = Fk.x * y0.x + Fk.y * y0.y, c0i = Fk.y * y0.x - Fk.x * y0.y;
+      const float c1r = Fk.x * y1.x + Fk.y * y1.y, c1i = Fk.y * y1.x - Fk.x * y1.y;
+      float acc = 0.f;
+      for (int r = 0; r < ntap; ++r) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(row + (long long)r * P.Mp + a));
+        float t = c0r * q.x - c0i * q.y;
+        t = fmaf(c1r, q.z, t);
+        t = fmaf(-c1i, q.w, t);
+        acc = fmaf(w[r], t, acc);
+      }
+      lk += acc;
+    }
+    lin += lk;
+  }
+  return lin;
+}
+
+// Quadratic term: sum_k |F_k|^2 conj(Y)^T U_k Y + Re(conj(F_k)^2 Y^T V_k Y), using the
+// upper triangle a <= b (U Hermitian, V symmetric); coefficients C[pair][k] =
+// (U, V) with the factor 2 of the off-diagonal pairs folded in.  Row partial sums.
+template <int K>
+__device__ __forceinline__ float quad_term(const PointC &P, const float4 *__restrict__ C, const SampleGeo &g,
+                                           const float2 *Ys, int ystride) {
+  float A[K], Br[K], Bi[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { A[k] = 0.f; Br[k] = 0.f; Bi[k] = 0.f; }
+  int p = 0;
+  for (int a = 0; a < P.M; ++a) {
+    const float2 ya = Ys[a * ystride];
+    float rA[K], rBr[K], rBi[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { rA[k] = 0.f; rBr[k] = 0.f; rBi[k] = 0.f; }
+    for (int b = a; b < P.M; ++b, ++p) {
+      const float2 yb = Ys[b * ystride];
+      const float pr = ya.x * yb.x + ya.y * yb.y;   // conj(ya) yb
+      const float pi = ya.x * yb.y - ya.y * yb.x;
+      const float qr = ya.x * yb.x - ya.y * yb.y;   // ya yb
+      const float qi = ya.x * yb.y + ya.y * yb.x;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float4 c = C[p * K + k];
+        rA[k] = fmaf(pr, c.x, fmaf(-pi, c.y, rA[k]));
+        rBr[k] = fmaf(qr, c.z, fmaf(-qi, c.w, rBr[k]));
+        rBi[k] = fmaf(qr, c.w, fmaf(qi, c.z, rBi[k]));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) { A[k] += rA[k]; Br[k] += rBr[k]; Bi[k] += rBi[k]; }
+  }
+  float quad = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float2 F = g.F[k];
+    const float f2 = F.x * F.x + F.y * F.y;
+    // conj(F)^2 = (Fr^2 - Fi^2) - 2 i Fr Fi
+    const float gr = F.x * F.x - F.y * F.y, gi = -2.f * F.x * F.y;
+    quad += f2 * A[k] + (gr * Br[k] - gi * Bi[k]);
+  }
+  return quad;
+}

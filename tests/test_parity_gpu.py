@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 oracle.
+
+Per-sample tolerance (derived in the design notes): |d lnL| <= 1e-3 for templates of
+optimal SNR <= 30, i.e. 1e-3 * max(1, <h|h> / 900), since FP32 arithmetic carries a
+relative error on the terms being cancelled, whose size is <h|h>.  lnL_marg: 1e-4.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import workload as W
+from oracle import likelihood as L
+from oracle import mc
+from oracle import philox as P
+
+pytestmark = pytest.mark.gpu
+
+TOL_LNL = 1e-3
+TOL_MARG = 1e-4
+
+
+def _hh(pt, th64):
+    """<h|h> of each sample's template: -2 lnL with Q = 0."""
+    z = dict(pt)
+    z["Q"] = np.zeros_like(pt["Q"])
+    return -2.0 * L.lnL_factorised(z, **th64)
+
+
+def _tol(pt, th64):
+    return TOL_LNL * np.maximum(1.0, _hh(pt, th64) / 900.0)
+
+
+@pytest.fixture(scope="module")
+def p_small():
+    return W.make_point(W.cfg_small(), 1)
+
+
+@pytest.fixture(scope="module")
+def p_full():
+    return W.make_point(W.cfg_full(), 2)
+
+
+def _random_theta(n, seed, t_lo, t_hi):
+    r = np.random.default_rng(seed)
+    th = dict(ra=r.uniform(0, 2 * np.pi, n), dec=np.arcsin(r.uniform(-1, 1, n)), t=r.uniform(t_lo, t_hi, n),
+              psi=r.uniform(0, np.pi, n), phi=r.uniform(0, 2 * np.pi, n), incl=np.arccos(r.uniform(-1, 1, n)),
+              dist=np.cbrt(r.uniform(1, 1000.0 ** 3, n)))
+    return {k: v.astype(np.float32) for k, v in th.items()}
+
+
+def _near_peak_theta(pt, n, seed, k=200):
+    """Prior draws concentrated on the high-likelihood region (to exercise the cancellation)."""
+    th = _random_theta(40 * n, seed, pt["t_lo"], pt["t_hi"])
+    v = L.lnL_factorised(pt, **{a: b.astype(np.float64) for a, b in th.items()})
+    top = np.argsort(v)[-k:]
+    r = np.random.default_rng(seed + 1)
+    out = {a: np.concatenate([b[top], b[:n - k]]) for a, b in th.items()}
+    # jitter the top ones a little to get many near-peak samples
+    out["t"][:k] += r.normal(0, 2e-4, k).astype(np.float32)
+    out["t"] = np.clip(out["t"], pt["t_lo"], pt["t_hi"]).astype(np.float32)
+    return out
+
+
+def _lnl_gpu(lib, h, th):
+    import torch
+    d = {k: torch.as_tensor(v, device="cuda") for k, v in th.items()}
+    out = lib.rift_ile_lnL(h, d["ra"], d["dec"], d["t"], d["psi"], d["phi"], d["incl"], d["dist"])
+    torch.cuda.synchronize()
+    lib.rift_ile_check(h)
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("which,n", [("p_small", 5001), ("p_full", 3001)])
+def test_lnl_array_parity(lib, cuda, request, which, n):
+    pt = request.getfixturevalue(which)
+    h = lib.rift_ile_create(pt)
+    th = _random_theta(n, 5, pt["t_lo"], pt["t_hi"])
+    th64 = {k: v.astype(np.float64) for k, v in th.items()}
+    got = _lnl_gpu(lib, h, th)
+    want = L.lnL_factorised(pt, **th64)
+    err = np.abs(got - want)
+    tol = _tol(pt, th64)
+    assert np.all(err <= tol), (err.max(), np.argmax(err / tol), want[np.argmax(err / tol)])
+
+
+@pytest.mark.parametrize("which", ["p_small", "p_full"])
+def test_lnl_near_peak(lib, cuda, request, which):
+    pt = request.getfixturevalue(which)
+    h = lib.rift_ile_create(pt)
+    th = _near_peak_theta(pt, 1000, 6)
+    th64 = {k: v.astype(np.float64) for k, v in th.items()}
+    got = _lnl_gpu(lib, h, th)
+    want = L.lnL_factorised(pt, **th64)
+    assert np.all(np.abs(got - want) <= _tol(pt, th64)), np.max(np.abs(got - want))
+
+
+@pytest.mark.parametrize("interp", [0, 1])
+def test_lnl_other_interpolation_rules(lib, cuda, p_small, interp):
+    h = lib.rift_ile_create(p_small, interp=interp)
+    th = _random_theta(2000, 7, p_small["t_lo"], p_small["t_hi"])
+    th64 = {k: v.astype(np.float64) for k, v in th.items()}
+    got = _lnl_gpu(lib, h, th)
+    want = L.lnL_factorised(p_small, **th64, interp=interp)
+    # nearest-sample rounding is a decision taken at .5: compare away from ties only
+    ok = np.abs(got - want) <= _tol(p_small, th64)
+    assert ok.mean() > (0.999 if interp == 0 else 1.0 - 1e-12)
+
+
+def test_lnl_host_matches_device(lib, cuda, p_small):
+    h = lib.rift_ile_create(p_small)
+    th = _random_theta(777, 8, p_small["t_lo"], p_small["t_hi"])
+    a = _lnl_gpu(lib, h, th)
+    b = lib.rift_ile_lnL_host(h, *[th[k] for k in ("ra", "dec", "t", "psi", "phi", "incl", "dist")])
+    assert np.array_equal(a.astype(np.float32), b)
+
+
+def test_lnl_empty_and_window_flag(lib, cuda, p_small):
+    import torch
+    h = lib.rift_ile_create(p_small)
+    e = torch.empty(0, dtype=torch.float32, device="cuda")
+    lib.rift_ile_lnL(h, e, e, e, e, e, e, e)
+    th = _random_theta(64, 9, p_small["t_lo"], p_small["t_hi"])
+    th["t"][3] = 1.0                      # far outside the Q window
+    with pytest.raises(lib.RiftError) as ex:
+        _lnl_gpu(lib, h, th)
+    assert ex.value.status == 2
+    lib.rift_ile_check(h)                 # the flag was cleared
+
+
+def test_draw_matches_oracle_uniforms(lib, cuda, p_small):
+    n = 10007
+    theta, lpq, _ = lib.rift_ile_draw(h := lib.rift_ile_create(p_small), 3, n, seed=99, point_id=0)
+    th = theta.cpu().numpy().astype(np.float64)
+    u = P.uniforms(99, 0, 3, np.arange(n, dtype=np.uint64), 8)
+    pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
+    ref = mc.prior_transform(u, pr)
+    assert np.array_equal(th[1], ref["sindec"])              # exact: 2u - 1
+    assert np.array_equal(th[5], ref["cosi"])
+    assert np.allclose(th[0], ref["ra"], rtol=2e-7, atol=0)
+    assert np.allclose(th[2], ref["t"], rtol=0, atol=1e-8)
+    assert np.allclose(th[6], ref["dist"], rtol=3e-7)
+    assert np.all(lpq.cpu().numpy() == 0)
+
+
+def _peaked_tables(pt, nb=64):
+    pr = mc.Prior(pt["t_lo"], pt["t_hi"])
+    r = mc.marginalize(pt, 555, 0, pr, 40000, 80000, 1e300, adaptive=True, n_bins=nb, keep=True, max_rounds=2)
+    h = r["history"][-1]
+    tab, _ = mc.rebuild_tables(h["ell"], h["bins"], nb, 0.8, 0.1)
+    return tab
+
+
+def test_draw_with_tables_bitexact_bins(lib, cuda, p_small):
+    nb = 64
+    tab = _peaked_tables(p_small, nb)
+    n = 20000
+    h = lib.rift_ile_create(p_small)
+    theta, lpq, bins = lib.rift_ile_draw(h, 1, n, tables=tab, seed=7, proposal="adaptive", n_bins=nb)
+    pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
+    th, b, lq = mc.draw(7, 0, 1, np.arange(n, dtype=np.uint64), pr, tab)
+    assert np.array_equal(bins.cpu().numpy(), b)
+    g = theta.cpu().numpy().astype(np.float64)
+    assert np.allclose(g[0], th["ra"], atol=2e-6)
+    assert np.allclose(g[2], th["t"], atol=1e-8)
+    assert np.allclose(lpq.cpu().numpy(), lq, atol=2e-6)
+
+
+def _marg_gpu(lib, h, **kw):
+    return lib.rift_ile_marginalize(h, **kw)
+
+
+def test_marginalize_small_parity(lib, cuda, p_small):
+    import torch
+    n = 100000
+    h = lib.rift_ile_create(p_small)
+    dbg = torch.empty(n, dtype=torch.float32, device="cuda")
+    res = _marg_gpu(lib, h, seed=21, n_per_round=n, max_evals=n, dbg_ell=dbg)
+    pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
+    ref = mc.marginalize(p_small, 21, 0, pr, n, n, 1e300)
+    assert res["n_evals"] == n
+    assert abs(res["lnL_marg"] - ref["lnL_marg"]) < TOL_MARG, (res["lnL_marg"], ref["lnL_marg"])
+    assert abs(res["n_eff"] - ref["n_eff"]) <= 1e-3 * ref["n_eff"] + 1e-3
+    th, _, _ = mc.draw(21, 0, 0, np.arange(n, dtype=np.uint64), pr)
+    want = mc.lnL_samples(p_small, th)
+    got = dbg.cpu().numpy().astype(np.float64)
+    th64 = dict(ra=th["ra"], dec=np.arcsin(th["sindec"]), t=th["t"], psi=th["psi"], phi=th["phi"],
+                incl=np.arccos(th["cosi"]), dist=th["dist"])
+    assert np.all(np.abs(got - want) <= _tol(p_small, th64))
+    # the device reduction equals the exact log-sum-exp of the device's own samples
+    own = mc.Accum.of(got).result()
+    assert abs(own[0] - res["lnL_marg"]) < 1e-9
+
+
+def test_marginalize_multiround_ragged(lib, cuda, p_small):
+    h = lib.rift_ile_create(p_small)
+    res = _marg_gpu(lib, h, seed=22, n_per_round=30000, max_evals=100000)
+    ref = mc.marginalize(p_small, 22, 0, mc.Prior(p_small["t_lo"], p_small["t_hi"]), 30000, 100000, 1e300)
+    assert res["rounds"] == 4 and res["n_evals"] == 100000 and ref["n_evals"] == 100000
+    assert abs(res["lnL_marg"] - ref["lnL_marg"]) < TOL_MARG
+
+
+def test_marginalize_stops_at_neff_target(lib, cuda, p_small):
+    """Sec. II.C stopping rule: with the n_eff reached after three rounds as the target, the run
+    stops at the first round whose pooled n_eff reaches it."""
+    h = lib.rift_ile_create(p_small)
+    kw = dict(seed=23, n_per_round=20000, proposal="adaptive", n_bins=50, beta=0.3)
+    ref = _marg_gpu(lib, h, max_evals=60000, **kw)
+    assert ref["rounds"] == 3 and ref["status"] == 7
+    res = _marg_gpu(lib, h, max_evals=2000000, n_eff_target=ref["n_eff"], **kw)
+    assert res["status"] == 0 and res["rounds"] <= 3 and res["n_eff"] >= ref["n_eff"]
+    assert res["n_evals"] == 20000 * res["rounds"]
+
+
+def test_marginalize_deterministic(lib, cuda, p_small):
+    h = lib.rift_ile_create(p_small)
+    a = _marg_gpu(lib, h, seed=24, n_per_round=50000, max_evals=150000, proposal="adaptive", n_bins=40)
+    b = _marg_gpu(lib, h, seed=24, n_per_round=50000, max_evals=150000, proposal="adaptive", n_bins=40)
+    assert a == b
+
+
+def test_adaptive_fixed_tables_parity(lib, cuda, p_small):
+    """Proposal tables fixed (the oracle's adapted tables, no rebuild): identical draws on both
+    sides, lnL_marg within 1e-4."""
+    nb = 64
+    tab = _peaked_tables(p_small, nb)
+    h = lib.rift_ile_create(p_small)
+    res = _marg_gpu(lib, h, seed=25, n_per_round=50000, max_evals=100000, proposal="adaptive", n_bins=nb,
+                    tables=tab, adapt_rounds=0)
+    ref = mc.marginalize(p_small, 25, 0, mc.Prior(p_small["t_lo"], p_small["t_hi"]), 50000, 100000, 1e300,
+                         adaptive=True, n_bins=nb, tables=tab, adapt_rounds=0)
+    assert abs(res["lnL_marg"] - ref["lnL_marg"]) < TOL_MARG, (res, ref["lnL_marg"])
+    assert abs(res["n_eff"] - ref["n_eff"]) <= 2e-3 * ref["n_eff"]
+
+
+def test_adaptive_table_rebuild_parity(lib, cuda, p_small):
+    """One adaptive update from the prior: the device's round-1 tables vs the oracle's rebuild
+    from its own round-0 weights (same draws)."""
+    import torch
+    nb = 50
+    n = 60000
+    h = lib.rift_ile_create(p_small)
+    dbg_t = torch.zeros((2, 3, nb + 1), dtype=torch.float32, device="cuda")
+    _marg_gpu(lib, h, seed=26, n_per_round=n, max_evals=2 * n, proposal="adaptive", n_bins=nb, dbg_tables=dbg_t)
+    pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
+    ref = mc.marginalize(p_small, 26, 0, pr, n, 2 * n, 1e300, adaptive=True, n_bins=nb, keep=True)
+    got = dbg_t.cpu().numpy()
+    assert np.array_equal(got[0], mc.uniform_tables(nb))
+    want = ref["history"][1]["tables"]
+    assert np.max(np.abs(got[1].astype(np.float64) - want.astype(np.float64))) < 2e-4
+
+
+@pytest.fixture(scope="module")
+def p_phys():
+    """A physical injection (3 detectors, l = 2 modes, SNR 10): a single-mode posterior."""
+    spec = W.PointSpec(dets=("H1", "L1", "V1"), modes=list(W.L2_MODES), fs=4096.0, snr=10.0, t_half=0.02)
+    tens = np.stack([W.detector(d)[0] for d in spec.dets])
+    pos = np.stack([W.detector(d)[1] for d in spec.dets])
+    coef, tk = L.injection((tens, pos), spec.modes, ra=2.0, dec=0.5, t=0.003, psi=0.3, phi=1.0, incl=0.6,
+                           dist=300.0, d_ref=spec.d_ref, t_ref_gps=spec.t_ref_gps)
+    return W.make_point(spec, 41, injection=(coef, tk))
+
+
+def test_adaptive_statistical_agreement(lib, cuda, p_phys):
+    """Adaptive proposal vs a long plain run: lnL_marg agrees within the combined MC error."""
+    h = lib.rift_ile_create(p_phys)
+    plain = _marg_gpu(lib, h, seed=28, n_per_round=100_000_000, max_evals=2_000_000_000)
+    ad = _marg_gpu(lib, h, seed=27, n_per_round=100000, max_evals=100_000_000, n_eff_target=1000.0,
+                   proposal="adaptive", n_bins=100)
+    assert plain["n_eff"] > 50, plain
+    s = math.hypot(ad["sigma"], plain["sigma"])
+    assert abs(ad["lnL_marg"] - plain["lnL_marg"]) < 5 * s + 0.02, (ad, plain)
+    assert ad["n_evals"] < plain["n_evals"]
+
+
+def test_marginalize_full_size_sampled(lib, cuda, p_full):
+    """The full-size workload in the launch configuration the benchmark times (1e7 samples,
+    one round): per-sample values on a sample of indices, including the highest-weight ones."""
+    import torch
+    n = 10_000_000
+    h = lib.rift_ile_create(p_full)
+    dbg = torch.empty(n, dtype=torch.float32, device="cuda")
+    res = _marg_gpu(lib, h, seed=31, n_per_round=n, max_evals=n, dbg_ell=dbg)
+    got = dbg.cpu().numpy().astype(np.float64)
+    own = mc.Accum.of(got).result()
+    assert abs(own[0] - res["lnL_marg"]) < 1e-8
+    r = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([np.argsort(got)[-300:], r.integers(0, n, 2000), [0, n - 1]])).astype(np.uint64)
+    pr = mc.Prior(p_full["t_lo"], p_full["t_hi"])
+    th, _, _ = mc.draw(31, 0, 0, idx, pr)
+    want = mc.lnL_samples(p_full, th)
+    th64 = dict(ra=th["ra"], dec=np.arcsin(th["sindec"]), t=th["t"], psi=th["psi"], phi=th["phi"],
+                incl=np.arccos(th["cosi"]), dist=th["dist"])
+    err = np.abs(got[idx.astype(np.int64)] - want)
+    assert np.all(err <= _tol(p_full, th64)), err.max()
+    # lnL_marg restricted to the checked top set agrees at 1e-4
+    top = np.argsort(got)[-300:]
+    sel = np.isin(idx.astype(np.int64), top)
+    a = mc.Accum.of(got[idx.astype(np.int64)][sel]).result()[0]
+    b = mc.Accum.of(want[sel]).result()[0]
+    assert abs(a - b) < TOL_MARG * 3, (a, b)
