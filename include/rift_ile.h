@@ -179,6 +179,31 @@ rift_status rift_ile_marginalize(rift_ile *h, const rift_mc_opts *opts, rift_mc_
 rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
 
 /*
+ * rift_ile_marginalize_static -- the same computation as rift_ile_marginalize (point 0,
+ * prior or adaptive proposal; same kernels, same results) for callers that cannot
+ * allocate device memory when they marginalise: programs that give (nearly) all device
+ * memory to another allocator at start-up, or that forbid device allocation after
+ * initialisation.  The paper has no counterpart; it is a deployment variant.
+ *
+ *  - Allocates nothing: no cudaMalloc/cudaFree, no library allocation.  Its scratch (block
+ *    partials, accumulator, adaptive histograms, tables, one round of per-sample weights)
+ *    is a file-scope device array of RIFT_STATIC_SCRATCH_BYTES that every device which
+ *    loads the library holds until the process exits.
+ *  - The first call on a device resolves that array's device address (and may load the
+ *    library's device code); make this first call before any stream capture.
+ *  - Limits: at most RIFT_STATIC_MAX_BLOCKS likelihood blocks per round (the grid is capped
+ *    to it) and, with the adaptive proposal, n_per_round <= RIFT_STATIC_MAX_ROUND; larger
+ *    rounds are rejected with RIFT_EINVAL.  opts->dbg_tables and opts->timing must be 0.
+ *  - Every call on a device shares the array and resets what must start from zero; calls
+ *    whose GPU work overlaps (different streams or host threads) race and must not be issued.
+ * The handle itself is created (and allocated) beforehand with rift_ile_create.
+ */
+#define RIFT_STATIC_MAX_BLOCKS 4096
+#define RIFT_STATIC_MAX_ROUND 131072
+#define RIFT_STATIC_SCRATCH_BYTES 1585664
+rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
+
+/*
  * Draw the samples of one round (prior or tables) without evaluating them: theta_out is
  * device [7][n] float32 rows (ra, sin dec, t, psi, phi, cos incl, D); lpq_out device [n]
  * (ln p - ln q), bins_out device [3][n] int32 or NULL.  tables: device [3][n_bins+1] or NULL.

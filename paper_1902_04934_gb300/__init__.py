@@ -82,6 +82,7 @@ def _load():
         "rift_ile_check": (I, [P]),
         "rift_ile_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
         "rift_ile_batch_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
+        "rift_ile_marginalize_static": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
         "rift_ile_draw": (I, [P, C.POINTER(McOpts), U32, P, S, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -245,6 +246,18 @@ def rift_ile_marginalize(h, **kw):
     o = _opts(keep=keep, **kw)
     r = McResult()
     st = _lib.rift_ile_marginalize(h.ptr, C.byref(o), C.byref(r))
+    if st not in (0, 7):
+        _check(h, st)
+    return r.as_dict()
+
+
+def rift_ile_marginalize_static(h, **kw):
+    """rift_ile_marginalize without device allocation (scratch in a static device array);
+    for callers that may not allocate device memory at that point.  See the C header."""
+    keep = []
+    o = _opts(keep=keep, **kw)
+    r = McResult()
+    st = _lib.rift_ile_marginalize_static(h.ptr, C.byref(o), C.byref(r))
     if st not in (0, 7):
         _check(h, st)
     return r.as_dict()

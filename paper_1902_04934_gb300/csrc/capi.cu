@@ -578,3 +578,22 @@ rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_
 }
 
 }  // extern "C"
+
+// Internal accessors used by the allocation-free entry point (noalloc.cu).
+rift_status rift_internal_point0(rift_ile *h, const PointC **host, const PointC **dev, const float2 **qa,
+                                 const float4 **ca, int *K, int *num_sms, uint32_t **flags, cudaStream_t *st) {
+  if (!h || h->pts.empty()) return RIFT_EINVAL;
+  *host = &h->pts[0].c;
+  *dev = h->pts_dev;
+  *qa = h->q_arena;
+  *ca = h->c_arena;
+  *K = h->K;
+  *num_sms = h->num_sms;
+  *flags = h->flags;
+  *st = h->stream;
+  return RIFT_OK;
+}
+
+rift_status rift_internal_fail(rift_ile *h, rift_status s, const char *msg) { return fail(h, s, msg); }
+
+rift_status rift_internal_validate_opts(rift_ile *h, const rift_mc_opts *o) { return check_opts(h, o); }
