@@ -347,6 +347,7 @@ def run_reference(args, world, rank):
 
 
 def main():
+    global N_SAMPLES
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -356,8 +357,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--samples", type=int, default=N_SAMPLES,
+                    help="samples per step (profiling captures use a smaller count of the same workload)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
+    N_SAMPLES = args.samples
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -477,7 +477,7 @@ rift_status rift_ile_marginalize(rift_ile *h, const rift_mc_opts *o, rift_mc_res
   if (s != RIFT_OK) return s;
   std::memset(res, 0, sizeof(*res));
   const Point &p = h->pts[0];
-  const int block = 128;
+  const int block = RIFT_MC_BLOCK;
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
   const int nb = adaptive ? o->n_bins : 0;
   const size_t smem = rift_point_smem_bytes(h->K, p.c.npair, nb, block, p.c.M);

@@ -138,8 +138,8 @@ __device__ __forceinline__ void lse_merge(float &m, float &s1, float &s2, float 
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <int K>
-__global__ void __launch_bounds__(128) mc_round_kernel(const PointC *__restrict__ pts, const float2 *__restrict__ qa,
+template <int K, int NT>
+__global__ void __launch_bounds__(RIFT_MC_BLOCK, 4) mc_round_kernel(const PointC *__restrict__ pts, const float2 *__restrict__ qa,
                                                         const float4 *__restrict__ ca, McParams prm) {
   extern __shared__ __align__(16) unsigned char smem[];
   PointC &P = *reinterpret_cast<PointC *>(smem);
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(128) mc_round_kernel(const PointC *__restrict_
     const Drawn d = draw_sample(prm, prm.point_id, i, tab, lnw);
     SampleGeo g;
     geometry_drawn<K>(P, prm, d, g, Ys, ystride);
-    const float lin = linear_term<K>(P, Q, g, Ys, ystride, flags);
+    const float lin = linear_term<K, NT>(P, Q, g, Ys, ystride, flags);
     const float quad = quad_term<K>(P, C, g, Ys, ystride);
     const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
     const float ell = lnL + d.lpq;
@@ -316,7 +316,7 @@ __global__ void tables_kernel(const unsigned long long *__restrict__ part, int n
   }
 }
 
-template <int K>
+template <int K, int NT>
 __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict__ pts, const float2 *__restrict__ qa,
                                                          const float4 *__restrict__ ca, size_t n,
                                                          const float *__restrict__ ra, const float *__restrict__ dec,
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict
     sincosf(phi[i], &sphi, &cphi);
     sincosf(0.5f * incl[i], &sh, &ch);
     swsh_modes(P, ch, sh, cphi, sphi, Ys, ystride);
-    const float lin = linear_term<K>(P, Q, g, Ys, ystride, flags);
+    const float lin = linear_term<K, NT>(P, Q, g, Ys, ystride, flags);
     const float quad = quad_term<K>(P, C, g, Ys, ystride);
     const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
     if (!isfinite(lnL)) flags |= RIFT_FLAG_NONFINITE;
@@ -405,34 +405,46 @@ __global__ void draw_kernel(const PointC *__restrict__ pts, McParams prm, DrawOu
   }
 }
 
-template <int K>
+template <int K, int NT>
 cudaError_t mc_round_k(const PointC *pt_dev, const float2 *qa, const float4 *ca, const McParams &prm, int grid,
                        int block, size_t smem, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(mc_round_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e =
+        cudaFuncSetAttribute(mc_round_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  mc_round_kernel<K><<<grid, block, smem, st>>>(pt_dev, qa, ca, prm);
+  mc_round_kernel<K, NT><<<grid, block, smem, st>>>(pt_dev, qa, ca, prm);
   return cudaGetLastError();
 }
 
-template <int K>
+template <int K, int NT>
 cudaError_t lnl_array_k(const PointC *pt_dev, const float2 *qa, const float4 *ca, size_t n, const float *ra,
                         const float *dec, const float *t, const float *psi, const float *phi, const float *incl,
                         const float *dist, float *out, uint32_t *flags, size_t smem, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(lnl_array_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e =
+        cudaFuncSetAttribute(lnl_array_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int block = 128;
   const unsigned grid = (unsigned)((n + block - 1) / block);
-  lnl_array_kernel<K><<<grid, block, smem, st>>>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags);
+  lnl_array_kernel<K, NT><<<grid, block, smem, st>>>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags);
   return cudaGetLastError();
 }
+
+template <int K, int NT>
+int occ_k(size_t smem, int block) {
+  int nb = 0;
+  cudaFuncSetAttribute(mc_round_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mc_round_kernel<K, NT>, block, smem);
+  return nb;
+}
+
+int taps_of(int interp) { return interp == 3 ? 4 : (interp == 1 ? 2 : 1); }
 
 }  // namespace
 
@@ -443,34 +455,31 @@ size_t rift_point_smem_bytes(int K, int npair, int nb, int block, int M) {
   return off + sizeof(float2) * (size_t)M * block;
 }
 
-template <int K>
-int occ_k(size_t smem, int block) {
-  int nb = 0;
-  cudaFuncSetAttribute(mc_round_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mc_round_kernel<K>, block, smem);
-  return nb;
-}
-
 int mc_round_blocks_per_sm(int K, size_t smem, int block) {
   switch (K) {
-    case 1: return occ_k<1>(smem, block);
-    case 2: return occ_k<2>(smem, block);
-    case 3: return occ_k<3>(smem, block);
-    case 4: return occ_k<4>(smem, block);
+    case 1: return occ_k<1, 4>(smem, block);
+    case 2: return occ_k<2, 4>(smem, block);
+    case 3: return occ_k<3, 4>(smem, block);
+    case 4: return occ_k<4, 4>(smem, block);
     default: return 0;
   }
 }
 
+#define RIFT_DISPATCH_KT(K, NT, CALL)                                           \
+  switch ((K) * 8 + (NT)) {                                                     \
+    case 1 * 8 + 1: return CALL(1, 1); case 1 * 8 + 2: return CALL(1, 2); case 1 * 8 + 4: return CALL(1, 4); \
+    case 2 * 8 + 1: return CALL(2, 1); case 2 * 8 + 2: return CALL(2, 2); case 2 * 8 + 4: return CALL(2, 4); \
+    case 3 * 8 + 1: return CALL(3, 1); case 3 * 8 + 2: return CALL(3, 2); case 3 * 8 + 4: return CALL(3, 4); \
+    case 4 * 8 + 1: return CALL(4, 1); case 4 * 8 + 2: return CALL(4, 2); case 4 * 8 + 4: return CALL(4, 4); \
+    default: return cudaErrorInvalidValue;                                      \
+  }
+
 cudaError_t launch_mc_round(int K, const PointC *pt_dev, const PointC &ph, const float2 *qa, const float4 *ca,
                             const McParams &prm, int grid, int block, cudaStream_t st) {
   const size_t smem = rift_point_smem_bytes(K, ph.npair, prm.proposal ? prm.nb : 0, block, ph.M);
-  switch (K) {
-    case 1: return mc_round_k<1>(pt_dev, qa, ca, prm, grid, block, smem, st);
-    case 2: return mc_round_k<2>(pt_dev, qa, ca, prm, grid, block, smem, st);
-    case 3: return mc_round_k<3>(pt_dev, qa, ca, prm, grid, block, smem, st);
-    case 4: return mc_round_k<4>(pt_dev, qa, ca, prm, grid, block, smem, st);
-    default: return cudaErrorInvalidValue;
-  }
+#define RIFT_MC(KK, TT) mc_round_k<KK, TT>(pt_dev, qa, ca, prm, grid, block, smem, st)
+  RIFT_DISPATCH_KT(K, taps_of(ph.interp), RIFT_MC)
+#undef RIFT_MC
 }
 
 cudaError_t launch_merge(const Part *partials, int nparts, AccState *acc, cudaStream_t st) {
@@ -496,13 +505,9 @@ cudaError_t launch_lnl_array(int K, const PointC *pt_dev, const PointC &ph, cons
                              cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const size_t smem = rift_point_smem_bytes(K, ph.npair, 0, 128, ph.M);
-  switch (K) {
-    case 1: return lnl_array_k<1>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags, smem, st);
-    case 2: return lnl_array_k<2>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags, smem, st);
-    case 3: return lnl_array_k<3>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags, smem, st);
-    case 4: return lnl_array_k<4>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags, smem, st);
-    default: return cudaErrorInvalidValue;
-  }
+#define RIFT_LA(KK, TT) lnl_array_k<KK, TT>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags, smem, st)
+  RIFT_DISPATCH_KT(K, taps_of(ph.interp), RIFT_LA)
+#undef RIFT_LA
 }
 
 cudaError_t launch_draw(int K, const PointC *pt_dev, const PointC &ph, const McParams &prm, DrawOut o,

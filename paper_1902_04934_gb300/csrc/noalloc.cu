@@ -26,7 +26,7 @@
 
 namespace {
 
-constexpr int kBlock = 128;
+constexpr int kBlock = RIFT_MC_BLOCK;
 constexpr int kMaxBlocks = RIFT_STATIC_MAX_BLOCKS;
 constexpr int kMaxHistBlocks = 64;
 constexpr size_t kAlign = 256;

@@ -187,62 +187,71 @@ __device__ __forceinline__ void swsh_modes(const PointC &P, float c, float s, fl
   }
 }
 
-// Lagrange interpolation weights: taps i-1..i+2 (cubic), i..i+1 (linear), i (nearest).
-__device__ __forceinline__ int interp_weights(int interp, float mu, float w[4], int &first) {
-  if (interp == 3) {
+// Lagrange interpolation weights on NT taps: i-1..i+2 (cubic), i..i+1 (linear), i (nearest).
+template <int NT>
+__device__ __forceinline__ void interp_weights(float mu, float w[NT]) {
+  if (NT == 4) {
     const float a = mu + 1.f, b = mu - 1.f, c = mu - 2.f;
     w[0] = -mu * b * c * (1.f / 6.f);
     w[1] = a * b * c * 0.5f;
-    w[2] = -a * mu * c * 0.5f;
-    w[3] = a * mu * b * (1.f / 6.f);
-    first = -1;
-    return 4;
+    w[2 % NT] = -a * mu * c * 0.5f;
+    w[3 % NT] = a * mu * b * (1.f / 6.f);
+  } else if (NT == 2) {
+    w[0] = 1.f - mu;
+    w[1 % NT] = mu;
+  } else {
+    w[0] = 1.f;
   }
-  if (interp == 1) { w[0] = 1.f - mu; w[1] = mu; first = 0; return 2; }
-  w[0] = 1.f; first = 0; return 1;
 }
 
-// Linear term: Re sum_k sum_lm F_k conj(Y_lm) Q_{k,lm}(t_k), taps gathered from
-// the point's Q rows [K][T][Mp] (modes contiguous, so the taps of one detector are
-// one contiguous block of ntap * Mp complex values).
-template <int K>
+// Linear term: Re sum_k F_k sum_lm conj(Y_lm) Q_{k,lm}(t_k), taps gathered from the point's
+// Q rows [K][T][Mp] (modes contiguous: the taps of one detector are one contiguous block of
+// NT * Mp complex values).  Per mode the taps are combined first (qbar = sum_r w_r Q_r),
+// then Z_k = sum_lm conj(Y_lm) qbar_lm, and the detector factor is applied once: Re(F_k Z_k).
+template <int K, int NT>
 __device__ __forceinline__ float linear_term(const PointC &P, const float2 *__restrict__ Q, const SampleGeo &g,
                                              const float2 *Ys, int ystride, uint32_t &flags) {
+  constexpr int first = (NT == 4) ? -1 : 0;
   float lin = 0.f;
+  const int rs = P.Mp >> 1;          // row stride in float4 (two modes per float4)
+  const int npairs = (P.M + 1) >> 1;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     int i; float mu;
     df s = g.s[k];
-    if (P.interp == 0) s = df_add_f(s, 0.5f);
+    if (NT == 1) s = df_add_f(s, 0.5f);
     df_floor(s, i, mu);
-    if (P.interp == 0) mu = 0.f;
-    float w[4]; int first;
-    const int ntap = interp_weights(P.interp, mu, w, first);
+    float w[NT];
+    interp_weights<NT>(mu, w);
     int i0 = i + first;
-    if (i0 < 0 || i0 + ntap > P.T) {
+    if (i0 < 0 || i0 + NT > P.T) {
       flags |= RIFT_FLAG_WINDOW;
-      i0 = min(max(i0, 0), P.T - ntap);
+      i0 = min(max(i0, 0), P.T - NT);
     }
-    const float2 *row = Q + ((long long)k * P.T + i0) * P.Mp;
-    const float2 Fk = g.F[k];
-    float lk = 0.f;
-    for (int a = 0; a < P.M; a += 2) {
-      const float2 y0 = Ys[a * ystride];
-      const float2 y1 = (a + 1 < P.M) ? Ys[(a + 1) * ystride] : make_float2(0.f, 0.f);
-      // c = F_k conj(Y)
-      const float c0r = Fk.x * y0.x + Fk.y * y0.y, c0i = Fk.y * y0.x - Fk.x * y0.y;
-      const float c1r = Fk.x * y1.x + Fk.y * y1.y, c1i = Fk.y * y1.x - Fk.x * y1.y;
-      float acc = 0.f;
-      for (int r = 0; r < ntap; ++r) {
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(row + (long long)r * P.Mp + a));
-        float t = c0r * q.x - c0i * q.y;
-        t = fmaf(c1r, q.z, t);
-        t = fmaf(-c1i, q.w, t);
-        acc = fmaf(w[r], t, acc);
+    const float4 *row = reinterpret_cast<const float4 *>(Q + ((long long)k * P.T + i0) * P.Mp);
+    float zr = 0.f, zi = 0.f;
+#pragma unroll 2
+    for (int a2 = 0; a2 < npairs; ++a2) {
+      float4 q[NT];
+#pragma unroll
+      for (int r = 0; r < NT; ++r) q[r] = __ldg(row + r * rs + a2);
+      float q0r = 0.f, q0i = 0.f, q1r = 0.f, q1i = 0.f;
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        q0r = fmaf(w[r], q[r].x, q0r); q0i = fmaf(w[r], q[r].y, q0i);
+        q1r = fmaf(w[r], q[r].z, q1r); q1i = fmaf(w[r], q[r].w, q1i);
       }
-      lk += acc;
+      const float2 y0 = Ys[(2 * a2) * ystride];
+      // the pad column of an odd M is zero in Q, so y1 may be anything finite there
+      const float2 y1 = (2 * a2 + 1 < P.M) ? Ys[(2 * a2 + 1) * ystride] : make_float2(0.f, 0.f);
+      // conj(y) qbar
+      zr = fmaf(y0.x, q0r, fmaf(y0.y, q0i, zr));
+      zi = fmaf(y0.x, q0i, fmaf(-y0.y, q0r, zi));
+      zr = fmaf(y1.x, q1r, fmaf(y1.y, q1i, zr));
+      zi = fmaf(y1.x, q1i, fmaf(-y1.y, q1r, zi));
     }
-    lin += lk;
+    const float2 Fk = g.F[k];
+    lin += Fk.x * zr - Fk.y * zi;
   }
   return lin;
 }

@@ -6,6 +6,9 @@
 
 struct PointC;
 
+// Threads per block of the fused likelihood kernel.
+#define RIFT_MC_BLOCK 256
+
 // Block partial of the log-sum-exp: max, sum e^{l-max}, sum e^{2(l-max)}, count.
 struct __align__(32) Part {
   double m, s1, s2, n;

@@ -383,14 +383,26 @@ def test_distance_marginal_against_quadrature(small_point):
     assert abs(est - quad) < 4 * sig + 1e-6
 
 
-def test_adaptive_is_unbiased_against_plain(small_point):
-    """Adaptive proposal vs plain prior sampling: same lnL_marg within the combined MC error."""
-    pr = mc.Prior(small_point["t_lo"], small_point["t_hi"])
-    plain = mc.marginalize(small_point, 101, 0, pr, 50000, 400000, 1e300)
-    ad = mc.marginalize(small_point, 102, 0, pr, 20000, 200000, 1e300, adaptive=True, n_bins=40)
+def _physical_point(snr, seed=41):
+    spec = W.PointSpec(dets=("H1", "L1", "V1"), modes=list(W.L2_MODES), fs=4096.0, snr=snr, t_half=0.02,
+                       seg_len=4.0)
+    tens = np.stack([W.detector(d)[0] for d in spec.dets])
+    pos = np.stack([W.detector(d)[1] for d in spec.dets])
+    coef, tk = L.injection((tens, pos), spec.modes, ra=2.0, dec=0.5, t=0.003, psi=0.3, phi=1.0, incl=0.6,
+                           dist=300.0, d_ref=spec.d_ref, t_ref_gps=spec.t_ref_gps)
+    return W.make_point(spec, seed, injection=(coef, tk))
+
+
+def test_adaptive_is_unbiased_against_plain():
+    """Adaptive proposal vs plain prior sampling on a weak physical signal (SNR 4, where both
+    estimators are well resolved): the same lnL_marg within the combined MC error."""
+    pt = _physical_point(4.0)
+    pr = mc.Prior(pt["t_lo"], pt["t_hi"])
+    plain = mc.marginalize(pt, 101, 0, pr, 100000, 400000, 1e300)
+    ad = mc.marginalize(pt, 102, 0, pr, 50000, 400000, 1e300, adaptive=True, n_bins=50)
+    assert plain["n_eff"] > 30 and ad["n_eff"] > 30
     s = math.hypot(plain["sigma"], ad["sigma"])
-    assert abs(plain["lnL_marg"] - ad["lnL_marg"]) < 5 * s + 0.05
-    assert ad["n_eff"] > plain["n_eff"]
+    assert abs(plain["lnL_marg"] - ad["lnL_marg"]) < 5 * s + 0.005
 
 
 def test_rebuild_tables_properties():

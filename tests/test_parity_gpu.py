@@ -254,8 +254,9 @@ def test_adaptive_table_rebuild_parity(lib, cuda, p_small):
 
 @pytest.fixture(scope="module")
 def p_phys():
-    """A physical injection (3 detectors, l = 2 modes, SNR 10): a single-mode posterior."""
-    spec = W.PointSpec(dets=("H1", "L1", "V1"), modes=list(W.L2_MODES), fs=4096.0, snr=10.0, t_half=0.02)
+    """A weak physical injection (3 detectors, l = 2 modes, SNR 5): a posterior broad enough
+    for a long plain run to resolve lnL_marg well."""
+    spec = W.PointSpec(dets=("H1", "L1", "V1"), modes=list(W.L2_MODES), fs=4096.0, snr=5.0, t_half=0.02)
     tens = np.stack([W.detector(d)[0] for d in spec.dets])
     pos = np.stack([W.detector(d)[1] for d in spec.dets])
     coef, tk = L.injection((tens, pos), spec.modes, ra=2.0, dec=0.5, t=0.003, psi=0.3, phi=1.0, incl=0.6,
@@ -268,8 +269,8 @@ def test_adaptive_statistical_agreement(lib, cuda, p_phys):
     h = lib.rift_ile_create(p_phys)
     plain = _marg_gpu(lib, h, seed=28, n_per_round=100_000_000, max_evals=2_000_000_000)
     ad = _marg_gpu(lib, h, seed=27, n_per_round=100000, max_evals=100_000_000, n_eff_target=1000.0,
-                   proposal="adaptive", n_bins=100)
-    assert plain["n_eff"] > 50, plain
+                   proposal="adaptive", n_bins=50)
+    assert plain["n_eff"] > 1000, plain
     s = math.hypot(ad["sigma"], plain["sigma"])
     assert abs(ad["lnL_marg"] - plain["lnL_marg"]) < 5 * s + 0.02, (ad, plain)
     assert ad["n_evals"] < plain["n_evals"]
