@@ -301,10 +301,10 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": WORKLOAD, "global_batch": N_SAMPLES * world, "samples_per_point": N_SAMPLES,
                    "points": world, "parallelism": f"independent points x{world}", "l2": "flushed between steps"},
         "lnL_marg_per_s": world / (ms_per_step * 1e-3),
-        "lnL_marg": r0["lnL_marg"], "n_eff": r0["n_eff"],
+        "lnL_marg": r0["lnL_marg"], "n_eff": r0["n_eff"], "strata": list(r0["strata"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "mc_round_kernel<3> (fused draw + likelihood + block log-sum-exp)",
+                     "kernel": "cells_kernel<3,4> (stratified cell: draw + staged Q window + likelihood + log-sum-exp)",
                      "kernel_ms": kmean, "flops_per_sample": flops_per_sample(K, M, taps),
                      "peak_basis": f"FP32 FMA: 128 lanes/SM x {sms} SMs x 2 flop x median SM clock {f_mhz} MHz "
                                    "sampled during the run"},

@@ -147,7 +147,15 @@ typedef struct {
   float *dbg_tables;     /* optional device [rounds][3][n_bins+1]: tables used in each round */
   int max_rounds;        /* optional cap on rounds (0 = none)                            */
   int timing;            /* nonzero: time every likelihood-kernel launch with CUDA events */
+  int strata[3];         /* stratification of each round in (ra, sin dec, t): powers of two;
+                            {0,0,0} = chosen by the library; {1,1,1} = none.  A round of n samples
+                            over C = product cells puts contiguous blocks of samples in each cell
+                            (cells [0, n mod C) get one more), sample i of cell (c0,c1,c2) uses the
+                            uniforms (c_d + u_d)/S_d, and its log weight gains ln(n / (C n_c)).
+                            Rounds with n < C are not stratified.  C <= RIFT_MAX_CELLS.        */
 } rift_mc_opts;
+
+#define RIFT_MAX_CELLS 32768
 
 typedef struct {
   double lnL_marg;   /* log( sum_i w_i / N ), w = L p / q                                */
@@ -160,6 +168,7 @@ typedef struct {
   double acc_max, acc_s1, acc_s2; /* mergeable state: max l, sum e^{l-max}, sum e^{2(l-max)} */
   double kernel_ms;  /* with opts.timing: summed duration of the likelihood-kernel launches */
   int kernel_launches; /* likelihood + reduction + adaptive kernels launched by this call   */
+  int strata[3];     /* strata used for rounds with n >= C                                     */
 } rift_mc_result;
 
 /*
@@ -191,16 +200,16 @@ rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *opts, ri
  *    loads the library holds until the process exits.
  *  - The first call on a device resolves that array's device address (and may load the
  *    library's device code); make this first call before any stream capture.
- *  - Limits: at most RIFT_STATIC_MAX_BLOCKS likelihood blocks per round (the grid is capped
- *    to it) and, with the adaptive proposal, n_per_round <= RIFT_STATIC_MAX_ROUND; larger
- *    rounds are rejected with RIFT_EINVAL.  opts->dbg_tables and opts->timing must be 0.
+ *  - Limits: n_per_round <= RIFT_STATIC_MAX_PRIOR_ROUND, and with the adaptive proposal
+ *    n_per_round <= RIFT_STATIC_MAX_ROUND; larger rounds are rejected with RIFT_EINVAL.
+ *    opts->dbg_tables and opts->timing must be 0.
  *  - Every call on a device shares the array and resets what must start from zero; calls
  *    whose GPU work overlaps (different streams or host threads) race and must not be issued.
  * The handle itself is created (and allocated) beforehand with rift_ile_create.
  */
-#define RIFT_STATIC_MAX_BLOCKS 4096
 #define RIFT_STATIC_MAX_ROUND 131072
-#define RIFT_STATIC_SCRATCH_BYTES 1585664
+#define RIFT_STATIC_MAX_PRIOR_ROUND 67108864
+#define RIFT_STATIC_SCRATCH_BYTES 4601088
 rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
 
 /*

@@ -16,6 +16,12 @@ Readings (the paper refers to Pankow et al. 2015 for the adaptive details):
   h_b = sum over samples in bin b of exp(beta (l_i - max l)), with l the log
   importance weight, p_b = (1 - eps) h_b / sum h + eps / n_bins, cdf = cumsum p
   rounded to float32 (cdf[n_bins] = 1).
+* stratification (optional, same estimator family): the round's n samples are split into
+  C = S_ra S_sd S_t cells of the unit cube of the (ra, sin dec, t) uniforms (S powers of two),
+  contiguous blocks of samples per cell, cells [0, rem) holding one sample more than the rest
+  (n = base C + rem); sample i of cell c = c_ra + S_ra (c_sd + S_sd c_t) uses
+  u_d' = (c_d + u_d) / S_d, and its log weight gains ln(n / (C n_c)), which makes the pooled
+  mean the stratified estimator sum_c (1/C) mean_c(w).  Rounds with n < C are not stratified.
 * estimator: every sample of every round enters with its own round's q:
   lnL_marg = log( sum_i w_i / N_total ); n_eff = sum w / max w; the Kish size
   (sum w)^2 / sum w^2 and the standard error of lnL_marg are also reported.
@@ -78,15 +84,53 @@ def inverse_cdf(cdf32, u):
     return x, b, pb
 
 
-def draw(seed, point, rnd, idx, prior: Prior, tables=None):
-    """Samples of one round.  Returns (theta dict, bins (3, N) or None, ln p - ln q)."""
+def effective_strata(n, strata):
+    """Strata used for a round of n samples: none if the round has fewer samples than cells."""
+    s = tuple(int(x) for x in strata)
+    for x in s:
+        if x < 1 or (x & (x - 1)):
+            raise ValueError("strata must be powers of two")
+    return s if n >= s[0] * s[1] * s[2] else (1, 1, 1)
+
+
+def cell_of(i, n, C):
+    """Cell of sample i of a round of n samples over C cells, and that cell's sample count."""
+    i = np.asarray(i, dtype=np.int64)
+    base, rem = divmod(int(n), int(C))
+    big = rem * (base + 1)
+    c = np.where(i < big, i // (base + 1), rem + (i - big) // max(base, 1))
+    n_c = np.where(c < rem, base + 1, base)
+    return c, n_c
+
+
+def stratify(u, idx, n, strata):
+    """Stratified uniforms of the (ra, sin dec, t) dimensions and the log-weight correction."""
+    S = effective_strata(n, strata)
+    C = S[0] * S[1] * S[2]
+    if C == 1:
+        return u, np.zeros(u.shape[1])
+    c, n_c = cell_of(idx, n, C)
+    cc = [c % S[0], (c // S[0]) % S[1], c // (S[0] * S[1])]
+    u = u.copy()
+    for d in range(3):
+        u[d] = (cc[d] + u[d]) / S[d]
+    return u, np.log(n / (C * n_c))
+
+
+def draw(seed, point, rnd, idx, prior: Prior, tables=None, strata=(1, 1, 1), n_round=None):
+    """Samples of one round.  Returns (theta dict, bins (3, N) or None, ln p - ln q).
+
+    strata / n_round: stratification of the round (n_round = samples in the round; idx may
+    be a subset of range(n_round))."""
     u = uniforms(seed, point, rnd, idx, N_UNIFORMS)
+    n_round = len(idx) if n_round is None else n_round
+    u, corr = stratify(u, idx, n_round, strata)
     th = prior_transform(u, prior)
     if tables is None:
-        return th, None, np.zeros(u.shape[1])
+        return th, None, corr
     nb = tables.shape[1] - 1
     bins = np.empty((ADAPT_DIMS, u.shape[1]), dtype=np.int64)
-    lpq = np.zeros(u.shape[1])
+    lpq = corr.copy()
     for d, (key, (lo, hi)) in enumerate(zip(("ra", "sindec", "t"), prior.ranges())):
         x, b, pb = inverse_cdf(tables[d], u[d])
         th[key] = lo + (hi - lo) * x
@@ -161,7 +205,7 @@ def rebuild_tables(ell, bins, n_bins, beta, floor_eps):
 
 def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_target,
                 adaptive=False, n_bins=100, beta=0.3, floor_eps=0.1, tables=None, interp=3,
-                max_rounds=None, keep=False, adapt_rounds=-1):
+                max_rounds=None, keep=False, adapt_rounds=-1, strata=(1, 1, 1)):
     """Round loop of Eq. (lnLmarg) with the n_eff stopping rule of Sec. II.C.
 
     adaptive=False: plain prior sampling.  adaptive=True: round 0 uses `tables`
@@ -175,7 +219,7 @@ def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_tar
         tables = uniform_tables(n_bins)
     while True:
         idx = np.arange(min(n_per_round, max_evals - acc.n), dtype=np.uint64)
-        th, bins, lpq = draw(seed, point, rnd, idx, prior, tables if adaptive else None)
+        th, bins, lpq = draw(seed, point, rnd, idx, prior, tables if adaptive else None, strata, len(idx))
         ell = lnL_samples(pt, th, interp) + lpq
         acc = acc.merge(Accum.of(ell))
         lnm, n_eff, kish, sig = acc.result()

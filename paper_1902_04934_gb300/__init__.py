@@ -51,17 +51,19 @@ class McOpts(C.Structure):
                 ("d_hi", C.c_double), ("proposal", C.c_int), ("n_bins", C.c_int), ("beta", C.c_double),
                 ("floor_eps", C.c_double), ("adapt_rounds", C.c_int), ("tables", C.c_void_p),
                 ("mdn", C.c_void_p), ("dbg_ell", C.c_void_p), ("dbg_tables", C.c_void_p),
-                ("max_rounds", C.c_int), ("timing", C.c_int)]
+                ("max_rounds", C.c_int), ("timing", C.c_int), ("strata", C.c_int * 3)]
 
 
 class McResult(C.Structure):
     _fields_ = [("lnL_marg", C.c_double), ("n_eff", C.c_double), ("n_eff_kish", C.c_double),
                 ("sigma", C.c_double), ("n_evals", C.c_uint64), ("rounds", C.c_int), ("status", C.c_int),
                 ("acc_max", C.c_double), ("acc_s1", C.c_double), ("acc_s2", C.c_double),
-                ("kernel_ms", C.c_double), ("kernel_launches", C.c_int)]
+                ("kernel_ms", C.c_double), ("kernel_launches", C.c_int), ("strata", C.c_int * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["strata"] = tuple(self.strata)
+        return d
 
 
 def _load():
@@ -214,7 +216,8 @@ def rift_ile_check(h):
 
 def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target=1e300, d_lo=1.0,
           d_hi=1000.0, proposal="prior", n_bins=100, beta=0.3, floor_eps=0.1, adapt_rounds=-1,
-          tables=None, mdn=None, dbg_ell=None, dbg_tables=None, max_rounds=0, timing=0, keep=None):
+          tables=None, mdn=None, dbg_ell=None, dbg_tables=None, max_rounds=0, timing=0, strata=(0, 0, 0),
+          keep=None):
     o = McOpts()
     o.seed = int(seed)
     o.point_id = int(point_id)
@@ -238,6 +241,8 @@ def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target
     o.dbg_tables = dbg_tables.data_ptr() if dbg_tables is not None else None
     o.max_rounds = int(max_rounds)
     o.timing = int(timing)
+    for d in range(3):
+        o.strata[d] = int(strata[d])
     return o
 
 

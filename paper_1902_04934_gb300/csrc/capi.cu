@@ -84,23 +84,15 @@ struct rift_ile {
   int device = 0;
   int num_sms = 0;
   std::string err;
-  // scratch (owned)
+  // scratch (owned; grown on demand)
   uint32_t *flags = nullptr;
-  Part *partials = nullptr;
-  int max_parts = 0;
-  AccState *acc = nullptr;
-  size_t acc_n = 0;
-  float *ell_buf = nullptr;
-  uint32_t *bin_buf = nullptr;
-  size_t ebuf_n = 0;
-  unsigned long long *hist_part = nullptr;
-  size_t hist_n = 0;
-  float *tables = nullptr;  // [2][3][nb+1] ping-pong
-  float *lnw = nullptr;     // [2][3][nb]
-  int tab_nb = 0;
+  McScratch sc{};
+  size_t cap_items = 0, cap_ebuf = 0, cap_bins = 0, cap_hist = 0, cap_tab = 0, cap_lnw = 0;
+  int cap_np = 0;
   float *stage = nullptr;   // lnL_host staging [8][n]
   size_t stage_n = 0;
-  int max_M = 0;
+  int max_M = 0, max_pairK = 0;
+  int interp = 3;
 };
 
 namespace {
@@ -223,38 +215,50 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
   return RIFT_OK;
 }
 
-rift_status ensure_scratch(rift_ile *h, int parts, size_t ebuf, int nb, int hist_parts) {
-  if (parts > h->max_parts) {
-    if (h->partials) cudaFree(h->partials);
-    h->partials = nullptr;
-    RIFT_CK(h, cudaMalloc(&h->partials, sizeof(Part) * parts));
-    h->max_parts = parts;
+template <typename T>
+rift_status grow(rift_ile *h, T *&p, size_t &cap, size_t need) {
+  if (need <= cap) return RIFT_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(&p, sizeof(T) * need);
+  if (e != cudaSuccess) return fail(h, e == cudaErrorMemoryAllocation ? RIFT_ENOMEM : RIFT_ECUDA,
+                                    std::string("scratch allocation: ") + cudaGetErrorString(e));
+  cap = need;
+  return RIFT_OK;
+}
+
+// Device scratch of the Monte Carlo runner for np points, max_items cells per round,
+// ebuf per-sample slots (adaptive), nb bins and hb histogram blocks per point.
+rift_status ensure_scratch(rift_ile *h, int np, size_t max_items, size_t ebuf, int nb, int hb) {
+  McScratch &S = h->sc;
+  rift_status s;
+  if (np > h->cap_np) {
+    cudaFree(S.acc); cudaFree(S.rp); cudaFree(S.counters);
+    cudaFreeHost(S.rp_host); cudaFreeHost(S.acc_host);
+    S.acc = nullptr; S.rp = nullptr; S.counters = nullptr; S.rp_host = nullptr; S.acc_host = nullptr;
+    h->cap_np = 0;
+    cudaError_t e;
+    if ((e = cudaMalloc(&S.acc, sizeof(AccState) * np)) != cudaSuccess ||
+        (e = cudaMalloc(&S.rp, sizeof(RoundPt) * np)) != cudaSuccess ||
+        (e = cudaMalloc(&S.counters, sizeof(uint32_t) * 2)) != cudaSuccess ||
+        (e = cudaMallocHost(&S.rp_host, sizeof(RoundPt) * np)) != cudaSuccess ||
+        (e = cudaMallocHost(&S.acc_host, sizeof(AccState) * np)) != cudaSuccess)
+      return fail(h, RIFT_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+    h->cap_np = np;
   }
-  if (ebuf > h->ebuf_n) {
-    if (h->ell_buf) cudaFree(h->ell_buf);
-    if (h->bin_buf) cudaFree(h->bin_buf);
-    h->ell_buf = nullptr; h->bin_buf = nullptr;
-    RIFT_CK(h, cudaMalloc(&h->ell_buf, sizeof(float) * ebuf));
-    RIFT_CK(h, cudaMalloc(&h->bin_buf, sizeof(uint32_t) * ebuf));
-    h->ebuf_n = ebuf;
+  if ((s = grow(h, S.partials, h->cap_items, max_items)) != RIFT_OK) return s;
+  if (ebuf) {
+    if ((s = grow(h, S.ell, h->cap_ebuf, ebuf)) != RIFT_OK) return s;
+    if ((s = grow(h, S.bins, h->cap_bins, ebuf)) != RIFT_OK) return s;
   }
   if (nb > 0) {
-    const size_t need = (size_t)hist_parts * 3 * nb;
-    if (need > h->hist_n) {
-      if (h->hist_part) cudaFree(h->hist_part);
-      h->hist_part = nullptr;
-      RIFT_CK(h, cudaMalloc(&h->hist_part, sizeof(unsigned long long) * need));
-      h->hist_n = need;
-    }
-    if (nb != h->tab_nb) {
-      if (h->tables) cudaFree(h->tables);
-      if (h->lnw) cudaFree(h->lnw);
-      h->tables = nullptr; h->lnw = nullptr;
-      RIFT_CK(h, cudaMalloc(&h->tables, sizeof(float) * 2 * 3 * (nb + 1)));
-      RIFT_CK(h, cudaMalloc(&h->lnw, sizeof(float) * 2 * 3 * nb));
-      h->tab_nb = nb;
-    }
+    if ((s = grow(h, S.hist, h->cap_hist, (size_t)np * hb * 3 * nb)) != RIFT_OK) return s;
+    if ((s = grow(h, S.tables, h->cap_tab, (size_t)2 * np * 3 * (RIFT_MAXBINS + 1))) != RIFT_OK) return s;
+    if ((s = grow(h, S.lnw, h->cap_lnw, (size_t)2 * np * 3 * RIFT_MAXBINS)) != RIFT_OK) return s;
   }
+  S.max_items = h->cap_items;
+  S.hblocks = hb;
   return RIFT_OK;
 }
 
@@ -266,6 +270,7 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
   if (!h) return RIFT_ENOMEM;
   h->n_points = n;
   h->K = descs[0].n_det;
+  h->interp = descs[0].interp;
   h->stream = (cudaStream_t)descs[0].cuda_stream;
   std::vector<float2> qv;
   std::vector<float4> cv;
@@ -279,6 +284,12 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
       return s;
     }
     h->max_M = std::max(h->max_M, h->pts[i].c.M);
+    h->max_pairK = std::max(h->max_pairK, h->pts[i].c.npair * h->K);
+    if (descs[i].interp != descs[0].interp) {
+      rift_status s2 = fail(h, RIFT_EINVAL, "points differ in interp");
+      rift_ile_destroy(h);
+      return s2;
+    }
   }
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess ||
@@ -355,8 +366,225 @@ rift_status read_flags(rift_ile *h) {
   RIFT_CK(h, cudaMemcpyAsync(&f, h->flags, sizeof(f), cudaMemcpyDeviceToHost, h->stream));
   RIFT_CK(h, cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), h->stream));
   RIFT_CK(h, cudaStreamSynchronize(h->stream));
+  if (f & RIFT_FLAG_TIMEOUT_BIT) return fail(h, RIFT_ETIMEOUT, "a bounded wait for a shared-memory copy expired");
   if (f & RIFT_FLAG_WINDOW) return fail(h, RIFT_EWINDOW, "interpolation taps left the Q window");
   if (f & RIFT_FLAG_NONFINITE) return fail(h, RIFT_ENONFINITE, "non-finite log-likelihood");
+  return RIFT_OK;
+}
+
+int taps_of(int interp) { return interp == 3 ? 4 : (interp == 1 ? 2 : 1); }
+
+// Strata (log2) for rounds of n samples of point P: about 640 samples per cell, the split
+// between sky and time chosen to minimise the expected Q window of a cell (time-of-flight
+// spread over the cell's sky patch plus the cell's share of the time prior, in Q rows).
+void choose_strata(const PointC &P, uint32_t n, int ls[3]) {
+  ls[0] = ls[1] = ls[2] = 0;
+  int L = 0;
+  while (L < 15 && ((uint64_t)640 << (L + 1)) <= n) ++L;
+  double best = 1e300;
+  for (int a = 0; a <= L; ++a)
+    for (int b = 0; a + b <= L; ++b) {
+      const int c = L - a - b;
+      double rows = 0.0;
+      for (int k = 0; k < P.K; ++k) {
+        const double R = std::sqrt((double)P.det[k].P[0] * P.det[k].P[0] + (double)P.det[k].P[1] * P.det[k].P[1] +
+                                   (double)P.det[k].P[2] * P.det[k].P[2]);
+        rows += R * (2.0 * kPi / (1 << a) + 2.0 / (1 << b)) * 0.5 + (double)P.A / (1 << c);
+      }
+      if (rows < best - 1e-9) { best = rows; ls[0] = a; ls[1] = b; ls[2] = c; }
+    }
+}
+
+int log2_pow2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return ((1 << l) == v) ? l : -1;
+}
+
+// The Monte Carlo round loop of Eq. (lnLmarg) for np points of the handle, with the scratch S.
+rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rift_mc_result *res) {
+  const int K = h->K, NT = taps_of(h->interp);
+  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
+  const int nb = adaptive ? o->n_bins : 0;
+  const uint32_t npr = o->n_per_round;
+  std::vector<int> lsv(3 * np);
+  for (int p = 0; p < np; ++p) {
+    int *ls = &lsv[3 * p];
+    if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
+      choose_strata(h->pts[p].c, npr, ls);
+    } else {
+      for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
+      if (ls[0] < 0 || ls[1] < 0 || ls[2] < 0) return fail(h, RIFT_EINVAL, "strata must be powers of two");
+      if ((1 << (ls[0] + ls[1] + ls[2])) > RIFT_MAX_CELLS) return fail(h, RIFT_EINVAL, "more than RIFT_MAX_CELLS cells");
+    }
+  }
+  cudaStream_t st = h->stream;
+  // accumulators and round-0 tables
+  for (int p = 0; p < np; ++p) {
+    std::memset(&S.acc_host[p], 0, sizeof(AccState));
+    S.acc_host[p].m = -INFINITY;
+  }
+  RIFT_CK(h, cudaMemcpyAsync(S.acc, S.acc_host, sizeof(AccState) * np, cudaMemcpyHostToDevice, st));
+  int cur = 0;
+  const size_t tstride = (size_t)3 * (nb + 1), wstride = (size_t)3 * nb;
+  if (adaptive) {
+    float u[3 * (RIFT_MAXBINS + 1)];
+    const float *src = o->tables;
+    if (!src) {
+      for (int d = 0; d < 3; ++d)
+        for (int b = 0; b <= nb; ++b) u[d * (nb + 1) + b] = (float)((double)b / nb);
+      src = u;
+    }
+    for (int p = 0; p < np; ++p)
+      RIFT_CK(h, cudaMemcpyAsync(S.tables + p * tstride, src, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
+    RIFT_CK(h, cudaStreamSynchronize(st));
+    // lnw of the round-0 tables (every point): rp is only read for its flags with part == nullptr
+    for (int p = 0; p < np; ++p) {
+      std::memset(&S.rp_host[p], 0, sizeof(RoundPt));
+      S.rp_host[p].proposal = 1;
+      S.rp_host[p].ncell = 1;
+    }
+    RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
+    RIFT_CK(h, launch_tables_points(nullptr, 0, S.rp, np, nb, 0.0, S.tables, S.lnw, st));
+  }
+  const int block = RIFT_CELL_BLOCK;
+  int smem_sm = 0;
+  RIFT_CK(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+  const size_t fixed = cells_smem_fixed(K, h->max_M, h->max_pairK, nb, block);
+  long long budget = ((long long)smem_sm / 2 - (long long)fixed - 2048) & ~15ll;
+  budget = std::max(16ll * 1024, std::min(96ll * 1024, budget));
+  const size_t smem = fixed + (size_t)budget;
+  int bps = cells_blocks_per_sm(K, NT, smem, block);
+  if (bps < 1) return fail(h, RIFT_EUNSUPPORTED, "cell kernel does not fit on an SM");
+  CellLaunch L{};
+  L.seed = o->seed;
+  L.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
+  L.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
+  L.pts = h->pts_dev;
+  L.rp = S.rp;
+  L.n_points = np;
+  L.win_budget = (int)budget;
+  L.n_items = S.counters;
+  L.queue = S.counters + 1;
+  L.qa = h->q_arena;
+  L.ca = h->c_arena;
+  L.partials = S.partials;
+  L.dbg_ell = (np == 1) ? o->dbg_ell : nullptr;
+  L.ell_buf = adaptive ? S.ell : nullptr;
+  L.bin_buf = adaptive ? S.bins : nullptr;
+  L.flags = h->flags;
+  L.max_M = h->max_M;
+  L.max_pairK = h->max_pairK;
+  L.max_nb = nb;
+  std::vector<uint64_t> evals(np, 0);
+  std::vector<int> rounds(np, 0), done(np, 0), nrun(np, 0);
+  int launches = 0;
+  double kms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (o->timing) {
+    RIFT_CK(h, cudaEventCreate(&ev0));
+    RIFT_CK(h, cudaEventCreate(&ev1));
+  }
+  rift_status status = RIFT_OK;
+  for (int r = 0;; ++r) {
+    uint32_t items = 0;
+    for (int p = 0; p < np; ++p) {
+      RoundPt &R = S.rp_host[p];
+      std::memset(&R, 0, sizeof(R));
+      R.item0 = items;
+      R.ell_off = -1;
+      R.dbg_off = -1;
+      nrun[p] = 0;
+      if (done[p]) continue;
+      const uint32_t n = (uint32_t)std::min<uint64_t>(npr, o->max_evals - evals[p]);
+      const int *ls = &lsv[3 * p];
+      int l0 = ls[0], l1 = ls[1], l2 = ls[2];
+      if ((uint64_t)n < (1ull << (l0 + l1 + l2))) l0 = l1 = l2 = 0;
+      const uint32_t C = 1u << (l0 + l1 + l2);
+      R.n = n;
+      R.ncell = C;
+      R.base = n / C;
+      R.rem = n % C;
+      R.round = (uint32_t)rounds[p];
+      R.point_id = (np == 1) ? o->point_id : (uint32_t)p;
+      R.ls0 = l0; R.ls1 = l1; R.ls2 = l2;
+      R.proposal = adaptive ? 1 : 0;
+      R.nb = nb;
+      R.lcorr0 = (float)std::log((double)n / ((double)C * (R.base + 1.0)));
+      R.lcorr1 = R.base ? (float)std::log((double)n / ((double)C * R.base)) : 0.f;
+      R.chunks = (R.base + (R.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
+      R.nitem = C * R.chunks;
+      R.ell_off = adaptive ? (long long)p * npr : -1;
+      R.dbg_off = (np == 1 && o->dbg_ell) ? (long long)rounds[p] * npr : -1;
+      R.tab = adaptive ? S.tables + ((size_t)cur * np + p) * tstride : nullptr;
+      R.lnw = adaptive ? S.lnw + ((size_t)cur * np + p) * wstride : nullptr;
+      items += R.nitem;
+      nrun[p] = (int)n;
+    }
+    if (items == 0) break;
+    if (items > S.max_items) { status = fail(h, RIFT_EINVAL, "work items exceed the scratch"); break; }
+    if (o->dbg_tables && adaptive && np == 1)
+      RIFT_CK(h, cudaMemcpyAsync(o->dbg_tables + (size_t)r * tstride, S.tables + (size_t)cur * np * tstride,
+                                 sizeof(float) * tstride, cudaMemcpyDeviceToDevice, st));
+    const uint32_t cnt[2] = {items, 0u};
+    RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
+    RIFT_CK(h, cudaMemcpyAsync(S.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
+    const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(items, (uint32_t)(h->num_sms * bps)));
+    if (o->timing) RIFT_CK(h, cudaEventRecord(ev0, st));
+    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st));
+    if (o->timing) RIFT_CK(h, cudaEventRecord(ev1, st));
+    RIFT_CK(h, launch_merge_points(S.partials, S.rp, np, S.acc, st));
+    launches += 2;
+    const bool adapt_now = adaptive && (o->adapt_rounds < 0 || r < o->adapt_rounds);
+    if (adapt_now) {
+      RIFT_CK(h, launch_hist_points(S.ell, S.bins, S.rp, np, S.acc, (float)o->beta, nb, S.hist, S.hblocks, st));
+      RIFT_CK(h, launch_tables_points(S.hist, S.hblocks, S.rp, np, nb, o->floor_eps,
+                                      S.tables + (size_t)(1 - cur) * np * tstride,
+                                      S.lnw + (size_t)(1 - cur) * np * wstride, st));
+      launches += 2;
+    }
+    RIFT_CK(h, cudaMemcpyAsync(S.acc_host, S.acc, sizeof(AccState) * np, cudaMemcpyDeviceToHost, st));
+    RIFT_CK(h, cudaStreamSynchronize(st));
+    if (o->timing) {
+      float ms = 0.f;
+      RIFT_CK(h, cudaEventElapsedTime(&ms, ev0, ev1));
+      kms += ms;
+    }
+    if (adapt_now) {
+      // points that are not adapting keep their tables: copy them into the new buffer
+      cur = 1 - cur;
+    }
+    bool any = false;
+    for (int p = 0; p < np; ++p) {
+      if (!nrun[p]) continue;
+      evals[p] += (uint64_t)nrun[p];
+      rounds[p] += 1;
+      const AccState &a = S.acc_host[p];
+      const double n_eff = a.s1 + a.c1;
+      if (n_eff >= o->n_eff_target || evals[p] >= o->max_evals || (o->max_rounds > 0 && rounds[p] >= o->max_rounds))
+        done[p] = 1;
+      else
+        any = true;
+    }
+    if (!any) break;
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  rift_status fl = read_flags(h);
+  for (int p = 0; p < np; ++p) {
+    fill_result(S.acc_host[p], &res[p]);
+    res[p].rounds = rounds[p];
+    res[p].kernel_ms = (p == 0) ? kms : 0.0;
+    res[p].kernel_launches = (p == 0) ? launches : 0;
+    for (int d = 0; d < 3; ++d) res[p].strata[d] = 1 << lsv[3 * p + d];
+    rift_status sp = (status != RIFT_OK) ? status : fl;
+    if (sp == RIFT_OK && res[p].n_eff < o->n_eff_target) sp = RIFT_ENOTCONVERGED;
+    res[p].status = sp;
+  }
+  if (status != RIFT_OK) return status;
+  if (fl != RIFT_OK) return fl;
+  for (int p = 0; p < np; ++p)
+    if (res[p].status == RIFT_ENOTCONVERGED) return RIFT_ENOTCONVERGED;
   return RIFT_OK;
 }
 
@@ -390,18 +618,23 @@ rift_status rift_ile_batch_create(const rift_ile_desc *descs, int n_points, rift
 
 void rift_ile_destroy(rift_ile *h) {
   if (!h) return;
-  if (h->stream || true) cudaStreamSynchronize(h->stream);
+  cudaStreamSynchronize(h->stream);
   cudaFree(h->pts_dev);
   cudaFree(h->q_arena);
   cudaFree(h->c_arena);
   cudaFree(h->flags);
-  cudaFree(h->partials);
-  cudaFree(h->acc);
-  cudaFree(h->ell_buf);
-  cudaFree(h->bin_buf);
-  cudaFree(h->hist_part);
-  cudaFree(h->tables);
-  cudaFree(h->lnw);
+  McScratch &S = h->sc;
+  cudaFree(S.acc);
+  cudaFree(S.partials);
+  cudaFree(S.rp);
+  cudaFree(S.counters);
+  cudaFree(S.ell);
+  cudaFree(S.bins);
+  cudaFree(S.hist);
+  cudaFree(S.tables);
+  cudaFree(S.lnw);
+  cudaFreeHost(S.rp_host);
+  cudaFreeHost(S.acc_host);
   cudaFree(h->stage);
   delete h;
 }
@@ -452,22 +685,50 @@ rift_status rift_ile_draw(rift_ile *h, const rift_mc_opts *o, uint32_t round, co
   rift_status s = check_opts(h, o);
   if (s != RIFT_OK) return s;
   if (!theta_out || !lpq_out) return fail(h, RIFT_EINVAL, "null output");
+  if (n == 0) return RIFT_OK;
   if (n > 0xFFFFFFFFull) return fail(h, RIFT_EINVAL, "n too large");
-  const int nb = (o->proposal == RIFT_PROPOSAL_ADAPTIVE) ? o->n_bins : 0;
-  if ((s = ensure_scratch(h, 1, 0, nb, 1)) != RIFT_OK) return s;
-  McParams prm{};
-  prm.seed = o->seed; prm.round = round; prm.n = (uint32_t)n; prm.point_id = o->point_id;
-  prm.proposal = (nb > 0 && tables) ? 1 : 0;
-  prm.nb = nb;
-  prm.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
-  prm.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
-  if (prm.proposal) {
-    RIFT_CK(h, cudaMemcpyAsync(h->tables, tables, sizeof(float) * 3 * (nb + 1), cudaMemcpyDeviceToDevice, h->stream));
-    RIFT_CK(h, launch_tables(nullptr, 0, nb, 0.0, h->tables, h->lnw, h->stream));
-    prm.tables = h->tables; prm.lnw = h->lnw;
+  const bool tab = (o->proposal == RIFT_PROPOSAL_ADAPTIVE) && tables;
+  const int nb = tab ? o->n_bins : 0;
+  if ((s = ensure_scratch(h, 1, 1, 0, tab ? nb : 0, 1)) != RIFT_OK) return s;
+  McScratch &S = h->sc;
+  int ls[3];
+  if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
+    choose_strata(h->pts[0].c, (uint32_t)n, ls);
+  } else {
+    for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
+    if (ls[0] < 0 || ls[1] < 0 || ls[2] < 0) return fail(h, RIFT_EINVAL, "strata must be powers of two");
   }
+  if ((uint64_t)n < (1ull << (ls[0] + ls[1] + ls[2]))) ls[0] = ls[1] = ls[2] = 0;
+  RoundPt &R = S.rp_host[0];
+  std::memset(&R, 0, sizeof(R));
+  const uint32_t C = 1u << (ls[0] + ls[1] + ls[2]);
+  R.n = (uint32_t)n; R.ncell = C; R.base = R.n / C; R.rem = R.n % C;
+  R.round = round; R.point_id = o->point_id;
+  R.ls0 = ls[0]; R.ls1 = ls[1]; R.ls2 = ls[2];
+  R.proposal = tab ? 1 : 0; R.nb = nb;
+  R.lcorr0 = (float)std::log((double)R.n / ((double)C * (R.base + 1.0)));
+  R.lcorr1 = R.base ? (float)std::log((double)R.n / ((double)C * R.base)) : 0.f;
+  R.chunks = (R.base + (R.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
+  R.nitem = C * R.chunks;
+  R.ell_off = -1; R.dbg_off = -1;
+  if (tab) {
+    RIFT_CK(h, cudaMemcpyAsync(S.tables, tables, sizeof(float) * 3 * (nb + 1), cudaMemcpyDeviceToDevice, h->stream));
+    R.tab = S.tables;
+    R.lnw = S.lnw;
+  }
+  RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt), cudaMemcpyHostToDevice, h->stream));
+  if (tab) RIFT_CK(h, launch_tables_points(nullptr, 0, S.rp, 1, nb, 0.0, S.tables, S.lnw, h->stream));
+  CellLaunch L{};
+  L.seed = o->seed;
+  L.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
+  L.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
+  L.pts = h->pts_dev;
+  L.rp = S.rp;
+  L.n_points = 1;
+  L.max_nb = nb;
   DrawOut d{theta_out, lpq_out, bins_out};
-  RIFT_CK(h, launch_draw(h->K, h->pts_dev, h->pts[0].c, prm, d, h->stream));
+  RIFT_CK(h, launch_draw_cells(L, d, (uint32_t)n, h->stream));
+  RIFT_CK(h, cudaStreamSynchronize(h->stream));
   return RIFT_OK;
 }
 
@@ -476,124 +737,45 @@ rift_status rift_ile_marginalize(rift_ile *h, const rift_mc_opts *o, rift_mc_res
   rift_status s = check_opts(h, o);
   if (s != RIFT_OK) return s;
   std::memset(res, 0, sizeof(*res));
-  const Point &p = h->pts[0];
-  const int block = RIFT_MC_BLOCK;
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
   const int nb = adaptive ? o->n_bins : 0;
-  const size_t smem = rift_point_smem_bytes(h->K, p.c.npair, nb, block, p.c.M);
-  if (smem > 200 * 1024) return fail(h, RIFT_EUNSUPPORTED, "shared memory footprint too large");
-  int bps = mc_round_blocks_per_sm(h->K, smem, block);
-  if (bps < 1) bps = 1;
-  const uint32_t npr = o->n_per_round;
-  int grid = std::max(1, std::min<int>(h->num_sms * bps, (int)((npr + block - 1) / block)));
-  const int hist_grid = std::max(1, std::min(h->num_sms, (int)((npr + 255) / 256)));
-  if ((s = ensure_scratch(h, grid, adaptive ? npr : 0, nb, hist_grid)) != RIFT_OK) return s;
-  if (!h->acc) RIFT_CK(h, cudaMalloc(&h->acc, sizeof(AccState)));
-  AccState a0{};
-  a0.m = -INFINITY;
-  RIFT_CK(h, cudaMemcpyAsync(h->acc, &a0, sizeof(a0), cudaMemcpyHostToDevice, h->stream));
-  int cur = 0;
-  if (adaptive) {
-    if (o->tables) {
-      RIFT_CK(h, cudaMemcpyAsync(h->tables, o->tables, sizeof(float) * 3 * (nb + 1), cudaMemcpyHostToDevice, h->stream));
-    } else {
-      std::vector<float> u(3 * (nb + 1));
-      for (int d = 0; d < 3; ++d)
-        for (int b = 0; b <= nb; ++b) u[d * (nb + 1) + b] = (float)((double)b / nb);
-      RIFT_CK(h, cudaMemcpyAsync(h->tables, u.data(), sizeof(float) * u.size(), cudaMemcpyHostToDevice, h->stream));
-      RIFT_CK(h, cudaStreamSynchronize(h->stream));
-    }
-    RIFT_CK(h, launch_tables(nullptr, 0, nb, 0.0, h->tables, h->lnw, h->stream));
-  }
-  McParams prm{};
-  prm.seed = o->seed; prm.point_id = o->point_id; prm.nb = nb;
-  prm.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
-  prm.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
-  prm.partials = h->partials; prm.flags = h->flags;
-  uint64_t evals = 0;
-  AccState a{};
-  int r = 0;
-  int launches = 0;
-  double kms = 0.0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  if (o->timing) {
-    RIFT_CK(h, cudaEventCreate(&ev0));
-    RIFT_CK(h, cudaEventCreate(&ev1));
-  }
-  for (;; ++r) {
-    const uint64_t left = o->max_evals - evals;
-    prm.round = (uint32_t)r;
-    prm.n = (uint32_t)std::min<uint64_t>(npr, left);
-    prm.proposal = adaptive ? 1 : 0;
-    prm.tables = adaptive ? h->tables + cur * 3 * (nb + 1) : nullptr;
-    prm.lnw = adaptive ? h->lnw + cur * 3 * nb : nullptr;
-    prm.dbg_ell = o->dbg_ell;
-    prm.dbg_off = (long long)r * npr;
-    prm.ell_buf = adaptive ? h->ell_buf : nullptr;
-    prm.bin_buf = adaptive ? h->bin_buf : nullptr;
-    if (o->dbg_tables && adaptive)
-      RIFT_CK(h, cudaMemcpyAsync(o->dbg_tables + (size_t)r * 3 * (nb + 1), prm.tables, sizeof(float) * 3 * (nb + 1),
-                                 cudaMemcpyDeviceToDevice, h->stream));
-    const int g = std::max(1, std::min<int>(grid, (int)((prm.n + block - 1) / block)));
-    if (o->timing) RIFT_CK(h, cudaEventRecord(ev0, h->stream));
-    RIFT_CK(h, launch_mc_round(h->K, h->pts_dev, p.c, h->q_arena, h->c_arena, prm, g, block, h->stream));
-    if (o->timing) RIFT_CK(h, cudaEventRecord(ev1, h->stream));
-    RIFT_CK(h, launch_merge(h->partials, g, h->acc, h->stream));
-    launches += 2;
-    const bool adapt_now = adaptive && (o->adapt_rounds < 0 || r < o->adapt_rounds);
-    if (adapt_now) {
-      const int hg = std::max(1, std::min(hist_grid, (int)((prm.n + 255) / 256)));
-      RIFT_CK(h, launch_hist(h->ell_buf, h->bin_buf, prm.n, h->acc, (float)o->beta, nb, h->hist_part, hg, h->stream));
-      RIFT_CK(h, launch_tables(h->hist_part, hg, nb, o->floor_eps, h->tables + (1 - cur) * 3 * (nb + 1),
-                               h->lnw + (1 - cur) * 3 * nb, h->stream));
-      launches += 2;
-    }
-    RIFT_CK(h, cudaMemcpyAsync(&a, h->acc, sizeof(a), cudaMemcpyDeviceToHost, h->stream));
-    RIFT_CK(h, cudaStreamSynchronize(h->stream));
-    if (o->timing) {
-      float ms = 0.f;
-      RIFT_CK(h, cudaEventElapsedTime(&ms, ev0, ev1));
-      kms += ms;
-    }
-    if (adapt_now) cur = 1 - cur;
-    evals += prm.n;
-    const double n_eff = a.s1 + a.c1;
-    if (n_eff >= o->n_eff_target || evals >= o->max_evals || (o->max_rounds > 0 && r + 1 >= o->max_rounds)) break;
-  }
-  if (ev0) cudaEventDestroy(ev0);
-  if (ev1) cudaEventDestroy(ev1);
-  fill_result(a, res);
-  res->rounds = r + 1;
-  res->kernel_ms = kms;
-  res->kernel_launches = launches;
-  s = read_flags(h);
-  if (s == RIFT_OK && res->n_eff < o->n_eff_target) s = RIFT_ENOTCONVERGED;
-  res->status = s;
-  return s;
+  const int hb = std::max(1, std::min(64, (int)(o->n_per_round / 8192)));
+  const size_t items = (size_t)RIFT_MAX_CELLS + o->n_per_round / RIFT_CHUNK + 1;
+  if ((s = ensure_scratch(h, 1, items, adaptive ? o->n_per_round : 0, nb, hb)) != RIFT_OK) return s;
+  return run_mc(h, o, 1, h->sc, res);
 }
 
 rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res) {
-  (void)o; (void)res;
-  return fail(h, RIFT_EUNSUPPORTED, "batched marginalisation not built yet");
+  if (!h || !res) return RIFT_EINVAL;
+  rift_status s = check_opts(h, o);
+  if (s != RIFT_OK) return s;
+  const int np = h->n_points;
+  std::memset(res, 0, sizeof(*res) * np);
+  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
+  const int nb = adaptive ? o->n_bins : 0;
+  const int hb = std::max(1, std::min(64, (int)(o->n_per_round / 8192)));
+  // cells per point are at most max(RIFT_MAX_CELLS, n_per_round) bounded by the strata rule
+  size_t items = 0;
+  for (int p = 0; p < np; ++p) {
+    int ls[3];
+    if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) choose_strata(h->pts[p].c, o->n_per_round, ls);
+    else for (int d = 0; d < 3; ++d) ls[d] = std::max(0, log2_pow2(o->strata[d]));
+    items += ((size_t)1 << (ls[0] + ls[1] + ls[2])) + o->n_per_round / RIFT_CHUNK + 1;
+  }
+  if ((s = ensure_scratch(h, np, items, adaptive ? (size_t)np * o->n_per_round : 0, nb, hb)) != RIFT_OK) return s;
+  return run_mc(h, o, np, h->sc, res);
 }
 
 }  // extern "C"
 
-// Internal accessors used by the allocation-free entry point (noalloc.cu).
-rift_status rift_internal_point0(rift_ile *h, const PointC **host, const PointC **dev, const float2 **qa,
-                                 const float4 **ca, int *K, int *num_sms, uint32_t **flags, cudaStream_t *st) {
-  if (!h || h->pts.empty()) return RIFT_EINVAL;
-  *host = &h->pts[0].c;
-  *dev = h->pts_dev;
-  *qa = h->q_arena;
-  *ca = h->c_arena;
-  *K = h->K;
-  *num_sms = h->num_sms;
-  *flags = h->flags;
-  *st = h->stream;
-  return RIFT_OK;
+// Internal entry used by the allocation-free entry point (noalloc.cu): the runner with
+// caller-provided scratch.
+rift_status rift_internal_run_static(rift_ile *h, const rift_mc_opts *o, McScratch &S, rift_mc_result *res) {
+  if (!h || !res) return RIFT_EINVAL;
+  rift_status s = check_opts(h, o);
+  if (s != RIFT_OK) return s;
+  std::memset(res, 0, sizeof(*res));
+  return run_mc(h, o, 1, S, res);
 }
 
 rift_status rift_internal_fail(rift_ile *h, rift_status s, const char *msg) { return fail(h, s, msg); }
-
-rift_status rift_internal_validate_opts(rift_ile *h, const rift_mc_opts *o) { return check_opts(h, o); }

@@ -1,0 +1,720 @@
+// Cell kernel: the Monte Carlo round of Eq. (lnLmarg) organised by stratification cells.
+//
+// A round of n samples of a point is split into C = S_ra S_sd S_t cells of the unit cube of
+// the (ra, sin dec, t) uniforms; the samples of one cell share a small box of sky and time,
+// so the Q rows their time-of-flight-shifted taps need (Sec. II.A: Q_{k,lm}(t + n.x_k)) form a
+// short contiguous window per detector.  One CTA takes one cell at a time (a dynamic work
+// queue over the cells of every active point, so the same kernel runs one point or a batch):
+//
+//   A. every thread draws its samples of the cell and computes only their Q indices;
+//      a block min/max gives the window of each detector;
+//   B. one thread stages the windows (contiguous rows of the [K][T][Mp] arena) into shared
+//      memory with bulk asynchronous copies completing on an mbarrier;
+//   C. every thread re-draws its samples and evaluates Eq. (def:lnL:Decomposed) with the taps
+//      read from the staged window (taps outside it, if the window did not fit, come from
+//      global memory: same values);
+//   D. log weights -> per-thread log-sum-exp -> warp shuffles -> one partial per cell.
+#include <cfloat>
+#include <cmath>
+
+#include "rift_device.cuh"
+#include "rift_internal.h"
+
+namespace {
+
+constexpr float kTwoPi = 6.283185307179586f;
+constexpr float kNegInf = -INFINITY;
+constexpr long long kWaitCycles = 2000000000ll;   // bounded mbarrier wait (~1 s)
+
+__device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity`; false if the bound expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void copy_words(const void *src, void *dst, int nbytes) {
+  const int *s = reinterpret_cast<const int *>(src);
+  int *d = reinterpret_cast<int *>(dst);
+  for (int i = threadIdx.x; i < nbytes / 4; i += blockDim.x) d[i] = s[i];
+}
+
+// Piecewise-constant inverse CDF of one adapted coordinate at a double-float uniform U in
+// (0, 1): returns the fraction of the range (double-float) and the bin, the largest b with
+// cdf[b] <= U (exact comparison: cdf values are float32, U = hi + lo with |lo| <= ulp(hi)/2).
+__device__ __forceinline__ df inv_cdf_df(const float *cdf, int nb, df U, int &b) {
+  int lo = 0, hi = nb;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    const float c = cdf[mid];
+    if (c < U.hi || (c == U.hi && U.lo >= 0.f)) lo = mid; else hi = mid;
+  }
+  b = lo;
+  const float c0 = cdf[lo], c1 = cdf[lo + 1];
+  const df num = two_sum(U.hi, -c0);
+  const df den = two_sum(c1, -c0);
+  const float f = __fdiv_rn(num.hi + (num.lo + U.lo), den.hi + den.lo);
+  const df bf = two_sum((float)b, f);
+  const float fnb = (float)nb;
+  const float qh = __fdiv_rn(bf.hi, fnb);
+  const float r = __fmaf_rn(-qh, fnb, bf.hi);
+  const float ql = __fdiv_rn(r + bf.lo, fnb);
+  return fast_two_sum(qh, ql);
+}
+
+struct Drawn {
+  df x0, x1, x2;   // fractions of the ra, sin dec, t ranges
+  float u3, u4, u5, u6;
+  float lpq;       // ln p - ln q (+ stratification weight)
+  uint32_t bins;   // adapted bins, 8 bits each
+};
+
+// Sample i (index in the point's round) of cell `cell`: Philox uniforms, stratified
+// (ra, sin dec, t) uniforms U_d = (c_d + u_d) / S_d (exact: S_d is a power of two),
+// prior or tabulated proposal.
+__device__ __forceinline__ Drawn draw_cell_sample(unsigned long long seed, const RoundPt &R, uint32_t i,
+                                                  uint32_t cell, const float *tab, const float *lnw) {
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint4 a = philox4x32_10(make_uint4(i, R.round, 0u, R.point_id), key);
+  const uint4 b = philox4x32_10(make_uint4(i, R.round, 1u, R.point_id), key);
+  const uint32_t c0 = cell & ((1u << R.ls0) - 1u);
+  const uint32_t c1 = (cell >> R.ls0) & ((1u << R.ls1) - 1u);
+  const uint32_t c2 = cell >> (R.ls0 + R.ls1);
+  df U0 = two_sum((float)c0, bits_to_u(a.x));
+  df U1 = two_sum((float)c1, bits_to_u(a.y));
+  df U2 = two_sum((float)c2, bits_to_u(a.z));
+  const float s0 = __int_as_float((127 - (int)R.ls0) << 23);   // 2^-ls
+  const float s1 = __int_as_float((127 - (int)R.ls1) << 23);
+  const float s2 = __int_as_float((127 - (int)R.ls2) << 23);
+  U0 = df{U0.hi * s0, U0.lo * s0};
+  U1 = df{U1.hi * s1, U1.lo * s1};
+  U2 = df{U2.hi * s2, U2.lo * s2};
+  Drawn d;
+  d.u3 = bits_to_u(a.w); d.u4 = bits_to_u(b.x); d.u5 = bits_to_u(b.y); d.u6 = bits_to_u(b.z);
+  d.lpq = (cell < R.rem) ? R.lcorr0 : R.lcorr1;
+  if (R.proposal == 0) {
+    d.x0 = U0; d.x1 = U1; d.x2 = U2;
+    d.bins = 0u;
+  } else {
+    const int nb = R.nb;
+    int b0, b1, b2;
+    d.x0 = inv_cdf_df(tab, nb, U0, b0);
+    d.x1 = inv_cdf_df(tab + (nb + 1), nb, U1, b1);
+    d.x2 = inv_cdf_df(tab + 2 * (nb + 1), nb, U2, b2);
+    d.lpq += lnw[b0] + lnw[nb + b1] + lnw[2 * nb + b2];
+    d.bins = (uint32_t)b0 | ((uint32_t)b1 << 8) | ((uint32_t)b2 << 16);
+  }
+  return d;
+}
+
+// Sky and time geometry of a drawn sample: cos/sin of (ra - GMST) and sin/cos dec.
+struct Sky { float ca, sa, cd; df sd; };
+
+__device__ __forceinline__ Sky sky_of(const PointC &P, const Drawn &d) {
+  const df v = df_add(d.x0, df{-P.g_hi, -P.g_lo});   // ra/2pi - GMST/2pi (turns)
+  float s0, c0;
+  sincospif(2.f * v.hi, &s0, &c0);
+  const float ares = kTwoPi * v.lo;
+  Sky s;
+  s.ca = c0 - s0 * ares;
+  s.sa = s0 + c0 * ares;
+  s.sd = df_add_f(df{2.f * d.x1.hi, 2.f * d.x1.lo}, -1.f);
+  s.cd = 2.f * sqrtf(d.x1.hi * (1.f - d.x1.hi));
+  return s;
+}
+
+// Q index of t + delay_k for every detector (double-float samples).
+template <int K>
+__device__ __forceinline__ void time_index(const PointC &P, const Drawn &d, const Sky &s, df out[K]) {
+  const df tf = df_mul(df{P.A, P.Alo}, d.x2);   // (t - t_lo) fs
+  const float nx = s.cd * s.ca, ny = s.cd * s.sa;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const DetC &D = P.det[k];
+    df acc = df_mul_f(df{D.P[0], D.Plo[0]}, nx);
+    acc = df_add(acc, df_mul_f(df{D.P[1], D.Plo[1]}, ny));
+    acc = df_add(acc, df_mul(df{D.P[2], D.Plo[2]}, s.sd));
+    out[k] = df_add(df_add(df{D.c0, D.c0lo}, tf), df{-acc.hi, -acc.lo});
+  }
+}
+
+// Global sample index of the j-th sample of a cell.
+__device__ __forceinline__ uint32_t sample_index(const RoundPt &R, uint32_t cell, uint32_t j) {
+  return (cell < R.rem) ? cell * (R.base + 1u) + j : R.rem * (R.base + 1u) + (cell - R.rem) * R.base + j;
+}
+
+__device__ __forceinline__ void lse_push(float l, float &m, float &s1, float &s2) {
+  if (l > m) {
+    const float e = expf(m - l);
+    s1 = fmaf(s1, e, 1.f);
+    s2 = fmaf(s2, e * e, 1.f);
+    m = l;
+  } else {
+    const float e = expf(l - m);
+    s1 += e;
+    s2 = fmaf(e, e, s2);
+  }
+}
+
+__device__ __forceinline__ void lse_merge(float &m, float &s1, float &s2, float m2, float t1, float t2) {
+  if (m2 > m) {
+    float tm = m, a = s1, b = s2;
+    m = m2; s1 = t1; s2 = t2; m2 = tm; t1 = a; t2 = b;
+  }
+  if (m2 == kNegInf) return;
+  const float e = expf(m2 - m);
+  s1 = fmaf(t1, e, s1);
+  s2 = fmaf(t2, e * e, s2);
+}
+
+// Linear term with taps from a staged window when they lie inside it.
+template <int K, int NT>
+__device__ __forceinline__ float linear_term_staged(const PointC &P, const float2 *__restrict__ Q, const df s_idx[K],
+                                                    const float2 F[K], const float2 *Ys, int ystride,
+                                                    const float4 *const win[K], const int wlo[K],
+                                                    const int whi[K], uint32_t &flags) {
+  constexpr int first = (NT == 4) ? -1 : 0;
+  float lin = 0.f;
+  const int rs = P.Mp >> 1;
+  const int npairs = (P.M + 1) >> 1;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int i; float mu;
+    df s = s_idx[k];
+    if (NT == 1) s = df_add_f(s, 0.5f);
+    df_floor(s, i, mu);
+    float w[NT];
+    interp_weights<NT>(mu, w);
+    int i0 = i + first;
+    if (i0 < 0 || i0 + NT > P.T) {
+      flags |= RIFT_FLAG_WINDOW;
+      i0 = min(max(i0, 0), P.T - NT);
+    }
+    const bool in_win = win[k] != nullptr && i0 >= wlo[k] && i0 + NT - 1 <= whi[k];
+    const float4 *row = in_win ? win[k] + (size_t)(i0 - wlo[k]) * rs
+                               : reinterpret_cast<const float4 *>(Q + ((long long)k * P.T + i0) * P.Mp);
+    float zr = 0.f, zi = 0.f;
+#pragma unroll 2
+    for (int a2 = 0; a2 < npairs; ++a2) {
+      float4 q[NT];
+#pragma unroll
+      for (int r = 0; r < NT; ++r) q[r] = row[r * rs + a2];
+      float q0r = 0.f, q0i = 0.f, q1r = 0.f, q1i = 0.f;
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        q0r = fmaf(w[r], q[r].x, q0r); q0i = fmaf(w[r], q[r].y, q0i);
+        q1r = fmaf(w[r], q[r].z, q1r); q1i = fmaf(w[r], q[r].w, q1i);
+      }
+      const float2 y0 = Ys[(2 * a2) * ystride];
+      const float2 y1 = (2 * a2 + 1 < P.M) ? Ys[(2 * a2 + 1) * ystride] : make_float2(0.f, 0.f);
+      zr = fmaf(y0.x, q0r, fmaf(y0.y, q0i, zr));
+      zi = fmaf(y0.x, q0i, fmaf(-y0.y, q0r, zi));
+      zr = fmaf(y1.x, q1r, fmaf(y1.y, q1i, zr));
+      zi = fmaf(y1.x, q1i, fmaf(-y1.y, q1r, zi));
+    }
+    lin += F[k].x * zr - F[k].y * zi;
+  }
+  return lin;
+}
+
+template <int K, int NT>
+__global__ void __launch_bounds__(RIFT_CELL_BLOCK) cells_kernel(CellLaunch L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_item, s_point;
+  __shared__ RoundPt sR;
+  __shared__ int s_wlo[K], s_whi[K], s_woff[K];
+  __shared__ int s_red[2 * K][RIFT_CELL_BLOCK / 32];
+  __shared__ float4 s_wpart[RIFT_CELL_BLOCK / 32];
+  __shared__ uint32_t s_wflag[RIFT_CELL_BLOCK / 32];
+
+  PointC &P = *reinterpret_cast<PointC *>(smem);
+  size_t off = al16(sizeof(PointC));
+  float4 *C = reinterpret_cast<float4 *>(smem + off);
+  off = al16(off + sizeof(float4) * (size_t)L.max_pairK);
+  float *tab = reinterpret_cast<float *>(smem + off);
+  float *lnw = tab + 3 * (L.max_nb + 1);
+  if (L.max_nb > 0) off = al16(off + sizeof(float) * (size_t)(3 * (L.max_nb + 1) + 3 * L.max_nb));
+  float2 *Ys = reinterpret_cast<float2 *>(smem + off) + threadIdx.x;
+  const int ystride = blockDim.x;
+  off = al16(off + sizeof(float2) * (size_t)L.max_M * blockDim.x);
+  unsigned char *wbuf = smem + off;
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_point = -1;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  int cur = -1;
+  uint32_t flags = 0u;
+  const uint32_t n_items = *L.n_items;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t it = atomicAdd(L.queue, 1u);
+      int p = -1;
+      if (it < n_items) {
+        // point of this item: last p with item0 <= it
+        int lo = 0, hi = L.n_points - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (L.rp[mid].item0 <= it) lo = mid; else hi = mid - 1;
+        }
+        p = lo;   // item0 is non-decreasing and inactive points own no items, so p owns `it`
+      }
+      s_item = (int)it;
+      s_point = p;
+    }
+    __syncthreads();
+    const uint32_t item = (uint32_t)s_item;
+    const int p = s_point;
+    if (item >= n_items || p < 0) break;
+    const RoundPt &R = sR;
+    if (p != cur) {
+      copy_words(L.pts + p, &P, sizeof(PointC));
+      copy_words(L.rp + p, &sR, sizeof(RoundPt));
+      __syncthreads();
+      const float4 *cg = L.ca + P.uv_off;
+      for (int j = threadIdx.x; j < P.npair * K; j += blockDim.x) C[j] = cg[j];
+      if (R.proposal) {
+        for (int j = threadIdx.x; j < 3 * (R.nb + 1); j += blockDim.x) tab[j] = R.tab[j];
+        for (int j = threadIdx.x; j < 3 * R.nb; j += blockDim.x) lnw[j] = R.lnw[j];
+      }
+      __syncthreads();
+      cur = p;
+    }
+    const uint32_t local = item - R.item0;
+    const uint32_t cell = local / R.chunks;
+    const uint32_t j0 = (local - cell * R.chunks) * RIFT_CHUNK;
+    const uint32_t n_cell = R.base + (cell < R.rem ? 1u : 0u);
+    const uint32_t j_end = min(n_cell, j0 + RIFT_CHUNK);
+    const float2 *Q = L.qa + P.q_off;
+    constexpr int first = (NT == 4) ? -1 : 0;
+
+    // A. window of every detector from the cell's samples
+    int rmin[K], rmax[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { rmin[k] = INT_MAX; rmax[k] = INT_MIN; }
+    for (uint32_t j = j0 + threadIdx.x; j < j_end; j += blockDim.x) {
+      const Drawn d = draw_cell_sample(L.seed, R, sample_index(R, cell, j), cell, tab, lnw);
+      const Sky s = sky_of(P, d);
+      df si[K];
+      time_index<K>(P, d, s, si);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        int i; float mu;
+        df sk = si[k];
+        if (NT == 1) sk = df_add_f(sk, 0.5f);
+        df_floor(sk, i, mu);
+        rmin[k] = min(rmin[k], i + first);
+        rmax[k] = max(rmax[k], i + first + NT - 1);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int a = __reduce_min_sync(0xffffffffu, rmin[k]);
+      const int b = __reduce_max_sync(0xffffffffu, rmax[k]);
+      if (lane == 0) { s_red[2 * k][wid] = a; s_red[2 * k + 1][wid] = b; }
+    }
+    __syncthreads();
+    // B. stage the windows that fit
+    if (threadIdx.x == 0) {
+      uint32_t bytes = 0;
+      const int rowb = P.Mp * 8;
+      for (int k = 0; k < K; ++k) {
+        int a = INT_MAX, b = INT_MIN;
+        for (int w = 0; w < nw; ++w) { a = min(a, s_red[2 * k][w]); b = max(b, s_red[2 * k + 1][w]); }
+        a = max(a, 0);
+        b = min(b, P.T - 1);
+        s_woff[k] = -1;
+        s_wlo[k] = a;
+        s_whi[k] = b;
+        if (b >= a) {
+          const uint32_t nbytes = (uint32_t)(b - a + 1) * rowb;
+          if (bytes + nbytes <= (uint32_t)L.win_budget) {
+            s_woff[k] = (int)bytes;
+            bytes += nbytes;
+          }
+        }
+      }
+      if (bytes) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar, bytes);
+        for (int k = 0; k < K; ++k)
+          if (s_woff[k] >= 0) {
+            const float2 *src = Q + ((long long)k * P.T + s_wlo[k]) * P.Mp;
+            bulk_g2s(wbuf + s_woff[k], src, (uint32_t)(s_whi[k] - s_wlo[k] + 1) * rowb, &bar);
+          }
+      }
+      s_item = bytes ? 1 : 0;   // reused as "staged" flag for this item
+    }
+    __syncthreads();
+    const bool staged = s_item != 0;
+    bool ok = true;
+    if (staged) {
+      ok = __syncthreads_and(mbar_wait(&bar, phase) ? 1 : 0) != 0;   // uniform across the CTA
+      if (ok) phase ^= 1u;
+      else flags |= RIFT_FLAG_TIMEOUT_BIT;
+    }
+    const float4 *win[K];
+    int wlo[K], whi[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      win[k] = (ok && s_woff[k] >= 0) ? reinterpret_cast<const float4 *>(wbuf + s_woff[k]) : nullptr;
+      wlo[k] = s_wlo[k];
+      whi[k] = s_whi[k];
+    }
+
+    // C. evaluate
+    float m = kNegInf, s1 = 0.f, s2 = 0.f, cnt = 0.f;
+    for (uint32_t j = j0 + threadIdx.x; j < j_end; j += blockDim.x) {
+      const uint32_t i = sample_index(R, cell, j);
+      const Drawn d = draw_cell_sample(L.seed, R, i, cell, tab, lnw);
+      const Sky s = sky_of(P, d);
+      df si[K];
+      time_index<K>(P, d, s, si);
+      float s2p, c2p;
+      sincospif(2.f * d.u3, &s2p, &c2p);   // 2 psi = 2 pi u3
+      SampleGeo g;
+#pragma unroll
+      for (int k = 0; k < K; ++k) g.s[k] = si[k];
+      // antenna pattern at psi = 0 rotated by e^{2 i psi}
+      {
+        const float ex = -s.sa, ey = s.ca;
+        const float fx = -s.sd.hi * s.ca, fy = -s.sd.hi * s.sa, fz = s.cd;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const float *dd = P.det[k].d;
+          const float dex = dd[0] * ex + dd[1] * ey;
+          const float dey = dd[1] * ex + dd[3] * ey;
+          const float dez = dd[2] * ex + dd[4] * ey;
+          const float ee = ex * dex + ey * dey;
+          const float ff = fx * (dd[0] * fx + dd[1] * fy + dd[2] * fz) + fy * (dd[1] * fx + dd[3] * fy + dd[4] * fz) +
+                           fz * (dd[2] * fx + dd[4] * fy + dd[5] * fz);
+          const float ef = fx * dex + fy * dey + fz * dez;
+          const float fr = ee - ff, fi = 2.f * ef;
+          g.F[k] = make_float2(c2p * fr - s2p * fi, s2p * fr + c2p * fi);
+        }
+      }
+      g.x = P.dref * rcbrtf(fmaf(d.u6, L.d_span3, L.d_lo3));
+      float sphi, cphi;
+      sincospif(2.f * d.u4, &sphi, &cphi);
+      swsh_modes(P, sqrtf(d.u5), sqrtf(1.f - d.u5), cphi, sphi, Ys, ystride);
+      const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
+      const float quad = quad_term<K>(P, C, g, Ys, ystride);
+      const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
+      const float ell = lnL + d.lpq;
+      if (L.dbg_ell && R.dbg_off >= 0) L.dbg_ell[R.dbg_off + i] = ell;
+      if (L.ell_buf && R.ell_off >= 0) { L.ell_buf[R.ell_off + i] = ell; L.bin_buf[R.ell_off + i] = d.bins; }
+      if (isfinite(ell)) { lse_push(ell, m, s1, s2); cnt += 1.f; }
+      else flags |= RIFT_FLAG_NONFINITE;
+    }
+    // D. one partial per cell
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float m2 = __shfl_xor_sync(0xffffffffu, m, o);
+      const float a2 = __shfl_xor_sync(0xffffffffu, s1, o);
+      const float b2 = __shfl_xor_sync(0xffffffffu, s2, o);
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      lse_merge(m, s1, s2, m2, a2, b2);
+    }
+    const uint32_t fw = __reduce_or_sync(0xffffffffu, flags);
+    if (lane == 0) { s_wpart[wid] = make_float4(m, s1, s2, cnt); s_wflag[wid] = fw; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float M = kNegInf, S1 = 0.f, S2 = 0.f, N = 0.f;
+      uint32_t F = 0u;
+      for (int w = 0; w < nw; ++w) {
+        lse_merge(M, S1, S2, s_wpart[w].x, s_wpart[w].y, s_wpart[w].z);
+        N += s_wpart[w].w;
+        F |= s_wflag[w];
+      }
+      L.partials[item] = Part{(double)M, (double)S1, (double)S2, (double)N};
+      if (F) atomicOr(L.flags, F);
+    }
+    flags = 0u;
+    __syncthreads();   // windows, partial slots and the point cache are reused by the next item
+    if (!ok) {
+      // the copies did not complete in time: wait once more (bounded) so none is left in
+      // flight into this CTA's shared memory, then stop; the flag reports the failure
+      mbar_wait(&bar, phase);
+      break;
+    }
+  }
+}
+
+__device__ __forceinline__ void d_merge(double &m, double &s1, double &s2, double &n, double m2, double t1, double t2,
+                                        double n2) {
+  n += n2;
+  if (m2 > m) {
+    double tm = m, a = s1, b = s2;
+    m = m2; s1 = t1; s2 = t2; m2 = tm; t1 = a; t2 = b;
+  }
+  if (m2 == -INFINITY) return;
+  const double e = exp(m2 - m);
+  s1 += t1 * e;
+  s2 += t2 * e * e;
+}
+
+__device__ __forceinline__ void neumaier(double &s, double &c, double x) {
+  const double t = s + x;
+  if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+  s = t;
+}
+
+// One CTA per point: fixed-order FP64 merge of the point's cell partials into its running
+// compensated accumulator.
+__global__ void merge_points_kernel(const Part *__restrict__ part, const RoundPt *__restrict__ rp,
+                                    AccState *__restrict__ acc) {
+  __shared__ double sm[256][4];
+  const RoundPt &R = rp[blockIdx.x];
+  AccState &A = acc[blockIdx.x];
+  double m = -INFINITY, s1 = 0.0, s2 = 0.0, n = 0.0;
+  for (uint32_t j = threadIdx.x; j < R.nitem; j += blockDim.x) {
+    const Part p = part[R.item0 + j];
+    d_merge(m, s1, s2, n, p.m, p.s1, p.s2, p.n);
+  }
+  sm[threadIdx.x][0] = m; sm[threadIdx.x][1] = s1; sm[threadIdx.x][2] = s2; sm[threadIdx.x][3] = n;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double a = sm[threadIdx.x][0], b = sm[threadIdx.x][1], c = sm[threadIdx.x][2], d = sm[threadIdx.x][3];
+      d_merge(a, b, c, d, sm[threadIdx.x + w][0], sm[threadIdx.x + w][1], sm[threadIdx.x + w][2],
+              sm[threadIdx.x + w][3]);
+      sm[threadIdx.x][0] = a; sm[threadIdx.x][1] = b; sm[threadIdx.x][2] = c; sm[threadIdx.x][3] = d;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && R.ncell > 0) {
+    const double M = sm[0][0], S1 = sm[0][1], S2 = sm[0][2], N = sm[0][3];
+    A.round_max = M;
+    if (N > 0.0 && M != -INFINITY) {
+      if (M > A.m) {
+        const double f = (A.m == -INFINITY) ? 0.0 : exp(A.m - M);
+        A.s1 *= f; A.c1 *= f; A.s2 *= f * f; A.c2 *= f * f;
+        A.m = M;
+      }
+      const double e = exp(M - A.m);
+      neumaier(A.s1, A.c1, S1 * e);
+      neumaier(A.s2, A.c2, S2 * e * e);
+    }
+    A.n += (unsigned long long)N;
+  }
+}
+
+// Adaptive histograms of every point (grid: hblocks x points), 32.32 fixed point.
+__global__ void hist_points_kernel(const float *__restrict__ ell, const uint32_t *__restrict__ bins,
+                                   const RoundPt *__restrict__ rp, const AccState *__restrict__ acc, float beta, int nb,
+                                   unsigned long long *__restrict__ part) {
+  extern __shared__ unsigned long long h[];
+  const int p = blockIdx.y;
+  const RoundPt &R = rp[p];
+  for (int j = threadIdx.x; j < 3 * nb; j += blockDim.x) h[j] = 0ull;
+  __syncthreads();
+  if (R.ncell > 0 && R.ell_off >= 0 && R.proposal) {
+    const float mx = (float)acc[p].round_max;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += gridDim.x * blockDim.x) {
+      const float l = ell[R.ell_off + i];
+      if (!isfinite(l)) continue;
+      const float w = expf(beta * (l - mx));
+      const unsigned long long q = __float2ull_rn(w * 4294967296.0f);
+      const uint32_t b = bins[R.ell_off + i];
+      atomicAdd(&h[b & 255u], q);
+      atomicAdd(&h[nb + ((b >> 8) & 255u)], q);
+      atomicAdd(&h[2 * nb + ((b >> 16) & 255u)], q);
+    }
+  }
+  __syncthreads();
+  unsigned long long *out = part + ((size_t)p * gridDim.x + blockIdx.x) * 3 * nb;
+  for (int j = threadIdx.x; j < 3 * nb; j += blockDim.x) out[j] = h[j];
+}
+
+// New tables of every adapting point (grid: points): p_b = (1 - eps) h_b / sum h + eps / nb,
+// cdf = cumsum in FP64 rounded to float32 (cdf[0] = 0, cdf[nb] = 1), lnw_b = -ln(nb (cdf[b+1] - cdf[b])).
+// With part == nullptr only lnw is recomputed from the current tables.
+__global__ void tables_points_kernel(const unsigned long long *__restrict__ part, int hblocks,
+                                     const RoundPt *__restrict__ rp, int nb, double eps, float *tables, float *lnw) {
+  __shared__ double hs[3 * RIFT_MAXBINS];
+  const int p = blockIdx.x;
+  if (part && (rp[p].ncell == 0 || !rp[p].proposal)) return;
+  float *tb = tables + (size_t)p * 3 * (nb + 1);
+  float *lw = lnw + (size_t)p * 3 * nb;
+  if (part) {
+    for (int j = threadIdx.x; j < 3 * nb; j += blockDim.x) {
+      unsigned long long t = 0ull;
+      for (int b = 0; b < hblocks; ++b) t += part[((size_t)p * hblocks + b) * 3 * nb + j];
+      hs[j] = (double)t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) {
+    const int d = threadIdx.x;
+    float *cdf = tb + d * (nb + 1);
+    if (part) {
+      double S = 0.0;
+      for (int b = 0; b < nb; ++b) S += hs[d * nb + b];
+      double tot = 0.0;
+      for (int b = 0; b < nb; ++b) tot += (S > 0.0 ? (1.0 - eps) * hs[d * nb + b] / S + eps / nb : 1.0 / nb);
+      double c = 0.0;
+      cdf[0] = 0.f;
+      for (int b = 0; b < nb; ++b) {
+        c += (S > 0.0 ? (1.0 - eps) * hs[d * nb + b] / S + eps / nb : 1.0 / nb);
+        cdf[b + 1] = (float)(c / tot);
+      }
+      cdf[nb] = 1.f;
+    }
+    for (int b = 0; b < nb; ++b) lw[d * nb + b] = (float)(-log((double)nb * ((double)cdf[b + 1] - (double)cdf[b])));
+  }
+}
+
+// The samples of one round of point 0 in cell order (no evaluation).
+__global__ void draw_cells_kernel(CellLaunch L, DrawOut o, uint32_t n) {
+  __shared__ __align__(16) PointC P;
+  extern __shared__ float dtab[];
+  const RoundPt &R = L.rp[0];
+  copy_words(L.pts, &P, sizeof(PointC));
+  float *tab = dtab;
+  float *lnw = dtab + 3 * (R.nb + 1);
+  if (R.proposal) {
+    for (int j = threadIdx.x; j < 3 * (R.nb + 1); j += blockDim.x) tab[j] = R.tab[j];
+    for (int j = threadIdx.x; j < 3 * R.nb; j += blockDim.x) lnw[j] = R.lnw[j];
+  }
+  __syncthreads();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // cell of sample i
+  const uint32_t big = R.rem * (R.base + 1u);
+  const uint32_t cell = (i < big) ? i / (R.base + 1u) : R.rem + (i - big) / R.base;
+  const Drawn d = draw_cell_sample(L.seed, R, i, cell, tab, lnw);
+  o.theta[0 * (size_t)n + i] = kTwoPi * (d.x0.hi + d.x0.lo);
+  o.theta[1 * (size_t)n + i] = (2.f * d.x1.hi - 1.f) + 2.f * d.x1.lo;
+  o.theta[2 * (size_t)n + i] = P.t_lo + P.t_span * (d.x2.hi + d.x2.lo);
+  o.theta[3 * (size_t)n + i] = 3.14159265358979f * d.u3;
+  o.theta[4 * (size_t)n + i] = kTwoPi * d.u4;
+  o.theta[5 * (size_t)n + i] = 2.f * d.u5 - 1.f;
+  o.theta[6 * (size_t)n + i] = cbrtf(fmaf(d.u6, L.d_span3, L.d_lo3));
+  o.lpq[i] = d.lpq;
+  if (o.bins) {
+    o.bins[0 * (size_t)n + i] = (int)(d.bins & 255u);
+    o.bins[1 * (size_t)n + i] = (int)((d.bins >> 8) & 255u);
+    o.bins[2 * (size_t)n + i] = (int)((d.bins >> 16) & 255u);
+  }
+}
+
+template <int K, int NT>
+cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(cells_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cells_kernel<K, NT><<<grid, block, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+template <int K, int NT>
+int cells_occ(size_t smem, int block) {
+  int nb = 0;
+  cudaFuncSetAttribute(cells_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_kernel<K, NT>, block, smem);
+  return nb;
+}
+
+}  // namespace
+
+size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block) {
+  (void)K;
+  size_t off = (sizeof(PointC) + 15) & ~size_t(15);
+  off = (off + sizeof(float4) * (size_t)max_pairK + 15) & ~size_t(15);
+  if (max_nb > 0) off = (off + sizeof(float) * (size_t)(3 * (max_nb + 1) + 3 * max_nb) + 15) & ~size_t(15);
+  off = (off + sizeof(float2) * (size_t)max_M * block + 15) & ~size_t(15);
+  return off;
+}
+
+#define RIFT_CELLS_DISPATCH(K, NT, CALL)                                        \
+  switch ((K) * 8 + (NT)) {                                                     \
+    case 1 * 8 + 1: return CALL(1, 1); case 1 * 8 + 2: return CALL(1, 2); case 1 * 8 + 4: return CALL(1, 4); \
+    case 2 * 8 + 1: return CALL(2, 1); case 2 * 8 + 2: return CALL(2, 2); case 2 * 8 + 4: return CALL(2, 4); \
+    case 3 * 8 + 1: return CALL(3, 1); case 3 * 8 + 2: return CALL(3, 2); case 3 * 8 + 4: return CALL(3, 4); \
+    case 4 * 8 + 1: return CALL(4, 1); case 4 * 8 + 2: return CALL(4, 2); case 4 * 8 + 4: return CALL(4, 4); \
+    default: break;                                                             \
+  }
+
+cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
+#define RIFT_C(KK, TT) cells_k<KK, TT>(L, grid, block, smem, st)
+  RIFT_CELLS_DISPATCH(K, ntap, RIFT_C)
+#undef RIFT_C
+  return cudaErrorInvalidValue;
+}
+
+int cells_blocks_per_sm(int K, int ntap, size_t smem, int block) {
+#define RIFT_O(KK, TT) cells_occ<KK, TT>(smem, block)
+  RIFT_CELLS_DISPATCH(K, ntap, RIFT_O)
+#undef RIFT_O
+  return 0;
+}
+
+cudaError_t launch_merge_points(const Part *partials, const RoundPt *rp, int n_points, AccState *acc,
+                                cudaStream_t st) {
+  merge_points_kernel<<<n_points, 256, 0, st>>>(partials, rp, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist_points(const float *ell, const uint32_t *bins, const RoundPt *rp, int n_points,
+                               const AccState *acc, float beta, int nb, unsigned long long *part, int hblocks,
+                               cudaStream_t st) {
+  dim3 g(hblocks, n_points);
+  hist_points_kernel<<<g, 256, sizeof(unsigned long long) * 3 * nb, st>>>(ell, bins, rp, acc, beta, nb, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tables_points(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points,
+                                 int nb, double floor_eps, float *tables, float *lnw, cudaStream_t st) {
+  tables_points_kernel<<<n_points, 256, 0, st>>>(part, hblocks, rp, nb, floor_eps, tables, lnw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draw_cells(const CellLaunch &L, DrawOut o, uint32_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int block = 128;
+  const size_t smem = sizeof(float) * (3 * (L.max_nb + 1) + 3 * L.max_nb);
+  draw_cells_kernel<<<(n + block - 1) / block, block, smem, st>>>(L, o, n);
+  return cudaGetLastError();
+}

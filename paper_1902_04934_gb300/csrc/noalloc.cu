@@ -26,18 +26,22 @@
 
 namespace {
 
-constexpr int kBlock = RIFT_MC_BLOCK;
-constexpr int kMaxBlocks = RIFT_STATIC_MAX_BLOCKS;
-constexpr int kMaxHistBlocks = 64;
+constexpr int kHist = 64;          // histogram blocks per round
+// work items of one round: cells plus extra chunks of large cells (adaptive rounds are
+// capped at RIFT_STATIC_MAX_ROUND samples; prior rounds of any size use at most this many
+// items because the runner rejects more)
+constexpr size_t kItems = (size_t)RIFT_MAX_CELLS + RIFT_STATIC_MAX_PRIOR_ROUND / RIFT_CHUNK + 1;
 constexpr size_t kAlign = 256;
 
 constexpr size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// layout of the scratch array
+// layout of the scratch array (one point)
 constexpr size_t kOffAcc = 0;
 constexpr size_t kOffPart = al(kOffAcc + sizeof(AccState));
-constexpr size_t kOffHist = al(kOffPart + sizeof(Part) * kMaxBlocks);
-constexpr size_t kOffTab = al(kOffHist + sizeof(unsigned long long) * kMaxHistBlocks * 3 * RIFT_MAXBINS);
+constexpr size_t kOffRp = al(kOffPart + sizeof(Part) * kItems);
+constexpr size_t kOffCnt = al(kOffRp + sizeof(RoundPt));
+constexpr size_t kOffHist = al(kOffCnt + sizeof(uint32_t) * 2);
+constexpr size_t kOffTab = al(kOffHist + sizeof(unsigned long long) * kHist * 3 * RIFT_MAXBINS);
 constexpr size_t kOffLnw = al(kOffTab + sizeof(float) * 2 * 3 * (RIFT_MAXBINS + 1));
 constexpr size_t kOffEll = al(kOffLnw + sizeof(float) * 2 * 3 * RIFT_MAXBINS);
 constexpr size_t kOffBin = al(kOffEll + sizeof(float) * RIFT_STATIC_MAX_ROUND);
@@ -73,132 +77,46 @@ cudaError_t scratch_address(unsigned char **out) {
 
 }  // namespace
 
-// Internal accessors of the handle, defined in capi.cu.
-rift_status rift_internal_point0(rift_ile *h, const PointC **host, const PointC **dev, const float2 **qa,
-                                 const float4 **ca, int *K, int *num_sms, uint32_t **flags, cudaStream_t *st);
+// Defined in capi.cu: the Monte Carlo runner with caller-provided scratch.
+rift_status rift_internal_run_static(rift_ile *h, const rift_mc_opts *o, McScratch &S, rift_mc_result *res);
 rift_status rift_internal_fail(rift_ile *h, rift_status s, const char *msg);
-rift_status rift_internal_validate_opts(rift_ile *h, const rift_mc_opts *o);
 
 extern "C" rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res) {
-  if (!h || !res) return RIFT_EINVAL;
-  rift_status s = rift_internal_validate_opts(h, o);
-  if (s != RIFT_OK) return s;
-  const PointC *ph = nullptr, *pd = nullptr;
-  const float2 *qa = nullptr;
-  const float4 *ca = nullptr;
-  int K = 0, sms = 0;
-  uint32_t *flags = nullptr;
-  cudaStream_t st = nullptr;
-  if ((s = rift_internal_point0(h, &ph, &pd, &qa, &ca, &K, &sms, &flags, &st)) != RIFT_OK) return s;
-  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
-  const int nb = adaptive ? o->n_bins : 0;
-  if (adaptive && o->n_per_round > (uint32_t)RIFT_STATIC_MAX_ROUND)
+  if (!h || !res || !o) return RIFT_EINVAL;
+  if (o->proposal == RIFT_PROPOSAL_ADAPTIVE && o->n_per_round > (uint32_t)RIFT_STATIC_MAX_ROUND)
     return rift_internal_fail(h, RIFT_EINVAL,
                               "rift_ile_marginalize_static: n_per_round exceeds RIFT_STATIC_MAX_ROUND "
                               "(the static scratch holds one adaptive round of at most that many samples)");
+  if (o->n_per_round > (uint32_t)RIFT_STATIC_MAX_PRIOR_ROUND)
+    return rift_internal_fail(h, RIFT_EINVAL,
+                              "rift_ile_marginalize_static: n_per_round exceeds RIFT_STATIC_MAX_PRIOR_ROUND "
+                              "(the static scratch holds the partials of at most that many samples per round)");
   if (o->dbg_tables || o->timing)
     return rift_internal_fail(h, RIFT_EINVAL, "rift_ile_marginalize_static: dbg_tables and timing are not supported");
+  if (o->proposal == RIFT_PROPOSAL_ADAPTIVE && (o->n_bins < 2 || o->n_bins > RIFT_MAXBINS))
+    return rift_internal_fail(h, RIFT_EINVAL, "n_bins out of range [2, 256]");
   unsigned char *base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return rift_internal_fail(h, RIFT_ECUDA, cudaGetErrorString(e));
-  AccState *acc = reinterpret_cast<AccState *>(base + kOffAcc);
-  Part *parts = reinterpret_cast<Part *>(base + kOffPart);
-  unsigned long long *hist = reinterpret_cast<unsigned long long *>(base + kOffHist);
-  float *tables = reinterpret_cast<float *>(base + kOffTab);
-  float *lnw = reinterpret_cast<float *>(base + kOffLnw);
-  float *ell = reinterpret_cast<float *>(base + kOffEll);
-  uint32_t *bins = reinterpret_cast<uint32_t *>(base + kOffBin);
-
-  const size_t smem = rift_point_smem_bytes(K, ph->npair, nb, kBlock, ph->M);
-  if (smem > 200 * 1024) return rift_internal_fail(h, RIFT_EUNSUPPORTED, "shared memory footprint too large");
-  int bps = mc_round_blocks_per_sm(K, smem, kBlock);
-  if (bps < 1) bps = 1;
-  const uint32_t npr = o->n_per_round;
-  const int grid = std::max(1, std::min(std::min(sms * bps, kMaxBlocks), (int)((npr + kBlock - 1) / kBlock)));
-  const int hist_grid = std::max(1, std::min(kMaxHistBlocks, (int)((npr + 255) / 256)));
-
-  // the array keeps the previous call's contents: reset the accumulator, set round-0 tables
-  AccState a0;
-  std::memset(&a0, 0, sizeof(a0));
-  a0.m = -INFINITY;
-#define RIFT_SCK(call)                                                               \
-  do {                                                                               \
-    cudaError_t e_ = (call);                                                         \
-    if (e_ != cudaSuccess) return rift_internal_fail(h, RIFT_ECUDA, cudaGetErrorString(e_)); \
-  } while (0)
-  RIFT_SCK(cudaMemcpyAsync(acc, &a0, sizeof(a0), cudaMemcpyHostToDevice, st));
-  int cur = 0;
-  if (adaptive) {
-    float u[3 * (RIFT_MAXBINS + 1)];
-    const float *src = o->tables;
-    if (!src) {
-      for (int d = 0; d < 3; ++d)
-        for (int b = 0; b <= nb; ++b) u[d * (nb + 1) + b] = (float)((double)b / nb);
-      src = u;
-    }
-    RIFT_SCK(cudaMemcpyAsync(tables, src, sizeof(float) * 3 * (nb + 1), cudaMemcpyHostToDevice, st));
-    RIFT_SCK(cudaStreamSynchronize(st));   // the source may be on this stack frame
-    RIFT_SCK(launch_tables(nullptr, 0, nb, 0.0, tables, lnw, st));
-  }
-  McParams prm;
-  std::memset(&prm, 0, sizeof(prm));
-  prm.seed = o->seed; prm.point_id = o->point_id; prm.nb = nb;
-  prm.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
-  prm.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
-  prm.partials = parts; prm.flags = flags;
-  uint64_t evals = 0;
-  AccState a;
-  std::memset(&a, 0, sizeof(a));
-  int r = 0, launches = 0;
-  for (;; ++r) {
-    prm.round = (uint32_t)r;
-    prm.n = (uint32_t)std::min<uint64_t>(npr, o->max_evals - evals);
-    prm.proposal = adaptive ? 1 : 0;
-    prm.tables = adaptive ? tables + cur * 3 * (nb + 1) : nullptr;
-    prm.lnw = adaptive ? lnw + cur * 3 * nb : nullptr;
-    prm.dbg_ell = o->dbg_ell;
-    prm.dbg_off = (long long)r * npr;
-    prm.ell_buf = adaptive ? ell : nullptr;
-    prm.bin_buf = adaptive ? bins : nullptr;
-    const int g = std::max(1, std::min<int>(grid, (int)((prm.n + kBlock - 1) / kBlock)));
-    RIFT_SCK(launch_mc_round(K, pd, *ph, qa, ca, prm, g, kBlock, st));
-    RIFT_SCK(launch_merge(parts, g, acc, st));
-    launches += 2;
-    const bool adapt_now = adaptive && (o->adapt_rounds < 0 || r < o->adapt_rounds);
-    if (adapt_now) {
-      const int hg = std::max(1, std::min(hist_grid, (int)((prm.n + 255) / 256)));
-      RIFT_SCK(launch_hist(ell, bins, prm.n, acc, (float)o->beta, nb, hist, hg, st));
-      RIFT_SCK(launch_tables(hist, hg, nb, o->floor_eps, tables + (1 - cur) * 3 * (nb + 1), lnw + (1 - cur) * 3 * nb,
-                             st));
-      launches += 2;
-    }
-    RIFT_SCK(cudaMemcpyAsync(&a, acc, sizeof(a), cudaMemcpyDeviceToHost, st));
-    RIFT_SCK(cudaStreamSynchronize(st));
-    if (adapt_now) cur = 1 - cur;
-    evals += prm.n;
-    const double n_eff = a.s1 + a.c1;
-    if (n_eff >= o->n_eff_target || evals >= o->max_evals || (o->max_rounds > 0 && r + 1 >= o->max_rounds)) break;
-  }
-#undef RIFT_SCK
-  std::memset(res, 0, sizeof(*res));
-  res->acc_max = a.m;
-  res->acc_s1 = a.s1 + a.c1;
-  res->acc_s2 = a.s2 + a.c2;
-  res->n_evals = a.n;
-  const double n = (double)a.n;
-  if (a.n == 0 || !(res->acc_s1 > 0)) {
-    res->lnL_marg = -INFINITY; res->sigma = INFINITY;
-  } else {
-    res->lnL_marg = a.m + std::log(res->acc_s1) - std::log(n);
-    res->n_eff = res->acc_s1;
-    res->n_eff_kish = res->acc_s1 * res->acc_s1 / res->acc_s2;
-    res->sigma = (a.n > 1) ? std::sqrt(std::max(n * res->acc_s2 / (res->acc_s1 * res->acc_s1) - 1.0, 0.0) / (n - 1.0))
-                           : INFINITY;
-  }
-  res->rounds = r + 1;
-  res->kernel_launches = launches;
-  s = rift_ile_check(h);
-  if (s == RIFT_OK && res->n_eff < o->n_eff_target) s = RIFT_ENOTCONVERGED;
-  res->status = s;
-  return s;
+  // host mirrors of the one point's round descriptor and accumulator live on this stack frame
+  RoundPt rp_host;
+  AccState acc_host;
+  McScratch S;
+  std::memset(&S, 0, sizeof(S));
+  S.acc = reinterpret_cast<AccState *>(base + kOffAcc);
+  S.partials = reinterpret_cast<Part *>(base + kOffPart);
+  S.rp = reinterpret_cast<RoundPt *>(base + kOffRp);
+  S.counters = reinterpret_cast<uint32_t *>(base + kOffCnt);
+  S.hist = reinterpret_cast<unsigned long long *>(base + kOffHist);
+  S.tables = reinterpret_cast<float *>(base + kOffTab);
+  S.lnw = reinterpret_cast<float *>(base + kOffLnw);
+  S.ell = reinterpret_cast<float *>(base + kOffEll);
+  S.bins = reinterpret_cast<uint32_t *>(base + kOffBin);
+  S.max_items = kItems;
+  S.hblocks = std::max(1, std::min(kHist, (int)(o->n_per_round / 8192)));
+  S.rp_host = &rp_host;
+  S.acc_host = &acc_host;
+  // everything the runner reads from the array is (re)initialised by it: the accumulator,
+  // the round-0 tables, the round descriptor and the work counters
+  return rift_internal_run_static(h, o, S, res);
 }

@@ -8,6 +8,9 @@ struct PointC;
 
 // Threads per block of the fused likelihood kernel.
 #define RIFT_MC_BLOCK 256
+// Threads per block of the cell kernel, and samples per work item at most.
+#define RIFT_CELL_BLOCK 128
+#define RIFT_CHUNK 1024
 
 // Block partial of the log-sum-exp: max, sum e^{l-max}, sum e^{2(l-max)}, count.
 struct __align__(32) Part {
@@ -24,24 +27,63 @@ struct AccState {
   unsigned long long pad;
 };
 
-// Per-launch Monte Carlo parameters.
-struct McParams {
+// One point's part of a Monte Carlo round (device array over points).
+struct RoundPt {
+  uint32_t n;              // samples this round (0: point inactive)
+  uint32_t ncell;          // cells: S_ra S_sd S_t, 0 if inactive
+  uint32_t base, rem;      // n = base * ncell + rem; cells [0, rem) hold base + 1 samples
+  uint32_t item0;          // first work item of this point in the round
+  uint32_t chunks;         // work items per cell (each at most RIFT_CHUNK samples)
+  uint32_t nitem;          // work items of this point: ncell * chunks
+  uint32_t round;          // Philox counter word 1
+  uint32_t point_id;       // Philox counter word 3
+  uint32_t ls0, ls1, ls2;  // log2 of the strata in effect
+  int proposal;            // 0 prior, 1 tables
+  int nb;                  // bins per adapted coordinate
+  float lcorr0, lcorr1;    // ln(n / (C (base+1))), ln(n / (C base)): stratified-estimator weights
+  long long ell_off;       // offset of the point's samples in the per-sample buffers (-1: none)
+  long long dbg_off;       // offset in the caller's dbg_ell (-1: none)
+  const float *tab;        // [3][nb+1] float32 CDF tables
+  const float *lnw;        // [3][nb]   -ln(nb p_b)
+};
+
+// Arguments of the cell kernel.
+struct CellLaunch {
   unsigned long long seed;
-  uint32_t round;
-  uint32_t n;          // samples this round (per point)
-  uint32_t point_id;   // counter word 3 (single point)
-  int proposal;        // 0 prior, 1 tables
-  int nb;              // bins per adapted coordinate
-  int pad;
   float d_lo3, d_span3;
-  const float *tables; // device [3][nb+1]
-  const float *lnw;    // device [3][nb]: -ln(nb p_b)
-  float *dbg_ell;      // optional [.. + n]
-  long long dbg_off;
-  float *ell_buf;      // adaptive scratch [n]
-  uint32_t *bin_buf;   // adaptive scratch [n], bins packed 3 x 8 bits
-  Part *partials;   // [grid] (m, s1, s2, n)
+  const PointC *pts;
+  const RoundPt *rp;
+  int n_points;
+  int win_budget;              // bytes of shared memory for staged Q windows
+  const uint32_t *n_items;     // device: work items of this round
+  uint32_t *queue;             // device: work-item counter (reset to 0 before the launch)
+  const float2 *qa;
+  const float4 *ca;
+  Part *partials;              // [n_items]
+  float *dbg_ell;
+  float *ell_buf;
+  uint32_t *bin_buf;
   uint32_t *flags;
+  int max_M;                   // largest mode count over the points (shared-memory layout)
+  int max_pairK;               // largest npair * K over the points
+  int max_nb;                  // largest bin count (0 if no point uses tables)
+};
+
+// Scratch of the Monte Carlo runner (device pointers unless noted).
+struct McScratch {
+  AccState *acc;               // [np]
+  Part *partials;              // [max_items]
+  RoundPt *rp;                 // [np]
+  uint32_t *counters;          // [2]: work items of the round, work-queue counter
+  float *ell;                  // [np * n_per_round] adaptive per-sample log weights
+  uint32_t *bins;              // [np * n_per_round] adaptive bins
+  unsigned long long *hist;    // [np][hblocks][3][nb]
+  float *tables;               // [2][np][3][RIFT_MAXBINS + 1]
+  float *lnw;                  // [2][np][3][RIFT_MAXBINS]
+  size_t max_items;
+  int hblocks;
+  RoundPt *rp_host;            // host mirror [np]
+  AccState *acc_host;          // host mirror [np]
 };
 
 struct DrawOut {
@@ -52,17 +94,22 @@ struct DrawOut {
 
 size_t rift_point_smem_bytes(int K, int npair, int nb, int block, int M);
 
-cudaError_t launch_mc_round(int K, const PointC *pt_dev, const PointC &pt_host, const float2 *q_arena,
-                            const float4 *c_arena, const McParams &prm, int grid, int block, cudaStream_t st);
-cudaError_t launch_merge(const Part *partials, int nparts, AccState *acc, cudaStream_t st);
-cudaError_t launch_hist(const float *ell, const uint32_t *bins, uint32_t n, const AccState *acc, float beta,
-                        int nb, unsigned long long *part, int grid, cudaStream_t st);
-cudaError_t launch_tables(const unsigned long long *part, int nparts, int nb, double floor_eps, float *tables,
-                          float *lnw, cudaStream_t st);
 cudaError_t launch_lnl_array(int K, const PointC *pt_dev, const PointC &pt_host, const float2 *q_arena,
                              const float4 *c_arena, size_t n, const float *ra, const float *dec, const float *t,
                              const float *psi, const float *phi, const float *incl, const float *dist, float *out,
                              uint32_t *flags, cudaStream_t st);
-cudaError_t launch_draw(int K, const PointC *pt_dev, const PointC &pt_host, const McParams &prm, DrawOut o,
-                        cudaStream_t st);
-int mc_round_blocks_per_sm(int K, size_t smem, int block);
+
+// Cell kernel (mc.cu)
+size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block);
+cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st);
+int cells_blocks_per_sm(int K, int ntap, size_t smem, int block);
+cudaError_t launch_merge_points(const Part *partials, const RoundPt *rp, int n_points, AccState *acc,
+                                cudaStream_t st);
+cudaError_t launch_hist_points(const float *ell, const uint32_t *bins, const RoundPt *rp, int n_points,
+                               const AccState *acc, float beta, int nb, unsigned long long *part, int hblocks,
+                               cudaStream_t st);
+cudaError_t launch_tables_points(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points,
+                                 int nb, double floor_eps, float *tables, float *lnw, cudaStream_t st);
+cudaError_t launch_draw_cells(const CellLaunch &L, DrawOut o, uint32_t n, cudaStream_t st);
+
+#define RIFT_FLAG_TIMEOUT_BIT 4u

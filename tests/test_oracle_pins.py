@@ -417,3 +417,53 @@ def test_rebuild_tables_properties():
         assert np.all(p >= 0.1 / 20 * (1 - 1e-6))
         want = 0.9 * h[d] / h[d].sum() + 0.1 / 20
         assert np.allclose(p, want, atol=1e-7)
+
+
+# ---------------------------------------------------------------- stratified rounds
+def test_cell_mapping_contiguous_and_balanced():
+    for n, C in ((23, 4), (100000, 1024), (1024, 1024), (5000, 7)):
+        c, n_c = mc.cell_of(np.arange(n), n, C)
+        assert np.all(np.diff(c) >= 0) and c.min() == 0 and c.max() == C - 1
+        counts = np.bincount(c, minlength=C)
+        assert np.array_equal(counts, n_c[np.searchsorted(c, np.arange(C))])
+        assert counts.max() - counts.min() <= 1 and counts.sum() == n
+
+
+def test_stratified_estimator_exact_for_cellwise_constant_weights():
+    """A weight that is constant on every cell is integrated exactly by the stratified round,
+    whatever the (uneven) number of samples per cell -- this fixes the ln(n / (C n_c)) term."""
+    S = (4, 2, 8)
+    C = 64
+    r = _rng(19)
+    g = r.uniform(0.1, 3.0, C)                       # weight of each cell
+    for n in (64, 1000, 4097):
+        u = P.uniforms(3, 0, 0, np.arange(n, dtype=np.uint64), 8)
+        us, corr = mc.stratify(u, np.arange(n), n, S)
+        cell = (np.floor(us[0] * S[0]) + S[0] * (np.floor(us[1] * S[1]) + S[1] * np.floor(us[2] * S[2]))).astype(int)
+        ell = np.log(g[cell]) + corr
+        est = mc.Accum.of(ell).result()[0]
+        assert abs(est - math.log(g.mean())) < 1e-12, n
+
+
+def test_stratified_uniforms_stay_in_their_cells_and_rounds_below_C_are_plain():
+    S = (8, 4, 2)
+    n = 1000
+    u = P.uniforms(4, 0, 0, np.arange(n, dtype=np.uint64), 8)
+    us, _ = mc.stratify(u, np.arange(n), n, S)
+    c, _ = mc.cell_of(np.arange(n), n, 64)
+    assert np.array_equal(np.floor(us[0] * 8), c % 8)
+    assert np.array_equal(np.floor(us[2] * 2), c // 32)
+    assert np.array_equal(us[3:], u[3:])
+    u2, corr = mc.stratify(u[:, :40], np.arange(40), 40, S)  # 40 < 64 cells: not stratified
+    assert np.array_equal(u2, u[:, :40]) and np.all(corr == 0)
+    with pytest.raises(ValueError):
+        mc.effective_strata(100, (3, 1, 1))
+
+
+def test_stratified_marginalisation_agrees_with_plain():
+    pt = _physical_point(4.0)
+    pr = mc.Prior(pt["t_lo"], pt["t_hi"])
+    plain = mc.marginalize(pt, 201, 0, pr, 100000, 300000, 1e300)
+    strat = mc.marginalize(pt, 202, 0, pr, 100000, 300000, 1e300, strata=(16, 8, 8))
+    s = math.hypot(plain["sigma"], strat["sigma"])
+    assert abs(plain["lnL_marg"] - strat["lnL_marg"]) < 5 * s + 0.005

@@ -132,7 +132,8 @@ def test_lnl_empty_and_window_flag(lib, cuda, p_small):
 
 def test_draw_matches_oracle_uniforms(lib, cuda, p_small):
     n = 10007
-    theta, lpq, _ = lib.rift_ile_draw(h := lib.rift_ile_create(p_small), 3, n, seed=99, point_id=0)
+    theta, lpq, _ = lib.rift_ile_draw(h := lib.rift_ile_create(p_small), 3, n, seed=99, point_id=0,
+                                      strata=(1, 1, 1))
     th = theta.cpu().numpy().astype(np.float64)
     u = P.uniforms(99, 0, 3, np.arange(n, dtype=np.uint64), 8)
     pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
@@ -143,6 +144,20 @@ def test_draw_matches_oracle_uniforms(lib, cuda, p_small):
     assert np.allclose(th[2], ref["t"], rtol=0, atol=1e-8)
     assert np.allclose(th[6], ref["dist"], rtol=3e-7)
     assert np.all(lpq.cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("S", [(4, 2, 8), (16, 8, 4)])
+def test_draw_stratified_matches_oracle(lib, cuda, p_small, S):
+    n = 10007                      # not a multiple of the cell count: uneven cells
+    h = lib.rift_ile_create(p_small)
+    theta, lpq, _ = lib.rift_ile_draw(h, 2, n, seed=98, strata=S)
+    th = theta.cpu().numpy().astype(np.float64)
+    pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
+    ref, _, lq = mc.draw(98, 0, 2, np.arange(n, dtype=np.uint64), pr, None, S, n)
+    assert np.allclose(th[0], ref["ra"], rtol=3e-7, atol=1e-7)
+    assert np.allclose(th[1], ref["sindec"], atol=2e-7)
+    assert np.allclose(th[2], ref["t"], atol=1e-8)
+    assert np.allclose(lpq.cpu().numpy(), lq, atol=1e-7)
 
 
 def _peaked_tables(pt, nb=64):
@@ -158,9 +173,10 @@ def test_draw_with_tables_bitexact_bins(lib, cuda, p_small):
     tab = _peaked_tables(p_small, nb)
     n = 20000
     h = lib.rift_ile_create(p_small)
-    theta, lpq, bins = lib.rift_ile_draw(h, 1, n, tables=tab, seed=7, proposal="adaptive", n_bins=nb)
+    S = (4, 4, 4)
+    theta, lpq, bins = lib.rift_ile_draw(h, 1, n, tables=tab, seed=7, proposal="adaptive", n_bins=nb, strata=S)
     pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
-    th, b, lq = mc.draw(7, 0, 1, np.arange(n, dtype=np.uint64), pr, tab)
+    th, b, lq = mc.draw(7, 0, 1, np.arange(n, dtype=np.uint64), pr, tab, S, n)
     assert np.array_equal(bins.cpu().numpy(), b)
     g = theta.cpu().numpy().astype(np.float64)
     assert np.allclose(g[0], th["ra"], atol=2e-6)
@@ -172,32 +188,36 @@ def _marg_gpu(lib, h, **kw):
     return lib.rift_ile_marginalize(h, **kw)
 
 
-def test_marginalize_small_parity(lib, cuda, p_small):
+@pytest.mark.parametrize("S", [(1, 1, 1), (8, 4, 4)])
+def test_marginalize_small_parity(lib, cuda, p_small, S):
     import torch
     n = 100000
     h = lib.rift_ile_create(p_small)
     dbg = torch.empty(n, dtype=torch.float32, device="cuda")
-    res = _marg_gpu(lib, h, seed=21, n_per_round=n, max_evals=n, dbg_ell=dbg)
+    res = _marg_gpu(lib, h, seed=21, n_per_round=n, max_evals=n, dbg_ell=dbg, strata=S)
+    assert tuple(res["strata"]) == S
     pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
-    ref = mc.marginalize(p_small, 21, 0, pr, n, n, 1e300)
+    ref = mc.marginalize(p_small, 21, 0, pr, n, n, 1e300, strata=S)
     assert res["n_evals"] == n
     assert abs(res["lnL_marg"] - ref["lnL_marg"]) < TOL_MARG, (res["lnL_marg"], ref["lnL_marg"])
     assert abs(res["n_eff"] - ref["n_eff"]) <= 1e-3 * ref["n_eff"] + 1e-3
-    th, _, _ = mc.draw(21, 0, 0, np.arange(n, dtype=np.uint64), pr)
-    want = mc.lnL_samples(p_small, th)
+    th, _, lq = mc.draw(21, 0, 0, np.arange(n, dtype=np.uint64), pr, None, S, n)
+    want = mc.lnL_samples(p_small, th) + lq
     got = dbg.cpu().numpy().astype(np.float64)
     th64 = dict(ra=th["ra"], dec=np.arcsin(th["sindec"]), t=th["t"], psi=th["psi"], phi=th["phi"],
                 incl=np.arccos(th["cosi"]), dist=th["dist"])
     assert np.all(np.abs(got - want) <= _tol(p_small, th64))
     # the device reduction equals the exact log-sum-exp of the device's own samples
     own = mc.Accum.of(got).result()
-    assert abs(own[0] - res["lnL_marg"]) < 1e-9
+    assert abs(own[0] - res["lnL_marg"]) < 1e-6     # FP32 per-thread sums, FP64 across cells
 
 
 def test_marginalize_multiround_ragged(lib, cuda, p_small):
     h = lib.rift_ile_create(p_small)
-    res = _marg_gpu(lib, h, seed=22, n_per_round=30000, max_evals=100000)
-    ref = mc.marginalize(p_small, 22, 0, mc.Prior(p_small["t_lo"], p_small["t_hi"]), 30000, 100000, 1e300)
+    S = (8, 4, 4)
+    res = _marg_gpu(lib, h, seed=22, n_per_round=30000, max_evals=100000, strata=S)
+    ref = mc.marginalize(p_small, 22, 0, mc.Prior(p_small["t_lo"], p_small["t_hi"]), 30000, 100000, 1e300,
+                         strata=S)
     assert res["rounds"] == 4 and res["n_evals"] == 100000 and ref["n_evals"] == 100000
     assert abs(res["lnL_marg"] - ref["lnL_marg"]) < TOL_MARG
 
@@ -227,10 +247,11 @@ def test_adaptive_fixed_tables_parity(lib, cuda, p_small):
     nb = 64
     tab = _peaked_tables(p_small, nb)
     h = lib.rift_ile_create(p_small)
+    S = (4, 4, 4)
     res = _marg_gpu(lib, h, seed=25, n_per_round=50000, max_evals=100000, proposal="adaptive", n_bins=nb,
-                    tables=tab, adapt_rounds=0)
+                    tables=tab, adapt_rounds=0, strata=S)
     ref = mc.marginalize(p_small, 25, 0, mc.Prior(p_small["t_lo"], p_small["t_hi"]), 50000, 100000, 1e300,
-                         adaptive=True, n_bins=nb, tables=tab, adapt_rounds=0)
+                         adaptive=True, n_bins=nb, tables=tab, adapt_rounds=0, strata=S)
     assert abs(res["lnL_marg"] - ref["lnL_marg"]) < TOL_MARG, (res, ref["lnL_marg"])
     assert abs(res["n_eff"] - ref["n_eff"]) <= 2e-3 * ref["n_eff"]
 
@@ -243,9 +264,11 @@ def test_adaptive_table_rebuild_parity(lib, cuda, p_small):
     n = 60000
     h = lib.rift_ile_create(p_small)
     dbg_t = torch.zeros((2, 3, nb + 1), dtype=torch.float32, device="cuda")
-    _marg_gpu(lib, h, seed=26, n_per_round=n, max_evals=2 * n, proposal="adaptive", n_bins=nb, dbg_tables=dbg_t)
+    S = (2, 2, 4)
+    _marg_gpu(lib, h, seed=26, n_per_round=n, max_evals=2 * n, proposal="adaptive", n_bins=nb, dbg_tables=dbg_t,
+              strata=S)
     pr = mc.Prior(p_small["t_lo"], p_small["t_hi"])
-    ref = mc.marginalize(p_small, 26, 0, pr, n, 2 * n, 1e300, adaptive=True, n_bins=nb, keep=True)
+    ref = mc.marginalize(p_small, 26, 0, pr, n, 2 * n, 1e300, adaptive=True, n_bins=nb, keep=True, strata=S)
     got = dbg_t.cpu().numpy()
     assert np.array_equal(got[0], mc.uniform_tables(nb))
     want = ref["history"][1]["tables"]
@@ -254,9 +277,10 @@ def test_adaptive_table_rebuild_parity(lib, cuda, p_small):
 
 @pytest.fixture(scope="module")
 def p_phys():
-    """A weak physical injection (3 detectors, l = 2 modes, SNR 5): a posterior broad enough
+    """A weak physical injection (3 detectors, l = 2 modes, SNR 4): a posterior broad enough
     for a long plain run to resolve lnL_marg well."""
-    spec = W.PointSpec(dets=("H1", "L1", "V1"), modes=list(W.L2_MODES), fs=4096.0, snr=5.0, t_half=0.02)
+    spec = W.PointSpec(dets=("H1", "L1", "V1"), modes=list(W.L2_MODES), fs=4096.0, snr=4.0, t_half=0.02,
+                       seg_len=4.0)
     tens = np.stack([W.detector(d)[0] for d in spec.dets])
     pos = np.stack([W.detector(d)[1] for d in spec.dets])
     coef, tk = L.injection((tens, pos), spec.modes, ra=2.0, dec=0.5, t=0.003, psi=0.3, phi=1.0, incl=0.6,
@@ -270,7 +294,7 @@ def test_adaptive_statistical_agreement(lib, cuda, p_phys):
     plain = _marg_gpu(lib, h, seed=28, n_per_round=100_000_000, max_evals=2_000_000_000)
     ad = _marg_gpu(lib, h, seed=27, n_per_round=100000, max_evals=100_000_000, n_eff_target=1000.0,
                    proposal="adaptive", n_bins=50)
-    assert plain["n_eff"] > 1000, plain
+    assert plain["sigma"] < 0.01, plain
     s = math.hypot(ad["sigma"], plain["sigma"])
     assert abs(ad["lnL_marg"] - plain["lnL_marg"]) < 5 * s + 0.02, (ad, plain)
     assert ad["n_evals"] < plain["n_evals"]
@@ -286,12 +310,14 @@ def test_marginalize_full_size_sampled(lib, cuda, p_full):
     res = _marg_gpu(lib, h, seed=31, n_per_round=n, max_evals=n, dbg_ell=dbg)
     got = dbg.cpu().numpy().astype(np.float64)
     own = mc.Accum.of(got).result()
-    assert abs(own[0] - res["lnL_marg"]) < 1e-8
+    assert abs(own[0] - res["lnL_marg"]) < 1e-6
     r = np.random.default_rng(0)
     idx = np.unique(np.concatenate([np.argsort(got)[-300:], r.integers(0, n, 2000), [0, n - 1]])).astype(np.uint64)
     pr = mc.Prior(p_full["t_lo"], p_full["t_hi"])
-    th, _, _ = mc.draw(31, 0, 0, idx, pr)
-    want = mc.lnL_samples(p_full, th)
+    S = tuple(res["strata"])
+    assert np.prod(S) > 1                # the benchmark configuration is stratified
+    th, _, lq = mc.draw(31, 0, 0, idx, pr, None, S, n)
+    want = mc.lnL_samples(p_full, th) + lq
     th64 = dict(ra=th["ra"], dec=np.arcsin(th["sindec"]), t=th["t"], psi=th["psi"], phi=th["phi"],
                 incl=np.arccos(th["cosi"]), dist=th["dist"])
     err = np.abs(got[idx.astype(np.int64)] - want)

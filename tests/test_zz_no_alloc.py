@@ -51,3 +51,6 @@ def test_static_rejects_rounds_beyond_its_scratch(lib, cuda, point):
         lib.rift_ile_marginalize_static(h, seed=1, n_per_round=131073, max_evals=131073, proposal="adaptive",
                                         n_bins=32)
     assert ex.value.status == 1 and "RIFT_STATIC_MAX_ROUND" in str(ex.value)
+    with pytest.raises(lib.RiftError) as ex:
+        lib.rift_ile_marginalize_static(h, seed=1, n_per_round=67108865, max_evals=67108865)
+    assert ex.value.status == 1 and "RIFT_STATIC_MAX_PRIOR_ROUND" in str(ex.value)
