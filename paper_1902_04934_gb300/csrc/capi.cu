@@ -93,6 +93,14 @@ struct rift_ile {
   size_t stage_n = 0;
   int max_M = 0, max_pairK = 0;
   int interp = 3;
+  // batched runs (graph replays)
+  PtState *pst = nullptr;
+  RoundCtl *ctl = nullptr;
+  RoundCtl *ctl_host = nullptr;
+  PtState *pst_host = nullptr;
+  int cap_pst = 0;
+  cudaStream_t gstream = nullptr;
+  int graph_rounds = 4;   // rounds per captured graph
 };
 
 namespace {
@@ -636,6 +644,11 @@ void rift_ile_destroy(rift_ile *h) {
   cudaFreeHost(S.rp_host);
   cudaFreeHost(S.acc_host);
   cudaFree(h->stage);
+  cudaFree(h->pst);
+  cudaFree(h->ctl);
+  cudaFreeHost(h->ctl_host);
+  cudaFreeHost(h->pst_host);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
   delete h;
 }
 
@@ -754,16 +767,164 @@ rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
   const int nb = adaptive ? o->n_bins : 0;
   const int hb = std::max(1, std::min(64, (int)(o->n_per_round / 8192)));
-  // cells per point are at most max(RIFT_MAX_CELLS, n_per_round) bounded by the strata rule
+  std::vector<int> lsv(3 * np);
   size_t items = 0;
   for (int p = 0; p < np; ++p) {
-    int ls[3];
-    if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) choose_strata(h->pts[p].c, o->n_per_round, ls);
-    else for (int d = 0; d < 3; ++d) ls[d] = std::max(0, log2_pow2(o->strata[d]));
+    int *ls = &lsv[3 * p];
+    if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
+      choose_strata(h->pts[p].c, o->n_per_round, ls);
+    } else {
+      for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
+      if (ls[0] < 0 || ls[1] < 0 || ls[2] < 0) return fail(h, RIFT_EINVAL, "strata must be powers of two");
+      if ((1 << (ls[0] + ls[1] + ls[2])) > RIFT_MAX_CELLS) return fail(h, RIFT_EINVAL, "more than RIFT_MAX_CELLS cells");
+    }
     items += ((size_t)1 << (ls[0] + ls[1] + ls[2])) + o->n_per_round / RIFT_CHUNK + 1;
   }
   if ((s = ensure_scratch(h, np, items, adaptive ? (size_t)np * o->n_per_round : 0, nb, hb)) != RIFT_OK) return s;
-  return run_mc(h, o, np, h->sc, res);
+  McScratch &S = h->sc;
+  if (np > h->cap_pst) {
+    cudaFree(h->pst); cudaFreeHost(h->pst_host);
+    h->pst = nullptr; h->pst_host = nullptr; h->cap_pst = 0;
+    RIFT_CK(h, cudaMalloc(&h->pst, sizeof(PtState) * np));
+    RIFT_CK(h, cudaMallocHost(&h->pst_host, sizeof(PtState) * np));
+    h->cap_pst = np;
+  }
+  if (!h->ctl) {
+    RIFT_CK(h, cudaMalloc(&h->ctl, sizeof(RoundCtl)));
+    RIFT_CK(h, cudaMallocHost(&h->ctl_host, sizeof(RoundCtl)));
+  }
+  if (!h->gstream) RIFT_CK(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+  cudaStream_t st = h->gstream;
+  RIFT_CK(h, cudaStreamSynchronize(h->stream));   // inputs uploaded on the handle's stream
+  const int K = h->K, NT = taps_of(h->interp);
+  // initial state
+  for (int p = 0; p < np; ++p) {
+    std::memset(&S.acc_host[p], 0, sizeof(AccState));
+    S.acc_host[p].m = -INFINITY;
+    std::memset(&h->pst_host[p], 0, sizeof(PtState));
+    for (int d = 0; d < 3; ++d) h->pst_host[p].ls[d] = lsv[3 * p + d];
+    std::memset(&S.rp_host[p], 0, sizeof(RoundPt));
+  }
+  std::memset(h->ctl_host, 0, sizeof(RoundCtl));
+  h->ctl_host->round = -1;
+  RIFT_CK(h, cudaMemcpyAsync(S.acc, S.acc_host, sizeof(AccState) * np, cudaMemcpyHostToDevice, st));
+  RIFT_CK(h, cudaMemcpyAsync(h->pst, h->pst_host, sizeof(PtState) * np, cudaMemcpyHostToDevice, st));
+  RIFT_CK(h, cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(RoundCtl), cudaMemcpyHostToDevice, st));
+  const size_t tstride = (size_t)3 * (nb + 1);
+  BatchCtl B{};
+  B.npr = o->n_per_round;
+  B.np = np;
+  B.max_evals = o->max_evals;
+  B.n_eff_target = o->n_eff_target;
+  B.max_rounds = o->max_rounds;
+  B.adaptive = adaptive ? 1 : 0;
+  B.adapt_rounds = o->adapt_rounds;
+  B.nb = nb;
+  B.tables = S.tables;
+  B.lnw = S.lnw;
+  if (adaptive) {
+    float u[3 * (RIFT_MAXBINS + 1)];
+    const float *src = o->tables;
+    if (!src) {
+      for (int d = 0; d < 3; ++d)
+        for (int b = 0; b <= nb; ++b) u[d * (nb + 1) + b] = (float)((double)b / nb);
+      src = u;
+    }
+    for (int p = 0; p < np; ++p)
+      RIFT_CK(h, cudaMemcpyAsync(S.tables + p * tstride, src, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
+    RIFT_CK(h, cudaStreamSynchronize(st));
+    for (int p = 0; p < np; ++p) { S.rp_host[p].proposal = 1; S.rp_host[p].ncell = 1; }
+    RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
+    RIFT_CK(h, launch_tables_points(nullptr, 0, S.rp, np, nb, 0.0, S.tables, S.lnw, st));
+    for (int p = 0; p < np; ++p) { S.rp_host[p].proposal = 0; S.rp_host[p].ncell = 0; }
+  }
+  RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
+  // launch shape of the persistent cell kernel
+  const int block = RIFT_CELL_BLOCK;
+  int smem_sm = 0;
+  RIFT_CK(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+  const size_t fixed = cells_smem_fixed(K, h->max_M, h->max_pairK, nb, block);
+  long long budget = ((long long)smem_sm / 2 - (long long)fixed - 2048) & ~15ll;
+  budget = std::max(16ll * 1024, std::min(96ll * 1024, budget));
+  const size_t smem = fixed + (size_t)budget;
+  const int bps = cells_blocks_per_sm(K, NT, smem, block);
+  if (bps < 1) return fail(h, RIFT_EUNSUPPORTED, "cell kernel does not fit on an SM");
+  CellLaunch L{};
+  L.seed = o->seed;
+  L.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
+  L.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
+  L.pts = h->pts_dev;
+  L.rp = S.rp;
+  L.n_points = np;
+  L.win_budget = (int)budget;
+  L.n_items = &h->ctl->n_items;
+  L.queue = &h->ctl->queue;
+  L.qa = h->q_arena;
+  L.ca = h->c_arena;
+  L.partials = S.partials;
+  L.ell_buf = adaptive ? S.ell : nullptr;
+  L.bin_buf = adaptive ? S.bins : nullptr;
+  L.flags = h->flags;
+  L.max_M = h->max_M;
+  L.max_pairK = h->max_pairK;
+  L.max_nb = nb;
+  const int grid = h->num_sms * bps;
+  // capture G rounds: update -> cells -> merge -> (adaptive) hist -> tables
+  const int G = std::max(1, h->graph_rounds);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  RIFT_CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t ce = cudaSuccess;
+  for (int g = 0; g < G && ce == cudaSuccess; ++g) {
+    if ((ce = launch_round_update(B, h->pst, S.acc, S.rp, h->ctl, st)) != cudaSuccess) break;
+    if ((ce = launch_cells(K, NT, L, grid, block, smem, st)) != cudaSuccess) break;
+    if ((ce = launch_merge_points(S.partials, S.rp, np, S.acc, st)) != cudaSuccess) break;
+    if (adaptive) {
+      if ((ce = launch_hist_ctl(S.ell, S.bins, S.rp, np, S.acc, (float)o->beta, nb, S.hist, S.hblocks, h->ctl, st)) !=
+          cudaSuccess)
+        break;
+      if ((ce = launch_tables_ctl(S.hist, S.hblocks, S.rp, np, nb, o->floor_eps, B, h->ctl, st)) != cudaSuccess) break;
+    }
+  }
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (ce != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(h, ce, "graph capture"); }
+  if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
+  ee = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaGraphInstantiate");
+  // replay until a round update finds no active point (all results accounted)
+  uint64_t max_np_evals = o->max_evals;
+  const uint64_t rounds_cap = (max_np_evals + o->n_per_round - 1) / o->n_per_round + 2;
+  const uint64_t replay_cap = (o->max_rounds > 0 ? std::min<uint64_t>(rounds_cap, o->max_rounds + 2) : rounds_cap) / G + 2;
+  int replays = 0;
+  rift_status status = RIFT_OK;
+  for (;;) {
+    cudaError_t e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(RoundCtl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { status = cuda_fail(h, e, "graph replay"); break; }
+    ++replays;
+    if (h->ctl_host->active == 0) break;
+    if ((uint64_t)replays > replay_cap) { status = fail(h, RIFT_ETIMEOUT, "batched run did not terminate"); break; }
+  }
+  cudaGraphExecDestroy(exec);
+  if (status != RIFT_OK) return status;
+  RIFT_CK(h, cudaMemcpyAsync(S.acc_host, S.acc, sizeof(AccState) * np, cudaMemcpyDeviceToHost, st));
+  RIFT_CK(h, cudaMemcpyAsync(h->pst_host, h->pst, sizeof(PtState) * np, cudaMemcpyDeviceToHost, st));
+  RIFT_CK(h, cudaStreamSynchronize(st));
+  rift_status fl = read_flags(h);
+  rift_status overall = fl;
+  for (int p = 0; p < np; ++p) {
+    fill_result(S.acc_host[p], &res[p]);
+    res[p].rounds = h->pst_host[p].rounds;
+    res[p].kernel_launches = (p == 0) ? replays * G * (adaptive ? 5 : 3) : 0;
+    for (int d = 0; d < 3; ++d) res[p].strata[d] = 1 << lsv[3 * p + d];
+    rift_status sp = fl;
+    if (sp == RIFT_OK && res[p].n_eff < o->n_eff_target) sp = RIFT_ENOTCONVERGED;
+    res[p].status = sp;
+    if (overall == RIFT_OK && sp != RIFT_OK) overall = sp;
+  }
+  return overall;
 }
 
 }  // extern "C"

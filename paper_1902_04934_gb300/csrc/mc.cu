@@ -541,8 +541,9 @@ __global__ void merge_points_kernel(const Part *__restrict__ part, const RoundPt
 // Adaptive histograms of every point (grid: hblocks x points), 32.32 fixed point.
 __global__ void hist_points_kernel(const float *__restrict__ ell, const uint32_t *__restrict__ bins,
                                    const RoundPt *__restrict__ rp, const AccState *__restrict__ acc, float beta, int nb,
-                                   unsigned long long *__restrict__ part) {
+                                   unsigned long long *__restrict__ part, const RoundCtl *ctl) {
   extern __shared__ unsigned long long h[];
+  if (ctl && !ctl->adapt_now) return;
   const int p = blockIdx.y;
   const RoundPt &R = rp[p];
   for (int j = threadIdx.x; j < 3 * nb; j += blockDim.x) h[j] = 0ull;
@@ -569,9 +570,17 @@ __global__ void hist_points_kernel(const float *__restrict__ ell, const uint32_t
 // cdf = cumsum in FP64 rounded to float32 (cdf[0] = 0, cdf[nb] = 1), lnw_b = -ln(nb (cdf[b+1] - cdf[b])).
 // With part == nullptr only lnw is recomputed from the current tables.
 __global__ void tables_points_kernel(const unsigned long long *__restrict__ part, int hblocks,
-                                     const RoundPt *__restrict__ rp, int nb, double eps, float *tables, float *lnw) {
+                                     const RoundPt *__restrict__ rp, int nb, double eps, float *tables, float *lnw,
+                                     const RoundCtl *ctl, int np) {
   __shared__ double hs[3 * RIFT_MAXBINS];
   const int p = blockIdx.x;
+  if (ctl) {
+    // batched run: write the buffer the next round reads
+    if (!ctl->adapt_now) return;
+    const int nbuf = ctl->tabbuf ^ 1;
+    tables += (size_t)nbuf * np * 3 * (nb + 1);
+    lnw += (size_t)nbuf * np * 3 * nb;
+  }
   if (part && (rp[p].ncell == 0 || !rp[p].proposal)) return;
   float *tb = tables + (size_t)p * 3 * (nb + 1);
   float *lw = lnw + (size_t)p * 3 * nb;
@@ -634,6 +643,93 @@ __global__ void draw_cells_kernel(CellLaunch L, DrawOut o, uint32_t n) {
     o.bins[0 * (size_t)n + i] = (int)(d.bins & 255u);
     o.bins[1 * (size_t)n + i] = (int)((d.bins >> 8) & 255u);
     o.bins[2 * (size_t)n + i] = (int)((d.bins >> 16) & 255u);
+  }
+}
+
+// Device-side round update of a batched run (one CTA): accounts the round that just ran
+// (evaluations, rounds, the n_eff / max_evals / max_rounds stopping rule of Sec. II.C per
+// point), prepares the next round of every active point (cells, chunks, stratified weights,
+// table buffer) and lays the points' work items out contiguously (block prefix sum).
+__global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState *__restrict__ S,
+                                                            const AccState *__restrict__ acc,
+                                                            RoundPt *__restrict__ rp, RoundCtl *ctl) {
+  __shared__ uint32_t sc[1024];
+  __shared__ uint32_t sa[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int prev_adapt = ctl->adapt_now;
+  const int r = ctl->round + 1;
+  const int tabbuf = ctl->tabbuf ^ (prev_adapt ? 1 : 0);
+  const int adapt_now = B.adaptive && (B.adapt_rounds < 0 || r < B.adapt_rounds);
+  const int per = (B.np + nt - 1) / nt;
+  const int p0 = min(B.np, tid * per), p1 = min(B.np, p0 + per);
+  const size_t tstride = (size_t)3 * (B.nb + 1), wstride = (size_t)3 * B.nb;
+  uint32_t items = 0, active = 0;
+  for (int p = p0; p < p1; ++p) {
+    RoundPt &R = rp[p];
+    PtState &st = S[p];
+    if (R.n > 0) {
+      st.evals += R.n;
+      st.rounds += 1;
+      const double n_eff = acc[p].s1 + acc[p].c1;
+      if (n_eff >= B.n_eff_target || st.evals >= B.max_evals || (B.max_rounds > 0 && st.rounds >= B.max_rounds))
+        st.done = 1;
+    }
+    RoundPt N;
+    memset(&N, 0, sizeof(N));
+    N.ell_off = -1;
+    N.dbg_off = -1;
+    if (!st.done) {
+      const uint32_t n = (uint32_t)min((unsigned long long)B.npr, B.max_evals - st.evals);
+      int l0 = st.ls[0], l1 = st.ls[1], l2 = st.ls[2];
+      if ((unsigned long long)n < (1ull << (l0 + l1 + l2))) l0 = l1 = l2 = 0;
+      const uint32_t C = 1u << (l0 + l1 + l2);
+      N.n = n;
+      N.ncell = C;
+      N.base = n / C;
+      N.rem = n % C;
+      N.chunks = (N.base + (N.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
+      N.nitem = C * N.chunks;
+      N.round = (uint32_t)st.rounds;
+      N.point_id = (uint32_t)p;
+      N.ls0 = l0; N.ls1 = l1; N.ls2 = l2;
+      N.proposal = B.adaptive ? 1 : 0;
+      N.nb = B.nb;
+      N.lcorr0 = (float)log((double)n / ((double)C * (N.base + 1.0)));
+      N.lcorr1 = N.base ? (float)log((double)n / ((double)C * N.base)) : 0.f;
+      N.ell_off = B.adaptive ? (long long)p * B.npr : -1;
+      if (B.adaptive) {
+        N.tab = B.tables + ((size_t)tabbuf * B.np + p) * tstride;
+        N.lnw = B.lnw + ((size_t)tabbuf * B.np + p) * wstride;
+      }
+      items += N.nitem;
+      active += 1;
+    }
+    R = N;
+  }
+  sc[tid] = items;
+  sa[tid] = active;
+  __syncthreads();
+  // inclusive scan of the per-thread item counts, total of the active counts
+  for (int o = 1; o < nt; o <<= 1) {
+    const uint32_t a = (tid >= o) ? sc[tid - o] : 0u;
+    const uint32_t b = (tid >= o) ? sa[tid - o] : 0u;
+    __syncthreads();
+    sc[tid] += a;
+    sa[tid] += b;
+    __syncthreads();
+  }
+  uint32_t base = sc[tid] - items;
+  for (int p = p0; p < p1; ++p) {
+    rp[p].item0 = base;
+    base += rp[p].nitem;
+  }
+  if (tid == nt - 1) {
+    ctl->n_items = sc[tid];
+    ctl->queue = 0u;
+    ctl->active = sa[tid];
+    ctl->round = r;
+    ctl->adapt_now = adapt_now;
+    ctl->tabbuf = tabbuf;
   }
 }
 
@@ -701,13 +797,34 @@ cudaError_t launch_hist_points(const float *ell, const uint32_t *bins, const Rou
                                const AccState *acc, float beta, int nb, unsigned long long *part, int hblocks,
                                cudaStream_t st) {
   dim3 g(hblocks, n_points);
-  hist_points_kernel<<<g, 256, sizeof(unsigned long long) * 3 * nb, st>>>(ell, bins, rp, acc, beta, nb, part);
+  hist_points_kernel<<<g, 256, sizeof(unsigned long long) * 3 * nb, st>>>(ell, bins, rp, acc, beta, nb, part,
+                                                                           nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tables_points(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points,
                                  int nb, double floor_eps, float *tables, float *lnw, cudaStream_t st) {
-  tables_points_kernel<<<n_points, 256, 0, st>>>(part, hblocks, rp, nb, floor_eps, tables, lnw);
+  tables_points_kernel<<<n_points, 256, 0, st>>>(part, hblocks, rp, nb, floor_eps, tables, lnw, nullptr, n_points);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round_update(const BatchCtl &B, PtState *st_dev, const AccState *acc, RoundPt *rp, RoundCtl *ctl,
+                                cudaStream_t st) {
+  round_update_kernel<<<1, 1024, 0, st>>>(B, st_dev, acc, rp, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist_ctl(const float *ell, const uint32_t *bins, const RoundPt *rp, int n_points,
+                            const AccState *acc, float beta, int nb, unsigned long long *part, int hblocks,
+                            const RoundCtl *ctl, cudaStream_t st) {
+  dim3 g(hblocks, n_points);
+  hist_points_kernel<<<g, 256, sizeof(unsigned long long) * 3 * nb, st>>>(ell, bins, rp, acc, beta, nb, part, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tables_ctl(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points, int nb,
+                              double floor_eps, const BatchCtl &B, const RoundCtl *ctl, cudaStream_t st) {
+  tables_points_kernel<<<n_points, 256, 0, st>>>(part, hblocks, rp, nb, floor_eps, B.tables, B.lnw, ctl, n_points);
   return cudaGetLastError();
 }
 

@@ -69,6 +69,40 @@ struct CellLaunch {
   int max_nb;                  // largest bin count (0 if no point uses tables)
 };
 
+// Device-side round control of a batched run replayed as a CUDA graph.
+struct RoundCtl {
+  uint32_t n_items;       // work items of the prepared round
+  uint32_t queue;         // work-queue counter of the cell kernel
+  uint32_t active;        // points in the prepared round
+  int round;              // number of the prepared round
+  int adapt_now;          // the prepared round rebuilds tables afterwards
+  int tabbuf;             // table buffer read by the prepared round
+  int pad0, pad1;
+};
+
+// Per-point progress of a batched run (device).
+struct PtState {
+  unsigned long long evals;
+  int rounds;
+  int done;
+  int ls[3];
+  int pad;
+};
+
+// Options of a batched run, as the device round-update kernel sees them.
+struct BatchCtl {
+  uint32_t npr;             // samples per round
+  int np;                   // points
+  unsigned long long max_evals;
+  double n_eff_target;
+  int max_rounds;           // 0: none
+  int adaptive;
+  int adapt_rounds;         // < 0: always
+  int nb;
+  float *tables;            // [2][np][3][nb+1]
+  float *lnw;               // [2][np][3][nb]
+};
+
 // Scratch of the Monte Carlo runner (device pointers unless noted).
 struct McScratch {
   AccState *acc;               // [np]
@@ -111,5 +145,12 @@ cudaError_t launch_hist_points(const float *ell, const uint32_t *bins, const Rou
 cudaError_t launch_tables_points(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points,
                                  int nb, double floor_eps, float *tables, float *lnw, cudaStream_t st);
 cudaError_t launch_draw_cells(const CellLaunch &L, DrawOut o, uint32_t n, cudaStream_t st);
+cudaError_t launch_round_update(const BatchCtl &B, PtState *st_dev, const AccState *acc, RoundPt *rp, RoundCtl *ctl,
+                                cudaStream_t st);
+cudaError_t launch_hist_ctl(const float *ell, const uint32_t *bins, const RoundPt *rp, int n_points,
+                            const AccState *acc, float beta, int nb, unsigned long long *part, int hblocks,
+                            const RoundCtl *ctl, cudaStream_t st);
+cudaError_t launch_tables_ctl(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points, int nb,
+                              double floor_eps, const BatchCtl &B, const RoundCtl *ctl, cudaStream_t st);
 
 #define RIFT_FLAG_TIMEOUT_BIT 4u
