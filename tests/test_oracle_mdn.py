@@ -1,0 +1,116 @@
+"""Pins of the learned-proposal oracle (oracle/mdn.py): gradients against central finite
+differences, normalisation of the proposal density on its box, agreement of the sampler with
+the density, the defensive bound, Adam's first step, bfloat16 rounding, GELU values."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import workload as W
+from oracle import mc
+from oracle import mdn
+from oracle import philox as P
+
+
+def _weights(seed, scale=0.3):
+    r = np.random.default_rng(seed)
+    return {k: r.normal(0.0, scale / math.sqrt(max(1, s[-1])), s) for k, s in mdn.SHAPES.items()}
+
+
+def _samples(seed, H, a, b):
+    r = np.random.default_rng(seed)
+    x = r.uniform(0.02, 0.98, (H, 5))
+    return a + (b - a) * x, r.uniform(0.1, 1.0, H)
+
+
+def test_gelu_and_bf16_reference_values():
+    assert mdn.gelu(np.array([0.0]))[0] == 0.0
+    assert abs(mdn.gelu(np.array([1.0]))[0] - 0.8413447460685429) < 1e-15      # x Phi(x) at 1
+    assert abs(mdn.gelu(np.array([-2.0]))[0] - (-2.0 * 0.022750131948179195)) < 1e-15
+    v = mdn.bf16_round(np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, -3.140625, 1e-30]))
+    assert v[0] == 1.0 and v[1] == 1.0 and v[2] == 1.0 + 2.0 ** -7 and v[3] == -3.140625
+    x = np.random.default_rng(0).normal(size=1000).astype(np.float32)
+    y = mdn.bf16_round(x)
+    assert np.all(np.abs(y - x) <= np.abs(x) * 2.0 ** -8)
+
+
+def test_head_gradient_matches_finite_differences():
+    a, b = mdn.bounds(-0.05, 0.05, 1.0, 1000.0)
+    th5, w = _samples(1, 40, a, b)
+    head = np.random.default_rng(2).normal(0, 0.5, mdn.N_OUT)
+    head[mdn.N_COMP + mdn.N_COMP * mdn.N_DIM:] = np.random.default_rng(3).uniform(-1.5, 0.5, 40)
+    _, g = mdn.nll_head_grad(head, th5, w, a, b)
+    for i in range(mdn.N_OUT):
+        e = np.zeros(mdn.N_OUT)
+        e[i] = 1e-6
+        fd = (mdn.nll_head_grad(head + e, th5, w, a, b)[0] - mdn.nll_head_grad(head - e, th5, w, a, b)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(fd)), i
+
+
+def test_weight_gradient_matches_finite_differences():
+    Wt = _weights(4)
+    a, b = mdn.bounds(-0.05, 0.05, 1.0, 1000.0)
+    S = np.random.default_rng(5).normal(0, 1, (3, mdn.N_IN))
+    samples = [_samples(10 + i, 20, a, b) for i in range(3)]
+    loss, g = mdn.loss_and_grad(Wt, S, samples, [a] * 3, [b] * 3)
+    flat = mdn.flatten(Wt)
+    gf = mdn.flatten(g)
+    r = np.random.default_rng(6)
+    for i in r.choice(flat.size, 40, replace=False):
+        e = np.zeros_like(flat)
+        e[i] = 1e-6
+        lp = mdn.loss_and_grad(mdn.unflatten(flat + e), S, samples, [a] * 3, [b] * 3)[0]
+        lm = mdn.loss_and_grad(mdn.unflatten(flat - e), S, samples, [a] * 3, [b] * 3)[0]
+        fd = (lp - lm) / 2e-6
+        assert abs(fd - gf[i]) <= 2e-5 * max(1.0, abs(fd)), i
+
+
+def test_proposal_density_is_normalised_on_its_box():
+    """E_prior[q_MDN / p5] = 1 for any head."""
+    pr = mc.Prior(-0.05, 0.05, 1.0, 1000.0)
+    a, b = mdn.bounds(pr.t_lo, pr.t_hi, pr.d_lo, pr.d_hi)
+    head = np.random.default_rng(7).normal(0, 0.6, mdn.N_OUT)[None]
+    u = P.uniforms(8, 0, 0, np.arange(400000, dtype=np.uint64), 8)
+    th = mc.prior_transform(u, pr)
+    th5 = np.stack([th["ra"], th["sindec"], th["t"], th["cosi"], np.log(th["dist"])], axis=-1)
+    lp = mdn.ln_prior5(th5, pr.d_lo, pr.d_hi, pr.t_lo, pr.t_hi)
+    ratio = np.exp(mdn.ln_q_mdn(th5, head, a, b) - lp)
+    assert abs(ratio.mean() - 1.0) < 5 * ratio.std() / math.sqrt(ratio.size) + 1e-3
+
+
+def test_sampler_agrees_with_density_and_defensive_bound():
+    """E_q[p5 / q] = 1 over the sampler's own draws (density and sampler agree), and p5/q <= 10."""
+    pr = mc.Prior(-0.05, 0.05, 1.0, 1000.0)
+    head = np.random.default_rng(9).normal(0, 0.6, mdn.N_OUT)[None]
+    u = P.uniforms(10, 0, 0, np.arange(300000, dtype=np.uint64), 10)
+    th, lpq = mdn.sample(u, head, pr)
+    r = np.exp(lpq)
+    assert abs(r.mean() - 1.0) < 5 * r.std() / math.sqrt(r.size) + 1e-3
+    assert np.max(lpq) <= math.log(1.0 / mdn.DEFENSIVE) + 1e-12
+    assert th["t"].min() > pr.t_lo and th["t"].max() < pr.t_hi
+
+
+def test_adam_first_step():
+    th = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 0.0])
+    new, m, v = mdn.adam(th, g, np.zeros(3), np.zeros(3), 1, 0.01)
+    assert np.allclose(new, th - 0.01 * g / (np.abs(g) + 1e-8))
+
+
+def test_summary_features_shape_and_physics():
+    pt = W.make_point(W.cfg_small(), 5)
+    s = mdn.summary(pt)
+    assert s.shape == (64,) and np.all(np.isfinite(s))
+    # the (2,2) mean time of each detector lies inside its Q window
+    T = pt["Q"].shape[2]
+    for k in range(2):
+        tau0 = pt["q_t0_gps"][k] - pt["t_ref_gps"]
+        assert tau0 <= s[10 * k] <= tau0 + (T - 1) / pt["fs"]
+    # a pure time shift of the data by an integer number of samples shifts the mean times
+    pt2 = dict(pt)
+    pt2["q_t0_gps"] = pt["q_t0_gps"] + 3.0 / pt["fs"]
+    s2 = mdn.summary(pt2)
+    assert abs((s2[0] - s[0]) - 3.0 / pt["fs"]) < 1e-12
+    assert np.allclose(s2[1:5], s[1:5])
