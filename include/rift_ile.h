@@ -188,6 +188,53 @@ rift_status rift_ile_marginalize(rift_ile *h, const rift_mc_opts *opts, rift_mc_
 rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
 
 /*
+ * Learned proposal (a mixture-density network over ra, sin dec, t, cos incl, ln D, conditioned
+ * on a 64-feature summary of each point's Q time series; defensive mixture with the prior).
+ * With opts.proposal = RIFT_PROPOSAL_LEARNED, rift_ile_marginalize and
+ * rift_ile_batch_marginalize sample every point from its learned proposal: from opts.mdn (the
+ * network is evaluated on the device on each point's summary) or, when opts.mdn is NULL, from
+ * the network heads last given by rift_ile_set_proposal_head.  Learned rounds are not stratified.
+ */
+typedef struct rift_mdn rift_mdn;
+#define RIFT_MDN_PARAMS 105048   /* W1[256][64] b1[256] W2[256][256] b2[256] W3[88][256] b3[88] */
+#define RIFT_MDN_SUMMARY 64
+#define RIFT_MDN_HEAD 88         /* 8 logits, 8x5 means, 8x5 log sigmas (clamped to [-8, 4])     */
+
+/* New network: weights uniform(-1,1) sqrt(3/fan_in) from Philox4x32-10 (key = seed), zero biases. */
+rift_status rift_mdn_create(uint64_t seed, rift_mdn **out);
+void rift_mdn_destroy(rift_mdn *m);
+const char *rift_mdn_last_error(const rift_mdn *m);
+/* Parameters in the layout above: host float32 [RIFT_MDN_PARAMS]; set resets Adam's state.
+ * get: which = 0 the float32 master copy, 1 the bfloat16 weights the kernels use. */
+rift_status rift_mdn_set_params(rift_mdn *m, const float *host);
+rift_status rift_mdn_get_params(rift_mdn *m, float *host, int which);
+/* head_dev[n][88] = network(summ_dev[n][64]) (device pointers). */
+rift_status rift_mdn_forward(rift_mdn *m, int n, const float *summ_dev, float *head_dev);
+/* Mean over the n points of the weighted negative log likelihood
+ *   -sum_j w[p][j] ln q_MDN(theta[p][j] | summ[p]),
+ * theta_dev [n][H][5] = (ra, sin dec, t, cos incl, ln D), w_dev [n][H], box_dev [n][2][5] the
+ * lower and upper bounds of the five coordinates; *loss_out and the weight gradient (host
+ * [RIFT_MDN_PARAMS], may be NULL). */
+rift_status rift_mdn_loss_grad(rift_mdn *m, int n, const float *summ_dev, const float *theta_dev, const float *w_dev,
+                               int H, const float *box_dev, double *loss_out, float *grad_host);
+/* `steps` Adam steps (lr; beta1 0.9, beta2 0.999, eps 1e-8) of the same loss on minibatches of
+ * `batch` consecutive points (cycling); loss_per_step: host [steps] or NULL. */
+rift_status rift_mdn_train(rift_mdn *m, int n, const float *summ_dev, const float *theta_dev, const float *w_dev,
+                           int H, const float *box_dev, int steps, int batch, double lr, double *loss_per_step);
+/* Summary features of every point of the handle: out_dev [n_points][64] (device). */
+rift_status rift_ile_batch_summary(rift_ile *h, float *out_dev);
+/* Learned proposal of every point from given network heads (host [n_points][88]). */
+rift_status rift_ile_set_proposal_head(rift_ile *h, const float *head_host);
+/* Boxes of the five learned coordinates of every point for distance prior [d_lo, d_hi]:
+ * host out [n_points][2][5]. */
+rift_status rift_ile_boxes(rift_ile *h, double d_lo, double d_hi, float *out_host);
+/* Training samples: runs rift_ile_batch_marginalize with opts, then draws H samples of each
+ * point's last round by systematic resampling with probabilities ~ exp(beta (l - max l)),
+ * writing theta_dev [n_points][H][5] (ra, sin dec, t, cos incl, ln D); res as the batch call. */
+rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *opts, int H, double beta, float *theta_dev,
+                                   rift_mc_result *res);
+
+/*
  * rift_ile_marginalize_static -- the same computation as rift_ile_marginalize (point 0,
  * prior or adaptive proposal; same kernels, same results) for callers that cannot
  * allocate device memory when they marginalise: programs that give (nearly) all device

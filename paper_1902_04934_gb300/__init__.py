@@ -86,6 +86,18 @@ def _load():
         "rift_ile_batch_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
         "rift_ile_marginalize_static": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
         "rift_ile_draw": (I, [P, C.POINTER(McOpts), U32, P, S, P, P, P]),
+        "rift_mdn_create": (I, [U64, C.POINTER(P)]),
+        "rift_mdn_destroy": (None, [P]),
+        "rift_mdn_last_error": (C.c_char_p, [P]),
+        "rift_mdn_set_params": (I, [P, P]),
+        "rift_mdn_get_params": (I, [P, P, I]),
+        "rift_mdn_forward": (I, [P, I, P, P]),
+        "rift_mdn_loss_grad": (I, [P, I, P, P, P, I, P, C.POINTER(D), P]),
+        "rift_mdn_train": (I, [P, I, P, P, P, I, P, I, I, D, P]),
+        "rift_ile_batch_summary": (I, [P, P]),
+        "rift_ile_set_proposal_head": (I, [P, P]),
+        "rift_ile_boxes": (I, [P, D, D, P]),
+        "rift_ile_batch_harvest": (I, [P, C.POINTER(McOpts), I, D, P, C.POINTER(McResult)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -276,6 +288,113 @@ def rift_ile_batch_marginalize(h, **kw):
     if st not in (0, 7):
         _check(h, st)
     return [r.as_dict() for r in res]
+
+
+MDN_PARAMS = 105048
+MDN_SUMMARY = 64
+MDN_HEAD = 88
+
+
+class Mdn:
+    """Owns a rift_mdn*."""
+
+    def __init__(self, ptr):
+        self.ptr = C.c_void_p(ptr)
+
+    def __del__(self):
+        try:
+            rift_mdn_destroy(self)
+        except Exception:
+            pass
+
+
+def _mcheck(m, status):
+    if status != 0:
+        raise RiftError(status, (_lib.rift_mdn_last_error(m.ptr) or b"").decode())
+
+
+def rift_mdn_create(seed=0):
+    out = C.c_void_p()
+    st = _lib.rift_mdn_create(int(seed), C.byref(out))
+    if st != 0:
+        raise RiftError(st, "rift_mdn_create failed")
+    return Mdn(out.value)
+
+
+def rift_mdn_destroy(m):
+    if m is not None and m.ptr:
+        _lib.rift_mdn_destroy(m.ptr)
+        m.ptr = C.c_void_p(None)
+
+
+def rift_mdn_set_params(m, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    assert a.size == MDN_PARAMS
+    _mcheck(m, _lib.rift_mdn_set_params(m.ptr, a.ctypes.data))
+
+
+def rift_mdn_get_params(m, which=0):
+    a = np.empty(MDN_PARAMS, dtype=np.float32)
+    _mcheck(m, _lib.rift_mdn_get_params(m.ptr, a.ctypes.data, int(which)))
+    return a
+
+
+def rift_mdn_forward(m, summ):
+    """summ: CUDA float32 tensor (n, 64) -> head (n, 88)."""
+    import torch
+    n = summ.shape[0]
+    out = torch.empty((n, MDN_HEAD), dtype=torch.float32, device=summ.device)
+    _mcheck(m, _lib.rift_mdn_forward(m.ptr, n, summ.data_ptr(), out.data_ptr()))
+    return out
+
+
+def rift_mdn_loss_grad(m, summ, theta, w, box):
+    """Device tensors summ (n,64), theta (n,H,5), w (n,H), box (n,2,5) -> (loss, grad numpy)."""
+    n, H = theta.shape[0], theta.shape[1]
+    loss = C.c_double()
+    g = np.empty(MDN_PARAMS, dtype=np.float32)
+    _mcheck(m, _lib.rift_mdn_loss_grad(m.ptr, n, summ.data_ptr(), theta.data_ptr(), w.data_ptr(), H,
+                                       box.data_ptr(), C.byref(loss), g.ctypes.data))
+    return loss.value, g
+
+
+def rift_mdn_train(m, summ, theta, w, box, steps, batch, lr):
+    n, H = theta.shape[0], theta.shape[1]
+    losses = np.empty(max(1, steps), dtype=np.float64)
+    _mcheck(m, _lib.rift_mdn_train(m.ptr, n, summ.data_ptr(), theta.data_ptr(), w.data_ptr(), H, box.data_ptr(),
+                                   int(steps), int(batch), float(lr), losses.ctypes.data))
+    return losses[:steps]
+
+
+def rift_ile_batch_summary(h):
+    import torch
+    out = torch.empty((h.n_points, MDN_SUMMARY), dtype=torch.float32, device="cuda")
+    _check(h, _lib.rift_ile_batch_summary(h.ptr, out.data_ptr()))
+    return out
+
+
+def rift_ile_set_proposal_head(h, head):
+    a = np.ascontiguousarray(head, dtype=np.float32).reshape(h.n_points, MDN_HEAD)
+    _check(h, _lib.rift_ile_set_proposal_head(h.ptr, a.ctypes.data))
+
+
+def rift_ile_boxes(h, d_lo=1.0, d_hi=1000.0):
+    out = np.empty((h.n_points, 2, 5), dtype=np.float32)
+    _check(h, _lib.rift_ile_boxes(h.ptr, float(d_lo), float(d_hi), out.ctypes.data))
+    return out
+
+
+def rift_ile_batch_harvest(h, H, beta=0.5, **kw):
+    """Run the batch and resample H samples per point from its last round -> (theta (np,H,5) CUDA, results)."""
+    import torch
+    keep = []
+    o = _opts(keep=keep, **kw)
+    theta = torch.empty((h.n_points, H, 5), dtype=torch.float32, device="cuda")
+    res = (McResult * h.n_points)()
+    st = _lib.rift_ile_batch_harvest(h.ptr, C.byref(o), int(H), float(beta), theta.data_ptr(), res)
+    if st not in (0, 7):
+        _check(h, st)
+    return theta, [r.as_dict() for r in res]
 
 
 def rift_ile_draw(h, rnd, n, tables=None, **kw):

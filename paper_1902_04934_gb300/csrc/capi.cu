@@ -101,6 +101,16 @@ struct rift_ile {
   int cap_pst = 0;
   cudaStream_t gstream = nullptr;
   int graph_rounds = 4;   // rounds per captured graph
+  // learned proposal
+  double *tau0 = nullptr;     // [np][RIFT_MAXK] Q index origins (s), for the summary
+  float *head = nullptr;      // [np][88] network heads (given or computed)
+  float *summ = nullptr;      // [np][64]
+  float *gmm = nullptr;       // [np][RIFT_GMM_FLOATS]
+  float *gcst = nullptr;      // [np][4]
+  bool head_given = false;
+  RoundPt *last = nullptr;    // [np]
+  int *hidx = nullptr;        // harvest indices
+  size_t cap_hidx = 0;
 };
 
 namespace {
@@ -326,6 +336,17 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
     rift_ile_destroy(h);
     return s;
   }
+  {
+    std::vector<double> t0((size_t)n * RIFT_MAX_DET, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < descs[i].n_det; ++k) t0[(size_t)i * RIFT_MAX_DET + k] = descs[i].q_t0_gps[k] - descs[i].t_ref_gps;
+    if ((e = cudaMalloc(&h->tau0, sizeof(double) * t0.size())) != cudaSuccess ||
+        (e = cudaMemcpy(h->tau0, t0.data(), sizeof(double) * t0.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      fprintf(stderr, "rift_ile_create: %s\n", cudaGetErrorString(e));
+      rift_ile_destroy(h);
+      return RIFT_ECUDA;
+    }
+  }
   *out = h;
   return RIFT_OK;
 }
@@ -346,7 +367,8 @@ rift_status check_opts(rift_ile *h, const rift_mc_opts *o) {
       }
     }
   } else if (o->proposal == RIFT_PROPOSAL_LEARNED) {
-    return fail(h, RIFT_EUNSUPPORTED, "learned proposal: use rift_mdn_* entry points");
+    if (!o->mdn && !h->head_given)
+      return fail(h, RIFT_EINVAL, "learned proposal needs opts.mdn or rift_ile_set_proposal_head");
   } else if (o->proposal != RIFT_PROPOSAL_PRIOR) {
     return fail(h, RIFT_EINVAL, "unknown proposal");
   }
@@ -409,16 +431,61 @@ int log2_pow2(int v) {
   return ((1 << l) == v) ? l : -1;
 }
 
+rift_status ensure_learned(rift_ile *h) {
+  const int np = h->n_points;
+  if (!h->gmm) {
+    RIFT_CK(h, cudaMalloc(&h->gmm, sizeof(float) * (size_t)np * RIFT_GMM_FLOATS));
+    RIFT_CK(h, cudaMalloc(&h->gcst, sizeof(float) * (size_t)np * 4));
+    RIFT_CK(h, cudaMalloc(&h->head, sizeof(float) * (size_t)np * RIFT_MDN_HEAD));
+    RIFT_CK(h, cudaMalloc(&h->summ, sizeof(float) * (size_t)np * RIFT_MDN_SUMMARY));
+  }
+  return RIFT_OK;
+}
+
+// The learned proposal of every point for distance prior [d_lo, d_hi]: per-point constants
+// (FP64 here), then the network on each point's summary (opts.mdn) or the given heads.
+rift_status prepare_learned(rift_ile *h, const rift_mc_opts *o, cudaStream_t st) {
+  rift_status s = ensure_learned(h);
+  if (s != RIFT_OK) return s;
+  const int np = h->n_points;
+  std::vector<float> c((size_t)np * 4);
+  for (int p = 0; p < np; ++p) {
+    const double tspan = h->pts[p].t_hi - h->pts[p].t_lo;
+    const double lnspan = std::log(o->d_hi) - std::log(o->d_lo);
+    c[4 * p + 0] = (float)(std::log(2.0 * kPi) + std::log(2.0) + std::log(tspan) + std::log(2.0) + std::log(lnspan));
+    c[4 * p + 1] = (float)(-std::log(2.0 * kPi) - std::log(2.0) - std::log(tspan) - std::log(2.0) + std::log(3.0) -
+                           std::log(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo));
+    c[4 * p + 2] = (float)std::log(o->d_lo);
+    c[4 * p + 3] = (float)lnspan;
+  }
+  RIFT_CK(h, cudaMemcpyAsync(h->gcst, c.data(), sizeof(float) * c.size(), cudaMemcpyHostToDevice, st));
+  if (o->mdn) {
+    RIFT_CK(h, launch_summary(h->pts_dev, h->q_arena, h->c_arena, h->tau0, np, h->summ, st));
+    RIFT_CK(h, launch_mdn_gmm(static_cast<const rift_mdn *>(o->mdn), h->summ, h->gcst, np, h->head, h->gmm, st));
+  } else {
+    RIFT_CK(h, launch_gmm_from_head(h->head, h->gcst, np, h->gmm, st));
+  }
+  RIFT_CK(h, cudaStreamSynchronize(st));
+  return RIFT_OK;
+}
+
 // The Monte Carlo round loop of Eq. (lnLmarg) for np points of the handle, with the scratch S.
 rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rift_mc_result *res) {
   const int K = h->K, NT = taps_of(h->interp);
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
+  const bool learned = (o->proposal == RIFT_PROPOSAL_LEARNED);
   const int nb = adaptive ? o->n_bins : 0;
   const uint32_t npr = o->n_per_round;
   std::vector<int> lsv(3 * np);
+  if (learned) {
+    rift_status s2 = prepare_learned(h, o, h->stream);
+    if (s2 != RIFT_OK) return s2;
+  }
   for (int p = 0; p < np; ++p) {
     int *ls = &lsv[3 * p];
-    if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
+    if (learned) {
+      ls[0] = ls[1] = ls[2] = 0;
+    } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
       choose_strata(h->pts[p].c, npr, ls);
     } else {
       for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
@@ -484,6 +551,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.max_M = h->max_M;
   L.max_pairK = h->max_pairK;
   L.max_nb = nb;
+  L.learned = learned ? 1 : 0;
   std::vector<uint64_t> evals(np, 0);
   std::vector<int> rounds(np, 0), done(np, 0), nrun(np, 0);
   int launches = 0;
@@ -516,8 +584,9 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
       R.round = (uint32_t)rounds[p];
       R.point_id = (np == 1) ? o->point_id : (uint32_t)p;
       R.ls0 = l0; R.ls1 = l1; R.ls2 = l2;
-      R.proposal = adaptive ? 1 : 0;
+      R.proposal = learned ? 2 : (adaptive ? 1 : 0);
       R.nb = nb;
+      R.gmm = learned ? h->gmm + (size_t)p * RIFT_GMM_FLOATS : nullptr;
       R.lcorr0 = (float)std::log((double)n / ((double)C * (R.base + 1.0)));
       R.lcorr1 = R.base ? (float)std::log((double)n / ((double)C * R.base)) : 0.f;
       R.chunks = (R.base + (R.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
@@ -644,6 +713,13 @@ void rift_ile_destroy(rift_ile *h) {
   cudaFreeHost(S.rp_host);
   cudaFreeHost(S.acc_host);
   cudaFree(h->stage);
+  cudaFree(h->tau0);
+  cudaFree(h->head);
+  cudaFree(h->summ);
+  cudaFree(h->gmm);
+  cudaFree(h->gcst);
+  cudaFree(h->last);
+  cudaFree(h->hidx);
   cudaFree(h->pst);
   cudaFree(h->ctl);
   cudaFreeHost(h->ctl_host);
@@ -701,11 +777,15 @@ rift_status rift_ile_draw(rift_ile *h, const rift_mc_opts *o, uint32_t round, co
   if (n == 0) return RIFT_OK;
   if (n > 0xFFFFFFFFull) return fail(h, RIFT_EINVAL, "n too large");
   const bool tab = (o->proposal == RIFT_PROPOSAL_ADAPTIVE) && tables;
+  const bool learned = (o->proposal == RIFT_PROPOSAL_LEARNED);
   const int nb = tab ? o->n_bins : 0;
   if ((s = ensure_scratch(h, 1, 1, 0, tab ? nb : 0, 1)) != RIFT_OK) return s;
+  if (learned && (s = prepare_learned(h, o, h->stream)) != RIFT_OK) return s;
   McScratch &S = h->sc;
   int ls[3];
-  if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
+  if (learned) {
+    ls[0] = ls[1] = ls[2] = 0;
+  } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
     choose_strata(h->pts[0].c, (uint32_t)n, ls);
   } else {
     for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
@@ -718,7 +798,8 @@ rift_status rift_ile_draw(rift_ile *h, const rift_mc_opts *o, uint32_t round, co
   R.n = (uint32_t)n; R.ncell = C; R.base = R.n / C; R.rem = R.n % C;
   R.round = round; R.point_id = o->point_id;
   R.ls0 = ls[0]; R.ls1 = ls[1]; R.ls2 = ls[2];
-  R.proposal = tab ? 1 : 0; R.nb = nb;
+  R.proposal = learned ? 2 : (tab ? 1 : 0); R.nb = nb;
+  R.gmm = learned ? h->gmm : nullptr;
   R.lcorr0 = (float)std::log((double)R.n / ((double)C * (R.base + 1.0)));
   R.lcorr1 = R.base ? (float)std::log((double)R.n / ((double)C * R.base)) : 0.f;
   R.chunks = (R.base + (R.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
@@ -758,20 +839,31 @@ rift_status rift_ile_marginalize(rift_ile *h, const rift_mc_opts *o, rift_mc_res
   return run_mc(h, o, 1, h->sc, res);
 }
 
+rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, bool keep_ell);
+
 rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res) {
+  return batch_run(h, o, res, false);
+}
+
+}  // extern "C"
+
+rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, bool keep_ell) {
   if (!h || !res) return RIFT_EINVAL;
   rift_status s = check_opts(h, o);
   if (s != RIFT_OK) return s;
   const int np = h->n_points;
   std::memset(res, 0, sizeof(*res) * np);
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
+  const bool learned = (o->proposal == RIFT_PROPOSAL_LEARNED);
   const int nb = adaptive ? o->n_bins : 0;
   const int hb = std::max(1, std::min(64, (int)(o->n_per_round / 8192)));
   std::vector<int> lsv(3 * np);
   size_t items = 0;
   for (int p = 0; p < np; ++p) {
     int *ls = &lsv[3 * p];
-    if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
+    if (learned) {
+      ls[0] = ls[1] = ls[2] = 0;
+    } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
       choose_strata(h->pts[p].c, o->n_per_round, ls);
     } else {
       for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
@@ -780,7 +872,9 @@ rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_
     }
     items += ((size_t)1 << (ls[0] + ls[1] + ls[2])) + o->n_per_round / RIFT_CHUNK + 1;
   }
-  if ((s = ensure_scratch(h, np, items, adaptive ? (size_t)np * o->n_per_round : 0, nb, hb)) != RIFT_OK) return s;
+  const bool keep = adaptive || keep_ell;
+  if ((s = ensure_scratch(h, np, items, keep ? (size_t)np * o->n_per_round : 0, nb, hb)) != RIFT_OK) return s;
+  if (keep_ell && !h->last) RIFT_CK(h, cudaMalloc(&h->last, sizeof(RoundPt) * np));
   McScratch &S = h->sc;
   if (np > h->cap_pst) {
     cudaFree(h->pst); cudaFreeHost(h->pst_host);
@@ -797,6 +891,7 @@ rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_
   cudaStream_t st = h->gstream;
   RIFT_CK(h, cudaStreamSynchronize(h->stream));   // inputs uploaded on the handle's stream
   const int K = h->K, NT = taps_of(h->interp);
+  if (learned && (s = prepare_learned(h, o, st)) != RIFT_OK) return s;
   // initial state
   for (int p = 0; p < np; ++p) {
     std::memset(&S.acc_host[p], 0, sizeof(AccState));
@@ -822,6 +917,10 @@ rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_
   B.nb = nb;
   B.tables = S.tables;
   B.lnw = S.lnw;
+  B.learned = learned ? 1 : 0;
+  B.keep_ell = keep_ell ? 1 : 0;
+  B.gmm = h->gmm;
+  B.last = keep_ell ? h->last : nullptr;
   if (adaptive) {
     float u[3 * (RIFT_MAXBINS + 1)];
     const float *src = o->tables;
@@ -862,12 +961,13 @@ rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_
   L.qa = h->q_arena;
   L.ca = h->c_arena;
   L.partials = S.partials;
-  L.ell_buf = adaptive ? S.ell : nullptr;
-  L.bin_buf = adaptive ? S.bins : nullptr;
+  L.ell_buf = keep ? S.ell : nullptr;
+  L.bin_buf = keep ? S.bins : nullptr;
   L.flags = h->flags;
   L.max_M = h->max_M;
   L.max_pairK = h->max_pairK;
   L.max_nb = nb;
+  L.learned = learned ? 1 : 0;
   const int grid = h->num_sms * bps;
   // capture G rounds: update -> cells -> merge -> (adaptive) hist -> tables
   const int G = std::max(1, h->graph_rounds);
@@ -926,6 +1026,66 @@ rift_status rift_ile_batch_marginalize(rift_ile *h, const rift_mc_opts *o, rift_
   }
   return overall;
 }
+
+extern "C" {
+
+rift_status rift_ile_batch_summary(rift_ile *h, float *out_dev) {
+  if (!h || !out_dev) return RIFT_EINVAL;
+  RIFT_CK(h, launch_summary(h->pts_dev, h->q_arena, h->c_arena, h->tau0, h->n_points, out_dev, h->stream));
+  RIFT_CK(h, cudaStreamSynchronize(h->stream));
+  return RIFT_OK;
+}
+
+rift_status rift_ile_set_proposal_head(rift_ile *h, const float *head_host) {
+  if (!h || !head_host) return RIFT_EINVAL;
+  rift_status s = ensure_learned(h);
+  if (s != RIFT_OK) return s;
+  RIFT_CK(h, cudaMemcpy(h->head, head_host, sizeof(float) * (size_t)h->n_points * RIFT_MDN_HEAD,
+                        cudaMemcpyHostToDevice));
+  h->head_given = true;
+  return RIFT_OK;
+}
+
+rift_status rift_ile_boxes(rift_ile *h, double d_lo, double d_hi, float *out) {
+  if (!h || !out || !(d_lo > 0) || !(d_hi > d_lo)) return RIFT_EINVAL;
+  for (int p = 0; p < h->n_points; ++p) {
+    float *o = out + (size_t)p * 10;
+    const double a[5] = {0.0, -1.0, h->pts[p].t_lo, -1.0, std::log(d_lo)};
+    const double b[5] = {2.0 * kPi, 1.0, h->pts[p].t_hi, 1.0, std::log(d_hi)};
+    for (int d = 0; d < 5; ++d) { o[d] = (float)a[d]; o[5 + d] = (float)b[d]; }
+  }
+  return RIFT_OK;
+}
+
+rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *o, int H, double beta, float *theta_dev,
+                                   rift_mc_result *res) {
+  if (!h || !o || !theta_dev || !res || H < 1 || !(beta > 0)) return RIFT_EINVAL;
+  rift_status s = batch_run(h, o, res, true);
+  if (s != RIFT_OK && s != RIFT_ENOTCONVERGED) return s;
+  const int np = h->n_points;
+  McScratch &S = h->sc;
+  const size_t need = (size_t)np * H;
+  if (need > h->cap_hidx) {
+    cudaFree(h->hidx);
+    h->hidx = nullptr;
+    h->cap_hidx = 0;
+    RIFT_CK(h, cudaMalloc(&h->hidx, sizeof(int) * need));
+    h->cap_hidx = need;
+  }
+  cudaStream_t st = h->gstream;
+  // the cumulative weights overwrite the per-sample log weights after they are read
+  RIFT_CK(h, launch_harvest(S.ell, h->last, S.acc, np, (float)beta, H, S.ell, h->hidx, st));
+  CellLaunch L{};
+  L.seed = o->seed;
+  L.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
+  L.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
+  L.pts = h->pts_dev;
+  L.n_points = np;
+  RIFT_CK(h, launch_harvest_theta(L, h->last, h->hidx, H, theta_dev, st));
+  RIFT_CK(h, cudaStreamSynchronize(st));
+  return s;
+}
+
 
 }  // extern "C"
 

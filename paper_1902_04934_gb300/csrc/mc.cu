@@ -97,7 +97,11 @@ __device__ __forceinline__ df inv_cdf_df(const float *cdf, int nb, df U, int &b)
 
 struct Drawn {
   df x0, x1, x2;   // fractions of the ra, sin dec, t ranges
-  float u3, u4, u5, u6;
+  float u_psi;     // 2 psi = 2 pi u_psi
+  float u_phi;     // phi = 2 pi u_phi
+  float c_frac;    // (1 + cos incl) / 2
+  float dist;      // D (Mpc)
+  float xd;        // D_ref / D
   float lpq;       // ln p - ln q (+ stratification weight)
   uint32_t bins;   // adapted bins, 8 bits each
 };
@@ -106,7 +110,8 @@ struct Drawn {
 // (ra, sin dec, t) uniforms U_d = (c_d + u_d) / S_d (exact: S_d is a power of two),
 // prior or tabulated proposal.
 __device__ __forceinline__ Drawn draw_cell_sample(unsigned long long seed, const RoundPt &R, uint32_t i,
-                                                  uint32_t cell, const float *tab, const float *lnw) {
+                                                  uint32_t cell, const float *tab, const float *lnw, float dref,
+                                                  float d_lo3, float d_span3) {
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   const uint4 a = philox4x32_10(make_uint4(i, R.round, 0u, R.point_id), key);
   const uint4 b = philox4x32_10(make_uint4(i, R.round, 1u, R.point_id), key);
@@ -123,7 +128,12 @@ __device__ __forceinline__ Drawn draw_cell_sample(unsigned long long seed, const
   U1 = df{U1.hi * s1, U1.lo * s1};
   U2 = df{U2.hi * s2, U2.lo * s2};
   Drawn d;
-  d.u3 = bits_to_u(a.w); d.u4 = bits_to_u(b.x); d.u5 = bits_to_u(b.y); d.u6 = bits_to_u(b.z);
+  d.u_psi = bits_to_u(a.w);
+  d.u_phi = bits_to_u(b.x);
+  d.c_frac = bits_to_u(b.y);
+  const float D3 = fmaf(bits_to_u(b.z), d_span3, d_lo3);
+  d.dist = cbrtf(D3);
+  d.xd = dref * rcbrtf(D3);
   d.lpq = (cell < R.rem) ? R.lcorr0 : R.lcorr1;
   if (R.proposal == 0) {
     d.x0 = U0; d.x1 = U1; d.x2 = U2;
@@ -138,6 +148,98 @@ __device__ __forceinline__ Drawn draw_cell_sample(unsigned long long seed, const
     d.bins = (uint32_t)b0 | ((uint32_t)b1 << 8) | ((uint32_t)b2 << 16);
   }
   return d;
+}
+
+// Sample i from the learned proposal G (layout RIFT_GMM_FLOATS): Box-Muller normals from
+// (u0,u1), (u2,u3), (u4,u5); component = first j with u6 < cumulative pi_j; u7 < 0.9 takes the
+// network, otherwise the prior transforms of u0..u4; u8 -> psi, u9 -> phi.  ln q is the
+// defensive mixture 0.9 q_MDN + 0.1 p5 with the logit change of variables.
+__device__ __forceinline__ Drawn draw_learned(unsigned long long seed, const RoundPt &R, uint32_t i, const float *G,
+                                              float dref, float d_lo3, float d_span3) {
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint4 a = philox4x32_10(make_uint4(i, R.round, 0u, R.point_id), key);
+  const uint4 b = philox4x32_10(make_uint4(i, R.round, 1u, R.point_id), key);
+  const uint4 c = philox4x32_10(make_uint4(i, R.round, 2u, R.point_id), key);
+  const float u0 = bits_to_u(a.x), u1 = bits_to_u(a.y), u2 = bits_to_u(a.z), u3 = bits_to_u(a.w);
+  const float u4 = bits_to_u(b.x), u5 = bits_to_u(b.y), u6 = bits_to_u(b.z), u7 = bits_to_u(b.w);
+  const float lnDlo = G[138], lnDspan = G[139];
+  float x[5], z[5];
+  if (u7 < 0.9f) {
+    float n[6];
+    const float uu[6] = {u0, u1, u2, u3, u4, u5};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float r = sqrtf(-2.f * logf(uu[2 * q]));
+      float sn, cs;
+      sincospif(2.f * uu[2 * q + 1], &sn, &cs);
+      n[2 * q] = r * cs;
+      n[2 * q + 1] = r * sn;
+    }
+    int j = 7;
+#pragma unroll
+    for (int q = 6; q >= 0; --q) if (u6 < G[8 + q]) j = q;
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) {
+      z[dd] = fmaf(expf(G[56 + 5 * j + dd]), n[dd], G[16 + 5 * j + dd]);
+      x[dd] = 1.f / (1.f + expf(-z[dd]));
+    }
+  } else {
+    const float D = cbrtf(fmaf(u4, d_span3, d_lo3));
+    x[0] = u0; x[1] = u1; x[2] = u2; x[3] = u3;
+    x[4] = fminf(fmaxf((logf(D) - lnDlo) / lnDspan, 1e-7f), 1.f - 6e-8f);
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) z[dd] = logf(x[dd]) - log1pf(-x[dd]);
+  }
+  // ln q_MDN: mixture in z plus the logit Jacobian, ln x + ln(1 - x) = -softplus(-z) - softplus(z)
+  float comp[8];
+  float mx = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float acc = G[j];
+#pragma unroll
+    for (int dd = 0; dd < 5; ++dd) {
+      const float t = (z[dd] - G[16 + 5 * j + dd]) * G[96 + 5 * j + dd];
+      acc -= 0.5f * t * t + G[56 + 5 * j + dd] + 0.91893853320467274f;
+    }
+    comp[j] = acc;
+    mx = fmaxf(mx, acc);
+  }
+  float se = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) se += expf(comp[j] - mx);
+  float jac = G[136];
+#pragma unroll
+  for (int dd = 0; dd < 5; ++dd) {
+    const float az = fabsf(z[dd]);
+    jac -= az + 2.f * log1pf(expf(-az));   // softplus(z) + softplus(-z) = |z| + 2 log(1 + e^{-|z|})
+  }
+  const float lq_mdn = mx + logf(se) - jac;
+  const float lnD = fmaf(x[4], lnDspan, lnDlo);
+  const float lp5 = G[137] + 3.f * lnD;
+  const float A = -0.10536051565782628f + lq_mdn;   // ln 0.9
+  const float B = -2.3025850929940457f + lp5;       // ln 0.1
+  const float M = fmaxf(A, B);
+  const float lnq = M + logf(expf(A - M) + expf(B - M));
+  Drawn d;
+  d.x0 = df{x[0], 0.f};
+  d.x1 = df{x[1], 0.f};
+  d.x2 = df{x[2], 0.f};
+  d.c_frac = x[3];
+  d.dist = expf(lnD);
+  d.xd = dref * expf(-lnD);
+  d.u_psi = bits_to_u(c.x);
+  d.u_phi = bits_to_u(c.y);
+  d.lpq = lp5 - lnq;
+  d.bins = 0u;
+  return d;
+}
+
+template <int LEARNED>
+__device__ __forceinline__ Drawn draw_any(unsigned long long seed, const RoundPt &R, uint32_t i, uint32_t cell,
+                                          const float *tab, const float *lnw, const float *G, float dref, float d_lo3,
+                                          float d_span3) {
+  if (LEARNED) return draw_learned(seed, R, i, G, dref, d_lo3, d_span3);
+  return draw_cell_sample(seed, R, i, cell, tab, lnw, dref, d_lo3, d_span3);
 }
 
 // Sky and time geometry of a drawn sample: cos/sin of (ra - GMST) and sin/cos dec.
@@ -250,12 +352,13 @@ __device__ __forceinline__ float linear_term_staged(const PointC &P, const float
   return lin;
 }
 
-template <int K, int NT>
+template <int K, int NT, int LEARNED>
 __global__ void __launch_bounds__(RIFT_CELL_BLOCK) cells_kernel(CellLaunch L) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_item, s_point;
   __shared__ RoundPt sR;
+  __shared__ float s_gmm[RIFT_GMM_FLOATS];
   __shared__ int s_wlo[K], s_whi[K], s_woff[K];
   __shared__ int s_red[2 * K][RIFT_CELL_BLOCK / 32];
   __shared__ float4 s_wpart[RIFT_CELL_BLOCK / 32];
@@ -312,9 +415,11 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK) cells_kernel(CellLaunch L) {
       __syncthreads();
       const float4 *cg = L.ca + P.uv_off;
       for (int j = threadIdx.x; j < P.npair * K; j += blockDim.x) C[j] = cg[j];
-      if (R.proposal) {
+      if (R.proposal == 1) {
         for (int j = threadIdx.x; j < 3 * (R.nb + 1); j += blockDim.x) tab[j] = R.tab[j];
         for (int j = threadIdx.x; j < 3 * R.nb; j += blockDim.x) lnw[j] = R.lnw[j];
+      } else if (R.proposal == 2) {
+        for (int j = threadIdx.x; j < RIFT_GMM_FLOATS; j += blockDim.x) s_gmm[j] = R.gmm[j];
       }
       __syncthreads();
       cur = p;
@@ -332,7 +437,8 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK) cells_kernel(CellLaunch L) {
 #pragma unroll
     for (int k = 0; k < K; ++k) { rmin[k] = INT_MAX; rmax[k] = INT_MIN; }
     for (uint32_t j = j0 + threadIdx.x; j < j_end; j += blockDim.x) {
-      const Drawn d = draw_cell_sample(L.seed, R, sample_index(R, cell, j), cell, tab, lnw);
+      const Drawn d = draw_any<LEARNED>(L.seed, R, sample_index(R, cell, j), cell, tab, lnw, s_gmm, P.dref, L.d_lo3,
+                                        L.d_span3);
       const Sky s = sky_of(P, d);
       df si[K];
       time_index<K>(P, d, s, si);
@@ -405,12 +511,12 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK) cells_kernel(CellLaunch L) {
     float m = kNegInf, s1 = 0.f, s2 = 0.f, cnt = 0.f;
     for (uint32_t j = j0 + threadIdx.x; j < j_end; j += blockDim.x) {
       const uint32_t i = sample_index(R, cell, j);
-      const Drawn d = draw_cell_sample(L.seed, R, i, cell, tab, lnw);
+      const Drawn d = draw_any<LEARNED>(L.seed, R, i, cell, tab, lnw, s_gmm, P.dref, L.d_lo3, L.d_span3);
       const Sky s = sky_of(P, d);
       df si[K];
       time_index<K>(P, d, s, si);
       float s2p, c2p;
-      sincospif(2.f * d.u3, &s2p, &c2p);   // 2 psi = 2 pi u3
+      sincospif(2.f * d.u_psi, &s2p, &c2p);   // 2 psi = 2 pi u_psi
       SampleGeo g;
 #pragma unroll
       for (int k = 0; k < K; ++k) g.s[k] = si[k];
@@ -432,10 +538,10 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK) cells_kernel(CellLaunch L) {
           g.F[k] = make_float2(c2p * fr - s2p * fi, s2p * fr + c2p * fi);
         }
       }
-      g.x = P.dref * rcbrtf(fmaf(d.u6, L.d_span3, L.d_lo3));
+      g.x = d.xd;
       float sphi, cphi;
-      sincospif(2.f * d.u4, &sphi, &cphi);
-      swsh_modes(P, sqrtf(d.u5), sqrtf(1.f - d.u5), cphi, sphi, Ys, ystride);
+      sincospif(2.f * d.u_phi, &sphi, &cphi);
+      swsh_modes(P, sqrtf(d.c_frac), sqrtf(1.f - d.c_frac), cphi, sphi, Ys, ystride);
       const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
       const float quad = quad_term<K>(P, C, g, Ys, ystride);
       const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
@@ -548,7 +654,7 @@ __global__ void hist_points_kernel(const float *__restrict__ ell, const uint32_t
   const RoundPt &R = rp[p];
   for (int j = threadIdx.x; j < 3 * nb; j += blockDim.x) h[j] = 0ull;
   __syncthreads();
-  if (R.ncell > 0 && R.ell_off >= 0 && R.proposal) {
+  if (R.ncell > 0 && R.ell_off >= 0 && R.proposal == 1) {
     const float mx = (float)acc[p].round_max;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += gridDim.x * blockDim.x) {
       const float l = ell[R.ell_off + i];
@@ -581,7 +687,7 @@ __global__ void tables_points_kernel(const unsigned long long *__restrict__ part
     tables += (size_t)nbuf * np * 3 * (nb + 1);
     lnw += (size_t)nbuf * np * 3 * nb;
   }
-  if (part && (rp[p].ncell == 0 || !rp[p].proposal)) return;
+  if (part && (rp[p].ncell == 0 || rp[p].proposal != 1)) return;
   float *tb = tables + (size_t)p * 3 * (nb + 1);
   float *lw = lnw + (size_t)p * 3 * nb;
   if (part) {
@@ -620,7 +726,7 @@ __global__ void draw_cells_kernel(CellLaunch L, DrawOut o, uint32_t n) {
   copy_words(L.pts, &P, sizeof(PointC));
   float *tab = dtab;
   float *lnw = dtab + 3 * (R.nb + 1);
-  if (R.proposal) {
+  if (R.proposal == 1) {
     for (int j = threadIdx.x; j < 3 * (R.nb + 1); j += blockDim.x) tab[j] = R.tab[j];
     for (int j = threadIdx.x; j < 3 * R.nb; j += blockDim.x) lnw[j] = R.lnw[j];
   }
@@ -630,14 +736,15 @@ __global__ void draw_cells_kernel(CellLaunch L, DrawOut o, uint32_t n) {
   // cell of sample i
   const uint32_t big = R.rem * (R.base + 1u);
   const uint32_t cell = (i < big) ? i / (R.base + 1u) : R.rem + (i - big) / R.base;
-  const Drawn d = draw_cell_sample(L.seed, R, i, cell, tab, lnw);
+  const Drawn d = (R.proposal == 2) ? draw_learned(L.seed, R, i, R.gmm, P.dref, L.d_lo3, L.d_span3)
+                                    : draw_cell_sample(L.seed, R, i, cell, tab, lnw, P.dref, L.d_lo3, L.d_span3);
   o.theta[0 * (size_t)n + i] = kTwoPi * (d.x0.hi + d.x0.lo);
   o.theta[1 * (size_t)n + i] = (2.f * d.x1.hi - 1.f) + 2.f * d.x1.lo;
   o.theta[2 * (size_t)n + i] = P.t_lo + P.t_span * (d.x2.hi + d.x2.lo);
-  o.theta[3 * (size_t)n + i] = 3.14159265358979f * d.u3;
-  o.theta[4 * (size_t)n + i] = kTwoPi * d.u4;
-  o.theta[5 * (size_t)n + i] = 2.f * d.u5 - 1.f;
-  o.theta[6 * (size_t)n + i] = cbrtf(fmaf(d.u6, L.d_span3, L.d_lo3));
+  o.theta[3 * (size_t)n + i] = 3.14159265358979f * d.u_psi;
+  o.theta[4 * (size_t)n + i] = kTwoPi * d.u_phi;
+  o.theta[5 * (size_t)n + i] = 2.f * d.c_frac - 1.f;
+  o.theta[6 * (size_t)n + i] = d.dist;
   o.lpq[i] = d.lpq;
   if (o.bins) {
     o.bins[0 * (size_t)n + i] = (int)(d.bins & 255u);
@@ -668,6 +775,7 @@ __global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState 
     RoundPt &R = rp[p];
     PtState &st = S[p];
     if (R.n > 0) {
+      if (B.last) B.last[p] = R;
       st.evals += R.n;
       st.rounds += 1;
       const double n_eff = acc[p].s1 + acc[p].c1;
@@ -692,11 +800,12 @@ __global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState 
       N.round = (uint32_t)st.rounds;
       N.point_id = (uint32_t)p;
       N.ls0 = l0; N.ls1 = l1; N.ls2 = l2;
-      N.proposal = B.adaptive ? 1 : 0;
+      N.proposal = B.learned ? 2 : (B.adaptive ? 1 : 0);
       N.nb = B.nb;
       N.lcorr0 = (float)log((double)n / ((double)C * (N.base + 1.0)));
       N.lcorr1 = N.base ? (float)log((double)n / ((double)C * N.base)) : 0.f;
-      N.ell_off = B.adaptive ? (long long)p * B.npr : -1;
+      N.ell_off = (B.adaptive || B.keep_ell) ? (long long)p * B.npr : -1;
+      if (B.learned) N.gmm = B.gmm + (size_t)p * RIFT_GMM_FLOATS;
       if (B.adaptive) {
         N.tab = B.tables + ((size_t)tabbuf * B.np + p) * tstride;
         N.lnw = B.lnw + ((size_t)tabbuf * B.np + p) * wstride;
@@ -733,24 +842,59 @@ __global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState 
   }
 }
 
-template <int K, int NT>
-cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
+// theta5 of harvested samples: for (point p, slot h) re-draw sample idx[p][h] of the point's
+// last round and write (ra, sin dec, t, cos incl, ln D) into theta[p][h][0..4].
+__global__ void harvest_theta_kernel(CellLaunch L, const RoundPt *__restrict__ last, const int *__restrict__ idx, int H,
+                                     float *__restrict__ theta) {
+  const int p = blockIdx.y;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  const RoundPt R = last[p];
+  const int i = idx[(size_t)p * H + h];
+  float *o = theta + ((size_t)p * H + h) * 5;
+  if (i < 0 || R.n == 0) {
+    for (int q = 0; q < 5; ++q) o[q] = NAN;
+    return;
+  }
+  const uint32_t big = R.rem * (R.base + 1u);
+  const uint32_t cell = ((uint32_t)i < big) ? (uint32_t)i / (R.base + 1u) : R.rem + ((uint32_t)i - big) / R.base;
+  const PointC *P = L.pts + p;
+  const Drawn d = (R.proposal == 2)
+                      ? draw_learned(L.seed, R, (uint32_t)i, R.gmm, P->dref, L.d_lo3, L.d_span3)
+                      : draw_cell_sample(L.seed, R, (uint32_t)i, cell, R.tab, R.lnw, P->dref, L.d_lo3, L.d_span3);
+  o[0] = kTwoPi * (d.x0.hi + d.x0.lo);
+  o[1] = (2.f * d.x1.hi - 1.f) + 2.f * d.x1.lo;
+  o[2] = P->t_lo + P->t_span * (d.x2.hi + d.x2.lo);
+  o[3] = 2.f * d.c_frac - 1.f;
+  o[4] = logf(d.dist);
+}
+
+template <int K, int NT, int LEARNED>
+cudaError_t cells_kl(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(cells_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaError_t e =
+        cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  cells_kernel<K, NT><<<grid, block, smem, st>>>(L);
+  cells_kernel<K, NT, LEARNED><<<grid, block, smem, st>>>(L);
   return cudaGetLastError();
 }
 
 template <int K, int NT>
+cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
+  return L.learned ? cells_kl<K, NT, 1>(L, grid, block, smem, st) : cells_kl<K, NT, 0>(L, grid, block, smem, st);
+}
+
+template <int K, int NT>
 int cells_occ(size_t smem, int block) {
-  int nb = 0;
-  cudaFuncSetAttribute(cells_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_kernel<K, NT>, block, smem);
-  return nb;
+  int nb = 0, nb2 = 0;
+  cudaFuncSetAttribute(cells_kernel<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(cells_kernel<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_kernel<K, NT, 0>, block, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, cells_kernel<K, NT, 1>, block, smem);
+  return nb < nb2 ? nb : nb2;
 }
 
 }  // namespace
@@ -825,6 +969,13 @@ cudaError_t launch_hist_ctl(const float *ell, const uint32_t *bins, const RoundP
 cudaError_t launch_tables_ctl(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points, int nb,
                               double floor_eps, const BatchCtl &B, const RoundCtl *ctl, cudaStream_t st) {
   tables_points_kernel<<<n_points, 256, 0, st>>>(part, hblocks, rp, nb, floor_eps, B.tables, B.lnw, ctl, n_points);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_harvest_theta(const CellLaunch &L, const RoundPt *last, const int *idx, int H, float *theta,
+                                 cudaStream_t st) {
+  dim3 g((H + 127) / 128, L.n_points);
+  harvest_theta_kernel<<<g, 128, 0, st>>>(L, last, idx, H, theta);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,632 @@
+// Learned proposal: mixture-density network over (ra, sin dec, t, cos incl, ln D), its
+// training (weighted negative log likelihood of harvested posterior samples, Adam), the
+// per-point summary it is conditioned on, and the harvest of training samples.
+//
+// Network: s (64) -> 256 -> 256 (GELU, erf form) -> 88 = 8 logits + 8x5 means + 8x5 log
+// sigmas; weights bfloat16 (rounded from a float32 master copy), activations and
+// accumulation float32.  One CTA per point for forward, loss and backward; weight gradients
+// are accumulated with float32 atomics (order-dependent in the last bits only).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rift_ile.h"
+#include "rift_device.cuh"
+#include "rift_internal.h"
+
+namespace {
+
+constexpr int NI = 64, NH = 256, NC = 8, ND = 5, NO = NC * (1 + 2 * ND);
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NI, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + NH * NH,
+              OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NO * NH, NPARAM = OFF_B3 + NO;
+static_assert(NPARAM == RIFT_MDN_PARAMS, "parameter count in the header is out of date");
+constexpr float LS_MIN = -8.f, LS_MAX = 4.f;
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+__device__ __forceinline__ float bf(const __nv_bfloat16 *w, int i) { return __bfloat162float(w[i]); }
+
+// dot of a bfloat16 row (16-byte aligned, n multiple of 8) with a float vector in shared memory
+__device__ __forceinline__ float row_dot(const __nv_bfloat16 *row, const float *x, int n, float acc) {
+  const uint4 *r = reinterpret_cast<const uint4 *>(row);
+  for (int q = 0; q < n / 8; ++q) {
+    const uint4 v = __ldg(r + q);
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(h[e]);
+      acc = fmaf(f.x, x[8 * q + 2 * e], acc);
+      acc = fmaf(f.y, x[8 * q + 2 * e + 1], acc);
+    }
+  }
+  return acc;
+}
+
+// head[p] = MLP(S[p]); cache[p] = pre-activations (a1, a2) for the backward pass
+__global__ void __launch_bounds__(256) mdn_forward_kernel(const __nv_bfloat16 *__restrict__ W,
+                                                          const float *__restrict__ S, int P,
+                                                          float *__restrict__ head, float *__restrict__ cache) {
+  const int p = blockIdx.x;
+  if (p >= P) return;
+  __shared__ float s[NI], h1[NH], h2[NH];
+  const int t = threadIdx.x;
+  if (t < NI) s[t] = S[(size_t)p * NI + t];
+  __syncthreads();
+  float a = row_dot(W + OFF_W1 + t * NI, s, NI, bf(W, OFF_B1 + t));
+  if (cache) cache[(size_t)p * 2 * NH + t] = a;
+  h1[t] = gelu(a);
+  __syncthreads();
+  a = row_dot(W + OFF_W2 + t * NH, h1, NH, bf(W, OFF_B2 + t));
+  if (cache) cache[(size_t)p * 2 * NH + NH + t] = a;
+  h2[t] = gelu(a);
+  __syncthreads();
+  if (t < NO) head[(size_t)p * NO + t] = row_dot(W + OFF_W3 + t * NH, h2, NH, bf(W, OFF_B3 + t));
+}
+
+// Weighted NLL of each point's H samples: loss[p] and dL/dhead[p] (scaled by `scale`).
+// theta: [P][H][5] (ra, sin dec, t, cos incl, ln D); w: [P][H]; box: [P][2][5] (a, b).
+__global__ void __launch_bounds__(128) mdn_loss_kernel(const float *__restrict__ head, const float *__restrict__ th,
+                                                       const float *__restrict__ w, const float *__restrict__ box,
+                                                       int H, float scale, float *__restrict__ gout,
+                                                       float *__restrict__ loss) {
+  const int p = blockIdx.x;
+  __shared__ float hd[NO], lpi[NC], isg[NC * ND], lsc[NC * ND];
+  __shared__ float red[NO + 1][4];
+  const int t = threadIdx.x;
+  if (t < NO) hd[t] = head[(size_t)p * NO + t];
+  __syncthreads();
+  if (t == 0) {
+    float mx = -INFINITY;
+    for (int j = 0; j < NC; ++j) mx = fmaxf(mx, hd[j]);
+    float se = 0.f;
+    for (int j = 0; j < NC; ++j) se += expf(hd[j] - mx);
+    for (int j = 0; j < NC; ++j) lpi[j] = hd[j] - mx - logf(se);
+  }
+  if (t < NC * ND) {
+    const float l = fminf(fmaxf(hd[NC + NC * ND + t], LS_MIN), LS_MAX);
+    lsc[t] = l;
+    isg[t] = expf(-l);
+  }
+  __syncthreads();
+  float acc[NO + 1];
+#pragma unroll
+  for (int q = 0; q <= NO; ++q) acc[q] = 0.f;
+  const float *a = box + (size_t)p * 10, *b = a + 5;
+  for (int j = t; j < H; j += blockDim.x) {
+    const float wj = w[(size_t)p * H + j];
+    float z[ND], jac = 0.f;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const float x = (th[((size_t)p * H + j) * ND + d] - a[d]) / (b[d] - a[d]);
+      z[d] = logf(x) - log1pf(-x);
+      jac += logf(b[d] - a[d]) + logf(x) + log1pf(-x);
+    }
+    float comp[NC], mx = -INFINITY;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float s = lpi[c];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        const float u = (z[d] - hd[NC + c * ND + d]) * isg[c * ND + d];
+        s -= 0.5f * u * u + lsc[c * ND + d] + 0.91893853320467274f;
+      }
+      comp[c] = s;
+      mx = fmaxf(mx, s);
+    }
+    float se = 0.f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) se += expf(comp[c] - mx);
+    const float lq = mx + logf(se);
+    acc[NO] -= wj * (lq - jac);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float r = expf(comp[c] - lq) * wj;
+      acc[c] -= r;
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        const float u = (z[d] - hd[NC + c * ND + d]) * isg[c * ND + d];
+        acc[NC + c * ND + d] -= r * u * isg[c * ND + d];
+        acc[NC + NC * ND + c * ND + d] -= r * (u * u - 1.f);
+      }
+    }
+    // + w pi_c (the softmax normalisation)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] += wj * expf(lpi[c]);
+  }
+  // block reduction (warp shuffles, then the four warps in a fixed order)
+  const int lane = t & 31, wid = t >> 5;
+#pragma unroll
+  for (int q = 0; q <= NO; ++q) {
+    float v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[q][wid] = v;
+  }
+  __syncthreads();
+  for (int q = t; q <= NO; q += blockDim.x) {
+    const float v = red[q][0] + red[q][1] + red[q][2] + red[q][3];
+    if (q < NO) {
+      float g = v * scale;
+      if (q >= NC + NC * ND) {
+        const float raw = hd[q];
+        if (!(raw > LS_MIN && raw < LS_MAX)) g = 0.f;
+      }
+      gout[(size_t)p * NO + q] = g;
+    } else {
+      loss[p] = v;
+    }
+  }
+}
+
+// Backpropagation of dL/dhead through the MLP; weight gradients accumulated with atomics.
+__global__ void __launch_bounds__(256) mdn_backward_kernel(const __nv_bfloat16 *__restrict__ W,
+                                                           const float *__restrict__ S,
+                                                           const float *__restrict__ cache,
+                                                           const float *__restrict__ gout, int P,
+                                                           float *__restrict__ grad) {
+  const int p = blockIdx.x;
+  if (p >= P) return;
+  __shared__ float s[NI], h1[NH], h2[NH], ga1[NH], ga2[NH], go[NO];
+  const int t = threadIdx.x;
+  if (t < NI) s[t] = S[(size_t)p * NI + t];
+  if (t < NO) go[t] = gout[(size_t)p * NO + t];
+  const float a1 = cache[(size_t)p * 2 * NH + t], a2 = cache[(size_t)p * 2 * NH + NH + t];
+  h1[t] = gelu(a1);
+  h2[t] = gelu(a2);
+  __syncthreads();
+  float gh2 = 0.f;
+  for (int o = 0; o < NO; ++o) gh2 = fmaf(go[o], bf(W, OFF_W3 + o * NH + t), gh2);
+  ga2[t] = gh2 * gelu_grad(a2);
+  __syncthreads();
+  float gh1 = 0.f;
+  for (int j = 0; j < NH; ++j) gh1 = fmaf(ga2[j], bf(W, OFF_W2 + j * NH + t), gh1);
+  ga1[t] = gh1 * gelu_grad(a1);
+  __syncthreads();
+  for (int o = 0; o < NO; ++o) atomicAdd(grad + OFF_W3 + o * NH + t, go[o] * h2[t]);
+  if (t < NO) atomicAdd(grad + OFF_B3 + t, go[t]);
+  for (int j = 0; j < NH; ++j) atomicAdd(grad + OFF_W2 + j * NH + t, ga2[j] * h1[t]);
+  atomicAdd(grad + OFF_B2 + t, ga2[t]);
+  for (int e = t; e < NH * NI; e += blockDim.x) atomicAdd(grad + OFF_W1 + e, ga1[e / NI] * s[e % NI]);
+  atomicAdd(grad + OFF_B1 + t, ga1[t]);
+}
+
+// Adam (Kingma & Ba 2015) on the float32 master copy, bfloat16 weights refreshed, gradient cleared.
+__global__ void mdn_adam_kernel(float *master, __nv_bfloat16 *w, float *grad, float *m, float *v, int n, float lr,
+                                float bc1, float bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = grad[i];
+  const float mm = 0.9f * m[i] + 0.1f * g;
+  const float vv = 0.999f * v[i] + 0.001f * g * g;
+  m[i] = mm;
+  v[i] = vv;
+  const float x = master[i] - lr * (mm / bc1) / (sqrtf(vv / bc2) + 1e-8f);
+  master[i] = x;
+  w[i] = __float2bfloat16_rn(x);
+  grad[i] = 0.f;
+}
+
+__global__ void mdn_round_kernel(const float *master, __nv_bfloat16 *w, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = __float2bfloat16_rn(master[i]);
+}
+
+// Per-point learned proposal for the sampler (layout RIFT_GMM_FLOATS) from the head; the
+// mixture weights are normalised in FP64 and rounded to float32 before their float32
+// cumulative sum, so the component choice can be reproduced exactly.  cst: [P][4] =
+// (sum ln(b - a), constant of ln p5, ln D_lo, ln D_hi - ln D_lo).
+__global__ void mdn_gmm_kernel(const float *__restrict__ head, const float *__restrict__ cst, int P,
+                               float *__restrict__ gmm) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float *h = head + (size_t)p * NO;
+  float *G = gmm + (size_t)p * RIFT_GMM_FLOATS;
+  double mx = -INFINITY;
+  for (int j = 0; j < NC; ++j) mx = fmax(mx, (double)h[j]);
+  double e[NC], se = 0.0;
+  for (int j = 0; j < NC; ++j) { e[j] = exp((double)h[j] - mx); se += e[j]; }
+  float cw = 0.f;
+  for (int j = 0; j < NC; ++j) {
+    const double pi = e[j] / se;
+    G[j] = (float)log(pi);
+    cw = __fadd_rn(cw, (float)pi);
+    G[8 + j] = cw;
+  }
+  for (int q = 0; q < NC * ND; ++q) {
+    const float l = fminf(fmaxf(h[NC + NC * ND + q], LS_MIN), LS_MAX);
+    G[16 + q] = h[NC + q];
+    G[56 + q] = l;
+    G[96 + q] = expf(-l);
+  }
+  for (int q = 0; q < 4; ++q) G[136 + q] = cst[(size_t)p * 4 + q];
+  for (int q = 140; q < RIFT_GMM_FLOATS; ++q) G[q] = 0.f;
+}
+
+// Summary of each point (64 features, layout as in the header).  One CTA per point.
+__global__ void __launch_bounds__(256) summary_kernel(const PointC *__restrict__ pts, const float2 *__restrict__ qa,
+                                                      const float4 *__restrict__ ca, const double *__restrict__ tau0,
+                                                      float *__restrict__ out) {
+  __shared__ __align__(16) PointC P;
+  __shared__ float red[8][8];
+  __shared__ float feats[NI];
+  __shared__ float tm22[RIFT_MAXK];
+  const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  {
+    const int *src = reinterpret_cast<const int *>(pts + p);
+    int *dst = reinterpret_cast<int *>(&P);
+    for (int i = t; i < (int)(sizeof(PointC) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  if (t < NI) feats[t] = 0.f;
+  __syncthreads();
+  const int K = P.K, T = P.T;
+  const float2 *Q = qa + P.q_off;
+  int nf = 0;
+  for (int k = 0; k < K; ++k) {
+    const float t0 = (float)tau0[(size_t)p * RIFT_MAXK + k];
+    for (int mi = 0; mi < 2; ++mi) {
+      const int want_m = mi == 0 ? 2 : -2;
+      int a = -1;
+      for (int q = 0; q < P.M; ++q)
+        if (P.mode[q].l == 2 && P.mode[q].m == want_m) a = q;
+      if (a < 0) {
+        if (mi == 0 && t == 0) tm22[k] = 0.f;
+        nf += 5;
+        continue;
+      }
+      // pass 1: max |Q|^2
+      float mx = 0.f;
+      for (int j = t; j < T; j += blockDim.x) {
+        const float2 q = Q[((size_t)k * T + j) * P.Mp + a];
+        mx = fmaxf(mx, __fadd_rn(__fmul_rn(q.x, q.x), __fmul_rn(q.y, q.y)));
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) red[0][wid] = mx;
+      __syncthreads();
+      mx = red[0][0];
+      for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[0][w]);
+      __syncthreads();
+      // pass 2: weights (|Q|^2 / max)^4: normalisation, mean time, weighted Q
+      float sw = 0.f, st = 0.f, sr = 0.f, si = 0.f;
+      for (int j = t; j < T; j += blockDim.x) {
+        const float2 q = Q[((size_t)k * T + j) * P.Mp + a];
+        const float r = __fadd_rn(__fmul_rn(q.x, q.x), __fmul_rn(q.y, q.y)) / mx;
+        const float r2 = r * r, w = r2 * r2;
+        sw += w; st += w * ((float)j / P.fs); sr += w * q.x; si += w * q.y;
+      }
+      float v[4] = {sw, st, sr, si};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0) red[1 + q][wid] = v[q];
+      }
+      __syncthreads();
+      float S[4];
+      for (int q = 0; q < 4; ++q) {
+        S[q] = 0.f;
+        for (int w = 0; w < 8; ++w) S[q] += red[1 + q][w];
+      }
+      const float tmr = S[1] / S[0];   // mean time relative to the first sample
+      __syncthreads();
+      // pass 3: spread about the mean
+      float sv = 0.f;
+      for (int j = t; j < T; j += blockDim.x) {
+        const float2 q = Q[((size_t)k * T + j) * P.Mp + a];
+        const float r = __fadd_rn(__fmul_rn(q.x, q.x), __fmul_rn(q.y, q.y)) / mx;
+        const float r2 = r * r, w = r2 * r2;
+        const float d = (float)j / P.fs - tmr;
+        sv += w * d * d;
+      }
+      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+      if (lane == 0) red[5][wid] = sv;
+      __syncthreads();
+      if (t == 0) {
+        float V = 0.f;
+        for (int w = 0; w < 8; ++w) V += red[5][w];
+        const float tm = t0 + tmr;
+        const float ph = atan2f(S[3], S[2]);
+        feats[nf + 0] = tm;
+        feats[nf + 1] = sqrtf(V / S[0]);
+        feats[nf + 2] = (logf(mx) * 4.f + logf(S[0] / (float)T)) / 8.f;
+        feats[nf + 3] = cosf(ph);
+        feats[nf + 4] = sinf(ph);
+        if (mi == 0) tm22[k] = tm;
+      }
+      __syncthreads();
+      nf += 5;
+    }
+  }
+  if (t == 0) {
+    // log sqrt(U_aa) of (2,2), (2,-2) per detector, from the diagonal pair coefficients
+    const int M = P.M;
+    for (int k = 0; k < K; ++k)
+      for (int mi = 0; mi < 2; ++mi) {
+        const int want_m = mi == 0 ? 2 : -2;
+        int a = -1;
+        for (int q = 0; q < M; ++q)
+          if (P.mode[q].l == 2 && P.mode[q].m == want_m) a = q;
+        float f = 0.f;
+        if (a >= 0) {
+          const int pair = a * M - a * (a - 1) / 2;   // index of (a, a) in the upper triangle
+          f = 0.5f * logf(ca[P.uv_off + (size_t)pair * K + k].x);
+        }
+        if (nf < NI) feats[nf] = f;
+        ++nf;
+      }
+    for (int i = 0; i < K; ++i)
+      for (int j = i + 1; j < K; ++j) {
+        if (nf < NI) feats[nf] = tm22[i] - tm22[j];
+        ++nf;
+      }
+  }
+  __syncthreads();
+  if (t < NI) out[(size_t)p * NI + t] = feats[t];
+}
+
+// Harvest: systematic resampling of H samples of each point from its last round, with
+// probabilities proportional to exp(beta (l - max l)); outputs theta5 and the sample index.
+__global__ void __launch_bounds__(256) harvest_kernel(const float *__restrict__ ell, const RoundPt *__restrict__ rp,
+                                                      const AccState *__restrict__ acc, float beta, int H,
+                                                      float *__restrict__ cdf_scratch, int *__restrict__ idx_out) {
+  const int p = blockIdx.x;
+  const RoundPt &R = rp[p];
+  __shared__ float carry;
+  __shared__ float wsum[8];
+  if (R.n == 0 || R.ell_off < 0) {
+    for (int h = threadIdx.x; h < H; h += blockDim.x) idx_out[(size_t)p * H + h] = -1;
+    return;
+  }
+  const float mx = (float)acc[p].round_max;
+  const float *e = ell + R.ell_off;
+  float *c = cdf_scratch + R.ell_off;
+  if (threadIdx.x == 0) carry = 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint32_t base = 0; base < R.n; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    float w = (i < R.n && isfinite(e[i])) ? expf(beta * (e[i] - mx)) : 0.f;
+    // inclusive block scan
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane == 31) wsum[wid] = w;
+    __syncthreads();
+    float off = carry;
+    for (int q = 0; q < wid; ++q) off += wsum[q];
+    w += off;
+    if (i < R.n) c[i] = w;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = w;
+    __syncthreads();
+  }
+  const float tot = carry;
+  for (int h = threadIdx.x; h < H; h += blockDim.x) {
+    const float target = ((float)h + 0.5f) / (float)H * tot;
+    int lo = 0, hi = (int)R.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (c[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    idx_out[(size_t)p * H + h] = lo;
+  }
+}
+
+}  // namespace
+
+struct rift_mdn {
+  float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+  __nv_bfloat16 *w = nullptr;
+  int step = 0;
+  std::string err;
+  // training scratch
+  float *head = nullptr, *cache = nullptr, *gout = nullptr, *loss = nullptr;
+  int cap = 0;
+};
+
+namespace {
+
+rift_status mfail(rift_mdn *m, rift_status s, const std::string &msg) {
+  if (m) m->err = msg;
+  return s;
+}
+
+#define MCK(m, call)                                                                        \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return mfail(m, RIFT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+rift_status mdn_scratch(rift_mdn *m, int P) {
+  if (P <= m->cap) return RIFT_OK;
+  cudaFree(m->head); cudaFree(m->cache); cudaFree(m->gout); cudaFree(m->loss);
+  m->head = m->cache = m->gout = m->loss = nullptr;
+  m->cap = 0;
+  MCK(m, cudaMalloc(&m->head, sizeof(float) * (size_t)P * NO));
+  MCK(m, cudaMalloc(&m->cache, sizeof(float) * (size_t)P * 2 * NH));
+  MCK(m, cudaMalloc(&m->gout, sizeof(float) * (size_t)P * NO));
+  MCK(m, cudaMalloc(&m->loss, sizeof(float) * (size_t)P));
+  m->cap = P;
+  return RIFT_OK;
+}
+
+// Philox-based initialisation: uniform(-1, 1) * sqrt(3 / fan_in) (variance 1 / fan_in), biases 0.
+void init_params(uint64_t seed, std::vector<float> &out) {
+  out.assign(NPARAM, 0.f);
+  auto fill = [&](int off, int rows, int cols, uint32_t tag) {
+    const double sc = std::sqrt(3.0 / cols);
+    for (int i = 0; i < rows * cols; ++i) {
+      // Philox4x32-10 of (i, tag, 0, 0) with the seed as key; first word
+      uint32_t c0 = (uint32_t)i, c1 = tag, c2 = 0, c3 = 0;
+      uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+      for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0, n1 = (uint32_t)p1, n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1,
+                       n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+      }
+      const double u = ((c0 >> 9) + 0.5) / 8388608.0;
+      out[off + i] = (float)((2.0 * u - 1.0) * sc);
+    }
+  };
+  fill(OFF_W1, NH, NI, 1);
+  fill(OFF_W2, NH, NH, 2);
+  fill(OFF_W3, NO, NH, 3);
+}
+
+}  // namespace
+
+extern "C" {
+
+rift_status rift_mdn_create(uint64_t seed, rift_mdn **out) {
+  if (!out) return RIFT_EINVAL;
+  *out = nullptr;
+  rift_mdn *m = new (std::nothrow) rift_mdn();
+  if (!m) return RIFT_ENOMEM;
+  std::vector<float> init;
+  init_params(seed, init);
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->master, sizeof(float) * NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc(&m->m, sizeof(float) * NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc(&m->v, sizeof(float) * NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc(&m->grad, sizeof(float) * NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc(&m->w, sizeof(__nv_bfloat16) * NPARAM)) != cudaSuccess ||
+      (e = cudaMemcpy(m->master, init.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(m->m, 0, sizeof(float) * NPARAM)) != cudaSuccess ||
+      (e = cudaMemset(m->v, 0, sizeof(float) * NPARAM)) != cudaSuccess ||
+      (e = cudaMemset(m->grad, 0, sizeof(float) * NPARAM)) != cudaSuccess) {
+    rift_mdn_destroy(m);
+    return e == cudaErrorMemoryAllocation ? RIFT_ENOMEM : RIFT_ECUDA;
+  }
+  mdn_round_kernel<<<(NPARAM + 255) / 256, 256>>>(m->master, m->w, NPARAM);
+  if (cudaDeviceSynchronize() != cudaSuccess) { rift_mdn_destroy(m); return RIFT_ECUDA; }
+  *out = m;
+  return RIFT_OK;
+}
+
+void rift_mdn_destroy(rift_mdn *m) {
+  if (!m) return;
+  cudaFree(m->master); cudaFree(m->m); cudaFree(m->v); cudaFree(m->grad); cudaFree(m->w);
+  cudaFree(m->head); cudaFree(m->cache); cudaFree(m->gout); cudaFree(m->loss);
+  delete m;
+}
+
+const char *rift_mdn_last_error(const rift_mdn *m) { return m ? m->err.c_str() : "null handle"; }
+
+rift_status rift_mdn_set_params(rift_mdn *m, const float *host) {
+  if (!m || !host) return RIFT_EINVAL;
+  MCK(m, cudaMemcpy(m->master, host, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+  MCK(m, cudaMemset(m->m, 0, sizeof(float) * NPARAM));
+  MCK(m, cudaMemset(m->v, 0, sizeof(float) * NPARAM));
+  MCK(m, cudaMemset(m->grad, 0, sizeof(float) * NPARAM));
+  m->step = 0;
+  mdn_round_kernel<<<(NPARAM + 255) / 256, 256>>>(m->master, m->w, NPARAM);
+  MCK(m, cudaDeviceSynchronize());
+  return RIFT_OK;
+}
+
+rift_status rift_mdn_get_params(rift_mdn *m, float *host, int which) {
+  if (!m || !host) return RIFT_EINVAL;
+  if (which == 0) {
+    MCK(m, cudaMemcpy(host, m->master, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<__nv_bfloat16> b(NPARAM);
+    MCK(m, cudaMemcpy(b.data(), m->w, sizeof(__nv_bfloat16) * NPARAM, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < NPARAM; ++i) host[i] = __bfloat162float(b[i]);
+  }
+  return RIFT_OK;
+}
+
+rift_status rift_mdn_forward(rift_mdn *m, int n, const float *summ_dev, float *head_dev) {
+  if (!m || n < 0 || (n && (!summ_dev || !head_dev))) return RIFT_EINVAL;
+  if (n == 0) return RIFT_OK;
+  mdn_forward_kernel<<<n, 256>>>(m->w, summ_dev, n, head_dev, nullptr);
+  MCK(m, cudaGetLastError());
+  MCK(m, cudaDeviceSynchronize());
+  return RIFT_OK;
+}
+
+rift_status rift_mdn_loss_grad(rift_mdn *m, int n, const float *summ_dev, const float *theta_dev, const float *w_dev,
+                               int H, const float *box_dev, double *loss_out, float *grad_host) {
+  if (!m || n < 1 || H < 1 || !summ_dev || !theta_dev || !w_dev || !box_dev) return RIFT_EINVAL;
+  rift_status s = mdn_scratch(m, n);
+  if (s != RIFT_OK) return s;
+  MCK(m, cudaMemset(m->grad, 0, sizeof(float) * NPARAM));
+  mdn_forward_kernel<<<n, 256>>>(m->w, summ_dev, n, m->head, m->cache);
+  mdn_loss_kernel<<<n, 128>>>(m->head, theta_dev, w_dev, box_dev, H, 1.f / n, m->gout, m->loss);
+  mdn_backward_kernel<<<n, 256>>>(m->w, summ_dev, m->cache, m->gout, n, m->grad);
+  MCK(m, cudaGetLastError());
+  std::vector<float> l(n);
+  MCK(m, cudaMemcpy(l.data(), m->loss, sizeof(float) * n, cudaMemcpyDeviceToHost));
+  double tot = 0.0;
+  for (float x : l) tot += x;
+  if (loss_out) *loss_out = tot / n;
+  if (grad_host) MCK(m, cudaMemcpy(grad_host, m->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+  MCK(m, cudaMemset(m->grad, 0, sizeof(float) * NPARAM));
+  return RIFT_OK;
+}
+
+rift_status rift_mdn_train(rift_mdn *m, int n, const float *summ_dev, const float *theta_dev, const float *w_dev,
+                           int H, const float *box_dev, int steps, int batch, double lr, double *loss_per_step) {
+  if (!m || n < 1 || H < 1 || steps < 0 || !summ_dev || !theta_dev || !w_dev || !box_dev || !(lr > 0))
+    return RIFT_EINVAL;
+  if (batch < 1 || batch > n) batch = n;
+  rift_status s = mdn_scratch(m, batch);
+  if (s != RIFT_OK) return s;
+  for (int it = 0; it < steps; ++it) {
+    const int p0 = (int)(((long long)it * batch) % n);
+    const int nb = std::min(batch, n - p0);
+    const float *S = summ_dev + (size_t)p0 * NI;
+    const float *th = theta_dev + (size_t)p0 * H * ND;
+    const float *w = w_dev + (size_t)p0 * H;
+    const float *bx = box_dev + (size_t)p0 * 10;
+    mdn_forward_kernel<<<nb, 256>>>(m->w, S, nb, m->head, m->cache);
+    mdn_loss_kernel<<<nb, 128>>>(m->head, th, w, bx, H, 1.f / nb, m->gout, m->loss);
+    mdn_backward_kernel<<<nb, 256>>>(m->w, S, m->cache, m->gout, nb, m->grad);
+    m->step += 1;
+    const float bc1 = 1.f - std::pow(0.9f, (float)m->step), bc2 = 1.f - std::pow(0.999f, (float)m->step);
+    mdn_adam_kernel<<<(NPARAM + 255) / 256, 256>>>(m->master, m->w, m->grad, m->m, m->v, NPARAM, (float)lr, bc1, bc2);
+    MCK(m, cudaGetLastError());
+    if (loss_per_step) {
+      std::vector<float> l(nb);
+      MCK(m, cudaMemcpy(l.data(), m->loss, sizeof(float) * nb, cudaMemcpyDeviceToHost));
+      double tot = 0.0;
+      for (float x : l) tot += x;
+      loss_per_step[it] = tot / nb;
+    }
+  }
+  MCK(m, cudaDeviceSynchronize());
+  return RIFT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- used by capi.cu
+cudaError_t launch_summary(const PointC *pts, const float2 *qa, const float4 *ca, const double *tau0, int np,
+                           float *out, cudaStream_t st) {
+  summary_kernel<<<np, 256, 0, st>>>(pts, qa, ca, tau0, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mdn_gmm(const rift_mdn *m, const float *summ, const float *cst, int np, float *head_scratch,
+                           float *gmm, cudaStream_t st) {
+  mdn_forward_kernel<<<np, 256, 0, st>>>(m->w, summ, np, head_scratch, nullptr);
+  mdn_gmm_kernel<<<(np + 127) / 128, 128, 0, st>>>(head_scratch, cst, np, gmm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gmm_from_head(const float *head, const float *cst, int np, float *gmm, cudaStream_t st) {
+  mdn_gmm_kernel<<<(np + 127) / 128, 128, 0, st>>>(head, cst, np, gmm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_harvest(const float *ell, const RoundPt *rp, const AccState *acc, int np, float beta, int H,
+                           float *cdf_scratch, int *idx_out, cudaStream_t st) {
+  harvest_kernel<<<np, 256, 0, st>>>(ell, rp, acc, beta, H, cdf_scratch, idx_out);
+  return cudaGetLastError();
+}

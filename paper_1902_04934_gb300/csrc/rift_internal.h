@@ -45,7 +45,13 @@ struct RoundPt {
   long long dbg_off;       // offset in the caller's dbg_ell (-1: none)
   const float *tab;        // [3][nb+1] float32 CDF tables
   const float *lnw;        // [3][nb]   -ln(nb p_b)
+  const float *gmm;        // [RIFT_GMM_FLOATS] learned proposal of the point (proposal 2)
 };
+
+// Learned proposal of one point as the sampler reads it (floats): ln pi[8], float32 cumulative
+// pi[8], mu[8][5], ln sigma[8][5], 1/sigma[8][5], sum_d ln(b_d - a_d), the constant part of
+// ln p5, ln D_lo, ln D_hi - ln D_lo, pad.
+#define RIFT_GMM_FLOATS 144
 
 // Arguments of the cell kernel.
 struct CellLaunch {
@@ -67,6 +73,7 @@ struct CellLaunch {
   int max_M;                   // largest mode count over the points (shared-memory layout)
   int max_pairK;               // largest npair * K over the points
   int max_nb;                  // largest bin count (0 if no point uses tables)
+  int learned;                 // every point samples from its learned proposal
 };
 
 // Device-side round control of a batched run replayed as a CUDA graph.
@@ -101,6 +108,10 @@ struct BatchCtl {
   int nb;
   float *tables;            // [2][np][3][nb+1]
   float *lnw;               // [2][np][3][nb]
+  int learned;              // points sample from their learned proposals (gmm)
+  int keep_ell;             // keep per-sample log weights of every round (harvest)
+  const float *gmm;         // [np][RIFT_GMM_FLOATS]
+  RoundPt *last;            // [np] the last round each point ran (harvest)
 };
 
 // Scratch of the Monte Carlo runner (device pointers unless noted).
@@ -150,6 +161,16 @@ cudaError_t launch_round_update(const BatchCtl &B, PtState *st_dev, const AccSta
 cudaError_t launch_hist_ctl(const float *ell, const uint32_t *bins, const RoundPt *rp, int n_points,
                             const AccState *acc, float beta, int nb, unsigned long long *part, int hblocks,
                             const RoundCtl *ctl, cudaStream_t st);
+cudaError_t launch_harvest_theta(const CellLaunch &L, const RoundPt *last, const int *idx, int H, float *theta,
+                                 cudaStream_t st);
+cudaError_t launch_summary(const PointC *pts, const float2 *qa, const float4 *ca, const double *tau0, int np,
+                           float *out, cudaStream_t st);
+struct rift_mdn;
+cudaError_t launch_mdn_gmm(const rift_mdn *m, const float *summ, const float *cst, int np, float *head_scratch,
+                           float *gmm, cudaStream_t st);
+cudaError_t launch_gmm_from_head(const float *head, const float *cst, int np, float *gmm, cudaStream_t st);
+cudaError_t launch_harvest(const float *ell, const RoundPt *rp, const AccState *acc, int np, float beta, int H,
+                           float *cdf_scratch, int *idx_out, cudaStream_t st);
 cudaError_t launch_tables_ctl(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points, int nb,
                               double floor_eps, const BatchCtl &B, const RoundCtl *ctl, cudaStream_t st);
 
