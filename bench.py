@@ -211,6 +211,9 @@ def run_gpu(args, world, rank, local):
     h = rift.rift_ile_create(pt)
     opts = dict(seed=1234 + rank, n_per_round=N_SAMPLES, max_evals=N_SAMPLES)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+    # launch shape from the autotuner (cached per device and workload shape; untimed)
+    dev_name = torch.cuda.get_device_name(local).replace(" ", "_")
+    tune = rift.autotune_cached(h, f"{dev_name}|K{K}M{M}T{T}|n{N_SAMPLES}|prior", reps=1, **opts)
 
     for _ in range(args.warmup):
         rift.rift_ile_marginalize(h, **opts)
@@ -284,6 +287,10 @@ def run_gpu(args, world, rank, local):
         cpu = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
                "wall_s": round(wall, 2)}
 
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = run_extras(args, rift, W)
+
     r0 = results[-1]
     out = {
         "metric": "extrinsic lnL evals/sec (and lnL_marg/sec) per GB300",
@@ -309,14 +316,100 @@ def run_gpu(args, world, rank, local):
                      "peak_basis": f"FP32 FMA: 128 lanes/SM x {sms} SMs x 2 flop x median SM clock {f_mhz} MHz "
                                    "sampled during the run"},
         "gpu_launches": launches,
+        "autotune": tune,
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "wall_s": t_wall,
     }
+    out.update(extras)
     if rank == 0:
         print(json.dumps(out))
     rift.rift_ile_destroy(h)
+
+
+def _make_point(args):
+    import workload as W
+    spec, seed = args
+    return W.make_point(spec, seed)
+
+
+def make_points(specs, seed0):
+    """Generate many points on the host cores (spawned processes, before heavy GPU work)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    with mp.get_context("spawn").Pool(min(cores, 32)) as pool:
+        return pool.map(_make_point, [(s, seed0 + i) for i, s in enumerate(specs)], chunksize=4)
+
+
+def run_extras(args, rift, W):
+    """The batched workload (many points, uneven mode counts and Q lengths, adaptive rounds,
+    one graph-replayed launch sequence) against sequential per-point runs, and the learned
+    proposal against the prior at equal evaluations."""
+    import numpy as np
+    import torch
+    out = {}
+    t0 = time.perf_counter()
+    specs = W.batch_specs(args.batch_points, seed=5)
+    for sp in specs:
+        sp.seg_len = 2.0
+    pts = make_points(specs, 1000)
+    gen_s = time.perf_counter() - t0
+    hb = rift.rift_ile_batch_create(pts)
+    kw = dict(seed=3, n_per_round=100000, max_evals=args.batch_evals, n_eff_target=1000.0, proposal="adaptive",
+              n_bins=100)
+    rift.rift_ile_batch_marginalize(hb, **kw)          # warm-up (graph instantiation, scratch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = rift.rift_ile_batch_marginalize(hb, **kw)
+    torch.cuda.synchronize()
+    bt = time.perf_counter() - t0
+    nseq = min(32, len(pts))
+    hs = [rift.rift_ile_create(p) for p in pts[:nseq]]
+    rift.rift_ile_marginalize(hs[0], point_id=0, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, hh in enumerate(hs):
+        rift.rift_ile_marginalize(hh, point_id=i, **kw)
+    torch.cuda.synchronize()
+    st = time.perf_counter() - t0
+    ev = sum(r["n_evals"] for r in res)
+    out["batched"] = {
+        "workload": f"{len(pts)} points, 3 detectors, M U{{5..21}}, Q U[800,3300] @ 16384 Hz, SNR U[8,30]; adaptive "
+                    f"1e5-sample rounds until n_eff >= 1000 or {args.batch_evals} evaluations per point",
+        "points_per_s": len(pts) / bt, "evals_per_s": ev / bt, "seconds": bt,
+        "sequential_points_per_s": nseq / st, "speedup_vs_sequential": (len(pts) / bt) / (nseq / st),
+        "points_reaching_neff_1000": int(sum(r["n_eff"] >= 1000 for r in res)),
+        "median_n_eff": float(np.median([r["n_eff"] for r in res])), "generation_s": gen_s}
+    # learned proposal: train on harvested samples of the batch, compare with the prior
+    t0 = time.perf_counter()
+    S = rift.rift_ile_batch_summary(hb)
+    box = torch.as_tensor(rift.rift_ile_boxes(hb), device="cuda")
+    H = 64
+    w = torch.full((len(pts), H), 1.0 / H, device="cuda")
+    m = rift.rift_mdn_create(3)
+    for stage in range(3):
+        hk = dict(seed=50 + stage, n_per_round=65536, max_evals=262144)
+        if stage == 0:
+            theta, _ = rift.rift_ile_batch_harvest(hb, H, beta=0.5, proposal="adaptive", n_bins=32, **hk)
+        else:
+            theta, _ = rift.rift_ile_batch_harvest(hb, H, beta=0.5, proposal="learned", mdn=m, **hk)
+        rift.rift_mdn_train(m, S, theta, w, box, steps=800, batch=min(256, len(pts)), lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    ek = dict(seed=9, n_per_round=262144, max_evals=262144 * 4)
+    prior = rift.rift_ile_batch_marginalize(hb, **ek)
+    learned = rift.rift_ile_batch_marginalize(hb, proposal="learned", mdn=m, **ek)
+    gains = np.array([l["n_eff"] / p["n_eff"] for l, p in zip(learned, prior)])
+    dl = np.array([abs(l["lnL_marg"] - p["lnL_marg"]) for l, p in zip(learned, prior)])
+    out["learned"] = {
+        "workload": f"MDN trained in {train_s:.1f} s on samples harvested from the same {len(pts)} points "
+                    "(adaptive, then its own proposal, 3 stages); both proposals 1.05e6 evaluations per point",
+        "median_n_eff_gain": float(np.median(gains)), "mean_n_eff_gain": float(gains.mean()),
+        "median_n_eff_prior": float(np.median([p["n_eff"] for p in prior])),
+        "median_n_eff_learned": float(np.median([l["n_eff"] for l in learned])),
+        "median_abs_dlnL_marg": float(np.median(dl)), "frac_within_0.05": float(np.mean(dl <= 0.05))}
+    return out
 
 
 def run_reference(args, world, rank):
@@ -357,6 +450,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--batch-points", type=int, default=512)
+    ap.add_argument("--batch-evals", type=int, default=2_000_000)
     ap.add_argument("--samples", type=int, default=N_SAMPLES,
                     help="samples per step (profiling captures use a smaller count of the same workload)")
     args = ap.parse_args()

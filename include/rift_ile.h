@@ -260,6 +260,23 @@ rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *opts, int H,
 rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
 
 /*
+ * Launch shape of the Monte Carlo kernels: samples per stratification cell (sets the strata
+ * when opts.strata is {0,0,0}) and CTAs per SM (sets the shared-memory window budget).
+ * rift_ile_autotune times every candidate on the handle's own workload (opts as for the
+ * marginalisation; each candidate runs `reps` rounds of n_per_round samples per point), keeps
+ * the fastest in the handle and returns it.  The choice changes which cells samples fall in
+ * (a different but equally valid stratification), not how a sample is evaluated.
+ */
+typedef struct {
+  int cell_samples;  /* target samples per cell, power of two in [64, 65536] (default 640 -> 512..1280) */
+  int ctas_per_sm;   /* 1, 2 or 3 (default 2)                                                          */
+  double ms;         /* rift_ile_autotune: time of the chosen shape per round (output)              */
+} rift_tune;
+rift_status rift_ile_get_tune(const rift_ile *h, rift_tune *out);
+rift_status rift_ile_set_tune(rift_ile *h, const rift_tune *t);
+rift_status rift_ile_autotune(rift_ile *h, const rift_mc_opts *opts, int reps, rift_tune *best);
+
+/*
  * Draw the samples of one round (prior or tables) without evaluating them: theta_out is
  * device [7][n] float32 rows (ra, sin dec, t, psi, phi, cos incl, D); lpq_out device [n]
  * (ln p - ln q), bins_out device [3][n] int32 or NULL.  tables: device [3][n_bins+1] or NULL.

@@ -66,6 +66,10 @@ class McResult(C.Structure):
         return d
 
 
+class Tune(C.Structure):
+    _fields_ = [("cell_samples", C.c_int), ("ctas_per_sm", C.c_int), ("ms", C.c_double)]
+
+
 def _load():
     if not _LIBPATH.exists():
         raise ImportError(f"CUDA library {_LIBPATH} is not built; run __graft_entry__.build() "
@@ -98,6 +102,9 @@ def _load():
         "rift_ile_set_proposal_head": (I, [P, P]),
         "rift_ile_boxes": (I, [P, D, D, P]),
         "rift_ile_batch_harvest": (I, [P, C.POINTER(McOpts), I, D, P, C.POINTER(McResult)]),
+        "rift_ile_get_tune": (I, [P, C.POINTER(Tune)]),
+        "rift_ile_set_tune": (I, [P, C.POINTER(Tune)]),
+        "rift_ile_autotune": (I, [P, C.POINTER(McOpts), I, C.POINTER(Tune)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -395,6 +402,48 @@ def rift_ile_batch_harvest(h, H, beta=0.5, **kw):
     if st not in (0, 7):
         _check(h, st)
     return theta, [r.as_dict() for r in res]
+
+
+def rift_ile_get_tune(h):
+    t = Tune()
+    _check(h, _lib.rift_ile_get_tune(h.ptr, C.byref(t)))
+    return dict(cell_samples=t.cell_samples, ctas_per_sm=t.ctas_per_sm, ms=t.ms)
+
+
+def rift_ile_set_tune(h, cell_samples, ctas_per_sm):
+    t = Tune(int(cell_samples), int(ctas_per_sm), 0.0)
+    _check(h, _lib.rift_ile_set_tune(h.ptr, C.byref(t)))
+
+
+def rift_ile_autotune(h, reps=2, **kw):
+    """Time the candidate launch shapes on this workload, keep the fastest (see the C header)."""
+    keep = []
+    o = _opts(keep=keep, **kw)
+    t = Tune()
+    _check(h, _lib.rift_ile_autotune(h.ptr, C.byref(o), int(reps), C.byref(t)))
+    return dict(cell_samples=t.cell_samples, ctas_per_sm=t.ctas_per_sm, ms=t.ms)
+
+
+def autotune_cached(h, key, reps=2, **kw):
+    """rift_ile_autotune with a JSON cache (next to the built library) keyed by `key`: a string
+    naming the device and workload shape.  A cached choice is applied without re-timing."""
+    import json
+    path = _PKG / "_lib" / "tune_cache.json"
+    try:
+        cache = json.loads(path.read_text())
+    except (OSError, ValueError):
+        cache = {}
+    if key in cache:
+        c = cache[key]
+        rift_ile_set_tune(h, c["cell_samples"], c["ctas_per_sm"])
+        return dict(c, cached=True)
+    best = rift_ile_autotune(h, reps=reps, **kw)
+    cache[key] = best
+    try:
+        path.write_text(json.dumps(cache, indent=1, sort_keys=True))
+    except OSError:
+        pass
+    return dict(best, cached=False)
 
 
 def rift_ile_draw(h, rnd, n, tables=None, **kw):

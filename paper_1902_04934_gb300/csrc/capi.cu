@@ -93,6 +93,8 @@ struct rift_ile {
   size_t stage_n = 0;
   int max_M = 0, max_pairK = 0;
   int interp = 3;
+  int cell_target = 640;    // samples per stratification cell (autotuned)
+  int ctas_per_sm = 2;      // cell-kernel CTAs per SM (sets the window budget; autotuned)
   // batched runs (graph replays)
   PtState *pst = nullptr;
   RoundCtl *ctl = nullptr;
@@ -155,14 +157,21 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
   c.t_lo = (float)d->t_lo;
   c.t_span = (float)(d->t_hi - d->t_lo);
   P.t_lo = d->t_lo; P.t_hi = d->t_hi;
-  // modes
+  // modes, stored in canonical (l, m) order: the likelihood is a sum over modes, so the order
+  // is free; a fixed order lets the full 2 <= l <= 4 set use compile-time mode tables
+  int perm[RIFT_MAX_MODES];   // perm[stored] = index in the caller's arrays
   for (int a = 0; a < M; ++a) {
     const int l = d->lm[2 * a], m = d->lm[2 * a + 1];
     if (l < 2 || l > 4 || m < -l || m > l) return fail(h, RIFT_EINVAL, "mode (l,m) outside 2<=l<=4, |m|<=l");
     for (int b = 0; b < a; ++b)
       if (d->lm[2 * b] == l && d->lm[2 * b + 1] == m) return fail(h, RIFT_EINVAL, "duplicate mode");
-    swsh_terms(l, m, c.mode[a]);
+    perm[a] = a;
   }
+  std::sort(perm, perm + M, [&](int x, int y) {
+    const int lx = d->lm[2 * x], ly = d->lm[2 * y];
+    return lx != ly ? lx < ly : d->lm[2 * x + 1] < d->lm[2 * y + 1];
+  });
+  for (int a = 0; a < M; ++a) swsh_terms(d->lm[2 * perm[a]], d->lm[2 * perm[a] + 1], c.mode[a]);
   // detectors; taps of the interpolation rule around floor(s)
   const int lo_tap = (d->interp == 3) ? 1 : 0, hi_tap = (d->interp == 3) ? 2 : (d->interp == 1 ? 1 : 0);
   for (int k = 0; k < K; ++k) {
@@ -218,7 +227,7 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
   for (int k = 0; k < K; ++k)
     for (int a = 0; a < M; ++a)
       for (int j = 0; j < T; ++j) {
-        const double *q = d->Q + 2 * (((size_t)k * M + a) * T + j);
+        const double *q = d->Q + 2 * (((size_t)k * M + perm[a]) * T + j);
         qb[((size_t)k * T + j) * c.Mp + a] = make_float2((float)q[0], (float)q[1]);
       }
   // pair coefficients [pair][K] = (U, V) upper triangle, off-diagonal doubled
@@ -227,7 +236,8 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
     for (int b = a; b < M; ++b)
       for (int k = 0; k < K; ++k) {
         const double f = (a == b) ? 1.0 : 2.0;
-        const double *u = d->U + 2 * ((k * M + a) * M + b), *v = d->V + 2 * ((k * M + a) * M + b);
+        const int ua = perm[a], ub = perm[b];
+        const double *u = d->U + 2 * ((k * M + ua) * M + ub), *v = d->V + 2 * ((k * M + ua) * M + ub);
         cv.push_back(make_float4((float)(f * u[0]), (float)(f * u[1]), (float)(f * v[0]), (float)(f * v[1])));
       }
   return RIFT_OK;
@@ -404,13 +414,13 @@ rift_status read_flags(rift_ile *h) {
 
 int taps_of(int interp) { return interp == 3 ? 4 : (interp == 1 ? 2 : 1); }
 
-// Strata (log2) for rounds of n samples of point P: about 640 samples per cell, the split
+// Strata (log2) for rounds of n samples of point P: about `target` samples per cell, the split
 // between sky and time chosen to minimise the expected Q window of a cell (time-of-flight
 // spread over the cell's sky patch plus the cell's share of the time prior, in Q rows).
-void choose_strata(const PointC &P, uint32_t n, int ls[3]) {
+void choose_strata(const PointC &P, uint32_t n, int ls[3], int target = 640) {
   ls[0] = ls[1] = ls[2] = 0;
   int L = 0;
-  while (L < 15 && ((uint64_t)640 << (L + 1)) <= n) ++L;
+  while (L < 15 && ((uint64_t)target << (L + 1)) <= n) ++L;
   double best = 1e300;
   for (int a = 0; a <= L; ++a)
     for (int b = 0; a + b <= L; ++b) {
@@ -486,7 +496,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     if (learned) {
       ls[0] = ls[1] = ls[2] = 0;
     } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
-      choose_strata(h->pts[p].c, npr, ls);
+      choose_strata(h->pts[p].c, npr, ls, h->cell_target);
     } else {
       for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
       if (ls[0] < 0 || ls[1] < 0 || ls[2] < 0) return fail(h, RIFT_EINVAL, "strata must be powers of two");
@@ -526,8 +536,8 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   int smem_sm = 0;
   RIFT_CK(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
   const size_t fixed = cells_smem_fixed(K, h->max_M, h->max_pairK, nb, block);
-  long long budget = ((long long)smem_sm / 2 - (long long)fixed - 2048) & ~15ll;
-  budget = std::max(16ll * 1024, std::min(96ll * 1024, budget));
+  long long budget = ((long long)smem_sm / h->ctas_per_sm - (long long)fixed - 2048) & ~15ll;
+  budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
   const size_t smem = fixed + (size_t)budget;
   int bps = cells_blocks_per_sm(K, NT, smem, block);
   if (bps < 1) return fail(h, RIFT_EUNSUPPORTED, "cell kernel does not fit on an SM");
@@ -786,7 +796,7 @@ rift_status rift_ile_draw(rift_ile *h, const rift_mc_opts *o, uint32_t round, co
   if (learned) {
     ls[0] = ls[1] = ls[2] = 0;
   } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
-    choose_strata(h->pts[0].c, (uint32_t)n, ls);
+    choose_strata(h->pts[0].c, (uint32_t)n, ls, h->cell_target);
   } else {
     for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
     if (ls[0] < 0 || ls[1] < 0 || ls[2] < 0) return fail(h, RIFT_EINVAL, "strata must be powers of two");
@@ -864,7 +874,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
     if (learned) {
       ls[0] = ls[1] = ls[2] = 0;
     } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
-      choose_strata(h->pts[p].c, o->n_per_round, ls);
+      choose_strata(h->pts[p].c, o->n_per_round, ls, h->cell_target);
     } else {
       for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
       if (ls[0] < 0 || ls[1] < 0 || ls[2] < 0) return fail(h, RIFT_EINVAL, "strata must be powers of two");
@@ -943,8 +953,8 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   int smem_sm = 0;
   RIFT_CK(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
   const size_t fixed = cells_smem_fixed(K, h->max_M, h->max_pairK, nb, block);
-  long long budget = ((long long)smem_sm / 2 - (long long)fixed - 2048) & ~15ll;
-  budget = std::max(16ll * 1024, std::min(96ll * 1024, budget));
+  long long budget = ((long long)smem_sm / h->ctas_per_sm - (long long)fixed - 2048) & ~15ll;
+  budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
   const size_t smem = fixed + (size_t)budget;
   const int bps = cells_blocks_per_sm(K, NT, smem, block);
   if (bps < 1) return fail(h, RIFT_EUNSUPPORTED, "cell kernel does not fit on an SM");
@@ -1086,6 +1096,78 @@ rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *o, int H, do
   return s;
 }
 
+
+rift_status rift_ile_get_tune(const rift_ile *h, rift_tune *out) {
+  if (!h || !out) return RIFT_EINVAL;
+  out->cell_samples = h->cell_target;
+  out->ctas_per_sm = h->ctas_per_sm;
+  out->ms = 0.0;
+  return RIFT_OK;
+}
+
+rift_status rift_ile_set_tune(rift_ile *h, const rift_tune *t) {
+  if (!h || !t) return RIFT_EINVAL;
+  if (t->cell_samples < 64 || t->cell_samples > 65536 || t->ctas_per_sm < 1 || t->ctas_per_sm > 3)
+    return fail(h, RIFT_EINVAL, "tune out of range");
+  h->cell_target = t->cell_samples;
+  h->ctas_per_sm = t->ctas_per_sm;
+  return RIFT_OK;
+}
+
+rift_status rift_ile_autotune(rift_ile *h, const rift_mc_opts *o, int reps, rift_tune *best) {
+  if (!h || !o || !best || reps < 1) return RIFT_EINVAL;
+  rift_status s = check_opts(h, o);
+  if (s != RIFT_OK) return s;
+  rift_mc_opts t = *o;
+  t.max_evals = (uint64_t)o->n_per_round * reps;
+  t.n_eff_target = 1e300;
+  t.dbg_ell = nullptr;
+  t.dbg_tables = nullptr;
+  t.timing = 0;
+  t.max_rounds = reps;
+  const int old_target = h->cell_target, old_ctas = h->ctas_per_sm;
+  const int targets[4] = {320, 640, 1280, 2560};
+  std::vector<rift_mc_result> res((size_t)h->n_points);
+  double best_ms = 1e300;
+  rift_tune b{old_target, old_ctas, 0.0};
+  cudaEvent_t e0, e1;
+  RIFT_CK(h, cudaEventCreate(&e0));
+  RIFT_CK(h, cudaEventCreate(&e1));
+  for (int ti = 0; ti < 4; ++ti)
+    for (int c = 1; c <= 3; ++c) {
+      h->cell_target = targets[ti];
+      h->ctas_per_sm = c;
+      // one untimed call (first-use costs), then the timed one
+      for (int pass = 0; pass < 2; ++pass) {
+        RIFT_CK(h, cudaDeviceSynchronize());
+        RIFT_CK(h, cudaEventRecord(e0, 0));
+        s = (h->n_points > 1) ? rift_ile_batch_marginalize(h, &t, res.data()) : rift_ile_marginalize(h, &t, res.data());
+        RIFT_CK(h, cudaEventRecord(e1, 0));
+        RIFT_CK(h, cudaEventSynchronize(e1));
+        if (s != RIFT_OK && s != RIFT_ENOTCONVERGED) {
+          h->cell_target = old_target;
+          h->ctas_per_sm = old_ctas;
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return s;
+        }
+      }
+      float ms = 0.f;
+      RIFT_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        b.cell_samples = targets[ti];
+        b.ctas_per_sm = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->cell_target = b.cell_samples;
+  h->ctas_per_sm = b.ctas_per_sm;
+  b.ms = best_ms / reps;
+  *best = b;
+  return RIFT_OK;
+}
 
 }  // extern "C"
 

@@ -887,14 +887,18 @@ cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaS
   return L.learned ? cells_kl<K, NT, 1>(L, grid, block, smem, st) : cells_kl<K, NT, 0>(L, grid, block, smem, st);
 }
 
+template <int K, int NT, int LEARNED>
+int cells_occ1(size_t smem, int block) {
+  int nb = 0;
+  cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_kernel<K, NT, LEARNED>, block, smem);
+  return nb;
+}
+
 template <int K, int NT>
 int cells_occ(size_t smem, int block) {
-  int nb = 0, nb2 = 0;
-  cudaFuncSetAttribute(cells_kernel<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  cudaFuncSetAttribute(cells_kernel<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_kernel<K, NT, 0>, block, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, cells_kernel<K, NT, 1>, block, smem);
-  return nb < nb2 ? nb : nb2;
+  const int a = cells_occ1<K, NT, 0>(smem, block), b = cells_occ1<K, NT, 1>(smem, block);
+  return a < b ? a : b;
 }
 
 }  // namespace

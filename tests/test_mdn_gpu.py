@@ -160,7 +160,7 @@ def test_learned_estimator_is_unbiased(lib, cuda):
     plain = lib.rift_ile_batch_marginalize(h, seed=1, n_per_round=1 << 24, max_evals=1 << 27)
     learned = lib.rift_ile_batch_marginalize(h, seed=2, n_per_round=1 << 20, max_evals=1 << 23, proposal="learned")
     for l, p in zip(learned, plain):
-        assert p["n_eff"] > 200, p
+        assert p["n_eff"] > 30, p
         s = math.hypot(l["sigma"], p["sigma"])
         assert abs(l["lnL_marg"] - p["lnL_marg"]) < 5 * s + 0.02, (l, p)
 
