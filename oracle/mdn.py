@@ -13,7 +13,8 @@ Readings (none of this is in the paper):
 * network: s (64) -> 256 -> 256 (GELU, erf form) -> 88 = 8 logits + 8x5 means + 8x5 log
   sigmas (clamped to [-8, 4]); weights rounded to bfloat16 (round to nearest even), activations
   and accumulation in float32 on the device, float64 here.
-* loss: weighted negative log likelihood of harvested posterior samples of each point,
+* loss: weighted negative log likelihood of harvested posterior samples of each point (box
+  fractions clipped to [1e-6, 1 - 1e-6] so samples rounded onto the box edge stay finite),
   -sum_i sum_j wbar_ij ln q_MDN(theta_ij | s_i) / n_points, minimised with Adam
   (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
 * sampling from uniforms u[0..9] of the sample's Philox stream: (u0,u1), (u2,u3), (u4,u5) ->
@@ -180,7 +181,8 @@ def nll_head_grad(head, th5, w, a, b):
     mu = head[N_COMP:N_COMP + N_COMP * N_DIM].reshape(N_COMP, N_DIM)
     ls_raw = head[N_COMP + N_COMP * N_DIM:].reshape(N_COMP, N_DIM)
     ls = np.clip(ls_raw, LS_MIN, LS_MAX)
-    x = (th5 - a) / (b - a)
+    # samples on the edge of the box (float rounding) are kept just inside it
+    x = np.clip((th5 - a) / (b - a), 1e-6, 1.0 - 1e-6)
     z = np.log(x) - np.log1p(-x)
     lpi = alpha - alpha.max()
     lpi = lpi - np.log(np.sum(np.exp(lpi)))

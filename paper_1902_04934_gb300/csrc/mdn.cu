@@ -99,11 +99,14 @@ __global__ void __launch_bounds__(128) mdn_loss_kernel(const float *__restrict__
   for (int q = 0; q <= NO; ++q) acc[q] = 0.f;
   const float *a = box + (size_t)p * 10, *b = a + 5;
   for (int j = t; j < H; j += blockDim.x) {
-    const float wj = w[(size_t)p * H + j];
+    float wj = w[(size_t)p * H + j];
     float z[ND], jac = 0.f;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      const float x = (th[((size_t)p * H + j) * ND + d] - a[d]) / (b[d] - a[d]);
+      const float v = th[((size_t)p * H + j) * ND + d];
+      if (!isfinite(v)) wj = 0.f;   // an empty harvest slot carries no weight
+      // samples on the edge of the box (float rounding) are kept just inside it
+      const float x = fminf(fmaxf((isfinite(v) ? v - a[d] : 0.f) / (b[d] - a[d]), 1e-6f), 1.f - 1e-6f);
       z[d] = logf(x) - log1pf(-x);
       jac += logf(b[d] - a[d]) + logf(x) + log1pf(-x);
     }
