@@ -134,6 +134,12 @@ def max_over_ranks(world, x: float) -> float:
     return float(t.item())
 
 
+def whole_job(world: int, local_ms: float, steps: int, units_per_rank: int):
+    """Whole-job time per step (the slowest rank) and throughput over all ranks' units."""
+    ms_per_step = max_over_ranks(world, local_ms) / steps
+    return ms_per_step, units_per_rank * world / (ms_per_step * 1e-3)
+
+
 def point_seed(rank: int) -> int:
     """Rank r marginalises its own independent point (weak scaling over points)."""
     return 2 + 1000 * rank
@@ -243,10 +249,8 @@ def run_gpu(args, world, rank, local):
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
 
-    total_ms = max_over_ranks(world, sum(step_ms))
-    ms_per_step = total_ms / args.steps
+    ms_per_step, value = whole_job(world, sum(step_ms), args.steps, N_SAMPLES)
     evals = N_SAMPLES * world
-    value = evals / (ms_per_step * 1e-3)
 
     # roofline of the likelihood kernel (FP32 ALU bound)
     taps = 4
