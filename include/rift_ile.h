@@ -261,15 +261,17 @@ rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_opts *opts, r
 
 /*
  * Launch shape of the Monte Carlo kernels: samples per stratification cell (sets the strata
- * when opts.strata is {0,0,0}) and CTAs per SM (sets the shared-memory window budget).
- * rift_ile_autotune times every candidate on the handle's own workload (opts as for the
- * marginalisation; each candidate runs `reps` rounds of n_per_round samples per point), keeps
- * the fastest in the handle and returns it.  The choice changes which cells samples fall in
- * (a different but equally valid stratification), not how a sample is evaluated.
+ * when opts.strata is {0,0,0}) and the shared-memory split (each cell-kernel CTA stages Q
+ * windows in the SM's shared memory / smem_split, less its fixed part; how many CTAs are
+ * resident is set by registers and shared memory).  rift_ile_autotune times every candidate
+ * on the handle's own workload (opts as for the marginalisation; each candidate runs `reps`
+ * rounds of n_per_round samples per point), keeps the fastest in the handle and returns it.
+ * The choice changes which cells samples fall in (a different but equally valid
+ * stratification), not how a sample is evaluated.
  */
 typedef struct {
-  int cell_samples;  /* target samples per cell, power of two in [64, 65536] (default 640 -> 512..1280) */
-  int ctas_per_sm;   /* 1, 2 or 3 (default 2)                                                          */
+  int cell_samples;  /* target samples per cell, in [64, 65536] (default 640 -> cells of 512..1280) */
+  int smem_split;    /* 1..8 (default 3)                                                            */
   double ms;         /* rift_ile_autotune: time of the chosen shape per round (output)              */
 } rift_tune;
 rift_status rift_ile_get_tune(const rift_ile *h, rift_tune *out);

@@ -67,7 +67,7 @@ class McResult(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("cell_samples", C.c_int), ("ctas_per_sm", C.c_int), ("ms", C.c_double)]
+    _fields_ = [("cell_samples", C.c_int), ("smem_split", C.c_int), ("ms", C.c_double)]
 
 
 def _load():
@@ -407,11 +407,11 @@ def rift_ile_batch_harvest(h, H, beta=0.5, **kw):
 def rift_ile_get_tune(h):
     t = Tune()
     _check(h, _lib.rift_ile_get_tune(h.ptr, C.byref(t)))
-    return dict(cell_samples=t.cell_samples, ctas_per_sm=t.ctas_per_sm, ms=t.ms)
+    return dict(cell_samples=t.cell_samples, smem_split=t.smem_split, ms=t.ms)
 
 
-def rift_ile_set_tune(h, cell_samples, ctas_per_sm):
-    t = Tune(int(cell_samples), int(ctas_per_sm), 0.0)
+def rift_ile_set_tune(h, cell_samples, smem_split):
+    t = Tune(int(cell_samples), int(smem_split), 0.0)
     _check(h, _lib.rift_ile_set_tune(h.ptr, C.byref(t)))
 
 
@@ -421,7 +421,7 @@ def rift_ile_autotune(h, reps=2, **kw):
     o = _opts(keep=keep, **kw)
     t = Tune()
     _check(h, _lib.rift_ile_autotune(h.ptr, C.byref(o), int(reps), C.byref(t)))
-    return dict(cell_samples=t.cell_samples, ctas_per_sm=t.ctas_per_sm, ms=t.ms)
+    return dict(cell_samples=t.cell_samples, smem_split=t.smem_split, ms=t.ms)
 
 
 def autotune_cached(h, key, reps=2, **kw):
@@ -433,9 +433,9 @@ def autotune_cached(h, key, reps=2, **kw):
         cache = json.loads(path.read_text())
     except (OSError, ValueError):
         cache = {}
-    if key in cache:
-        c = cache[key]
-        rift_ile_set_tune(h, c["cell_samples"], c["ctas_per_sm"])
+    c = cache.get(key)
+    if isinstance(c, dict) and "cell_samples" in c and "smem_split" in c:
+        rift_ile_set_tune(h, c["cell_samples"], c["smem_split"])
         return dict(c, cached=True)
     best = rift_ile_autotune(h, reps=reps, **kw)
     cache[key] = best

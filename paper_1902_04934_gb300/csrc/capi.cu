@@ -94,7 +94,7 @@ struct rift_ile {
   int max_M = 0, max_pairK = 0;
   int interp = 3;
   int cell_target = 640;    // samples per stratification cell (autotuned)
-  int ctas_per_sm = 2;      // cell-kernel CTAs per SM (sets the window budget; autotuned)
+  int smem_split = 3;       // shared-memory split of the cell kernel (sets the window budget; autotuned)
   // batched runs (graph replays)
   PtState *pst = nullptr;
   RoundCtl *ctl = nullptr;
@@ -171,7 +171,16 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
     const int lx = d->lm[2 * x], ly = d->lm[2 * y];
     return lx != ly ? lx < ly : d->lm[2 * x + 1] < d->lm[2 * y + 1];
   });
-  for (int a = 0; a < M; ++a) swsh_terms(d->lm[2 * perm[a]], d->lm[2 * perm[a] + 1], c.mode[a]);
+  for (int a = 0; a < M; ++a) {
+    swsh_terms(d->lm[2 * perm[a]], d->lm[2 * perm[a] + 1], c.mode[a]);
+    c.canon_mask |= 1u << canon_index(c.mode[a].l, c.mode[a].m);
+  }
+  for (int j = 0; j < RIFT_MAXM; ++j) {
+    ModeC t;
+    swsh_terms(canon_l(j), canon_m(j), t);
+    if (t.nterm != canon_rmax(j) - canon_rmin(j) + 1) return fail(h, RIFT_EINVAL, "internal: harmonic table");
+    for (int r = 0; r < t.nterm; ++r) c.ccoef[j][r] = t.coef[r];
+  }
   // detectors; taps of the interpolation rule around floor(s)
   const int lo_tap = (d->interp == 3) ? 1 : 0, hi_tap = (d->interp == 3) ? 2 : (d->interp == 1 ? 1 : 0);
   for (int k = 0; k < K; ++k) {
@@ -536,7 +545,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   int smem_sm = 0;
   RIFT_CK(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
   const size_t fixed = cells_smem_fixed(K, h->max_M, h->max_pairK, nb, block);
-  long long budget = ((long long)smem_sm / h->ctas_per_sm - (long long)fixed - 2048) & ~15ll;
+  long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
   budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
   const size_t smem = fixed + (size_t)budget;
   int bps = cells_blocks_per_sm(K, NT, smem, block);
@@ -953,7 +962,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   int smem_sm = 0;
   RIFT_CK(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
   const size_t fixed = cells_smem_fixed(K, h->max_M, h->max_pairK, nb, block);
-  long long budget = ((long long)smem_sm / h->ctas_per_sm - (long long)fixed - 2048) & ~15ll;
+  long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
   budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
   const size_t smem = fixed + (size_t)budget;
   const int bps = cells_blocks_per_sm(K, NT, smem, block);
@@ -1100,17 +1109,17 @@ rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *o, int H, do
 rift_status rift_ile_get_tune(const rift_ile *h, rift_tune *out) {
   if (!h || !out) return RIFT_EINVAL;
   out->cell_samples = h->cell_target;
-  out->ctas_per_sm = h->ctas_per_sm;
+  out->smem_split = h->smem_split;
   out->ms = 0.0;
   return RIFT_OK;
 }
 
 rift_status rift_ile_set_tune(rift_ile *h, const rift_tune *t) {
   if (!h || !t) return RIFT_EINVAL;
-  if (t->cell_samples < 64 || t->cell_samples > 65536 || t->ctas_per_sm < 1 || t->ctas_per_sm > 3)
+  if (t->cell_samples < 64 || t->cell_samples > 65536 || t->smem_split < 1 || t->smem_split > 8)
     return fail(h, RIFT_EINVAL, "tune out of range");
   h->cell_target = t->cell_samples;
-  h->ctas_per_sm = t->ctas_per_sm;
+  h->smem_split = t->smem_split;
   return RIFT_OK;
 }
 
@@ -1125,18 +1134,19 @@ rift_status rift_ile_autotune(rift_ile *h, const rift_mc_opts *o, int reps, rift
   t.dbg_tables = nullptr;
   t.timing = 0;
   t.max_rounds = reps;
-  const int old_target = h->cell_target, old_ctas = h->ctas_per_sm;
-  const int targets[4] = {320, 640, 1280, 2560};
+  const int old_target = h->cell_target, old_ctas = h->smem_split;
+  const int targets[3] = {320, 640, 1280}, splits[4] = {2, 3, 4, 6};
   std::vector<rift_mc_result> res((size_t)h->n_points);
   double best_ms = 1e300;
   rift_tune b{old_target, old_ctas, 0.0};
   cudaEvent_t e0, e1;
   RIFT_CK(h, cudaEventCreate(&e0));
   RIFT_CK(h, cudaEventCreate(&e1));
-  for (int ti = 0; ti < 4; ++ti)
-    for (int c = 1; c <= 3; ++c) {
+  for (int ti = 0; ti < 3; ++ti)
+    for (int si = 0; si < 4; ++si) {
+      const int c = splits[si];
       h->cell_target = targets[ti];
-      h->ctas_per_sm = c;
+      h->smem_split = c;
       // one untimed call (first-use costs), then the timed one
       for (int pass = 0; pass < 2; ++pass) {
         RIFT_CK(h, cudaDeviceSynchronize());
@@ -1146,7 +1156,7 @@ rift_status rift_ile_autotune(rift_ile *h, const rift_mc_opts *o, int reps, rift
         RIFT_CK(h, cudaEventSynchronize(e1));
         if (s != RIFT_OK && s != RIFT_ENOTCONVERGED) {
           h->cell_target = old_target;
-          h->ctas_per_sm = old_ctas;
+          h->smem_split = old_ctas;
           cudaEventDestroy(e0);
           cudaEventDestroy(e1);
           return s;
@@ -1157,13 +1167,13 @@ rift_status rift_ile_autotune(rift_ile *h, const rift_mc_opts *o, int reps, rift
       if (ms < best_ms) {
         best_ms = ms;
         b.cell_samples = targets[ti];
-        b.ctas_per_sm = c;
+        b.smem_split = c;
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->cell_target = b.cell_samples;
-  h->ctas_per_sm = b.ctas_per_sm;
+  h->smem_split = b.smem_split;
   b.ms = best_ms / reps;
   *best = b;
   return RIFT_OK;

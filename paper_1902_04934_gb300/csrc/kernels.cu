@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict
     float sphi, cphi, ch, sh;
     sincosf(phi[i], &sphi, &cphi);
     sincosf(0.5f * incl[i], &sh, &ch);
-    swsh_modes(P, ch, sh, cphi, sphi, Ys, ystride);
+    swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
     const float lin = linear_term<K, NT>(P, Q, g, Ys, ystride, flags);
     const float quad = quad_term<K>(P, C, g, Ys, ystride);
     const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);

@@ -353,7 +353,7 @@ __device__ __forceinline__ float linear_term_staged(const PointC &P, const float
 }
 
 template <int K, int NT, int LEARNED>
-__global__ void __launch_bounds__(RIFT_CELL_BLOCK) cells_kernel(CellLaunch L) {
+__global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel(CellLaunch L) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_item, s_point;
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK) cells_kernel(CellLaunch L) {
       g.x = d.xd;
       float sphi, cphi;
       sincospif(2.f * d.u_phi, &sphi, &cphi);
-      swsh_modes(P, sqrtf(d.c_frac), sqrtf(1.f - d.c_frac), cphi, sphi, Ys, ystride);
+      swsh_canonical(P, sqrtf(d.c_frac), sqrtf(1.f - d.c_frac), cphi, sphi, Ys, ystride);
       const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
       const float quad = quad_term<K>(P, C, g, Ys, ystride);
       const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);

@@ -45,7 +45,21 @@ struct PointC {
   float tmin_idx, tmax_idx; // first/last admissible interpolation base index (window check)
   DetC det[RIFT_MAXK];
   ModeC mode[RIFT_MAXM];
+  // the same harmonics by canonical index j (l = 2..4, m = -l..l in order): bit j of canon_mask
+  // is set when mode j is present; its terms r = r_min(j).. have coefficients ccoef[j][r - r_min(j)]
+  uint32_t canon_mask, pad2, pad3, pad4;
+  float ccoef[RIFT_MAXM][RIFT_MAXTERM];
 };
+
+// Canonical mode index j <-> (l, m) and the Goldberg terms of -2Y_lm present for it:
+// r from max(0, m + 2) to min(l + 2, l + m), exponent of cos(theta/2) k = 2 r - 2 - m.
+__host__ __device__ constexpr int canon_l(int j) { return j < 5 ? 2 : (j < 12 ? 3 : 4); }
+__host__ __device__ constexpr int canon_m(int j) { return j < 5 ? j - 2 : (j < 12 ? j - 8 : j - 16); }
+__host__ __device__ constexpr int canon_rmin(int j) { return canon_m(j) + 2 > 0 ? canon_m(j) + 2 : 0; }
+__host__ __device__ constexpr int canon_rmax(int j) {
+  return canon_l(j) + canon_m(j) < canon_l(j) + 2 ? canon_l(j) + canon_m(j) : canon_l(j) + 2;
+}
+__host__ __device__ constexpr int canon_index(int l, int m) { return l * l - 4 + (m + l); }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11), written from the published round function.
@@ -152,38 +166,35 @@ __device__ __forceinline__ void response_delay(const PointC &P, float ca, float 
   }
 }
 
-// -2Y_lm for all modes of the point into smem column Ys[a * stride] (float2).
-__device__ __forceinline__ void swsh_modes(const PointC &P, float c, float s, float cphi, float sphi,
-                                           float2 *Ys, int stride) {
+// -2Y_lm of the present modes, unrolled over the canonical table so every power index is a
+// compile-time constant; stored mode a = number of present canonical modes before j.
+__device__ __forceinline__ void swsh_canonical(const PointC &P, float c, float s, float cphi, float sphi,
+                                               float2 *Ys, int stride) {
   float cp[9], sp[9];
   cp[0] = 1.f; sp[0] = 1.f;
 #pragma unroll
   for (int j = 1; j < 9; ++j) { cp[j] = cp[j - 1] * c; sp[j] = sp[j - 1] * s; }
-  // e^{i m phi}, m = 0..4
   float2 e[5];
   e[0] = make_float2(1.f, 0.f);
   e[1] = make_float2(cphi, sphi);
   e[2] = make_float2(cphi * cphi - sphi * sphi, 2.f * cphi * sphi);
   e[3] = make_float2(e[2].x * cphi - e[2].y * sphi, e[2].x * sphi + e[2].y * cphi);
   e[4] = make_float2(e[2].x * e[2].x - e[2].y * e[2].y, 2.f * e[2].x * e[2].y);
-  for (int a = 0; a < P.M; ++a) {
-    const ModeC &md = P.mode[a];
-    float v = 0.f;
-    for (int j = 0; j < md.nterm; ++j) {
-      // indices are bounded by construction (0 <= kc <= 2l <= 8); select from the
-      // unrolled register arrays without dynamic indexing
-      const int kc = md.kc[j], ks = 2 * md.l - kc;
-      float pc = 1.f, ps = 1.f;
+  const uint32_t mask = P.canon_mask;
 #pragma unroll
-      for (int q = 1; q < 9; ++q) { if (q == kc) pc = cp[q]; if (q == ks) ps = sp[q]; }
-      v = fmaf(md.coef[j], pc * ps, v);
+  for (int j = 0; j < RIFT_MAXM; ++j) {
+    if (mask & (1u << j)) {
+      float v = 0.f;
+#pragma unroll
+      for (int r = canon_rmin(j); r <= canon_rmax(j); ++r) {
+        const int kc = 2 * r - 2 - canon_m(j);
+        v = fmaf(P.ccoef[j][r - canon_rmin(j)], cp[kc] * sp[2 * canon_l(j) - kc], v);
+      }
+      const int am = canon_m(j) < 0 ? -canon_m(j) : canon_m(j);
+      const float2 em = e[am];
+      const int a = __popc(mask & ((1u << j) - 1u));
+      Ys[a * stride] = make_float2(v * em.x, canon_m(j) < 0 ? -(v * em.y) : v * em.y);
     }
-    const int am = md.m < 0 ? -md.m : md.m;
-    float2 em = e[0];
-#pragma unroll
-    for (int q = 1; q < 5; ++q) if (q == am) em = e[q];
-    if (md.m < 0) em.y = -em.y;
-    Ys[a * stride] = make_float2(v * em.x, v * em.y);
   }
 }
 

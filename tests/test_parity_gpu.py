@@ -241,6 +241,30 @@ def test_marginalize_deterministic(lib, cuda, p_small):
     assert a == b
 
 
+def test_launch_shape_does_not_change_results(lib, cuda, p_small):
+    """With the strata fixed, the shared-memory split only decides which Q taps come from the
+    staged window and which from global memory: same values, so bit-identical results."""
+    import torch
+    h = lib.rift_ile_create(p_small)
+    n = 40000
+    outs = []
+    for split in (1, 3, 8):
+        lib.rift_ile_set_tune(h, 640, split)
+        assert lib.rift_ile_get_tune(h)["smem_split"] == split
+        dbg = torch.empty(n, dtype=torch.float32, device="cuda")
+        r = lib.rift_ile_marginalize(h, seed=41, n_per_round=n, max_evals=n, strata=(8, 4, 16), dbg_ell=dbg)
+        torch.cuda.synchronize()
+        outs.append((r["lnL_marg"], dbg.cpu().numpy()))
+    for lm, ell in outs[1:]:
+        assert lm == outs[0][0]
+        assert np.array_equal(ell, outs[0][1])
+    with pytest.raises(lib.RiftError):
+        lib.rift_ile_set_tune(h, 640, 9)
+    best = lib.rift_ile_autotune(h, reps=1, seed=42, n_per_round=n, max_evals=n)
+    assert best["cell_samples"] in (320, 640, 1280) and best["smem_split"] in (2, 3, 4, 6)
+    lib.rift_ile_destroy(h)
+
+
 def test_adaptive_fixed_tables_parity(lib, cuda, p_small):
     """Proposal tables fixed (the oracle's adapted tables, no rebuild): identical draws on both
     sides, lnL_marg within 1e-4."""
