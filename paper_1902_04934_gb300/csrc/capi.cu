@@ -239,15 +239,17 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
         const double *q = d->Q + 2 * (((size_t)k * M + perm[a]) * T + j);
         qb[((size_t)k * T + j) * c.Mp + a] = make_float2((float)q[0], (float)q[1]);
       }
-  // pair coefficients [pair][K] = (U, V) upper triangle, off-diagonal doubled
+  // pair coefficients [pair_slot(a, b)][K] = (U, V) upper triangle, off-diagonal doubled
   c.uv_off = (long long)cv.size();
+  cv.resize(cv.size() + (size_t)c.npair * K);
   for (int a = 0; a < M; ++a)
     for (int b = a; b < M; ++b)
       for (int k = 0; k < K; ++k) {
         const double f = (a == b) ? 1.0 : 2.0;
         const int ua = perm[a], ub = perm[b];
         const double *u = d->U + 2 * ((k * M + ua) * M + ub), *v = d->V + 2 * ((k * M + ua) * M + ub);
-        cv.push_back(make_float4((float)(f * u[0]), (float)(f * u[1]), (float)(f * v[0]), (float)(f * v[1])));
+        cv[c.uv_off + (size_t)pair_slot(a, b, M) * K + k] =
+            make_float4((float)(f * u[0]), (float)(f * u[1]), (float)(f * v[0]), (float)(f * v[1]));
       }
   return RIFT_OK;
 }

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(256) summary_kernel(const PointC *__restrict__
           if (P.mode[q].l == 2 && P.mode[q].m == want_m) a = q;
         float f = 0.f;
         if (a >= 0) {
-          const int pair = a * M - a * (a - 1) / 2;   // index of (a, a) in the upper triangle
+          const int pair = pair_slot(a, a, M);
           f = 0.5f * logf(ca[P.uv_off + (size_t)pair * K + k].x);
         }
         if (nf < NI) feats[nf] = f;

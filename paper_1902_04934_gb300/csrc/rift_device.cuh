@@ -267,37 +267,71 @@ __device__ __forceinline__ float linear_term(const PointC &P, const float2 *__re
   return lin;
 }
 
+// Slot of the mode pair (a, b), a <= b, in the pair-coefficient layout of quad_term: rows in
+// blocks of two (a0 = 2 j, a0 + 1), each block ordered (a0,a0), (a0,a0+1), (a0+1,a0+1), then
+// (a0,b), (a0+1,b) for b = a0+2 .. M-1; a block of one row (odd M) holds (a0,a0) only.  Blocks
+// before block j hold sum_{i<j} (2M - 4i - 1) = j (2M - 1) - 2 j (j - 1) pairs.
+__host__ __device__ inline int pair_slot(int a, int b, int M) {
+  const int j = a >> 1, a0 = 2 * j;
+  const int base = j * (2 * M - 1) - 2 * j * (j - 1);
+  if (b == a) return base + (a == a0 ? 0 : 2);
+  if (b == a0 + 1) return base + 1;   // (a0, a0 + 1)
+  return base + 3 + 2 * (b - a0 - 2) + (a - a0);
+}
+
 // Quadratic term: sum_k |F_k|^2 conj(Y)^T U_k Y + Re(conj(F_k)^2 Y^T V_k Y), using the
-// upper triangle a <= b (U Hermitian, V symmetric); coefficients C[pair][k] =
-// (U, V) with the factor 2 of the off-diagonal pairs folded in.  Row partial sums.
+// upper triangle a <= b (U Hermitian, V symmetric); coefficients C[pair_slot][k] = (U, V) with
+// the factor 2 of the off-diagonal pairs folded in.  Rows go in blocks of two so that one load
+// of Y_b serves two pairs; each row keeps its own partial sums (pairs in order b = a..M-1),
+// added to the totals row by row.
+template <int K>
+__device__ __forceinline__ void quad_pair(float2 ya, float2 yb, const float4 *__restrict__ c, float (&rA)[K],
+                                          float (&rBr)[K], float (&rBi)[K]) {
+  const float pr = ya.x * yb.x + ya.y * yb.y;   // conj(ya) yb
+  const float pi = ya.x * yb.y - ya.y * yb.x;
+  const float qr = ya.x * yb.x - ya.y * yb.y;   // ya yb
+  const float qi = ya.x * yb.y + ya.y * yb.x;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float4 ck = c[k];
+    rA[k] = fmaf(pr, ck.x, fmaf(-pi, ck.y, rA[k]));
+    rBr[k] = fmaf(qr, ck.z, fmaf(-qi, ck.w, rBr[k]));
+    rBi[k] = fmaf(qr, ck.w, fmaf(qi, ck.z, rBi[k]));
+  }
+}
+
 template <int K>
 __device__ __forceinline__ float quad_term(const PointC &P, const float4 *__restrict__ C, const SampleGeo &g,
                                            const float2 *Ys, int ystride) {
   float A[K], Br[K], Bi[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) { A[k] = 0.f; Br[k] = 0.f; Bi[k] = 0.f; }
-  int p = 0;
-  for (int a = 0; a < P.M; ++a) {
-    const float2 ya = Ys[a * ystride];
-    float rA[K], rBr[K], rBi[K];
+  const int M = P.M;
+  const float4 *c = C;
+  for (int a0 = 0; a0 < M; a0 += 2) {
+    float rA[K], rBr[K], rBi[K], sA[K], sBr[K], sBi[K];   // rows a0 and a0 + 1
 #pragma unroll
-    for (int k = 0; k < K; ++k) { rA[k] = 0.f; rBr[k] = 0.f; rBi[k] = 0.f; }
-    for (int b = a; b < P.M; ++b, ++p) {
-      const float2 yb = Ys[b * ystride];
-      const float pr = ya.x * yb.x + ya.y * yb.y;   // conj(ya) yb
-      const float pi = ya.x * yb.y - ya.y * yb.x;
-      const float qr = ya.x * yb.x - ya.y * yb.y;   // ya yb
-      const float qi = ya.x * yb.y + ya.y * yb.x;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float4 c = C[p * K + k];
-        rA[k] = fmaf(pr, c.x, fmaf(-pi, c.y, rA[k]));
-        rBr[k] = fmaf(qr, c.z, fmaf(-qi, c.w, rBr[k]));
-        rBi[k] = fmaf(qr, c.w, fmaf(qi, c.z, rBi[k]));
+    for (int k = 0; k < K; ++k) { rA[k] = 0.f; rBr[k] = 0.f; rBi[k] = 0.f; sA[k] = 0.f; sBr[k] = 0.f; sBi[k] = 0.f; }
+    const float2 y0 = Ys[a0 * ystride];
+    quad_pair<K>(y0, y0, c, rA, rBr, rBi);
+    c += K;
+    if (a0 + 1 < M) {
+      const float2 y1 = Ys[(a0 + 1) * ystride];
+      quad_pair<K>(y0, y1, c, rA, rBr, rBi);
+      quad_pair<K>(y1, y1, c + K, sA, sBr, sBi);
+      c += 2 * K;
+      for (int b = a0 + 2; b < M; ++b, c += 2 * K) {
+        const float2 yb = Ys[b * ystride];
+        quad_pair<K>(y0, yb, c, rA, rBr, rBi);
+        quad_pair<K>(y1, yb, c + K, sA, sBr, sBi);
       }
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) { A[k] += rA[k]; Br[k] += rBr[k]; Bi[k] += rBi[k]; }
+    if (a0 + 1 < M) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) { A[k] += sA[k]; Br[k] += sBr[k]; Bi[k] += sBi[k]; }
+    }
   }
   float quad = 0.f;
 #pragma unroll
