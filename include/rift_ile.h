@@ -153,7 +153,19 @@ typedef struct {
                             (cells [0, n mod C) get one more), sample i of cell (c0,c1,c2) uses the
                             uniforms (c_d + u_d)/S_d, and its log weight gains ln(n / (C n_c)).
                             Rounds with n < C are not stratified.  C <= RIFT_MAX_CELLS.        */
+  const void *resume;    /* optional host RIFT_MC_STATE_BYTES blob written through `save` by an earlier
+                            call on the same point with the same options (seed, point_id,
+                            n_per_round, proposal, n_bins, beta, floor_eps, d_lo, d_hi, strata):
+                            the run continues from it (round index, compensated accumulator,
+                            adapted tables), so a run stopped after r rounds and resumed gives
+                            bit for bit the result of the uninterrupted run; max_evals and
+                            max_rounds count the resumed rounds too.  RIFT_EINVAL if the blob does
+                            not match the handle or the options.  Single-point calls only.       */
+  void *save;            /* optional host buffer of RIFT_MC_STATE_BYTES: the sampler state at return  */
 } rift_mc_opts;
+
+/* Size of the sampler-state blob of rift_mc_opts.resume / save (same library build and byte order). */
+#define RIFT_MC_STATE_BYTES 8192
 
 #define RIFT_MAX_CELLS 32768
 

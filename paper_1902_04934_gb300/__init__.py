@@ -51,7 +51,11 @@ class McOpts(C.Structure):
                 ("d_hi", C.c_double), ("proposal", C.c_int), ("n_bins", C.c_int), ("beta", C.c_double),
                 ("floor_eps", C.c_double), ("adapt_rounds", C.c_int), ("tables", C.c_void_p),
                 ("mdn", C.c_void_p), ("dbg_ell", C.c_void_p), ("dbg_tables", C.c_void_p),
-                ("max_rounds", C.c_int), ("timing", C.c_int), ("strata", C.c_int * 3)]
+                ("max_rounds", C.c_int), ("timing", C.c_int), ("strata", C.c_int * 3),
+                ("resume", C.c_void_p), ("save", C.c_void_p)]
+
+
+MC_STATE_BYTES = 8192   # RIFT_MC_STATE_BYTES
 
 
 class McResult(C.Structure):
@@ -236,7 +240,7 @@ def rift_ile_check(h):
 def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target=1e300, d_lo=1.0,
           d_hi=1000.0, proposal="prior", n_bins=100, beta=0.3, floor_eps=0.1, adapt_rounds=-1,
           tables=None, mdn=None, dbg_ell=None, dbg_tables=None, max_rounds=0, timing=0, strata=(0, 0, 0),
-          keep=None):
+          resume=None, save=None, keep=None):
     o = McOpts()
     o.seed = int(seed)
     o.point_id = int(point_id)
@@ -262,17 +266,30 @@ def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target
     o.timing = int(timing)
     for d in range(3):
         o.strata[d] = int(strata[d])
+    if resume is not None:
+        rb = C.create_string_buffer(bytes(resume), MC_STATE_BYTES)
+        keep.append(rb)
+        o.resume = C.cast(rb, C.c_void_p)
+    if save is not None:
+        keep.append(save)
+        o.save = C.cast(save, C.c_void_p)
     return o
 
 
-def rift_ile_marginalize(h, **kw):
+def rift_ile_marginalize(h, save=False, **kw):
+    """One point's marginalisation (see the C header).  resume=<bytes> continues a run whose
+    state an earlier call returned with save=True (the dict's "state" entry)."""
     keep = []
-    o = _opts(keep=keep, **kw)
+    buf = C.create_string_buffer(MC_STATE_BYTES) if save else None
+    o = _opts(keep=keep, save=buf, **kw)
     r = McResult()
     st = _lib.rift_ile_marginalize(h.ptr, C.byref(o), C.byref(r))
     if st not in (0, 7):
         _check(h, st)
-    return r.as_dict()
+    d = r.as_dict()
+    if save:
+        d["state"] = buf.raw
+    return d
 
 
 def rift_ile_marginalize_static(h, **kw):

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -64,6 +65,20 @@ void swsh_terms(int l, int m, ModeC &out) {
       out.nterm++;
     }
   }
+}
+
+// Host-side fault injection for tests of the error paths: RIFT_FAULT names one fault.
+//   alloc       device allocation in rift_ile_create fails (before any CUDA call)      -> RIFT_ENOMEM
+//   h2d         the host-to-device upload in rift_ile_create fails                     -> RIFT_ECUDA
+//   nan_sample  sample 0 of round 0 of every point gets a NaN log weight (excluded from
+//               the sums and reported through the status word)                        -> RIFT_ENONFINITE
+//   stage_timeout  the cell kernel announces its window copies on the mbarrier but never
+//               issues them, so its bounded wait (about 1 s) runs out; the CTA records the
+//               timeout, waits once more (bounded), and stops                          -> RIFT_ETIMEOUT
+// Nothing here touches device memory out of bounds or traps, and every wait is bounded.
+bool fault_is(const char *name) {
+  const char *f = std::getenv("RIFT_FAULT");
+  return f && std::strcmp(f, name) == 0;
 }
 
 struct Point {
@@ -330,6 +345,12 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
       return s2;
     }
   }
+  if (fault_is("alloc")) {
+    rift_status s0 = fail(h, RIFT_ENOMEM, "injected fault: device allocation failed");
+    fprintf(stderr, "rift_ile_create: %s\n", h->err.c_str());
+    rift_ile_destroy(h);
+    return s0;
+  }
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
@@ -344,6 +365,7 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
       (e = cudaMalloc(&h->q_arena, sizeof(float2) * std::max<size_t>(qv.size(), 2))) != cudaSuccess ||
       (e = cudaMalloc(&h->c_arena, sizeof(float4) * std::max<size_t>(cv.size(), 1))) != cudaSuccess ||
       (e = cudaMalloc(&h->flags, sizeof(uint32_t))) != cudaSuccess ||
+      (e = fault_is("h2d") ? cudaErrorInvalidValue : cudaSuccess) != cudaSuccess ||
       (e = cudaMemcpyAsync(h->pts_dev, pc.data(), sizeof(PointC) * n, cudaMemcpyHostToDevice, h->stream)) !=
           cudaSuccess ||
       (e = cudaMemcpyAsync(h->q_arena, qv.data(), sizeof(float2) * qv.size(), cudaMemcpyHostToDevice, h->stream)) !=
@@ -490,6 +512,44 @@ rift_status prepare_learned(rift_ile *h, const rift_mc_opts *o, cudaStream_t st)
   return RIFT_OK;
 }
 
+// Sampler state between calls (rift_mc_opts.resume / save): everything the next round of a
+// single-point run depends on.
+struct McStateBlob {
+  uint32_t magic, version;
+  uint64_t seed;
+  uint32_t point_id, n_per_round;
+  int32_t K, M, T, proposal, n_bins, ls[3];
+  double beta, floor_eps, d_lo, d_hi;
+  uint32_t rounds, pad;
+  uint64_t evals;
+  AccState acc;
+  float tables[3 * (RIFT_MAXBINS + 1)];
+  float lnw[3 * RIFT_MAXBINS];
+};
+static_assert(sizeof(McStateBlob) <= RIFT_MC_STATE_BYTES, "state blob larger than RIFT_MC_STATE_BYTES");
+constexpr uint32_t kStateMagic = 0x53464952u;   // "RIFS"
+
+void state_header(const rift_ile *h, const rift_mc_opts *o, const int ls[3], McStateBlob &b) {
+  std::memset(&b, 0, sizeof(b));
+  b.magic = kStateMagic;
+  b.version = 1;
+  b.seed = o->seed;
+  b.point_id = o->point_id;
+  b.n_per_round = o->n_per_round;
+  b.K = h->pts[0].c.K; b.M = h->pts[0].c.M; b.T = h->pts[0].c.T;
+  b.proposal = o->proposal;
+  b.n_bins = (o->proposal == RIFT_PROPOSAL_ADAPTIVE) ? o->n_bins : 0;
+  for (int d = 0; d < 3; ++d) b.ls[d] = ls[d];
+  b.beta = o->beta; b.floor_eps = o->floor_eps; b.d_lo = o->d_lo; b.d_hi = o->d_hi;
+}
+
+bool state_matches(const McStateBlob &a, const McStateBlob &b) {
+  return a.magic == b.magic && a.version == b.version && a.seed == b.seed && a.point_id == b.point_id &&
+         a.n_per_round == b.n_per_round && a.K == b.K && a.M == b.M && a.T == b.T && a.proposal == b.proposal &&
+         a.n_bins == b.n_bins && a.ls[0] == b.ls[0] && a.ls[1] == b.ls[1] && a.ls[2] == b.ls[2] &&
+         a.beta == b.beta && a.floor_eps == b.floor_eps && a.d_lo == b.d_lo && a.d_hi == b.d_hi;
+}
+
 // The Monte Carlo round loop of Eq. (lnLmarg) for np points of the handle, with the scratch S.
 rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rift_mc_result *res) {
   const int K = h->K, NT = taps_of(h->interp);
@@ -515,15 +575,27 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     }
   }
   cudaStream_t st = h->stream;
+  if ((o->resume || o->save) && (np != 1 || h->n_points != 1))
+    return fail(h, RIFT_EINVAL, "resume/save need a single-point handle");
+  McStateBlob hdr, in{};
+  if (o->resume || o->save) state_header(h, o, lsv.data(), hdr);
+  if (o->resume) {
+    std::memcpy(&in, o->resume, sizeof(in));
+    if (!state_matches(in, hdr)) return fail(h, RIFT_EINVAL, "resume state does not match this handle and options");
+  }
   // accumulators and round-0 tables
   for (int p = 0; p < np; ++p) {
     std::memset(&S.acc_host[p], 0, sizeof(AccState));
     S.acc_host[p].m = -INFINITY;
   }
+  if (o->resume) S.acc_host[0] = in.acc;
   RIFT_CK(h, cudaMemcpyAsync(S.acc, S.acc_host, sizeof(AccState) * np, cudaMemcpyHostToDevice, st));
   int cur = 0;
   const size_t tstride = (size_t)3 * (nb + 1), wstride = (size_t)3 * nb;
-  if (adaptive) {
+  if (adaptive && o->resume) {
+    RIFT_CK(h, cudaMemcpyAsync(S.tables, in.tables, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
+    RIFT_CK(h, cudaMemcpyAsync(S.lnw, in.lnw, sizeof(float) * wstride, cudaMemcpyHostToDevice, st));
+  } else if (adaptive) {
     float u[3 * (RIFT_MAXBINS + 1)];
     const float *src = o->tables;
     if (!src) {
@@ -573,8 +645,19 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.max_pairK = h->max_pairK;
   L.max_nb = nb;
   L.learned = learned ? 1 : 0;
+  L.fault_nan = fault_is("nan_sample") ? 1 : 0;
+  L.fault_stall = fault_is("stage_timeout") ? 1 : 0;
   std::vector<uint64_t> evals(np, 0);
   std::vector<int> rounds(np, 0), done(np, 0), nrun(np, 0);
+  int r0 = 0;
+  if (o->resume) {
+    evals[0] = in.evals;
+    rounds[0] = (int)in.rounds;
+    r0 = rounds[0];
+    const double n_eff = in.acc.s1 + in.acc.c1;
+    if (n_eff >= o->n_eff_target || evals[0] >= o->max_evals || (o->max_rounds > 0 && rounds[0] >= o->max_rounds))
+      done[0] = 1;
+  }
   int launches = 0;
   double kms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -583,7 +666,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     RIFT_CK(h, cudaEventCreate(&ev1));
   }
   rift_status status = RIFT_OK;
-  for (int r = 0;; ++r) {
+  for (int r = r0;; ++r) {
     uint32_t items = 0;
     for (int p = 0; p < np; ++p) {
       RoundPt &R = S.rp_host[p];
@@ -622,7 +705,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     if (items == 0) break;
     if (items > S.max_items) { status = fail(h, RIFT_EINVAL, "work items exceed the scratch"); break; }
     if (o->dbg_tables && adaptive && np == 1)
-      RIFT_CK(h, cudaMemcpyAsync(o->dbg_tables + (size_t)r * tstride, S.tables + (size_t)cur * np * tstride,
+      RIFT_CK(h, cudaMemcpyAsync(o->dbg_tables + (size_t)(r - r0) * tstride, S.tables + (size_t)cur * np * tstride,
                                  sizeof(float) * tstride, cudaMemcpyDeviceToDevice, st));
     const uint32_t cnt[2] = {items, 0u};
     RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
@@ -668,6 +751,21 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   }
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
+  if (o->save && status == RIFT_OK) {
+    McStateBlob outb = hdr;
+    outb.rounds = (uint32_t)rounds[0];
+    outb.evals = evals[0];
+    outb.acc = S.acc_host[0];
+    if (adaptive) {
+      RIFT_CK(h, cudaMemcpyAsync(outb.tables, S.tables + (size_t)cur * tstride, sizeof(float) * tstride,
+                                 cudaMemcpyDeviceToHost, st));
+      RIFT_CK(h, cudaMemcpyAsync(outb.lnw, S.lnw + (size_t)cur * wstride, sizeof(float) * wstride,
+                                 cudaMemcpyDeviceToHost, st));
+      RIFT_CK(h, cudaStreamSynchronize(st));
+    }
+    std::memset(o->save, 0, RIFT_MC_STATE_BYTES);
+    std::memcpy(o->save, &outb, sizeof(outb));
+  }
   rift_status fl = read_flags(h);
   for (int p = 0; p < np; ++p) {
     fill_result(S.acc_host[p], &res[p]);
@@ -872,6 +970,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   if (!h || !res) return RIFT_EINVAL;
   rift_status s = check_opts(h, o);
   if (s != RIFT_OK) return s;
+  if (o->resume || o->save) return fail(h, RIFT_EUNSUPPORTED, "resume/save: single-point marginalisation only");
   const int np = h->n_points;
   std::memset(res, 0, sizeof(*res) * np);
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
@@ -989,6 +1088,8 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   L.max_pairK = h->max_pairK;
   L.max_nb = nb;
   L.learned = learned ? 1 : 0;
+  L.fault_nan = fault_is("nan_sample") ? 1 : 0;
+  L.fault_stall = fault_is("stage_timeout") ? 1 : 0;
   const int grid = h->num_sms * bps;
   // capture G rounds: update -> cells -> merge -> (adaptive) hist -> tables
   const int G = std::max(1, h->graph_rounds);
@@ -1136,6 +1237,8 @@ rift_status rift_ile_autotune(rift_ile *h, const rift_mc_opts *o, int reps, rift
   t.dbg_tables = nullptr;
   t.timing = 0;
   t.max_rounds = reps;
+  t.resume = nullptr;
+  t.save = nullptr;
   const int old_target = h->cell_target, old_ctas = h->smem_split;
   const int targets[3] = {320, 640, 1280}, splits[4] = {2, 3, 4, 6};
   std::vector<rift_mc_result> res((size_t)h->n_points);

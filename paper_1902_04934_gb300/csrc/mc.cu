@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel(CellLaunch L)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bar, bytes);
         for (int k = 0; k < K; ++k)
-          if (s_woff[k] >= 0) {
+          if (s_woff[k] >= 0 && !L.fault_stall) {   // (an injected fault leaves the announced bytes unissued)
             const float2 *src = Q + ((long long)k * P.T + s_wlo[k]) * P.Mp;
             bulk_g2s(wbuf + s_woff[k], src, (uint32_t)(s_whi[k] - s_wlo[k] + 1) * rowb, &bar);
           }
@@ -545,7 +545,8 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel(CellLaunch L)
       const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
       const float quad = quad_term<K>(P, C, g, Ys, ystride);
       const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
-      const float ell = lnL + d.lpq;
+      float ell = lnL + d.lpq;
+      if (L.fault_nan && i == 0u && R.round == 0u) ell = __int_as_float(0x7fc00000);   // injected (host-requested) fault
       if (L.dbg_ell && R.dbg_off >= 0) L.dbg_ell[R.dbg_off + i] = ell;
       if (L.ell_buf && R.ell_off >= 0) { L.ell_buf[R.ell_off + i] = ell; L.bin_buf[R.ell_off + i] = d.bins; }
       if (isfinite(ell)) { lse_push(ell, m, s1, s2); cnt += 1.f; }

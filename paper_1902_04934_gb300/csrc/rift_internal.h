@@ -74,6 +74,8 @@ struct CellLaunch {
   int max_pairK;               // largest npair * K over the points
   int max_nb;                  // largest bin count (0 if no point uses tables)
   int learned;                 // every point samples from its learned proposal
+  int fault_nan;               // injected fault: sample 0 of round 0 of every point has a NaN log weight
+  int fault_stall;             // injected fault: window copies announced on the mbarrier but never issued
 };
 
 // Device-side round control of a batched run replayed as a CUDA graph.

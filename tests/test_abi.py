@@ -6,6 +6,8 @@ from __future__ import annotations
 import ctypes
 import re
 import subprocess
+
+import pytest
 from pathlib import Path
 
 ROOT = Path(__file__).resolve().parents[1]
@@ -72,6 +74,17 @@ def test_create_rejects_bad_descriptors_on_host(lib):
         assert e.status == 1
 
 
+def test_injected_allocation_fault_on_host(lib, monkeypatch):
+    """RIFT_FAULT=alloc makes rift_ile_create report RIFT_ENOMEM before any device call (host-side
+    fault injection; no GPU is touched)."""
+    import workload as W
+    pt = W.make_point(W.cfg_small(), 3)
+    monkeypatch.setenv("RIFT_FAULT", "alloc")
+    with pytest.raises(lib.RiftError) as e:
+        lib.rift_ile_create(pt)
+    assert e.value.status == 3
+
+
 def test_product_path_has_no_oracle_import():
     """The library package never imports or loads the oracle (no CPU fallback)."""
     pkg = ROOT / "paper_1902_04934_gb300"
@@ -79,3 +92,36 @@ def test_product_path_has_no_oracle_import():
         txt = f.read_text()
         assert not re.search(r"^\s*(import|from)\s+oracle", txt, flags=re.M), f
         assert "oracle/" not in txt, f
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """sizeof/offsetof of every public struct, compiled from the header with the host C
+    compiler, equal the ctypes layouts the binding marshals."""
+    import ctypes as C
+    import shutil
+    import subprocess
+
+    import paper_1902_04934_gb300 as rift
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"rift_ile_desc": rift.Desc, "rift_mc_opts": rift.McOpts, "rift_mc_result": rift.McResult,
+               "rift_tune": rift.Tune}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/rift_ile.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append('  printf("RIFT_MC_STATE_BYTES %d\\n", RIFT_MC_STATE_BYTES);')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-o", str(exe), str(src)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                  text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+    assert int(got["RIFT_MC_STATE_BYTES"]) == rift.MC_STATE_BYTES

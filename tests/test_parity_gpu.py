@@ -265,6 +265,29 @@ def test_launch_shape_does_not_change_results(lib, cuda, p_small):
     lib.rift_ile_destroy(h)
 
 
+def test_resume_continues_bit_for_bit(lib, cuda, p_small):
+    """A run saved after 2 of 5 rounds and resumed equals the uninterrupted run exactly (adaptive
+    tables, accumulator, round index); a state from other options or a damaged blob is refused."""
+    kw = dict(seed=43, n_per_round=30000, n_eff_target=1e300, proposal="adaptive", n_bins=48, max_evals=150000)
+    h = lib.rift_ile_create(p_small)
+    full = lib.rift_ile_marginalize(h, **kw)
+    part = lib.rift_ile_marginalize(h, save=True, max_rounds=2, **kw)
+    assert part["rounds"] == 2 and part["n_evals"] == 60000
+    rest = lib.rift_ile_marginalize(h, resume=part["state"], save=True, **kw)
+    for key in ("lnL_marg", "n_eff", "n_eff_kish", "sigma", "n_evals", "rounds", "acc_max", "acc_s1", "acc_s2"):
+        assert rest[key] == full[key], key
+    # resuming a finished run does no more work
+    again = lib.rift_ile_marginalize(h, resume=rest["state"], **kw)
+    assert again["n_evals"] == full["n_evals"] and again["lnL_marg"] == full["lnL_marg"]
+    with pytest.raises(lib.RiftError):
+        lib.rift_ile_marginalize(h, resume=part["state"], **dict(kw, seed=44))
+    bad = bytearray(part["state"])
+    bad[0] ^= 0xFF
+    with pytest.raises(lib.RiftError):
+        lib.rift_ile_marginalize(h, resume=bytes(bad), **kw)
+    lib.rift_ile_destroy(h)
+
+
 def test_adaptive_fixed_tables_parity(lib, cuda, p_small):
     """Proposal tables fixed (the oracle's adapted tables, no rebuild): identical draws on both
     sides, lnL_marg within 1e-4."""
