@@ -113,6 +113,18 @@ rift_status rift_ile_lnL_host(rift_ile *h, size_t n, const float *ra, const floa
                               const float *psi, const float *phi, const float *incl, const float *dist,
                               float *lnL_out);
 
+/*
+ * Time-marginalised log-likelihood, Eq. (lnL:tmarg) (Sec. II.C: the event time is marginalised
+ * by direct quadrature for each draw of the other extrinsic parameters), at caller draws of
+ * point 0: ln L_margT = ln (1/J) sum_j exp(lnL(theta, t_j)), midpoint rule on the sampling
+ * interval of Q, t_j = t_lo + (j + 1/2)/fs, j < J = floor((t_hi - t_lo) fs), with lnL of
+ * rift_ile_lnL.  Device float32 arrays of length n: ra, dec, psi, phi, incl, D (Mpc); out:
+ * device, length n.  Asynchronous on the handle's stream; window and non-finite flags as for
+ * rift_ile_lnL.
+ */
+rift_status rift_ile_lnL_tmarg(rift_ile *h, size_t n, const float *ra, const float *dec, const float *psi,
+                               const float *phi, const float *incl, const float *dist, float *out);
+
 /* Reads and clears the device status word (out-of-window taps, non-finite lnL). */
 rift_status rift_ile_check(rift_ile *h);
 
@@ -162,6 +174,12 @@ typedef struct {
                             max_rounds count the resumed rounds too.  RIFT_EINVAL if the blob does
                             not match the handle or the options.  Single-point calls only.       */
   void *save;            /* optional host buffer of RIFT_MC_STATE_BYTES: the sampler state at return  */
+  int time_marg;         /* nonzero: each draw integrates the event time by quadrature, Eq. (lnL:tmarg)
+                            (rift_ile_lnL_tmarg), instead of sampling it; the draws cover (ra, dec,
+                            psi, phi, incl, D), strata and adaptive tables cover (ra, sin dec) only
+                            (the time table stays uniform), n_evals counts draws.  Prior or adaptive
+                            proposals, single-point and multi-point handles through
+                            rift_ile_marginalize; not with the learned proposal or the batched runner. */
 } rift_mc_opts;
 
 /* Size of the sampler-state blob of rift_mc_opts.resume / save (same library build and byte order). */

@@ -33,6 +33,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from .tmarg import lnL_tmarg
 from .likelihood import lnL_factorised
 from .philox import uniforms
 
@@ -203,9 +204,25 @@ def rebuild_tables(ell, bins, n_bins, beta, floor_eps):
     return out, h
 
 
+def uniform_time_table(n_bins: int):
+    """The time table of a time-marginalised adaptive run: the uniform density built the way
+    every rebuilt table is (running FP64 sum of the bin masses, normalised, rounded to FP32)."""
+    c = 0.0
+    out = np.empty(n_bins + 1, dtype=np.float32)
+    out[0] = 0.0
+    tot = 0.0
+    for _ in range(n_bins):
+        tot += 1.0 / n_bins
+    for b in range(n_bins):
+        c += 1.0 / n_bins
+        out[b + 1] = np.float32(c / tot)
+    out[n_bins] = 1.0
+    return out
+
+
 def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_target,
                 adaptive=False, n_bins=100, beta=0.3, floor_eps=0.1, tables=None, interp=3,
-                max_rounds=None, keep=False, adapt_rounds=-1, strata=(1, 1, 1)):
+                max_rounds=None, keep=False, adapt_rounds=-1, strata=(1, 1, 1), time_marg=False):
     """Round loop of Eq. (lnLmarg) with the n_eff stopping rule of Sec. II.C.
 
     adaptive=False: plain prior sampling.  adaptive=True: round 0 uses `tables`
@@ -220,7 +237,12 @@ def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_tar
     while True:
         idx = np.arange(min(n_per_round, max_evals - acc.n), dtype=np.uint64)
         th, bins, lpq = draw(seed, point, rnd, idx, prior, tables if adaptive else None, strata, len(idx))
-        ell = lnL_samples(pt, th, interp) + lpq
+        if time_marg:
+            # Eq. (lnL:tmarg): the draw's t is unused, the event time is integrated by quadrature
+            ell = lnL_tmarg(pt, th["ra"], np.arcsin(th["sindec"]), th["psi"], th["phi"], np.arccos(th["cosi"]),
+                            th["dist"], interp=interp) + lpq
+        else:
+            ell = lnL_samples(pt, th, interp) + lpq
         acc = acc.merge(Accum.of(ell))
         lnm, n_eff, kish, sig = acc.result()
         if keep:
@@ -230,6 +252,8 @@ def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_tar
             break
         if adaptive and (adapt_rounds < 0 or rnd - 1 < adapt_rounds):
             tables, _ = rebuild_tables(ell, bins, n_bins, beta, floor_eps)
+            if time_marg:
+                tables[2] = uniform_time_table(n_bins)
     lnm, n_eff, kish, sig = acc.result()
     out = dict(lnL_marg=lnm, n_eff=n_eff, kish=kish, sigma=sig, n_evals=acc.n, rounds=rnd, acc=acc)
     if keep:

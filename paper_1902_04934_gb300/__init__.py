@@ -52,7 +52,7 @@ class McOpts(C.Structure):
                 ("floor_eps", C.c_double), ("adapt_rounds", C.c_int), ("tables", C.c_void_p),
                 ("mdn", C.c_void_p), ("dbg_ell", C.c_void_p), ("dbg_tables", C.c_void_p),
                 ("max_rounds", C.c_int), ("timing", C.c_int), ("strata", C.c_int * 3),
-                ("resume", C.c_void_p), ("save", C.c_void_p)]
+                ("resume", C.c_void_p), ("save", C.c_void_p), ("time_marg", C.c_int)]
 
 
 MC_STATE_BYTES = 8192   # RIFT_MC_STATE_BYTES
@@ -89,6 +89,7 @@ def _load():
         "rift_ile_n_points": (I, [P]),
         "rift_ile_lnL": (I, [P, S] + [P] * 8),
         "rift_ile_lnL_host": (I, [P, S] + [P] * 8),
+        "rift_ile_lnL_tmarg": (I, [P, S] + [P] * 7),
         "rift_ile_check": (I, [P]),
         "rift_ile_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
         "rift_ile_batch_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
@@ -224,6 +225,17 @@ def rift_ile_lnL(h, ra, dec, t, psi, phi, incl, dist, out=None):
     return out
 
 
+def rift_ile_lnL_tmarg(h, ra, dec, psi, phi, incl, dist, out=None):
+    """Time-marginalised lnL of device draws (CUDA float32 tensors; asynchronous), see the C header."""
+    import torch
+    n = ra.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=ra.device)
+    ptrs = [_dptr(a, n) for a in (ra, dec, psi, phi, incl, dist, out)]
+    _check(h, _lib.rift_ile_lnL_tmarg(h.ptr, n, *ptrs))
+    return out
+
+
 def rift_ile_lnL_host(h, ra, dec, t, psi, phi, incl, dist):
     """Host-buffer call: numpy float32 in, numpy float32 out (copies inside the library)."""
     arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (ra, dec, t, psi, phi, incl, dist)]
@@ -240,7 +252,7 @@ def rift_ile_check(h):
 def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target=1e300, d_lo=1.0,
           d_hi=1000.0, proposal="prior", n_bins=100, beta=0.3, floor_eps=0.1, adapt_rounds=-1,
           tables=None, mdn=None, dbg_ell=None, dbg_tables=None, max_rounds=0, timing=0, strata=(0, 0, 0),
-          resume=None, save=None, keep=None):
+          resume=None, save=None, time_marg=0, keep=None):
     o = McOpts()
     o.seed = int(seed)
     o.point_id = int(point_id)
@@ -266,6 +278,7 @@ def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target
     o.timing = int(timing)
     for d in range(3):
         o.strata[d] = int(strata[d])
+    o.time_marg = int(time_marg)
     if resume is not None:
         rb = C.create_string_buffer(bytes(resume), MC_STATE_BYTES)
         keep.append(rb)

@@ -163,6 +163,7 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
   PointC &c = P.c;
   std::memset(&c, 0, sizeof(c));
   c.K = K; c.M = M; c.T = T; c.Mp = (M + 1) & ~1; c.npair = M * (M + 1) / 2; c.interp = d->interp;
+  c.J = std::max(1, (int)std::floor((d->t_hi - d->t_lo) * d->fs + 1e-9));
   c.fs = (float)d->fs;
   if ((double)c.fs != d->fs) return fail(h, RIFT_EINVAL, "fs must be exactly representable in float32");
   c.dref = (float)d->d_ref_mpc;
@@ -415,6 +416,8 @@ rift_status check_opts(rift_ile *h, const rift_mc_opts *o) {
   } else if (o->proposal != RIFT_PROPOSAL_PRIOR) {
     return fail(h, RIFT_EINVAL, "unknown proposal");
   }
+  if (o->time_marg && o->proposal == RIFT_PROPOSAL_LEARNED)
+    return fail(h, RIFT_EUNSUPPORTED, "time marginalisation with the learned proposal");
   return RIFT_OK;
 }
 
@@ -468,6 +471,16 @@ void choose_strata(const PointC &P, uint32_t n, int ls[3], int target = 640) {
     }
 }
 
+// Strata of a time-marginalised round: about `target` draws per cell over (ra, sin dec) only,
+// two ra cells per sin dec cell (the ra range is pi times the sin dec range).
+void choose_strata_sky(uint32_t n, int ls[3], int target) {
+  int L = 0;
+  while (L < 15 && ((uint64_t)target << (L + 1)) <= n) ++L;
+  ls[1] = L / 2;
+  ls[0] = L - ls[1];
+  ls[2] = 0;
+}
+
 int log2_pow2(int v) {
   int l = 0;
   while ((1 << l) < v) ++l;
@@ -518,7 +531,7 @@ struct McStateBlob {
   uint32_t magic, version;
   uint64_t seed;
   uint32_t point_id, n_per_round;
-  int32_t K, M, T, proposal, n_bins, ls[3];
+  int32_t K, M, T, proposal, n_bins, ls[3], time_marg, pad2;
   double beta, floor_eps, d_lo, d_hi;
   uint32_t rounds, pad;
   uint64_t evals;
@@ -540,6 +553,7 @@ void state_header(const rift_ile *h, const rift_mc_opts *o, const int ls[3], McS
   b.proposal = o->proposal;
   b.n_bins = (o->proposal == RIFT_PROPOSAL_ADAPTIVE) ? o->n_bins : 0;
   for (int d = 0; d < 3; ++d) b.ls[d] = ls[d];
+  b.time_marg = o->time_marg ? 1 : 0;
   b.beta = o->beta; b.floor_eps = o->floor_eps; b.d_lo = o->d_lo; b.d_hi = o->d_hi;
 }
 
@@ -547,6 +561,7 @@ bool state_matches(const McStateBlob &a, const McStateBlob &b) {
   return a.magic == b.magic && a.version == b.version && a.seed == b.seed && a.point_id == b.point_id &&
          a.n_per_round == b.n_per_round && a.K == b.K && a.M == b.M && a.T == b.T && a.proposal == b.proposal &&
          a.n_bins == b.n_bins && a.ls[0] == b.ls[0] && a.ls[1] == b.ls[1] && a.ls[2] == b.ls[2] &&
+         a.time_marg == b.time_marg &&
          a.beta == b.beta && a.floor_eps == b.floor_eps && a.d_lo == b.d_lo && a.d_hi == b.d_hi;
 }
 
@@ -567,11 +582,13 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     if (learned) {
       ls[0] = ls[1] = ls[2] = 0;
     } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
-      choose_strata(h->pts[p].c, npr, ls, h->cell_target);
+      if (o->time_marg) choose_strata_sky(npr, ls, 128);
+      else choose_strata(h->pts[p].c, npr, ls, h->cell_target);
     } else {
       for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
       if (ls[0] < 0 || ls[1] < 0 || ls[2] < 0) return fail(h, RIFT_EINVAL, "strata must be powers of two");
       if ((1 << (ls[0] + ls[1] + ls[2])) > RIFT_MAX_CELLS) return fail(h, RIFT_EINVAL, "more than RIFT_MAX_CELLS cells");
+      if (o->time_marg && ls[2] != 0) return fail(h, RIFT_EINVAL, "time-marginalised rounds are not stratified in t");
     }
   }
   cudaStream_t st = h->stream;
@@ -622,7 +639,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
   budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
   const size_t smem = fixed + (size_t)budget;
-  int bps = cells_blocks_per_sm(K, NT, smem, block);
+  int bps = cells_blocks_per_sm(K, NT, smem, block, o->time_marg ? 1 : 0);
   if (bps < 1) return fail(h, RIFT_EUNSUPPORTED, "cell kernel does not fit on an SM");
   CellLaunch L{};
   L.seed = o->seed;
@@ -647,6 +664,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.learned = learned ? 1 : 0;
   L.fault_nan = fault_is("nan_sample") ? 1 : 0;
   L.fault_stall = fault_is("stage_timeout") ? 1 : 0;
+  L.tmarg = o->time_marg ? 1 : 0;
   std::vector<uint64_t> evals(np, 0);
   std::vector<int> rounds(np, 0), done(np, 0), nrun(np, 0);
   int r0 = 0;
@@ -691,6 +709,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
       R.proposal = learned ? 2 : (adaptive ? 1 : 0);
       R.nb = nb;
       R.gmm = learned ? h->gmm + (size_t)p * RIFT_GMM_FLOATS : nullptr;
+      R.tmarg = o->time_marg ? 1 : 0;
       R.lcorr0 = (float)std::log((double)n / ((double)C * (R.base + 1.0)));
       R.lcorr1 = R.base ? (float)std::log((double)n / ((double)C * R.base)) : 0.f;
       R.chunks = (R.base + (R.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
@@ -863,6 +882,17 @@ rift_status rift_ile_lnL(rift_ile *h, size_t n, const float *ra, const float *de
   return RIFT_OK;
 }
 
+rift_status rift_ile_lnL_tmarg(rift_ile *h, size_t n, const float *ra, const float *dec, const float *psi,
+                               const float *phi, const float *incl, const float *dist, float *out) {
+  if (!h) return RIFT_EINVAL;
+  if (n == 0) return RIFT_OK;
+  if (!ra || !dec || !psi || !phi || !incl || !dist || !out) return fail(h, RIFT_EINVAL, "null draw array");
+  const Point &p = h->pts[0];
+  RIFT_CK(h, launch_lnl_tmarg(h->K, h->pts_dev, p.c, h->q_arena, h->c_arena, n, ra, dec, psi, phi, incl, dist, out,
+                              h->flags, h->stream));
+  return RIFT_OK;
+}
+
 rift_status rift_ile_lnL_host(rift_ile *h, size_t n, const float *ra, const float *dec, const float *t,
                               const float *psi, const float *phi, const float *incl, const float *dist,
                               float *lnL_out) {
@@ -971,6 +1001,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   rift_status s = check_opts(h, o);
   if (s != RIFT_OK) return s;
   if (o->resume || o->save) return fail(h, RIFT_EUNSUPPORTED, "resume/save: single-point marginalisation only");
+  if (o->time_marg) return fail(h, RIFT_EUNSUPPORTED, "time marginalisation: use rift_ile_marginalize");
   const int np = h->n_points;
   std::memset(res, 0, sizeof(*res) * np);
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
@@ -1090,6 +1121,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   L.learned = learned ? 1 : 0;
   L.fault_nan = fault_is("nan_sample") ? 1 : 0;
   L.fault_stall = fault_is("stage_timeout") ? 1 : 0;
+  L.tmarg = o->time_marg ? 1 : 0;
   const int grid = h->num_sms * bps;
   // capture G rounds: update -> cells -> merge -> (adaptive) hist -> tables
   const int G = std::max(1, h->graph_rounds);

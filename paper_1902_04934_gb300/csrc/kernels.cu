@@ -79,6 +79,78 @@ __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict
   if (flags) atomicOr(flags_out, flags);
 }
 
+// Time-marginalised likelihood of caller draws (ra, dec, psi, phi, incl, D): Eq. (lnL:tmarg)
+// by the midpoint rule on the Q sampling interval (tmarg_term).
+template <int K, int NT>
+__global__ void __launch_bounds__(128) lnl_tmarg_array_kernel(
+    const PointC *__restrict__ pts, const float2 *__restrict__ qa, const float4 *__restrict__ ca, size_t n,
+    const float *__restrict__ ra, const float *__restrict__ dec, const float *__restrict__ psi,
+    const float *__restrict__ phi, const float *__restrict__ incl, const float *__restrict__ dist,
+    float *__restrict__ out, uint32_t *flags_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  PointC &P = *reinterpret_cast<PointC *>(smem);
+  load_point(pts, &P);
+  __syncthreads();
+  size_t off = align16(sizeof(PointC));
+  float4 *C = reinterpret_cast<float4 *>(smem + off);
+  off = align16(off + sizeof(float4) * (size_t)P.npair * K);
+  float2 *Ys = reinterpret_cast<float2 *>(smem + off) + threadIdx.x;
+  const int ystride = blockDim.x;
+  const float4 *cg = ca + P.uv_off;
+  for (int j = threadIdx.x; j < P.npair * K; j += blockDim.x) C[j] = cg[j];
+  __syncthreads();
+  const float2 *Q = qa + P.q_off;
+  uint32_t flags = 0u;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float r = ra[i];
+    const float ph = __fmul_rn(r, 0.15915494309189535f);
+    const float pl = __fmaf_rn(r, 0.15915494309189535f, -ph) + r * 6.4206382e-09f;
+    const df v = df_add(fast_two_sum(ph, pl), df{-P.g_hi, -P.g_lo});
+    float s0, c0;
+    sincospif(2.f * v.hi, &s0, &c0);
+    const float ares = kTwoPi * v.lo;
+    const float cA = c0 - s0 * ares, sA = s0 + c0 * ares;
+    float sdh, cd;
+    sincosf(dec[i], &sdh, &cd);
+    float s2p, c2p;
+    sincosf(2.f * psi[i], &s2p, &c2p);
+    df base[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) base[k] = df_add_f(df{P.det[k].c0, P.det[k].c0lo}, 0.5f);   // t_0 = t_lo + 1/(2 fs)
+    SampleGeo g;
+    response_delay<K>(P, cA, sA, df{sdh, 0.f}, cd, c2p, s2p, g, base);
+    g.x = __fdiv_rn(P.dref, dist[i]);
+    float sphi, cphi, ch, sh;
+    sincosf(phi[i], &sphi, &cphi);
+    sincosf(0.5f * incl[i], &sh, &ch);
+    swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
+    const float quad = quad_term<K>(P, C, g, Ys, ystride);
+    const float lm = tmarg_term<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
+    if (!isfinite(lm)) flags |= RIFT_FLAG_NONFINITE;
+    out[i] = lm;
+  }
+  if (flags) atomicOr(flags_out, flags);
+}
+
+template <int K, int NT>
+cudaError_t lnl_tmarg_k(const PointC *pt_dev, const float2 *qa, const float4 *ca, size_t n, const float *ra,
+                        const float *dec, const float *psi, const float *phi, const float *incl, const float *dist,
+                        float *out, uint32_t *flags, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e =
+        cudaFuncSetAttribute(lnl_tmarg_array_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int block = 128;
+  const unsigned grid = (unsigned)((n + block - 1) / block);
+  lnl_tmarg_array_kernel<K, NT><<<grid, block, smem, st>>>(pt_dev, qa, ca, n, ra, dec, psi, phi, incl, dist, out,
+                                                          flags);
+  return cudaGetLastError();
+}
+
 template <int K, int NT>
 cudaError_t lnl_array_k(const PointC *pt_dev, const float2 *qa, const float4 *ca, size_t n, const float *ra,
                         const float *dec, const float *t, const float *psi, const float *phi, const float *incl,
@@ -125,5 +197,15 @@ cudaError_t launch_lnl_array(int K, const PointC *pt_dev, const PointC &ph, cons
 #define RIFT_LA(KK, TT) lnl_array_k<KK, TT>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags, smem, st)
   RIFT_DISPATCH_KT(K, taps_of(ph.interp), RIFT_LA)
 #undef RIFT_LA
+}
+
+cudaError_t launch_lnl_tmarg(int K, const PointC *pt_dev, const PointC &ph, const float2 *qa, const float4 *ca,
+                             size_t n, const float *ra, const float *dec, const float *psi, const float *phi,
+                             const float *incl, const float *dist, float *out, uint32_t *flags, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const size_t smem = rift_point_smem_bytes(K, ph.npair, 0, 128, ph.M);
+#define RIFT_LT(KK, TT) lnl_tmarg_k<KK, TT>(pt_dev, qa, ca, n, ra, dec, psi, phi, incl, dist, out, flags, smem, st)
+  RIFT_DISPATCH_KT(K, taps_of(ph.interp), RIFT_LT)
+#undef RIFT_LT
 }
 

@@ -352,8 +352,25 @@ __device__ __forceinline__ float linear_term_staged(const PointC &P, const float
   return lin;
 }
 
-template <int K, int NT, int LEARNED>
-__global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel(CellLaunch L) {
+// Q index of t_0 + delay_k for the time quadrature: (t_lo - tau0_k) fs + 1/2 - fs x_k . n.
+template <int K>
+__device__ __forceinline__ void delay_index(const PointC &P, const Sky &s, df out[K]) {
+  const float nx = s.cd * s.ca, ny = s.cd * s.sa;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const DetC &D = P.det[k];
+    df acc = df_mul_f(df{D.P[0], D.Plo[0]}, nx);
+    acc = df_add(acc, df_mul_f(df{D.P[1], D.Plo[1]}, ny));
+    acc = df_add(acc, df_mul(df{D.P[2], D.Plo[2]}, s.sd));
+    out[k] = df_add(df_add_f(df{D.c0, D.c0lo}, 0.5f), df{-acc.hi, -acc.lo});
+  }
+}
+
+// TMARG: the event time is marginalised by quadrature (Eq. lnL:tmarg) instead of sampled; the
+// sample's t uniform is unused, its Q rows span the whole time window (no staging), and the
+// likelihood is tmarg_term.
+template <int K, int NT, int LEARNED, int TMARG>
+__global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(CellLaunch L) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_item, s_point;
@@ -432,6 +449,13 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel(CellLaunch L)
     const float2 *Q = L.qa + P.q_off;
     constexpr int first = (NT == 4) ? -1 : 0;
 
+    const float4 *win[K];
+    int wlo[K], whi[K];
+    bool ok = true;
+    if (TMARG) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) { win[k] = nullptr; wlo[k] = 0; whi[k] = -1; }
+    } else {
     // A. window of every detector from the cell's samples
     int rmin[K], rmax[K];
 #pragma unroll
@@ -492,19 +516,17 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel(CellLaunch L)
     }
     __syncthreads();
     const bool staged = s_item != 0;
-    bool ok = true;
     if (staged) {
       ok = __syncthreads_and(mbar_wait(&bar, phase) ? 1 : 0) != 0;   // uniform across the CTA
       if (ok) phase ^= 1u;
       else flags |= RIFT_FLAG_TIMEOUT_BIT;
     }
-    const float4 *win[K];
-    int wlo[K], whi[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       win[k] = (ok && s_woff[k] >= 0) ? reinterpret_cast<const float4 *>(wbuf + s_woff[k]) : nullptr;
       wlo[k] = s_wlo[k];
       whi[k] = s_whi[k];
+    }
     }
 
     // C. evaluate
@@ -514,7 +536,8 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel(CellLaunch L)
       const Drawn d = draw_any<LEARNED>(L.seed, R, i, cell, tab, lnw, s_gmm, P.dref, L.d_lo3, L.d_span3);
       const Sky s = sky_of(P, d);
       df si[K];
-      time_index<K>(P, d, s, si);
+      if (TMARG) delay_index<K>(P, s, si);
+      else time_index<K>(P, d, s, si);
       float s2p, c2p;
       sincospif(2.f * d.u_psi, &s2p, &c2p);   // 2 psi = 2 pi u_psi
       SampleGeo g;
@@ -542,9 +565,15 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel(CellLaunch L)
       float sphi, cphi;
       sincospif(2.f * d.u_phi, &sphi, &cphi);
       swsh_canonical(P, sqrtf(d.c_frac), sqrtf(1.f - d.c_frac), cphi, sphi, Ys, ystride);
-      const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
-      const float quad = quad_term<K>(P, C, g, Ys, ystride);
-      const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
+      float lnL;
+      if (TMARG) {
+        const float quad = quad_term<K>(P, C, g, Ys, ystride);
+        lnL = tmarg_term<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
+      } else {
+        const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
+        const float quad = quad_term<K>(P, C, g, Ys, ystride);
+        lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
+      }
       float ell = lnL + d.lpq;
       if (L.fault_nan && i == 0u && R.round == 0u) ell = __int_as_float(0x7fc00000);   // injected (host-requested) fault
       if (L.dbg_ell && R.dbg_off >= 0) L.dbg_ell[R.dbg_off + i] = ell;
@@ -704,7 +733,8 @@ __global__ void tables_points_kernel(const unsigned long long *__restrict__ part
     float *cdf = tb + d * (nb + 1);
     if (part) {
       double S = 0.0;
-      for (int b = 0; b < nb; ++b) S += hs[d * nb + b];
+      if (!(d == 2 && rp[p].tmarg))   // the time table of a time-marginalised run stays uniform
+        for (int b = 0; b < nb; ++b) S += hs[d * nb + b];
       double tot = 0.0;
       for (int b = 0; b < nb; ++b) tot += (S > 0.0 ? (1.0 - eps) * hs[d * nb + b] / S + eps / nb : 1.0 / nb);
       double c = 0.0;
@@ -870,35 +900,37 @@ __global__ void harvest_theta_kernel(CellLaunch L, const RoundPt *__restrict__ l
   o[4] = logf(d.dist);
 }
 
-template <int K, int NT, int LEARNED>
+template <int K, int NT, int LEARNED, int TMARG>
 cudaError_t cells_kl(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED, TMARG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  cells_kernel<K, NT, LEARNED><<<grid, block, smem, st>>>(L);
+  cells_kernel<K, NT, LEARNED, TMARG><<<grid, block, smem, st>>>(L);
   return cudaGetLastError();
 }
 
 template <int K, int NT>
 cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
-  return L.learned ? cells_kl<K, NT, 1>(L, grid, block, smem, st) : cells_kl<K, NT, 0>(L, grid, block, smem, st);
+  if (L.tmarg) return cells_kl<K, NT, 0, 1>(L, grid, block, smem, st);
+  return L.learned ? cells_kl<K, NT, 1, 0>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 0>(L, grid, block, smem, st);
 }
 
-template <int K, int NT, int LEARNED>
+template <int K, int NT, int LEARNED, int TMARG>
 int cells_occ1(size_t smem, int block) {
   int nb = 0;
-  cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_kernel<K, NT, LEARNED>, block, smem);
+  cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED, TMARG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_kernel<K, NT, LEARNED, TMARG>, block, smem);
   return nb;
 }
 
 template <int K, int NT>
-int cells_occ(size_t smem, int block) {
-  const int a = cells_occ1<K, NT, 0>(smem, block), b = cells_occ1<K, NT, 1>(smem, block);
+int cells_occ(size_t smem, int block, int tmarg) {
+  if (tmarg) return cells_occ1<K, NT, 0, 1>(smem, block);
+  const int a = cells_occ1<K, NT, 0, 0>(smem, block), b = cells_occ1<K, NT, 1, 0>(smem, block);
   return a < b ? a : b;
 }
 
@@ -929,8 +961,8 @@ cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int blo
   return cudaErrorInvalidValue;
 }
 
-int cells_blocks_per_sm(int K, int ntap, size_t smem, int block) {
-#define RIFT_O(KK, TT) cells_occ<KK, TT>(smem, block)
+int cells_blocks_per_sm(int K, int ntap, size_t smem, int block, int tmarg) {
+#define RIFT_O(KK, TT) cells_occ<KK, TT>(smem, block, tmarg)
   RIFT_CELLS_DISPATCH(K, ntap, RIFT_O)
 #undef RIFT_O
   return 0;

@@ -35,7 +35,8 @@ struct ModeC {
 // it into shared memory.
 struct PointC {
   int K, M, T, Mp;    // detectors, modes, Q samples, Q row stride (M rounded up to even)
-  int npair, interp, pad0, pad1;
+  int npair, interp;
+  int J, pad1;        // J: points of the time quadrature, floor((t_hi - t_lo) fs)
   long long q_off;    // offset of this point's Q in the Q arena (float2 units), 16-byte aligned
   long long uv_off;   // offset of this point's pair coefficients (float4 units)
   float fs, dref;     // Q rate (Hz), D_ref (Mpc)
@@ -343,4 +344,83 @@ __device__ __forceinline__ float quad_term(const PointC &P, const float4 *__rest
     quad += f2 * A[k] + (gr * Br[k] - gi * Bi[k]);
   }
   return quad;
+}
+
+// ---------------------------------------------------------------------------
+// Time-marginalised likelihood, Eq. (lnL:tmarg): ln (1/J) sum_j exp(lnL(theta, t_j)) over the
+// midpoints t_j = t_lo + (j + 1/2)/fs, j < J.  For detector k the Q index of t_j + delay_k is
+// s0_k + j with s0_k = (t_lo - tau0_k) fs + 1/2 + delay_k fs, so the interpolation weights are
+// the same for every j and consecutive j use consecutive rows: Z_k[i] = sum_lm conj(Y_lm)
+// Q_{k,lm}[i] is formed once per row and the NT taps slide along.  lnL_j = x (Re sum_k F_k
+// Zbar_k(j) - x quad / 4); the log-sum-exp over j keeps a running maximum.
+// Y: the point's harmonics in registers (pairs of modes, zero beyond M).
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ float2 z_row(const float4 *__restrict__ row, const float2 (&y)[RIFT_MAXM + 1], int npairs) {
+  float zr = 0.f, zi = 0.f;
+#pragma unroll
+  for (int a2 = 0; a2 < (RIFT_MAXM + 1) / 2; ++a2) {
+    if (a2 < npairs) {
+      const float4 q = row[a2];
+      const float2 y0 = y[2 * a2], y1 = y[2 * a2 + 1];
+      // conj(y) q
+      zr = fmaf(y0.x, q.x, fmaf(y0.y, q.y, zr));
+      zi = fmaf(y0.x, q.y, fmaf(-y0.y, q.x, zi));
+      zr = fmaf(y1.x, q.z, fmaf(y1.y, q.w, zr));
+      zi = fmaf(y1.x, q.w, fmaf(-y1.y, q.z, zi));
+    }
+  }
+  return make_float2(zr, zi);
+}
+
+template <int K, int NT>
+__device__ __forceinline__ float tmarg_term(const PointC &P, const float2 *__restrict__ Q, const df s0[K],
+                                            const float2 F[K], const float2 *Ys, int ystride, float x, float quad,
+                                            uint32_t &flags) {
+  constexpr int first = (NT == 4) ? -1 : 0;
+  float2 y[RIFT_MAXM + 1];
+#pragma unroll
+  for (int a = 0; a < RIFT_MAXM + 1; ++a) y[a] = (a < P.M) ? Ys[a * ystride] : make_float2(0.f, 0.f);
+  const int rs = P.Mp >> 1, npairs = (P.M + 1) >> 1;
+  const int J = P.J;
+  float w[K][NT];
+  int r0[K];
+  float2 z[K][NT];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int i; float mu;
+    df sk = s0[k];
+    if (NT == 1) sk = df_add_f(sk, 0.5f);
+    df_floor(sk, i, mu);
+    interp_weights<NT>(mu, w[k]);
+    r0[k] = i + first;
+    if (r0[k] < 0 || r0[k] + J - 1 + NT > P.T) {
+      flags |= RIFT_FLAG_WINDOW;
+      r0[k] = min(max(r0[k], 0), P.T - NT - (J - 1));
+      if (r0[k] < 0) r0[k] = 0;
+    }
+    const float4 *base = reinterpret_cast<const float4 *>(Q + ((long long)k * P.T + r0[k]) * P.Mp);
+#pragma unroll
+    for (int r = 0; r < NT - 1; ++r) z[k][r] = z_row<NT>(base + (size_t)r * rs, y, npairs);
+  }
+  const float c = -0.25f * x * quad;
+  float m = -INFINITY, s = 0.f;
+  for (int j = 0; j < J; ++j) {
+    float lin = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int row = min(r0[k] + j + NT - 1, P.T - 1);
+      z[k][NT - 1] = z_row<NT>(reinterpret_cast<const float4 *>(Q + ((long long)k * P.T + row) * P.Mp), y, npairs);
+      float zr = 0.f, zi = 0.f;
+#pragma unroll
+      for (int r = 0; r < NT; ++r) { zr = fmaf(w[k][r], z[k][r].x, zr); zi = fmaf(w[k][r], z[k][r].y, zi); }
+      lin += F[k].x * zr - F[k].y * zi;
+#pragma unroll
+      for (int r = 0; r < NT - 1; ++r) z[k][r] = z[k][r + 1];
+    }
+    const float l = x * (lin + c);
+    if (l > m) { s = fmaf(s, expf(m - l), 1.f); m = l; }
+    else s += expf(l - m);
+  }
+  return m + logf(s) - logf((float)J);
 }

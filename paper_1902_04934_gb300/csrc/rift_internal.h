@@ -46,6 +46,8 @@ struct RoundPt {
   const float *tab;        // [3][nb+1] float32 CDF tables
   const float *lnw;        // [3][nb]   -ln(nb p_b)
   const float *gmm;        // [RIFT_GMM_FLOATS] learned proposal of the point (proposal 2)
+  int tmarg;               // time marginalised by quadrature: the t table stays uniform
+  int pad_;
 };
 
 // Learned proposal of one point as the sampler reads it (floats): ln pi[8], float32 cumulative
@@ -76,6 +78,7 @@ struct CellLaunch {
   int learned;                 // every point samples from its learned proposal
   int fault_nan;               // injected fault: sample 0 of round 0 of every point has a NaN log weight
   int fault_stall;             // injected fault: window copies announced on the mbarrier but never issued
+  int tmarg;                   // the event time is marginalised by quadrature (Eq. lnL:tmarg)
 };
 
 // Device-side round control of a batched run replayed as a CUDA graph.
@@ -145,11 +148,14 @@ cudaError_t launch_lnl_array(int K, const PointC *pt_dev, const PointC &pt_host,
                              const float4 *c_arena, size_t n, const float *ra, const float *dec, const float *t,
                              const float *psi, const float *phi, const float *incl, const float *dist, float *out,
                              uint32_t *flags, cudaStream_t st);
+cudaError_t launch_lnl_tmarg(int K, const PointC *pt_dev, const PointC &ph, const float2 *qa, const float4 *ca,
+                             size_t n, const float *ra, const float *dec, const float *psi, const float *phi,
+                             const float *incl, const float *dist, float *out, uint32_t *flags, cudaStream_t st);
 
 // Cell kernel (mc.cu)
 size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block);
 cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st);
-int cells_blocks_per_sm(int K, int ntap, size_t smem, int block);
+int cells_blocks_per_sm(int K, int ntap, size_t smem, int block, int tmarg = 0);
 cudaError_t launch_merge_points(const Part *partials, const RoundPt *rp, int n_points, AccState *acc,
                                 cudaStream_t st);
 cudaError_t launch_hist_points(const float *ell, const uint32_t *bins, const RoundPt *rp, int n_points,

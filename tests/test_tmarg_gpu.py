@@ -1,0 +1,140 @@
+"""GPU parity of the time-marginalised likelihood, Eq. (lnL:tmarg), against the FP64 oracle.
+
+Per draw the tolerance is that of the per-sample likelihood, 1e-3 * max(1, <h|h>/900): the
+log-sum-exp over the time grid is dominated by its largest terms, whose errors it inherits."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import workload as W
+from oracle import likelihood as L
+from oracle import tmarg as TM
+
+pytestmark = pytest.mark.gpu
+
+
+def _draws(n, seed):
+    r = np.random.default_rng(seed)
+    th = dict(ra=r.uniform(0, 2 * np.pi, n), dec=np.arcsin(r.uniform(-1, 1, n)), psi=r.uniform(0, np.pi, n),
+              phi=r.uniform(0, 2 * np.pi, n), incl=np.arccos(r.uniform(-1, 1, n)),
+              dist=np.cbrt(r.uniform(1, 1000.0 ** 3, n)))
+    return {k: v.astype(np.float32) for k, v in th.items()}
+
+
+def _tol(pt, th64):
+    z = dict(pt)
+    z["Q"] = np.zeros_like(pt["Q"])
+    hh = -2.0 * L.lnL_factorised(z, t=np.zeros_like(th64["ra"]), **th64)
+    return 1e-3 * np.maximum(1.0, hh / 900.0)
+
+
+def _gpu(lib, h, th):
+    import torch
+    d = {k: torch.as_tensor(v, device="cuda") for k, v in th.items()}
+    out = lib.rift_ile_lnL_tmarg(h, d["ra"], d["dec"], d["psi"], d["phi"], d["incl"], d["dist"])
+    torch.cuda.synchronize()
+    lib.rift_ile_check(h)
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("which,n,interp", [("small", 1500, 3), ("small", 400, 1), ("small", 400, 0),
+                                            ("full", 160, 3)])
+def test_tmarg_array_parity(lib, cuda, which, n, interp):
+    spec = W.cfg_small() if which == "small" else W.cfg_full()
+    pt = W.make_point(spec, 8)
+    h = lib.rift_ile_create(pt, interp=interp)
+    th = _draws(n, 9)
+    th64 = {k: v.astype(np.float64) for k, v in th.items()}
+    got = _gpu(lib, h, th)
+    want = TM.lnL_tmarg(pt, interp=interp, **th64)
+    err = np.abs(got - want)
+    tol = _tol(pt, th64)
+    i = int(np.argmax(err / tol))
+    assert np.all(err <= tol), (float(err[i]), float(tol[i]), float(want[i]), i)
+    lib.rift_ile_destroy(h)
+
+
+def test_tmarg_near_the_peak(lib, cuda):
+    """Draws concentrated where L_margT is largest (the terms that dominate lnL_marg)."""
+    pt = W.make_point(W.cfg_small(), 8)
+    h = lib.rift_ile_create(pt)
+    th = _draws(4000, 10)
+    th64 = {k: v.astype(np.float64) for k, v in th.items()}
+    got = _gpu(lib, h, th)
+    top = np.argsort(got)[-200:]
+    sub = {k: v[top] for k, v in th64.items()}
+    want = TM.lnL_tmarg(pt, **sub)
+    err = np.abs(got[top] - want)
+    assert np.all(err <= _tol(pt, sub)), float(err.max())
+    lib.rift_ile_destroy(h)
+
+
+def _marg(lib, h, n, **kw):
+    import torch
+    dbg = torch.full((kw["max_evals"],), float("nan"), dtype=torch.float32, device="cuda")
+    r = lib.rift_ile_marginalize(h, dbg_ell=dbg, time_marg=1, n_per_round=n, **kw)
+    torch.cuda.synchronize()
+    return r, dbg.cpu().numpy().astype(np.float64)
+
+
+def test_tmarg_marginalize_matches_oracle(lib, cuda):
+    """Same Philox draws on both sides (the t uniform unused), sky strata 4 x 2: per-draw log weights
+    within the per-draw tolerance, lnL_marg within 1e-4."""
+    from oracle import mc
+    pt = W.make_point(W.cfg_small(), 8)
+    h = lib.rift_ile_create(pt)
+    n, S = 1500, (4, 2, 1)
+    res, ell = _marg(lib, h, n, seed=71, max_evals=2 * n, strata=S)
+    pr = mc.Prior(pt["t_lo"], pt["t_hi"])
+    ref = mc.marginalize(pt, 71, 0, pr, n, 2 * n, 1e300, strata=S, time_marg=True, keep=True)
+    want = np.concatenate([hh["ell"] for hh in ref["history"]])
+    th0, _, _ = mc.draw(71, 0, 0, np.arange(n, dtype=np.uint64), pr, None, S, n)
+    th1, _, _ = mc.draw(71, 0, 1, np.arange(n, dtype=np.uint64), pr, None, S, n)
+    th64 = {k: np.concatenate([th0[k], th1[k]]) for k in th0}
+    tol = _tol(pt, dict(ra=th64["ra"], dec=np.arcsin(th64["sindec"]), psi=th64["psi"], phi=th64["phi"],
+                        incl=np.arccos(th64["cosi"]), dist=th64["dist"]))
+    assert np.all(np.abs(ell - want) <= tol), float(np.max(np.abs(ell - want) / tol))
+    assert abs(res["lnL_marg"] - ref["lnL_marg"]) < 1e-4, (res["lnL_marg"], ref["lnL_marg"])
+    assert res["n_evals"] == 2 * n and res["strata"] == S
+    lib.rift_ile_destroy(h)
+
+
+def test_tmarg_adaptive_fixed_tables_matches_oracle(lib, cuda):
+    """Adaptive (ra, sin dec) tables given, time table uniform, no rebuild: identical draws."""
+    from oracle import mc
+    pt = W.make_point(W.cfg_small(), 8)
+    nb = 32
+    r = np.random.default_rng(4)
+    tab = np.empty((3, nb + 1), dtype=np.float32)
+    for d in range(2):
+        p = r.uniform(0.2, 3.0, nb)
+        c = np.concatenate([[0.0], np.cumsum(p / p.sum())])
+        tab[d] = c.astype(np.float32)
+        tab[d, 0], tab[d, -1] = 0.0, 1.0
+    tab[2] = mc.uniform_time_table(nb)
+    h = lib.rift_ile_create(pt)
+    n = 1200
+    res, _ = _marg(lib, h, n, seed=72, max_evals=n, proposal="adaptive", n_bins=nb, tables=tab, adapt_rounds=0,
+                   strata=(2, 2, 1))
+    ref = mc.marginalize(pt, 72, 0, mc.Prior(pt["t_lo"], pt["t_hi"]), n, n, 1e300, adaptive=True, n_bins=nb,
+                         tables=tab, adapt_rounds=0, strata=(2, 2, 1), time_marg=True)
+    assert abs(res["lnL_marg"] - ref["lnL_marg"]) < 1e-4, (res["lnL_marg"], ref["lnL_marg"])
+    lib.rift_ile_destroy(h)
+
+
+def test_tmarg_estimate_agrees_with_sampled_time(lib, cuda):
+    """Both estimators target the same L_marg (time integral by quadrature or by sampling): on a
+    weak signal, where both converge, they agree within their Monte Carlo errors."""
+    spec = W.cfg_small()
+    spec.snr = 4.0
+    pt = W.make_point(spec, 12)
+    h = lib.rift_ile_create(pt)
+    a = lib.rift_ile_marginalize(h, seed=73, n_per_round=1_000_000, max_evals=4_000_000)
+    b = lib.rift_ile_marginalize(h, seed=74, n_per_round=20000, max_evals=80000, time_marg=1)
+    sig = math.hypot(a["sigma"], b["sigma"])
+    assert abs(a["lnL_marg"] - b["lnL_marg"]) < 4 * sig + 0.01, (a, b)
+    assert b["n_eff"] > 50
+    lib.rift_ile_destroy(h)
