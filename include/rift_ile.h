@@ -114,8 +114,8 @@ rift_status rift_ile_lnL_host(rift_ile *h, size_t n, const float *ra, const floa
                               float *lnL_out);
 
 /*
- * Time-marginalised log-likelihood, Eq. (lnL:tmarg) (Sec. II.C: the event time is marginalised
- * by direct quadrature for each draw of the other extrinsic parameters), at caller draws of
+ * Time-marginalised log-likelihood, Eq. (lnL:tmarg) (Sec. II.C: the event time is integrated
+ * numerically for every draw of the other extrinsic parameters), at caller draws of
  * point 0: ln L_margT = ln (1/J) sum_j exp(lnL(theta, t_j)), midpoint rule on the sampling
  * interval of Q, t_j = t_lo + (j + 1/2)/fs, j < J = floor((t_hi - t_lo) fs), with lnL of
  * rift_ile_lnL.  Device float32 arrays of length n: ra, dec, psi, phi, incl, D (Mpc); out:

@@ -2,8 +2,8 @@
 and the benchmark's CPU leg use this package).
 
 Eq. (lnL:tmarg): for each Monte Carlo draw of the extrinsic parameters other than the event time,
-L_margT = int L dt / T over the coincidence window T (Sec. II.C: the event time is marginalised
-by direct quadrature, the other coordinates by Monte Carlo).
+L_margT = int L dt / T over the coincidence window T (Sec. II.C: the event time is integrated
+numerically for every draw, the other coordinates by Monte Carlo).
 
 Reading of the quadrature (the paper does not print it): the midpoint rule on the sampling
 interval of the Q time series, t_j = t_lo + (j + 1/2) / fs for j = 0 .. J-1 with
