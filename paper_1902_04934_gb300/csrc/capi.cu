@@ -582,7 +582,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     if (learned) {
       ls[0] = ls[1] = ls[2] = 0;
     } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
-      if (o->time_marg) choose_strata_sky(npr, ls, 128);
+      if (o->time_marg) choose_strata_sky(npr, ls, std::max(16, h->cell_target / 5));   // a draw costs ~J samples
       else choose_strata(h->pts[p].c, npr, ls, h->cell_target);
     } else {
       for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
