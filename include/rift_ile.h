@@ -178,8 +178,8 @@ typedef struct {
                             (rift_ile_lnL_tmarg), instead of sampling it; the draws cover (ra, dec,
                             psi, phi, incl, D), strata and adaptive tables cover (ra, sin dec) only
                             (the time table stays uniform), n_evals counts draws.  Prior or adaptive
-                            proposals, single-point and multi-point handles through
-                            rift_ile_marginalize; not with the learned proposal or the batched runner. */
+                            proposals, single-point calls and the batched runner; not with the
+                            learned proposal (RIFT_EUNSUPPORTED).                                 */
 } rift_mc_opts;
 
 /* Size of the sampler-state blob of rift_mc_opts.resume / save (same library build and byte order). */

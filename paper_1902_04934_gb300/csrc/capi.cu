@@ -1001,7 +1001,6 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   rift_status s = check_opts(h, o);
   if (s != RIFT_OK) return s;
   if (o->resume || o->save) return fail(h, RIFT_EUNSUPPORTED, "resume/save: single-point marginalisation only");
-  if (o->time_marg) return fail(h, RIFT_EUNSUPPORTED, "time marginalisation: use rift_ile_marginalize");
   const int np = h->n_points;
   std::memset(res, 0, sizeof(*res) * np);
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
@@ -1015,11 +1014,13 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
     if (learned) {
       ls[0] = ls[1] = ls[2] = 0;
     } else if (o->strata[0] == 0 && o->strata[1] == 0 && o->strata[2] == 0) {
-      choose_strata(h->pts[p].c, o->n_per_round, ls, h->cell_target);
+      if (o->time_marg) choose_strata_sky(o->n_per_round, ls, std::max(16, h->cell_target / 5));
+      else choose_strata(h->pts[p].c, o->n_per_round, ls, h->cell_target);
     } else {
       for (int d = 0; d < 3; ++d) ls[d] = log2_pow2(o->strata[d]);
       if (ls[0] < 0 || ls[1] < 0 || ls[2] < 0) return fail(h, RIFT_EINVAL, "strata must be powers of two");
       if ((1 << (ls[0] + ls[1] + ls[2])) > RIFT_MAX_CELLS) return fail(h, RIFT_EINVAL, "more than RIFT_MAX_CELLS cells");
+      if (o->time_marg && ls[2] != 0) return fail(h, RIFT_EINVAL, "time-marginalised rounds are not stratified in t");
     }
     items += ((size_t)1 << (ls[0] + ls[1] + ls[2])) + o->n_per_round / RIFT_CHUNK + 1;
   }
@@ -1072,6 +1073,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   B.keep_ell = keep_ell ? 1 : 0;
   B.gmm = h->gmm;
   B.last = keep_ell ? h->last : nullptr;
+  B.tmarg = o->time_marg ? 1 : 0;
   if (adaptive) {
     float u[3 * (RIFT_MAXBINS + 1)];
     const float *src = o->tables;
@@ -1097,7 +1099,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
   budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
   const size_t smem = fixed + (size_t)budget;
-  const int bps = cells_blocks_per_sm(K, NT, smem, block);
+  const int bps = cells_blocks_per_sm(K, NT, smem, block, o->time_marg ? 1 : 0);
   if (bps < 1) return fail(h, RIFT_EUNSUPPORTED, "cell kernel does not fit on an SM");
   CellLaunch L{};
   L.seed = o->seed;

@@ -837,6 +837,7 @@ __global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState 
       N.lcorr1 = N.base ? (float)log((double)n / ((double)C * N.base)) : 0.f;
       N.ell_off = (B.adaptive || B.keep_ell) ? (long long)p * B.npr : -1;
       if (B.learned) N.gmm = B.gmm + (size_t)p * RIFT_GMM_FLOATS;
+      N.tmarg = B.tmarg;
       if (B.adaptive) {
         N.tab = B.tables + ((size_t)tabbuf * B.np + p) * tstride;
         N.lnw = B.lnw + ((size_t)tabbuf * B.np + p) * wstride;

@@ -117,6 +117,7 @@ struct BatchCtl {
   int keep_ell;             // keep per-sample log weights of every round (harvest)
   const float *gmm;         // [np][RIFT_GMM_FLOATS]
   RoundPt *last;            // [np] the last round each point ran (harvest)
+  int tmarg;                // the event time is marginalised by quadrature
 };
 
 // Scratch of the Monte Carlo runner (device pointers unless noted).

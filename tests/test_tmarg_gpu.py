@@ -138,3 +138,21 @@ def test_tmarg_estimate_agrees_with_sampled_time(lib, cuda):
     assert abs(a["lnL_marg"] - b["lnL_marg"]) < 4 * sig + 0.01, (a, b)
     assert b["n_eff"] > 50
     lib.rift_ile_destroy(h)
+
+
+def test_tmarg_batch_equals_single_point_runs(lib, cuda):
+    """The batched graph runner with the time quadrature gives every point exactly its
+    single-point result (same draws, same rounds, same stopping)."""
+    specs = W.batch_specs(3, seed=8, t_range=(800, 1200))
+    pts = [W.make_point(sp, 20 + i) for i, sp in enumerate(specs)]
+    hb = lib.rift_ile_batch_create(pts)
+    kw = dict(seed=81, n_per_round=4000, max_evals=12000, n_eff_target=1e300, time_marg=1, proposal="adaptive",
+              n_bins=32)
+    batch = lib.rift_ile_batch_marginalize(hb, **kw)
+    for i, p in enumerate(pts):
+        h = lib.rift_ile_create(p)
+        one = lib.rift_ile_marginalize(h, point_id=i, **kw)
+        assert batch[i]["n_evals"] == one["n_evals"] and batch[i]["rounds"] == one["rounds"]
+        assert batch[i]["lnL_marg"] == one["lnL_marg"], (i, batch[i]["lnL_marg"], one["lnL_marg"])
+        lib.rift_ile_destroy(h)
+    lib.rift_ile_destroy(hb)
