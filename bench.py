@@ -439,7 +439,25 @@ def run_extras(args, rift, W):
         "median_n_eff_learned": float(np.median([l["n_eff"] for l in learned])),
         "median_abs_dlnL_marg": float(np.median(dl)), "frac_within_0.05": float(np.mean(dl <= 0.05))}
     out["time_marginalised"] = run_tmarg(rift, W, pts[:16])
+    out["quv"] = run_quv(rift, W)
     return out
+
+
+def run_quv(rift, W):
+    """Eq. (QUV) on the device for the full-size point (direct sums over the band: no FFT), the
+    wall time of the C call including its uploads and downloads, after one warm call."""
+    pt = W.make_point(W.cfg_full(), point_seed(0))
+    rift.rift_quv(pt)
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        rift.rift_quv(pt)
+        times.append(time.perf_counter() - t0)
+    K, M, T = pt["Q"].shape
+    nb = int((pt["weight"] != 0).any(axis=0).sum())
+    return {"workload": f"K={K}, M={M}, n_t={T}, {nb} band bins of {len(pt['freqs'])}",
+            "ms_per_point": 1e3 * statistics.median(times),
+            "complex_macs": K * M * T * nb + 2 * K * M * M * nb}
 
 
 def run_tmarg(rift, W, pts):

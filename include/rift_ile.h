@@ -125,6 +125,54 @@ rift_status rift_ile_lnL_host(rift_ile *h, size_t n, const float *ra, const floa
 rift_status rift_ile_lnL_tmarg(rift_ile *h, size_t n, const float *ra, const float *dec, const float *psi,
                                const float *phi, const float *incl, const float *dist, float *out);
 
+/*
+ * Frequency-domain description of one point, for forming Q, U, V of Eq. (QUV) on the device.
+ * Host arrays, FP64 unless noted, copied during the call (the caller keeps ownership).
+ * Frequency grid: n_f bins, bin i at f_i = nu[i] * df with integer nu[i] (negative for f < 0);
+ * mirror[i] is the bin of -f_i.  weight[k][i] = 1/S_k(|f_i|) inside the band, 0 outside
+ * (Eq. overlap).  Q grid: n_t samples of detector k at q_t0_gps[k] + j/fs, with fs/df an integer
+ * n >= n_t.  The remaining fields are those of rift_ile_desc.
+ */
+typedef struct {
+  int n_det;                /* K                                                      */
+  const double *det_tensor; /* [K][3][3]                                              */
+  const double *det_pos;    /* [K][3] metres                                          */
+  int n_modes;              /* M                                                      */
+  const int *lm;            /* [M][2]                                                 */
+  int n_f;                  /* frequency bins                                         */
+  const int *nu;            /* [n_f] f_i / df (int32)                                 */
+  double df;                /* Hz                                                     */
+  const double *hlm;        /* [M][n_f] complex128 h_lm(f_i) (at D_ref)               */
+  const double *data;       /* [K][n_f] complex128 d_k(f_i)                           */
+  const double *weight;     /* [K][n_f] band / S_k(|f_i|)                             */
+  const int *mirror;        /* [n_f] bin of -f_i (int32)                              */
+  int n_t;                  /* Q samples per (detector, mode)                         */
+  const double *q_t0_gps;   /* [K] GPS time of Q sample 0                             */
+  double fs;                /* Q sampling rate, Hz                                    */
+  double t_ref_gps, d_ref_mpc, t_lo, t_hi;
+  int interp;
+  void *cuda_stream;
+} rift_ile_fd_desc;
+
+/*
+ * Eq. (QUV) on the device (direct sums over the bins with nonzero weight; FP32 terms summed in
+ * blocks of 32 into double-float totals):
+ *   Q[k][m][j] = 2 df sum_i exp(2 pi i f_i tau_j) conj(h_m(f_i)) d_k(f_i) w_k(f_i),
+ *                tau_j = q_t0_gps[k] - t_ref_gps + j/fs,
+ *   U[k][m][m'] = 2 df sum_i conj(h_m(f_i)) h_m'(f_i) w_k(f_i),
+ *   V[k][m][m'] = 2 df sum_i h_m(-f_i) h_m'(f_i) w_k(f_i).
+ * Outputs: host complex128 arrays in the layouts of rift_ile_desc (Q [K][M][n_t], U, V [K][M][M]).
+ * Synchronous on d->cuda_stream.  RIFT_EINVAL for inconsistent grids; detail in
+ * rift_quv_last_error() (per thread).
+ */
+rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V);
+const char *rift_quv_last_error(void);
+
+/* rift_quv followed by rift_ile_create on the result (U made exactly Hermitian and V exactly
+ * symmetric by averaging each pair of transposed elements): a handle built from frequency-domain
+ * inputs. */
+rift_status rift_ile_create_fd(const rift_ile_fd_desc *d, rift_ile **out);
+
 /* Reads and clears the device status word (out-of-window taps, non-finite lnL). */
 rift_status rift_ile_check(rift_ile *h);
 

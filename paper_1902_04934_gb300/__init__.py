@@ -45,6 +45,14 @@ class Desc(C.Structure):
                 ("t_hi", C.c_double), ("interp", C.c_int), ("cuda_stream", C.c_void_p)]
 
 
+class FdDesc(C.Structure):
+    _fields_ = [("n_det", C.c_int), ("det_tensor", C.c_void_p), ("det_pos", C.c_void_p), ("n_modes", C.c_int),
+                ("lm", C.c_void_p), ("n_f", C.c_int), ("nu", C.c_void_p), ("df", C.c_double), ("hlm", C.c_void_p),
+                ("data", C.c_void_p), ("weight", C.c_void_p), ("mirror", C.c_void_p), ("n_t", C.c_int),
+                ("q_t0_gps", C.c_void_p), ("fs", C.c_double), ("t_ref_gps", C.c_double), ("d_ref_mpc", C.c_double),
+                ("t_lo", C.c_double), ("t_hi", C.c_double), ("interp", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
 class McOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("point_id", C.c_uint32), ("n_per_round", C.c_uint32),
                 ("max_evals", C.c_uint64), ("n_eff_target", C.c_double), ("d_lo", C.c_double),
@@ -91,6 +99,9 @@ def _load():
         "rift_ile_lnL_host": (I, [P, S] + [P] * 8),
         "rift_ile_lnL_tmarg": (I, [P, S] + [P] * 7),
         "rift_ile_check": (I, [P]),
+        "rift_quv": (I, [P, P, P, P]),
+        "rift_quv_last_error": (C.c_char_p, []),
+        "rift_ile_create_fd": (I, [P, C.POINTER(P)]),
         "rift_ile_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
         "rift_ile_batch_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
         "rift_ile_marginalize_static": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
@@ -177,6 +188,58 @@ def _desc(pt, interp=3, stream=None, keep=None):
     d.interp = int(interp)
     d.cuda_stream = stream
     return d
+
+
+def _fd_desc(pt, interp=3, stream=None, keep=None):
+    """Frequency-domain descriptor of a point dict with freqs, df, hlm, data, weight, mirror, n_t."""
+    K = int(np.asarray(pt["det_tensor"]).shape[0])
+    hlm = np.ascontiguousarray(np.asarray(pt["hlm"], dtype=np.complex128))
+    M, nf = hlm.shape
+    df = float(pt["df"])
+    arrs = dict(det_tensor=_f64(pt["det_tensor"]), det_pos=_f64(pt["det_pos"]),
+                lm=np.ascontiguousarray(np.asarray(pt["lm"], dtype=np.int32).reshape(-1, 2)),
+                nu=np.ascontiguousarray(np.rint(np.asarray(pt["freqs"]) / df).astype(np.int32)),
+                hlm=hlm.view(np.float64),
+                data=np.ascontiguousarray(np.asarray(pt["data"], dtype=np.complex128)).view(np.float64),
+                weight=_f64(pt["weight"]), mirror=np.ascontiguousarray(np.asarray(pt["mirror"], dtype=np.int32)),
+                q_t0_gps=_f64(pt["q_t0_gps"]))
+    if keep is not None:
+        keep.append(arrs)
+    d = FdDesc()
+    d.n_det, d.n_modes, d.n_f, d.n_t = K, M, nf, int(pt["n_t"])
+    for key in ("det_tensor", "det_pos", "lm", "nu", "hlm", "data", "weight", "mirror", "q_t0_gps"):
+        setattr(d, key, arrs[key].ctypes.data)
+    d.df, d.fs = df, float(pt["fs"])
+    d.t_ref_gps, d.d_ref_mpc = float(pt["t_ref_gps"]), float(pt["d_ref_mpc"])
+    d.t_lo, d.t_hi = float(pt["t_lo"]), float(pt["t_hi"])
+    d.interp = int(interp)
+    d.cuda_stream = stream
+    return d
+
+
+def rift_quv(pt, stream=None):
+    """Eq. (QUV) on the device from the point's frequency-domain arrays: (Q, U, V) complex128."""
+    keep = []
+    d = _fd_desc(pt, 3, stream, keep)
+    K, M, T = d.n_det, d.n_modes, d.n_t
+    Q = np.empty((K, M, T), dtype=np.complex128)
+    U = np.empty((K, M, M), dtype=np.complex128)
+    V = np.empty((K, M, M), dtype=np.complex128)
+    st = _lib.rift_quv(C.byref(d), Q.ctypes.data, U.ctypes.data, V.ctypes.data)
+    if st != 0:
+        raise RiftError(st, (_lib.rift_quv_last_error() or b"").decode())
+    return Q, U, V
+
+
+def rift_ile_create_fd(pt, interp=3, stream=None):
+    """A handle whose Q, U, V are formed on the device from frequency-domain inputs."""
+    keep = []
+    d = _fd_desc(pt, interp, stream, keep)
+    out = C.c_void_p()
+    st = _lib.rift_ile_create_fd(C.byref(d), C.byref(out))
+    if st != 0:
+        raise RiftError(st, (_lib.rift_quv_last_error() or b"rift_ile_create_fd failed").decode())
+    return Handle(out.value, 1)
 
 
 def rift_ile_create(pt, interp=3, stream=None):

@@ -1,0 +1,279 @@
+// Mode inner products of Eq. (QUV) on the device, from frequency-domain mode waveforms, data
+// and noise weights:
+//   Q_{k,lm}(tau_j) = 2 df sum_f exp(2 pi i f tau_j) conj(h_lm(f)) d_k(f) w_k(f),
+//   U_{k,lm,l'm'}   = 2 df sum_f conj(h_lm(f)) h_l'm'(f) w_k(f),
+//   V_{k,lm,l'm'}   = 2 df sum_f h_lm(-f) h_l'm'(f) w_k(f),
+// w_k = band / S_k (Eq. overlap).  The grid is f = nu df (integer nu) and tau_j = tau0_k + j / fs
+// with n = fs / df an integer, so exp(2 pi i f tau_j) = exp(2 pi i nu df tau0_k)
+// exp(2 pi i (nu j mod n) / n): the first factor is folded into the per-bin data term on the host
+// in FP64, the second comes from an exact integer index.  Sums are FP32 over blocks of 32 bins
+// added into double-float totals.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rift_ile.h"
+#include "rift_device.cuh"
+
+namespace {
+
+constexpr int kQThreads = 128;   // grid times per CTA
+constexpr int kQModes = 7;       // modes per CTA
+constexpr int kChunk = 256;      // band bins staged per pass
+
+__device__ __forceinline__ void df_acc(df &acc, float v) { acc = df_add_f(acc, v); }
+
+// Q of detector blockIdx.z, modes [blockIdx.y * kQModes, +kQModes), times [blockIdx.x * kQThreads, +).
+// X[a][b] = conj(h_a(f_b)) B_k(f_b) is formed per staged chunk; the twiddle index nu_b j mod n
+// advances by j between consecutive bins of the same run and is recomputed at run starts.
+__global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restrict__ H, const float2 *__restrict__ Bk,
+                                                          const int *__restrict__ nu, const int *__restrict__ run_start,
+                                                          int nb, int M, int nt, int n, double2 *__restrict__ Q) {
+  __shared__ float2 sX[kQModes][kChunk];
+  __shared__ int sNu[kChunk], sRun[kChunk];
+  const int k = blockIdx.z, a0 = blockIdx.y * kQModes;
+  const int j = blockIdx.x * kQThreads + threadIdx.x;
+  const int ma = min(kQModes, M - a0);
+  df accr[kQModes], acci[kQModes];
+#pragma unroll
+  for (int a = 0; a < kQModes; ++a) { accr[a] = df{0.f, 0.f}; acci[a] = df{0.f, 0.f}; }
+  const float inv_n2 = 2.0f / (float)n;
+  int idx = 0;
+  for (int b0 = 0; b0 < nb; b0 += kChunk) {
+    const int cb = min(kChunk, nb - b0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cb * kQModes; t += blockDim.x) {
+      const int a = t / cb, b = t - a * cb;
+      float2 x = make_float2(0.f, 0.f);
+      if (a < ma) {
+        const float2 h = H[(size_t)(a0 + a) * nb + b0 + b];
+        const float2 c = Bk[(size_t)k * nb + b0 + b];
+        x = make_float2(h.x * c.x + h.y * c.y, h.x * c.y - h.y * c.x);   // conj(h) c
+      }
+      sX[a][b] = x;
+    }
+    for (int t = threadIdx.x; t < cb; t += blockDim.x) { sNu[t] = nu[b0 + t]; sRun[t] = run_start[b0 + t]; }
+    __syncthreads();
+    float pr[kQModes], pi[kQModes];
+#pragma unroll
+    for (int a = 0; a < kQModes; ++a) { pr[a] = 0.f; pi[a] = 0.f; }
+    for (int b = 0; b < cb; ++b) {
+      if (b == 0 || sRun[b]) idx = (int)(((long long)sNu[b] * j) % n);
+      else { idx += j; if (idx >= n) idx -= n; }
+      float sn, cs;
+      sincospif((float)idx * inv_n2, &sn, &cs);
+#pragma unroll
+      for (int a = 0; a < kQModes; ++a) {
+        const float2 x = sX[a][b];
+        pr[a] = fmaf(x.x, cs, fmaf(-x.y, sn, pr[a]));
+        pi[a] = fmaf(x.x, sn, fmaf(x.y, cs, pi[a]));
+      }
+      if ((b & 31) == 31 || b == cb - 1) {
+#pragma unroll
+        for (int a = 0; a < kQModes; ++a) { df_acc(accr[a], pr[a]); df_acc(acci[a], pi[a]); pr[a] = 0.f; pi[a] = 0.f; }
+      }
+    }
+  }
+  if (j < nt) {
+#pragma unroll
+    for (int a = 0; a < kQModes; ++a)
+      if (a < ma)
+        Q[((size_t)k * M + a0 + a) * nt + j] =
+            make_double2((double)accr[a].hi + (double)accr[a].lo, (double)acci[a].hi + (double)acci[a].lo);
+  }
+}
+
+// U and V of detector blockIdx.y, pair (a, b) over a flat thread index: Hw[k][b] = h_b w_k (formed on
+// the host in FP64, so the size of 1/S stays out of FP32), Hm[a] = h_a(-f); scale[k] undoes the
+// power-of-two scalings and carries 2 df.
+__global__ void quv_uv_kernel(const float2 *__restrict__ H, const float2 *__restrict__ Hm, const float2 *__restrict__ Hw,
+                              int nb, int M, double2 *__restrict__ U, double2 *__restrict__ V,
+                              const double *__restrict__ scale) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  if (p >= M * M) return;
+  const int a = p / M, b = p - a * M;
+  df ur{0.f, 0.f}, ui{0.f, 0.f}, vr{0.f, 0.f}, vi{0.f, 0.f};
+  float pur = 0.f, pui = 0.f, pvr = 0.f, pvi = 0.f;
+  const float2 *ha = H + (size_t)a * nb, *hma = Hm + (size_t)a * nb, *yb = Hw + ((size_t)k * M + b) * nb;
+  for (int i = 0; i < nb; ++i) {
+    const float2 x = ha[i], y = yb[i], z = hma[i];
+    pur = fmaf(x.x, y.x, fmaf(x.y, y.y, pur));     // conj(x) y
+    pui = fmaf(x.x, y.y, fmaf(-x.y, y.x, pui));
+    pvr = fmaf(z.x, y.x, fmaf(-z.y, y.y, pvr));    // z y
+    pvi = fmaf(z.x, y.y, fmaf(z.y, y.x, pvi));
+    if ((i & 31) == 31 || i == nb - 1) {
+      df_acc(ur, pur); df_acc(ui, pui); df_acc(vr, pvr); df_acc(vi, pvi);
+      pur = pui = pvr = pvi = 0.f;
+    }
+  }
+  const size_t o = ((size_t)k * M + a) * M + b;
+  const double sc = scale[k];
+  U[o] = make_double2(sc * ((double)ur.hi + ur.lo), sc * ((double)ui.hi + ui.lo));
+  V[o] = make_double2(sc * ((double)vr.hi + vr.lo), sc * ((double)vi.hi + vi.lo));
+}
+
+// Power of two that brings the largest magnitude of a set near 1 (1 for an all-zero set).
+double unit_scale(double vmax) { return vmax > 0.0 && std::isfinite(vmax) ? std::ldexp(1.0, -std::ilogb(vmax)) : 1.0; }
+
+thread_local std::string g_quv_err;
+
+rift_status quv_fail(rift_status s, const std::string &m) {
+  g_quv_err = m;
+  return s;
+}
+
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *rift_quv_last_error(void) { return g_quv_err.c_str(); }
+
+rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V) {
+  if (!d || !Q || !U || !V) return quv_fail(RIFT_EINVAL, "null argument");
+  const int K = d->n_det, M = d->n_modes, nf = d->n_f, nt = d->n_t;
+  if (K < 1 || K > RIFT_MAX_DET || M < 1 || M > RIFT_MAX_MODES || nf < 1 || nt < 1)
+    return quv_fail(RIFT_EINVAL, "sizes out of range");
+  if (!d->nu || !d->hlm || !d->data || !d->weight || !d->mirror || !d->q_t0_gps)
+    return quv_fail(RIFT_EINVAL, "null array in descriptor");
+  if (!(d->df > 0) || !(d->fs > 0)) return quv_fail(RIFT_EINVAL, "df and fs must be positive");
+  const double nd = d->fs / d->df;
+  const long long n = llround(nd);
+  if (n < 2 || std::fabs(nd - (double)n) > 1e-9 * nd || n > (1ll << 30))
+    return quv_fail(RIFT_EINVAL, "fs / df must be an integer (the Q grid and the frequency grid share it)");
+  if ((long long)nt > n) return quv_fail(RIFT_EINVAL, "n_t exceeds fs / df samples");
+  // band bins: weight nonzero in some detector; their mirrors
+  std::vector<int> band;
+  for (int i = 0; i < nf; ++i) {
+    if (d->mirror[i] < 0 || d->mirror[i] >= nf) return quv_fail(RIFT_EINVAL, "mirror index out of range");
+    bool in = false;
+    for (int k = 0; k < K; ++k) in = in || d->weight[(size_t)k * nf + i] != 0.0;
+    if (in) band.push_back(i);
+  }
+  const int nb = (int)band.size();
+  if (nb == 0) return quv_fail(RIFT_EINVAL, "no bin has a nonzero weight");
+  // operands rescaled by powers of two so that FP32 holds them whatever the strain units
+  double hmax = 0.0;
+  std::vector<double> bmax(K, 0.0), wmax(K, 0.0);
+  std::vector<double> Bd(2 * (size_t)K * nb);
+  std::vector<int> nuv(nb), run(nb);
+  for (int b = 0; b < nb; ++b) {
+    const int i = band[b];
+    long long v = d->nu[i] % n;
+    if (v < 0) v += n;
+    nuv[b] = (int)v;
+    run[b] = (b == 0 || nuv[b] != (nuv[b - 1] + 1) % n) ? 1 : 0;
+    for (int a = 0; a < M; ++a) {
+      hmax = std::max(hmax, std::hypot(d->hlm[2 * ((size_t)a * nf + i)], d->hlm[2 * ((size_t)a * nf + i) + 1]));
+      const int im = d->mirror[i];
+      hmax = std::max(hmax, std::hypot(d->hlm[2 * ((size_t)a * nf + im)], d->hlm[2 * ((size_t)a * nf + im) + 1]));
+    }
+    for (int k = 0; k < K; ++k) {
+      const double w = d->weight[(size_t)k * nf + i];
+      const double *x = d->data + 2 * ((size_t)k * nf + i);
+      const double tau0 = d->q_t0_gps[k] - d->t_ref_gps;
+      const double ph = 2.0 * 3.14159265358979323846 * std::fmod((double)d->nu[i] * d->df * tau0, 1.0);
+      const double c = std::cos(ph), sn = std::sin(ph), f = 2.0 * d->df * w;
+      double *bd = &Bd[2 * ((size_t)k * nb + b)];
+      bd[0] = f * (x[0] * c - x[1] * sn);
+      bd[1] = f * (x[0] * sn + x[1] * c);
+      bmax[k] = std::max(bmax[k], std::hypot(bd[0], bd[1]));
+      for (int a = 0; a < M; ++a)
+        wmax[k] = std::max(wmax[k], w * std::hypot(d->hlm[2 * ((size_t)a * nf + i)], d->hlm[2 * ((size_t)a * nf + i) + 1]));
+    }
+  }
+  const double sH = unit_scale(hmax);
+  std::vector<double> sB(K), sW(K), qscale(K), uvscale(K);
+  for (int k = 0; k < K; ++k) {
+    sB[k] = unit_scale(bmax[k]);
+    sW[k] = unit_scale(wmax[k]);
+    qscale[k] = 1.0 / (sH * sB[k]);
+    uvscale[k] = 2.0 * d->df / (sH * sW[k]);
+  }
+  std::vector<float2> H((size_t)M * nb), Hm((size_t)M * nb), B((size_t)K * nb), Hw((size_t)K * M * nb);
+  for (int b = 0; b < nb; ++b) {
+    const int i = band[b];
+    for (int a = 0; a < M; ++a) {
+      const double *h = d->hlm + 2 * ((size_t)a * nf + i), *hm = d->hlm + 2 * ((size_t)a * nf + d->mirror[i]);
+      H[(size_t)a * nb + b] = make_float2((float)(h[0] * sH), (float)(h[1] * sH));
+      Hm[(size_t)a * nb + b] = make_float2((float)(hm[0] * sH), (float)(hm[1] * sH));
+      for (int k = 0; k < K; ++k) {
+        const double w = d->weight[(size_t)k * nf + i] * sW[k];
+        Hw[((size_t)k * M + a) * nb + b] = make_float2((float)(h[0] * w), (float)(h[1] * w));
+      }
+    }
+    for (int k = 0; k < K; ++k) {
+      const double *bd = &Bd[2 * ((size_t)k * nb + b)];
+      B[(size_t)k * nb + b] = make_float2((float)(bd[0] * sB[k]), (float)(bd[1] * sB[k]));
+    }
+  }
+  cudaStream_t st = (cudaStream_t)d->cuda_stream;
+  DevBuf dH, dHm, dB, dHw, dnu, drun, dQ, dU, dV, dsc;
+  cudaError_t e;
+  auto up = [&](DevBuf &buf, const void *src, size_t bytes) {
+    cudaError_t r = cudaMalloc(&buf.p, bytes);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, st);
+    return r;
+  };
+  if ((e = up(dH, H.data(), sizeof(float2) * H.size())) != cudaSuccess ||
+      (e = up(dHm, Hm.data(), sizeof(float2) * Hm.size())) != cudaSuccess ||
+      (e = up(dB, B.data(), sizeof(float2) * B.size())) != cudaSuccess ||
+      (e = up(dHw, Hw.data(), sizeof(float2) * Hw.size())) != cudaSuccess ||
+      (e = up(dsc, uvscale.data(), sizeof(double) * K)) != cudaSuccess ||
+      (e = up(dnu, nuv.data(), sizeof(int) * nuv.size())) != cudaSuccess ||
+      (e = up(drun, run.data(), sizeof(int) * run.size())) != cudaSuccess ||
+      (e = cudaMalloc(&dQ.p, sizeof(double2) * (size_t)K * M * nt)) != cudaSuccess ||
+      (e = cudaMalloc(&dU.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess ||
+      (e = cudaMalloc(&dV.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess)
+    return quv_fail(e == cudaErrorMemoryAllocation ? RIFT_ENOMEM : RIFT_ECUDA, cudaGetErrorString(e));
+  dim3 gq((nt + kQThreads - 1) / kQThreads, (M + kQModes - 1) / kQModes, K);
+  quv_q_kernel<<<gq, kQThreads, 0, st>>>((const float2 *)dH.p, (const float2 *)dB.p, (const int *)dnu.p,
+                                         (const int *)drun.p, nb, M, nt, (int)n, (double2 *)dQ.p);
+  dim3 guv((M * M + 127) / 128, K);
+  quv_uv_kernel<<<guv, 128, 0, st>>>((const float2 *)dH.p, (const float2 *)dHm.p, (const float2 *)dHw.p, nb, M,
+                                     (double2 *)dU.p, (double2 *)dV.p, (const double *)dsc.p);
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(Q, dQ.p, sizeof(double2) * (size_t)K * M * nt, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(U, dU.p, sizeof(double2) * (size_t)K * M * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(V, dV.p, sizeof(double2) * (size_t)K * M * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return quv_fail(RIFT_ECUDA, cudaGetErrorString(e));
+  for (int k = 0; k < K; ++k)   // undo the scalings of the data term and the waveforms
+    for (size_t o = 2 * (size_t)k * M * nt; o < 2 * (size_t)(k + 1) * M * nt; ++o) Q[o] *= qscale[k];
+  return RIFT_OK;
+}
+
+rift_status rift_ile_create_fd(const rift_ile_fd_desc *d, rift_ile **out) {
+  if (!d || !out) return quv_fail(RIFT_EINVAL, "null argument");
+  const size_t K = (size_t)std::max(d->n_det, 0), M = (size_t)std::max(d->n_modes, 0), T = (size_t)std::max(d->n_t, 0);
+  std::vector<double> Q(2 * K * M * T), U(2 * K * M * M), V(2 * K * M * M);
+  rift_status s = rift_quv(d, Q.data(), U.data(), V.data());
+  if (s != RIFT_OK) return s;
+  // U_ab and U_ba (V_ab and V_ba) are separate sums: make U Hermitian and V symmetric exactly
+  for (size_t k = 0; k < K; ++k)
+    for (size_t a = 0; a < M; ++a)
+      for (size_t b = a; b < M; ++b) {
+        double *u1 = &U[2 * ((k * M + a) * M + b)], *u2 = &U[2 * ((k * M + b) * M + a)];
+        double *v1 = &V[2 * ((k * M + a) * M + b)], *v2 = &V[2 * ((k * M + b) * M + a)];
+        const double ur = 0.5 * (u1[0] + u2[0]), ui = 0.5 * (u1[1] - u2[1]);
+        const double vr = 0.5 * (v1[0] + v2[0]), vi = 0.5 * (v1[1] + v2[1]);
+        u1[0] = ur; u1[1] = ui; u2[0] = ur; u2[1] = -ui;
+        v1[0] = vr; v1[1] = vi; v2[0] = vr; v2[1] = vi;
+      }
+  rift_ile_desc c;
+  std::memset(&c, 0, sizeof(c));
+  c.n_det = d->n_det; c.det_tensor = d->det_tensor; c.det_pos = d->det_pos;
+  c.n_modes = d->n_modes; c.lm = d->lm; c.n_t = d->n_t; c.Q = Q.data(); c.q_t0_gps = d->q_t0_gps;
+  c.fs = d->fs; c.U = U.data(); c.V = V.data(); c.t_ref_gps = d->t_ref_gps; c.d_ref_mpc = d->d_ref_mpc;
+  c.t_lo = d->t_lo; c.t_hi = d->t_hi; c.interp = d->interp; c.cuda_stream = d->cuda_stream;
+  return rift_ile_create(&c, out);
+}
+
+}  // extern "C"

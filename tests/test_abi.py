@@ -106,7 +106,7 @@ def test_struct_layouts_match_the_binding(tmp_path):
     if cc is None:
         pytest.skip("no host C compiler")
     structs = {"rift_ile_desc": rift.Desc, "rift_mc_opts": rift.McOpts, "rift_mc_result": rift.McResult,
-               "rift_tune": rift.Tune}
+               "rift_tune": rift.Tune, "rift_ile_fd_desc": rift.FdDesc}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/rift_ile.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
