@@ -340,7 +340,7 @@ def run_gpu(args, world, rank, local):
         "lnL_marg": r0["lnL_marg"], "n_eff": r0["n_eff"], "strata": list(r0["strata"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(),
-                     "kernel": "cells_kernel<3,4,0> (stratified cell: draw + staged Q window + likelihood + log-sum-exp)",
+                     "kernel": "cells_kernel<3,4,0,0> (stratified cell: draw + staged Q window + likelihood + log-sum-exp)",
                      "kernel_ms": kmean, "flops_per_sample": flops_per_sample(K, M, taps),
                      "peak_basis": f"FP32 FMA: 128 lanes/SM x {sms} SMs x 2 flop x median SM clock {f_mhz} MHz "
                                    "sampled during the run"},
