@@ -225,9 +225,10 @@ typedef struct {
   int time_marg;         /* nonzero: each draw integrates the event time by quadrature, Eq. (lnL:tmarg)
                             (rift_ile_lnL_tmarg), instead of sampling it; the draws cover (ra, dec,
                             psi, phi, incl, D), strata and adaptive tables cover (ra, sin dec) only
-                            (the time table stays uniform), n_evals counts draws.  Prior or adaptive
-                            proposals, single-point calls and the batched runner; not with the
-                            learned proposal (RIFT_EUNSUPPORTED).                                 */
+                            (the time table stays uniform), n_evals counts draws.  All proposals,
+                            single-point calls and the batched runner; with the learned proposal
+                            the mixture's time coordinate is integrated out (dropped from each
+                            diagonal component) and the weight is that of the other four.        */
 } rift_mc_opts;
 
 /* Size of the sampler-state blob of rift_mc_opts.resume / save (same library build and byte order). */

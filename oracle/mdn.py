@@ -125,12 +125,15 @@ def ln_qz(z, alpha, mu, ls):
     return (m + np.log(np.sum(np.exp(comp - m), axis=-1, keepdims=True)))[:, 0]
 
 
-def ln_q_mdn(th5, head, a, b):
-    """ln q_MDN(theta5) including the logit Jacobian; head (N, 88) or (1, 88)."""
-    x = (th5 - a) / (b - a)
+def ln_q_mdn(th5, head, a, b, dims=None):
+    """ln q_MDN(theta5) including the logit Jacobian; head (N, 88) or (1, 88).  dims: the
+    coordinates kept (the mixture is diagonal, so dropping one integrates it out exactly)."""
+    dims = list(range(N_DIM)) if dims is None else list(dims)
+    x = ((th5 - a) / (b - a))[:, dims]
     z = np.log(x) - np.log1p(-x)
     alpha, mu, ls = split_head(head)
-    return ln_qz(z, alpha, mu, ls) - np.sum(np.log(b - a) + np.log(x) + np.log1p(-x), axis=-1)
+    return ln_qz(z, alpha, mu[..., dims], ls[..., dims]) - np.sum(np.log((b - a)[dims]) + np.log(x) + np.log1p(-x),
+                                                                   axis=-1)
 
 
 def ln_q_defensive(th5, head, a, b, lnp5):
@@ -139,8 +142,11 @@ def ln_q_defensive(th5, head, a, b, lnp5):
 
 
 # ---------------------------------------------------------------- sampling
-def sample(u, head, prior):
-    """Uniforms (10, N) -> theta dict (ra, sindec, t, psi, phi, cosi, dist), ln p5 - ln q."""
+def sample(u, head, prior, time_marg=False):
+    """Uniforms (10, N) -> theta dict (ra, sindec, t, psi, phi, cosi, dist), ln p5 - ln q.
+
+    time_marg: the event time is integrated by quadrature (Eq. lnL:tmarg), so the weight is that
+    of the other four coordinates: ln p4 - ln q4, q4 = 0.9 q_MDN (t dropped) + 0.1 p4."""
     alpha, mu, ls = split_head(head)
     alpha, mu, ls = alpha[0], mu[0], ls[0]
     n = []
@@ -165,9 +171,14 @@ def sample(u, head, prior):
                    np.log(np.cbrt(prior.d_lo ** 3 + u[4] * (prior.d_hi ** 3 - prior.d_lo ** 3)))], axis=-1)
     th5 = np.where(use_prior[:, None], pr, th5)
     lnp5 = ln_prior5(th5, prior.d_lo, prior.d_hi, prior.t_lo, prior.t_hi)
-    lq = ln_q_defensive(th5, np.atleast_2d(head), a, b, lnp5)
     th = dict(ra=th5[:, 0], sindec=th5[:, 1], t=th5[:, 2], cosi=th5[:, 3], dist=np.exp(th5[:, 4]),
               psi=math.pi * u[8], phi=2.0 * math.pi * u[9])
+    if time_marg:
+        lnp4 = lnp5 + math.log(prior.t_hi - prior.t_lo)
+        lq4 = np.logaddexp(math.log(1.0 - DEFENSIVE) + ln_q_mdn(th5, np.atleast_2d(head), a, b, dims=(0, 1, 3, 4)),
+                           math.log(DEFENSIVE) + lnp4)
+        return th, lnp4 - lq4
+    lq = ln_q_defensive(th5, np.atleast_2d(head), a, b, lnp5)
     return th, lnp5 - lq
 
 

@@ -416,8 +416,6 @@ rift_status check_opts(rift_ile *h, const rift_mc_opts *o) {
   } else if (o->proposal != RIFT_PROPOSAL_PRIOR) {
     return fail(h, RIFT_EINVAL, "unknown proposal");
   }
-  if (o->time_marg && o->proposal == RIFT_PROPOSAL_LEARNED)
-    return fail(h, RIFT_EUNSUPPORTED, "time marginalisation with the learned proposal");
   return RIFT_OK;
 }
 
@@ -508,8 +506,10 @@ rift_status prepare_learned(rift_ile *h, const rift_mc_opts *o, cudaStream_t st)
   for (int p = 0; p < np; ++p) {
     const double tspan = h->pts[p].t_hi - h->pts[p].t_lo;
     const double lnspan = std::log(o->d_hi) - std::log(o->d_lo);
-    c[4 * p + 0] = (float)(std::log(2.0 * kPi) + std::log(2.0) + std::log(tspan) + std::log(2.0) + std::log(lnspan));
-    c[4 * p + 1] = (float)(-std::log(2.0 * kPi) - std::log(2.0) - std::log(tspan) - std::log(2.0) + std::log(3.0) -
+    // time integrated by quadrature: the box and the prior of (ra, sin dec, cos incl, ln D) only
+    const double lt = o->time_marg ? 0.0 : std::log(tspan);
+    c[4 * p + 0] = (float)(std::log(2.0 * kPi) + std::log(2.0) + lt + std::log(2.0) + std::log(lnspan));
+    c[4 * p + 1] = (float)(-std::log(2.0 * kPi) - std::log(2.0) - lt - std::log(2.0) + std::log(3.0) -
                            std::log(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo));
     c[4 * p + 2] = (float)std::log(o->d_lo);
     c[4 * p + 3] = (float)lnspan;

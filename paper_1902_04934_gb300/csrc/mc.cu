@@ -154,6 +154,7 @@ __device__ __forceinline__ Drawn draw_cell_sample(unsigned long long seed, const
 // (u0,u1), (u2,u3), (u4,u5); component = first j with u6 < cumulative pi_j; u7 < 0.9 takes the
 // network, otherwise the prior transforms of u0..u4; u8 -> psi, u9 -> phi.  ln q is the
 // defensive mixture 0.9 q_MDN + 0.1 p5 with the logit change of variables.
+template <int TM>
 __device__ __forceinline__ Drawn draw_learned(unsigned long long seed, const RoundPt &R, uint32_t i, const float *G,
                                               float dref, float d_lo3, float d_span3) {
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -198,6 +199,7 @@ __device__ __forceinline__ Drawn draw_learned(unsigned long long seed, const Rou
     float acc = G[j];
 #pragma unroll
     for (int dd = 0; dd < 5; ++dd) {
+      if (TM && dd == 2) continue;   // time integrated by quadrature: the diagonal mixture drops it exactly
       const float t = (z[dd] - G[16 + 5 * j + dd]) * G[96 + 5 * j + dd];
       acc -= 0.5f * t * t + G[56 + 5 * j + dd] + 0.91893853320467274f;
     }
@@ -210,6 +212,7 @@ __device__ __forceinline__ Drawn draw_learned(unsigned long long seed, const Rou
   float jac = G[136];
 #pragma unroll
   for (int dd = 0; dd < 5; ++dd) {
+    if (TM && dd == 2) continue;
     const float az = fabsf(z[dd]);
     jac -= az + 2.f * log1pf(expf(-az));   // softplus(z) + softplus(-z) = |z| + 2 log(1 + e^{-|z|})
   }
@@ -234,11 +237,11 @@ __device__ __forceinline__ Drawn draw_learned(unsigned long long seed, const Rou
   return d;
 }
 
-template <int LEARNED>
+template <int LEARNED, int TM = 0>
 __device__ __forceinline__ Drawn draw_any(unsigned long long seed, const RoundPt &R, uint32_t i, uint32_t cell,
                                           const float *tab, const float *lnw, const float *G, float dref, float d_lo3,
                                           float d_span3) {
-  if (LEARNED) return draw_learned(seed, R, i, G, dref, d_lo3, d_span3);
+  if (LEARNED) return draw_learned<TM>(seed, R, i, G, dref, d_lo3, d_span3);
   return draw_cell_sample(seed, R, i, cell, tab, lnw, dref, d_lo3, d_span3);
 }
 
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(C
     float m = kNegInf, s1 = 0.f, s2 = 0.f, cnt = 0.f;
     for (uint32_t j = j0 + threadIdx.x; j < j_end; j += blockDim.x) {
       const uint32_t i = sample_index(R, cell, j);
-      const Drawn d = draw_any<LEARNED>(L.seed, R, i, cell, tab, lnw, s_gmm, P.dref, L.d_lo3, L.d_span3);
+      const Drawn d = draw_any<LEARNED, TMARG>(L.seed, R, i, cell, tab, lnw, s_gmm, P.dref, L.d_lo3, L.d_span3);
       const Sky s = sky_of(P, d);
       df si[K];
       if (TMARG) delay_index<K>(P, s, si);
@@ -767,7 +770,7 @@ __global__ void draw_cells_kernel(CellLaunch L, DrawOut o, uint32_t n) {
   // cell of sample i
   const uint32_t big = R.rem * (R.base + 1u);
   const uint32_t cell = (i < big) ? i / (R.base + 1u) : R.rem + (i - big) / R.base;
-  const Drawn d = (R.proposal == 2) ? draw_learned(L.seed, R, i, R.gmm, P.dref, L.d_lo3, L.d_span3)
+  const Drawn d = (R.proposal == 2) ? draw_learned<0>(L.seed, R, i, R.gmm, P.dref, L.d_lo3, L.d_span3)
                                     : draw_cell_sample(L.seed, R, i, cell, tab, lnw, P.dref, L.d_lo3, L.d_span3);
   o.theta[0 * (size_t)n + i] = kTwoPi * (d.x0.hi + d.x0.lo);
   o.theta[1 * (size_t)n + i] = (2.f * d.x1.hi - 1.f) + 2.f * d.x1.lo;
@@ -892,7 +895,7 @@ __global__ void harvest_theta_kernel(CellLaunch L, const RoundPt *__restrict__ l
   const uint32_t cell = ((uint32_t)i < big) ? (uint32_t)i / (R.base + 1u) : R.rem + ((uint32_t)i - big) / R.base;
   const PointC *P = L.pts + p;
   const Drawn d = (R.proposal == 2)
-                      ? draw_learned(L.seed, R, (uint32_t)i, R.gmm, P->dref, L.d_lo3, L.d_span3)
+                      ? draw_learned<0>(L.seed, R, (uint32_t)i, R.gmm, P->dref, L.d_lo3, L.d_span3)
                       : draw_cell_sample(L.seed, R, (uint32_t)i, cell, R.tab, R.lnw, P->dref, L.d_lo3, L.d_span3);
   o[0] = kTwoPi * (d.x0.hi + d.x0.lo);
   o[1] = (2.f * d.x1.hi - 1.f) + 2.f * d.x1.lo;
@@ -916,7 +919,7 @@ cudaError_t cells_kl(const CellLaunch &L, int grid, int block, size_t smem, cuda
 
 template <int K, int NT>
 cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
-  if (L.tmarg) return cells_kl<K, NT, 0, 1>(L, grid, block, smem, st);
+  if (L.tmarg) return L.learned ? cells_kl<K, NT, 1, 1>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 1>(L, grid, block, smem, st);
   return L.learned ? cells_kl<K, NT, 1, 0>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 0>(L, grid, block, smem, st);
 }
 
@@ -930,7 +933,7 @@ int cells_occ1(size_t smem, int block) {
 
 template <int K, int NT>
 int cells_occ(size_t smem, int block, int tmarg) {
-  if (tmarg) return cells_occ1<K, NT, 0, 1>(smem, block);
+  if (tmarg) return std::min(cells_occ1<K, NT, 0, 1>(smem, block), cells_occ1<K, NT, 1, 1>(smem, block));
   const int a = cells_occ1<K, NT, 0, 0>(smem, block), b = cells_occ1<K, NT, 1, 0>(smem, block);
   return a < b ? a : b;
 }

@@ -156,3 +156,28 @@ def test_tmarg_batch_equals_single_point_runs(lib, cuda):
         assert batch[i]["lnL_marg"] == one["lnL_marg"], (i, batch[i]["lnL_marg"], one["lnL_marg"])
         lib.rift_ile_destroy(h)
     lib.rift_ile_destroy(hb)
+
+
+def test_tmarg_learned_matches_oracle(lib, cuda):
+    """Learned proposal with the time quadrature: the mixture's time coordinate is integrated out
+    (dropped from each diagonal component), the weight is that of the other four coordinates."""
+    from oracle import mc, mdn
+    from oracle import philox as P
+    pt = W.make_point(W.cfg_small(), 8)
+    a, b = mdn.bounds(pt["t_lo"], pt["t_hi"], 1.0, 1000.0)
+    r = np.random.default_rng(5)
+    head = np.zeros(88, dtype=np.float32)
+    head[:8] = r.normal(0, 1, 8)
+    head[8:48] = r.normal(0, 1.0, 40)
+    head[48:88] = r.uniform(-1.0, 0.5, 40)
+    h = lib.rift_ile_create(pt)
+    lib.rift_ile_set_proposal_head(h, head[None])
+    n = 1500
+    res = lib.rift_ile_marginalize(h, seed=91, n_per_round=n, max_evals=n, proposal="learned", time_marg=1)
+    u = P.uniforms(91, 0, 0, np.arange(n, dtype=np.uint64), 10)
+    th, lq = mdn.sample(u, head.astype(np.float64)[None], mc.Prior(pt["t_lo"], pt["t_hi"]), time_marg=True)
+    ell = TM.lnL_tmarg(pt, th["ra"], np.arcsin(th["sindec"]), th["psi"], th["phi"], np.arccos(th["cosi"]),
+                       th["dist"]) + lq
+    want = mc.Accum.of(ell).result()
+    assert abs(res["lnL_marg"] - want[0]) < 1e-4, (res["lnL_marg"], want[0], res["n_eff"])
+    lib.rift_ile_destroy(h)
