@@ -159,6 +159,18 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   }
   const int nb = (int)band.size();
   if (nb == 0) return quv_fail(RIFT_EINVAL, "no bin has a nonzero weight");
+  for (int i : band) {
+    for (int a = 0; a < M; ++a)
+      for (int c = 0; c < 2; ++c)
+        if (!std::isfinite(d->hlm[2 * ((size_t)a * nf + i) + c]) || !std::isfinite(d->hlm[2 * ((size_t)a * nf + d->mirror[i]) + c]))
+          return quv_fail(RIFT_EINVAL, "non-finite mode waveform in the band");
+    for (int k = 0; k < K; ++k) {
+      if (!std::isfinite(d->weight[(size_t)k * nf + i]) || d->weight[(size_t)k * nf + i] < 0.0)
+        return quv_fail(RIFT_EINVAL, "weights must be finite and non-negative");
+      for (int c = 0; c < 2; ++c)
+        if (!std::isfinite(d->data[2 * ((size_t)k * nf + i) + c])) return quv_fail(RIFT_EINVAL, "non-finite data in the band");
+    }
+  }
   // operands rescaled by powers of two so that FP32 holds them whatever the strain units
   double hmax = 0.0;
   std::vector<double> bmax(K, 0.0), wmax(K, 0.0);

@@ -65,3 +65,13 @@ def test_inconsistent_grids_are_refused(lib, cuda):
     with pytest.raises(lib.RiftError) as e:
         lib.rift_quv(bad)
     assert e.value.status == 1
+
+
+def test_non_finite_inputs_are_refused(lib, cuda):
+    pt = W.make_point(W.cfg_small(), 16)
+    band = np.flatnonzero(pt["weight"][0])
+    data = pt["data"].copy()
+    data[0, band[10]] = np.nan
+    with pytest.raises(lib.RiftError) as e:
+        lib.rift_quv(dict(pt, data=data))
+    assert e.value.status == 1

@@ -181,3 +181,20 @@ def test_tmarg_learned_matches_oracle(lib, cuda):
     want = mc.Accum.of(ell).result()
     assert abs(res["lnL_marg"] - want[0]) < 1e-4, (res["lnL_marg"], want[0], res["n_eff"])
     lib.rift_ile_destroy(h)
+
+
+def test_tmarg_resume_and_static_scratch(lib, cuda):
+    """Checkpoint/resume and the allocation-free entry point carry the time quadrature too."""
+    pt = W.make_point(W.cfg_small(), 8)
+    h = lib.rift_ile_create(pt)
+    kw = dict(seed=95, n_per_round=1000, max_evals=4000, n_eff_target=1e300, time_marg=1, proposal="adaptive",
+              n_bins=24)
+    full = lib.rift_ile_marginalize(h, **kw)
+    part = lib.rift_ile_marginalize(h, save=True, max_rounds=2, **kw)
+    rest = lib.rift_ile_marginalize(h, resume=part["state"], **kw)
+    assert rest["lnL_marg"] == full["lnL_marg"] and rest["n_evals"] == full["n_evals"]
+    with pytest.raises(lib.RiftError):   # a sampled-time run cannot resume a time-marginalised one
+        lib.rift_ile_marginalize(h, resume=part["state"], **dict(kw, time_marg=0))
+    st = lib.rift_ile_marginalize_static(h, **kw)
+    assert st["lnL_marg"] == full["lnL_marg"] and st["n_evals"] == full["n_evals"]
+    lib.rift_ile_destroy(h)
