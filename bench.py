@@ -146,7 +146,7 @@ def recorded_traffic():
     src = ROOT / "paper_1902_04934_gb300" / "csrc"
     try:
         kv = dict(l.strip().split("=", 1) for l in rec.read_text().splitlines() if "=" in l and not l.startswith("#"))
-        h = hashlib.sha256(b"".join((src / f).read_bytes() for f in ("mc.cu", "rift_device.cuh", "rift_internal.h")))
+        h = hashlib.sha256(b"".join((src / f).read_bytes() for f in ("mc.cu", "draw.cuh", "rift_device.cuh", "rift_internal.h")))
     except OSError:
         return None
     # the Q arena is read about once per launch whatever the sample count, so the figure is

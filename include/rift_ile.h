@@ -314,6 +314,45 @@ rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *opts, int H,
                                    rift_mc_result *res);
 
 /*
+ * Extrinsic posterior samples (Eq. (lnLmarg) read as a posterior: the importance-sampled draws
+ * theta_i ~ q of a marginalisation, weighted by w_i = L_i p_i / q_i, are samples of the
+ * extrinsic posterior at the intrinsic point; Sec. VI: the same integration yields the
+ * extrinsic distributions).  Both calls run the marginalisation of rift_ile_batch_marginalize
+ * with `opts` (every point of the handle; a single-point handle is a batch of one; res
+ * [n_points] as there; RIFT_ENOTCONVERGED is returned with the samples written) and then read
+ * the draws of each point's LAST round.  Every column is float32:
+ *   0 ra (rad)   1 dec (rad)   2 t (s from t_ref, geocentre)   3 psi   4 phi   5 incl (rad)
+ *   6 D (Mpc)    7 lnL (Eq. (def:lnL:Decomposed); with time_marg, as described per call)
+ *   8 ln p - ln q (rift_ile_samples only; includes the stratification factor ln(n / (C n_c)))
+ * so that the weight of an exported draw is exp(lnL + ln p - ln q).  lnL is the draw's log
+ * weight minus ln p - ln q, both as the sampler computed them in FP32.
+ * Errors: RIFT_EINVAL for NULL or inconsistent arguments, the statuses of the marginalisation.
+ */
+#define RIFT_SAMPLE_COLS 9
+#define RIFT_POSTERIOR_COLS 8
+
+/* Weighted export: out_dev [n_points][cap][RIFT_SAMPLE_COLS] (device, caller-owned) receives the
+ * first min(n_p, cap) draws of point p's last round in draw order, NaN rows after them;
+ * n_out [n_points] (host) receives n_p, the number of draws of that round.  cap may be 0 (counts
+ * only; out_dev may then be NULL).  With time_marg, column 2 is NaN (the time was integrated
+ * out) and column 7 is the time-marginalised lnL of Eq. (lnL:tmarg). */
+rift_status rift_ile_samples(rift_ile *h, const rift_mc_opts *opts, size_t cap, float *out_dev, uint64_t *n_out,
+                             rift_mc_result *res);
+
+/* H equal-weight posterior samples per point: systematic resampling of the last round, slot h
+ * taking the first draw i with C_i > (h + 1/2) C_{n-1} / H, C the cumulative sums (FP64) of
+ * exp(l_i - max l).  out_dev [n_points][H][RIFT_POSTERIOR_COLS] (device); idx_dev [n_points][H]
+ * (device, may be NULL) receives the resampled draw (its row in rift_ile_samples), -1 for a point
+ * without draws (its rows are NaN).  With time_marg, each resampled draw then gets its event time
+ * from the conditional on the quadrature grid of Eq. (lnL:tmarg), P(t_j | rest) proportional to
+ * L(t_j), t_j = t_lo + (j + 1/2)/fs: the first j whose cumulative probability exceeds u, u the
+ * uniform of Philox block 3 of counter (h, 0, point id) (the sampler uses blocks 0-2); column 7 is
+ * then lnL(t_j).  A non-finite likelihood there gives RIFT_ENONFINITE, taps outside the Q window
+ * RIFT_EWINDOW. */
+rift_status rift_ile_posterior(rift_ile *h, const rift_mc_opts *opts, int H, float *out_dev, int *idx_dev,
+                               rift_mc_result *res);
+
+/*
  * rift_ile_marginalize_static -- the same computation as rift_ile_marginalize (point 0,
  * prior or adaptive proposal; same kernels, same results) for callers that cannot
  * allocate device memory when they marginalise: programs that give (nearly) all device

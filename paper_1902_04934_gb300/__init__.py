@@ -118,6 +118,8 @@ def _load():
         "rift_ile_set_proposal_head": (I, [P, P]),
         "rift_ile_boxes": (I, [P, D, D, P]),
         "rift_ile_batch_harvest": (I, [P, C.POINTER(McOpts), I, D, P, C.POINTER(McResult)]),
+        "rift_ile_samples": (I, [P, C.POINTER(McOpts), S, P, C.POINTER(U64), C.POINTER(McResult)]),
+        "rift_ile_posterior": (I, [P, C.POINTER(McOpts), I, P, P, C.POINTER(McResult)]),
         "rift_ile_get_tune": (I, [P, C.POINTER(Tune)]),
         "rift_ile_set_tune": (I, [P, C.POINTER(Tune)]),
         "rift_ile_autotune": (I, [P, C.POINTER(McOpts), I, C.POINTER(Tune)]),
@@ -495,6 +497,40 @@ def rift_ile_batch_harvest(h, H, beta=0.5, **kw):
     if st not in (0, 7):
         _check(h, st)
     return theta, [r.as_dict() for r in res]
+
+
+SAMPLE_COLS = ("ra", "dec", "t", "psi", "phi", "incl", "dist", "lnL", "lnpq")
+POSTERIOR_COLS = SAMPLE_COLS[:8]
+
+
+def rift_ile_samples(h, cap, **kw):
+    """Marginalise every point and export the draws of its last round with their weights ->
+    (rows (np, cap, 9) CUDA float32 with columns SAMPLE_COLS, draws per point, results)."""
+    import torch
+    keep = []
+    o = _opts(keep=keep, **kw)
+    rows = torch.empty((h.n_points, int(cap), len(SAMPLE_COLS)), dtype=torch.float32, device="cuda")
+    n = (C.c_uint64 * h.n_points)()
+    res = (McResult * h.n_points)()
+    st = _lib.rift_ile_samples(h.ptr, C.byref(o), int(cap), rows.data_ptr() if cap else None, n, res)
+    if st not in (0, 7):
+        _check(h, st)
+    return rows, list(n), [r.as_dict() for r in res]
+
+
+def rift_ile_posterior(h, H, **kw):
+    """Marginalise every point and draw H equal-weight posterior samples from its last round ->
+    (rows (np, H, 8) CUDA float32 with columns POSTERIOR_COLS, resampled draw (np, H) int32, results)."""
+    import torch
+    keep = []
+    o = _opts(keep=keep, **kw)
+    rows = torch.empty((h.n_points, int(H), len(POSTERIOR_COLS)), dtype=torch.float32, device="cuda")
+    idx = torch.empty((h.n_points, int(H)), dtype=torch.int32, device="cuda")
+    res = (McResult * h.n_points)()
+    st = _lib.rift_ile_posterior(h.ptr, C.byref(o), int(H), rows.data_ptr(), idx.data_ptr(), res)
+    if st not in (0, 7):
+        _check(h, st)
+    return rows, idx, [r.as_dict() for r in res]
 
 
 def rift_ile_get_tune(h):

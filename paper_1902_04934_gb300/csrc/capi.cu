@@ -1074,6 +1074,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   B.gmm = h->gmm;
   B.last = keep_ell ? h->last : nullptr;
   B.tmarg = o->time_marg ? 1 : 0;
+  B.point_id1 = o->point_id;
   if (adaptive) {
     float u[3 * (RIFT_MAXBINS + 1)];
     const float *src = o->tables;
@@ -1213,6 +1214,17 @@ rift_status rift_ile_boxes(rift_ile *h, double d_lo, double d_hi, float *out) {
   return RIFT_OK;
 }
 
+// Arguments the row and harvest kernels need to re-draw the samples of a run made with `o`.
+static CellLaunch rows_launch(const rift_ile *h, const rift_mc_opts *o) {
+  CellLaunch L{};
+  L.seed = o->seed;
+  L.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
+  L.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
+  L.pts = h->pts_dev;
+  L.n_points = h->n_points;
+  return L;
+}
+
 rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *o, int H, double beta, float *theta_dev,
                                    rift_mc_result *res) {
   if (!h || !o || !theta_dev || !res || H < 1 || !(beta > 0)) return RIFT_EINVAL;
@@ -1229,16 +1241,61 @@ rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *o, int H, do
     h->cap_hidx = need;
   }
   cudaStream_t st = h->gstream;
-  // the cumulative weights overwrite the per-sample log weights after they are read
-  RIFT_CK(h, launch_harvest(S.ell, h->last, S.acc, np, (float)beta, H, S.ell, h->hidx, st));
-  CellLaunch L{};
-  L.seed = o->seed;
-  L.d_lo3 = (float)(o->d_lo * o->d_lo * o->d_lo);
-  L.d_span3 = (float)(o->d_hi * o->d_hi * o->d_hi - o->d_lo * o->d_lo * o->d_lo);
-  L.pts = h->pts_dev;
-  L.n_points = np;
+  RIFT_CK(h, launch_resample(S.ell, h->last, S.acc, np, (float)beta, H, h->hidx, st));
+  const CellLaunch L = rows_launch(h, o);
   RIFT_CK(h, launch_harvest_theta(L, h->last, h->hidx, H, theta_dev, st));
   RIFT_CK(h, cudaStreamSynchronize(st));
+  return s;
+}
+
+rift_status rift_ile_samples(rift_ile *h, const rift_mc_opts *o, size_t cap, float *out_dev, uint64_t *n_out,
+                             rift_mc_result *res) {
+  if (!h || !o || !res || !n_out || (cap > 0 && !out_dev)) return RIFT_EINVAL;
+  rift_status s = batch_run(h, o, res, true);
+  if (s != RIFT_OK && s != RIFT_ENOTCONVERGED) return s;
+  const int np = h->n_points;
+  cudaStream_t st = h->gstream;
+  const CellLaunch L = rows_launch(h, o);
+  RIFT_CK(h, launch_rows(L, h->last, h->sc.ell, nullptr, cap, RIFT_SAMPLE_COLS, np, out_dev, st));
+  std::vector<RoundPt> last(np);
+  RIFT_CK(h, cudaMemcpyAsync(last.data(), h->last, sizeof(RoundPt) * np, cudaMemcpyDeviceToHost, st));
+  RIFT_CK(h, cudaStreamSynchronize(st));
+  for (int p = 0; p < np; ++p) n_out[p] = last[p].n;
+  return s;
+}
+
+rift_status rift_ile_posterior(rift_ile *h, const rift_mc_opts *o, int H, float *out_dev, int *idx_dev,
+                               rift_mc_result *res) {
+  if (!h || !o || !res || !out_dev || H < 1) return RIFT_EINVAL;
+  rift_status s = batch_run(h, o, res, true);
+  if (s != RIFT_OK && s != RIFT_ENOTCONVERGED) return s;
+  const int np = h->n_points;
+  int *idx = idx_dev;
+  if (!idx) {
+    const size_t need = (size_t)np * H;
+    if (need > h->cap_hidx) {
+      cudaFree(h->hidx);
+      h->hidx = nullptr;
+      h->cap_hidx = 0;
+      RIFT_CK(h, cudaMalloc(&h->hidx, sizeof(int) * need));
+      h->cap_hidx = need;
+    }
+    idx = h->hidx;
+  }
+  cudaStream_t st = h->gstream;
+  RIFT_CK(h, launch_resample(h->sc.ell, h->last, h->sc.acc, np, 1.0f, H, idx, st));
+  const CellLaunch L = rows_launch(h, o);
+  RIFT_CK(h, launch_rows(L, h->last, h->sc.ell, idx, (size_t)H, RIFT_POSTERIOR_COLS, np, out_dev, st));
+  if (o->time_marg) {
+    RIFT_CK(h, cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), st));
+    RIFT_CK(h, launch_tdraw(h->K, h->interp, h->pts_dev, np, h->max_pairK / h->K, h->max_M, h->q_arena, h->c_arena,
+                            h->last, o->seed, H, out_dev, h->flags, st));
+  }
+  RIFT_CK(h, cudaStreamSynchronize(st));
+  if (o->time_marg) {
+    const rift_status f = read_flags(h);
+    if (f != RIFT_OK) return f;
+  }
   return s;
 }
 

@@ -79,6 +79,36 @@ __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict
   if (flags) atomicOr(flags_out, flags);
 }
 
+// Geometry, harmonics and quadratic form of a caller draw (ra, dec, psi, phi, incl, D) whose time
+// is integrated: g.s[k] is the Q index of the first quadrature time t_lo + 1/(2 fs) plus the time
+// of flight to detector k.  Returns the quadratic form.
+template <int K>
+__device__ __forceinline__ float tmarg_setup(const PointC &P, const float4 *C, float r, float dec, float psi,
+                                             float phi, float incl, float dist, SampleGeo &g, float2 *Ys,
+                                             int ystride) {
+  const float ph = __fmul_rn(r, 0.15915494309189535f);
+  const float pl = __fmaf_rn(r, 0.15915494309189535f, -ph) + r * 6.4206382e-09f;
+  const df v = df_add(fast_two_sum(ph, pl), df{-P.g_hi, -P.g_lo});
+  float s0, c0;
+  sincospif(2.f * v.hi, &s0, &c0);
+  const float ares = kTwoPi * v.lo;
+  const float cA = c0 - s0 * ares, sA = s0 + c0 * ares;
+  float sdh, cd;
+  sincosf(dec, &sdh, &cd);
+  float s2p, c2p;
+  sincosf(2.f * psi, &s2p, &c2p);
+  df base[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) base[k] = df_add_f(df{P.det[k].c0, P.det[k].c0lo}, 0.5f);   // t_0 = t_lo + 1/(2 fs)
+  response_delay<K>(P, cA, sA, df{sdh, 0.f}, cd, c2p, s2p, g, base);
+  g.x = __fdiv_rn(P.dref, dist);
+  float sphi, cphi, ch, sh;
+  sincosf(phi, &sphi, &cphi);
+  sincosf(0.5f * incl, &sh, &ch);
+  swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
+  return quad_term<K>(P, C, g, Ys, ystride);
+}
+
 // Time-marginalised likelihood of caller draws (ra, dec, psi, phi, incl, D): Eq. (lnL:tmarg)
 // by the midpoint rule on the Q sampling interval (tmarg_term).
 template <int K, int NT>
@@ -103,32 +133,57 @@ __global__ void __launch_bounds__(128) lnl_tmarg_array_kernel(
   uint32_t flags = 0u;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
-    const float r = ra[i];
-    const float ph = __fmul_rn(r, 0.15915494309189535f);
-    const float pl = __fmaf_rn(r, 0.15915494309189535f, -ph) + r * 6.4206382e-09f;
-    const df v = df_add(fast_two_sum(ph, pl), df{-P.g_hi, -P.g_lo});
-    float s0, c0;
-    sincospif(2.f * v.hi, &s0, &c0);
-    const float ares = kTwoPi * v.lo;
-    const float cA = c0 - s0 * ares, sA = s0 + c0 * ares;
-    float sdh, cd;
-    sincosf(dec[i], &sdh, &cd);
-    float s2p, c2p;
-    sincosf(2.f * psi[i], &s2p, &c2p);
-    df base[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) base[k] = df_add_f(df{P.det[k].c0, P.det[k].c0lo}, 0.5f);   // t_0 = t_lo + 1/(2 fs)
     SampleGeo g;
-    response_delay<K>(P, cA, sA, df{sdh, 0.f}, cd, c2p, s2p, g, base);
-    g.x = __fdiv_rn(P.dref, dist[i]);
-    float sphi, cphi, ch, sh;
-    sincosf(phi[i], &sphi, &cphi);
-    sincosf(0.5f * incl[i], &sh, &ch);
-    swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
-    const float quad = quad_term<K>(P, C, g, Ys, ystride);
+    const float quad = tmarg_setup<K>(P, C, ra[i], dec[i], psi[i], phi[i], incl[i], dist[i], g, Ys, ystride);
     const float lm = tmarg_term<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
     if (!isfinite(lm)) flags |= RIFT_FLAG_NONFINITE;
     out[i] = lm;
+  }
+  if (flags) atomicOr(flags_out, flags);
+}
+
+// Event times of resampled time-marginalised draws (grid: slots x points): row h of point p,
+// out[p][h] = (ra, dec, t, psi, phi, incl, D, lnL), gets t = t_j drawn from the conditional on the
+// quadrature grid (tmarg_pick) with the uniform of Philox block 3 of counter (h, 0, point) (the
+// sampler's streams use blocks 0-2), and lnL = lnL(t_j).  Rows that are NaN stay NaN.
+template <int K, int NT>
+__global__ void __launch_bounds__(128) tdraw_kernel(const PointC *__restrict__ pts, const float2 *__restrict__ qa,
+                                                     const float4 *__restrict__ ca, const RoundPt *__restrict__ last,
+                                                     unsigned long long seed, int H, float *__restrict__ out,
+                                                     uint32_t *flags_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int p = blockIdx.y;
+  PointC &P = *reinterpret_cast<PointC *>(smem);
+  load_point(pts + p, &P);
+  __syncthreads();
+  size_t off = align16(sizeof(PointC));
+  float4 *C = reinterpret_cast<float4 *>(smem + off);
+  off = align16(off + sizeof(float4) * (size_t)P.npair * K);
+  float2 *Ys = reinterpret_cast<float2 *>(smem + off) + threadIdx.x;
+  const int ystride = blockDim.x;
+  const float4 *cg = ca + P.uv_off;
+  for (int j = threadIdx.x; j < P.npair * K; j += blockDim.x) C[j] = cg[j];
+  __syncthreads();
+  const float2 *Q = qa + P.q_off;
+  uint32_t flags = 0u;
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h < H) {
+    float *o = out + ((size_t)p * H + h) * 8;
+    if (!isnan(o[0])) {
+      const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+      const uint4 b = philox4x32_10(make_uint4((uint32_t)h, 0u, 3u, last[p].point_id), key);
+      SampleGeo g;
+      const float quad = tmarg_setup<K>(P, C, o[0], o[1], o[3], o[4], o[5], o[6], g, Ys, ystride);
+      float l;
+      const int j = tmarg_pick<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, bits_to_u(b.x), l, flags);
+      if (j < 0) {
+        o[2] = NAN; o[7] = NAN;
+        flags |= RIFT_FLAG_NONFINITE;
+      } else {
+        o[2] = P.t_lo + ((float)j + 0.5f) / P.fs;
+        o[7] = l;
+      }
+    }
   }
   if (flags) atomicOr(flags_out, flags);
 }
@@ -165,6 +220,21 @@ cudaError_t lnl_array_k(const PointC *pt_dev, const float2 *qa, const float4 *ca
   const int block = 128;
   const unsigned grid = (unsigned)((n + block - 1) / block);
   lnl_array_kernel<K, NT><<<grid, block, smem, st>>>(pt_dev, qa, ca, n, ra, dec, t, psi, phi, incl, dist, out, flags);
+  return cudaGetLastError();
+}
+
+template <int K, int NT>
+cudaError_t tdraw_k(const PointC *pts, const float2 *qa, const float4 *ca, const RoundPt *last,
+                    unsigned long long seed, int np, int H, float *out, uint32_t *flags, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tdraw_kernel<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int block = 128;
+  const dim3 grid((unsigned)((H + block - 1) / block), (unsigned)np);
+  tdraw_kernel<K, NT><<<grid, block, smem, st>>>(pts, qa, ca, last, seed, H, out, flags);
   return cudaGetLastError();
 }
 
@@ -209,3 +279,13 @@ cudaError_t launch_lnl_tmarg(int K, const PointC *pt_dev, const PointC &ph, cons
 #undef RIFT_LT
 }
 
+
+cudaError_t launch_tdraw(int K, int interp, const PointC *pts, int np, int max_npair, int max_M, const float2 *qa,
+                         const float4 *ca, const RoundPt *last, unsigned long long seed, int H, float *out,
+                         uint32_t *flags, cudaStream_t st) {
+  if (np == 0 || H == 0) return cudaSuccess;
+  const size_t smem = rift_point_smem_bytes(K, max_npair, 0, 128, max_M);
+#define RIFT_TD(KK, TT) tdraw_k<KK, TT>(pts, qa, ca, last, seed, np, H, out, flags, smem, st)
+  RIFT_DISPATCH_KT(K, taps_of(interp), RIFT_TD)
+#undef RIFT_TD
+}

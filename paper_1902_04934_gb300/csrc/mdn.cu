@@ -1,6 +1,6 @@
 // Learned proposal: mixture-density network over (ra, sin dec, t, cos incl, ln D), its
 // training (weighted negative log likelihood of harvested posterior samples, Adam), the
-// per-point summary it is conditioned on, and the harvest of training samples.
+// per-point summary it is conditioned on.
 //
 // Network: s (64) -> 256 -> 256 (GELU, erf form) -> 88 = 8 logits + 8x5 means + 8x5 log
 // sigmas; weights bfloat16 (rounded from a float32 master copy), activations and
@@ -370,55 +370,6 @@ __global__ void __launch_bounds__(256) summary_kernel(const PointC *__restrict__
   if (t < NI) out[(size_t)p * NI + t] = feats[t];
 }
 
-// Harvest: systematic resampling of H samples of each point from its last round, with
-// probabilities proportional to exp(beta (l - max l)); outputs theta5 and the sample index.
-__global__ void __launch_bounds__(256) harvest_kernel(const float *__restrict__ ell, const RoundPt *__restrict__ rp,
-                                                      const AccState *__restrict__ acc, float beta, int H,
-                                                      float *__restrict__ cdf_scratch, int *__restrict__ idx_out) {
-  const int p = blockIdx.x;
-  const RoundPt &R = rp[p];
-  __shared__ float carry;
-  __shared__ float wsum[8];
-  if (R.n == 0 || R.ell_off < 0) {
-    for (int h = threadIdx.x; h < H; h += blockDim.x) idx_out[(size_t)p * H + h] = -1;
-    return;
-  }
-  const float mx = (float)acc[p].round_max;
-  const float *e = ell + R.ell_off;
-  float *c = cdf_scratch + R.ell_off;
-  if (threadIdx.x == 0) carry = 0.f;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (uint32_t base = 0; base < R.n; base += blockDim.x) {
-    const uint32_t i = base + threadIdx.x;
-    float w = (i < R.n && isfinite(e[i])) ? expf(beta * (e[i] - mx)) : 0.f;
-    // inclusive block scan
-    for (int o = 1; o < 32; o <<= 1) {
-      const float y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane == 31) wsum[wid] = w;
-    __syncthreads();
-    float off = carry;
-    for (int q = 0; q < wid; ++q) off += wsum[q];
-    w += off;
-    if (i < R.n) c[i] = w;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = w;
-    __syncthreads();
-  }
-  const float tot = carry;
-  for (int h = threadIdx.x; h < H; h += blockDim.x) {
-    const float target = ((float)h + 0.5f) / (float)H * tot;
-    int lo = 0, hi = (int)R.n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (c[mid] > target) hi = mid; else lo = mid + 1;
-    }
-    idx_out[(size_t)p * H + h] = lo;
-  }
-}
-
 }  // namespace
 
 struct rift_mdn {
@@ -628,8 +579,3 @@ cudaError_t launch_gmm_from_head(const float *head, const float *cst, int np, fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_harvest(const float *ell, const RoundPt *rp, const AccState *acc, int np, float beta, int H,
-                           float *cdf_scratch, int *idx_out, cudaStream_t st) {
-  harvest_kernel<<<np, 256, 0, st>>>(ell, rp, acc, beta, H, cdf_scratch, idx_out);
-  return cudaGetLastError();
-}

@@ -352,7 +352,8 @@ __device__ __forceinline__ float quad_term(const PointC &P, const float4 *__rest
 // s0_k + j with s0_k = (t_lo - tau0_k) fs + 1/2 + delay_k fs, so the interpolation weights are
 // the same for every j and consecutive j use consecutive rows: Z_k[i] = sum_lm conj(Y_lm)
 // Q_{k,lm}[i] is formed once per row and the NT taps slide along.  lnL_j = x (Re sum_k F_k
-// Zbar_k(j) - x quad / 4); the log-sum-exp over j keeps a running maximum.
+// Zbar_k(j) - x quad / 4).  tgrid_scan walks the grid and hands each lnL_j to a visitor;
+// tmarg_term takes their log-sum-exp with a running maximum.
 // Y: the point's harmonics in registers (pairs of modes, zero beyond M).
 // ---------------------------------------------------------------------------
 template <int NT>
@@ -373,10 +374,10 @@ __device__ __forceinline__ float2 z_row(const float4 *__restrict__ row, const fl
   return make_float2(zr, zi);
 }
 
-template <int K, int NT>
-__device__ __forceinline__ float tmarg_term(const PointC &P, const float2 *__restrict__ Q, const df s0[K],
-                                            const float2 F[K], const float2 *Ys, int ystride, float x, float quad,
-                                            uint32_t &flags) {
+template <int K, int NT, class Visit>
+__device__ __forceinline__ void tgrid_scan(const PointC &P, const float2 *__restrict__ Q, const df s0[K],
+                                           const float2 F[K], const float2 *Ys, int ystride, float x, float quad,
+                                           uint32_t &flags, Visit &&visit) {
   constexpr int first = (NT == 4) ? -1 : 0;
   float2 y[RIFT_MAXM + 1];
 #pragma unroll
@@ -404,7 +405,6 @@ __device__ __forceinline__ float tmarg_term(const PointC &P, const float2 *__res
     for (int r = 0; r < NT - 1; ++r) z[k][r] = z_row<NT>(base + (size_t)r * rs, y, npairs);
   }
   const float c = -0.25f * x * quad;
-  float m = -INFINITY, s = 0.f;
   for (int j = 0; j < J; ++j) {
     float lin = 0.f;
 #pragma unroll
@@ -418,9 +418,45 @@ __device__ __forceinline__ float tmarg_term(const PointC &P, const float2 *__res
 #pragma unroll
       for (int r = 0; r < NT - 1; ++r) z[k][r] = z[k][r + 1];
     }
-    const float l = x * (lin + c);
+    visit(j, x * (lin + c));
+  }
+}
+
+template <int K, int NT>
+__device__ __forceinline__ float tmarg_term(const PointC &P, const float2 *__restrict__ Q, const df s0[K],
+                                            const float2 F[K], const float2 *Ys, int ystride, float x, float quad,
+                                            uint32_t &flags) {
+  float m = -INFINITY, s = 0.f;
+  tgrid_scan<K, NT>(P, Q, s0, F, Ys, ystride, x, quad, flags, [&](int, float l) {
     if (l > m) { s = fmaf(s, expf(m - l), 1.f); m = l; }
     else s += expf(l - m);
-  }
-  return m + logf(s) - logf((float)J);
+  });
+  return m + logf(s) - logf((float)P.J);
+}
+
+// Event time of a draw from its conditional on the same grid, P(t_j | rest) proportional to
+// exp(lnL_j): the first j with sum_{i<=j} e^{lnL_i - m} > u sum_i e^{lnL_i - m} (m the maximum), or
+// the last j of positive weight when rounding leaves the cumulative sum short of the target.
+// Returns j (-1 if no j has a finite positive weight) and lnL_j.
+template <int K, int NT>
+__device__ __forceinline__ int tmarg_pick(const PointC &P, const float2 *__restrict__ Q, const df s0[K],
+                                          const float2 F[K], const float2 *Ys, int ystride, float x, float quad,
+                                          float u, float &l_out, uint32_t &flags) {
+  float m = -INFINITY, s = 0.f;
+  tgrid_scan<K, NT>(P, Q, s0, F, Ys, ystride, x, quad, flags, [&](int, float l) {
+    if (l > m) { s = fmaf(s, expf(m - l), 1.f); m = l; }
+    else s += expf(l - m);
+  });
+  const float target = u * s;
+  float c = 0.f, lp = NAN, ll = NAN;
+  int jp = -1, jl = -1;
+  tgrid_scan<K, NT>(P, Q, s0, F, Ys, ystride, x, quad, flags, [&](int j, float l) {
+    const float e = expf(l - m);
+    c += e;
+    if (e > 0.f) { jl = j; ll = l; }
+    if (jp < 0 && c > target) { jp = j; lp = l; }
+  });
+  if (jp < 0) { jp = jl; lp = ll; }
+  l_out = lp;
+  return jp;
 }

@@ -118,6 +118,7 @@ struct BatchCtl {
   const float *gmm;         // [np][RIFT_GMM_FLOATS]
   RoundPt *last;            // [np] the last round each point ran (harvest)
   int tmarg;                // the event time is marginalised by quadrature
+  uint32_t point_id1;       // Philox point word of a single-point handle (batches use the point index)
 };
 
 // Scratch of the Monte Carlo runner (device pointers unless noted).
@@ -178,8 +179,14 @@ struct rift_mdn;
 cudaError_t launch_mdn_gmm(const rift_mdn *m, const float *summ, const float *cst, int np, float *head_scratch,
                            float *gmm, cudaStream_t st);
 cudaError_t launch_gmm_from_head(const float *head, const float *cst, int np, float *gmm, cudaStream_t st);
-cudaError_t launch_harvest(const float *ell, const RoundPt *rp, const AccState *acc, int np, float beta, int H,
-                           float *cdf_scratch, int *idx_out, cudaStream_t st);
+// posterior samples (posterior.cu, kernels.cu)
+cudaError_t launch_rows(const CellLaunch &L, const RoundPt *last, const float *ell, const int *idx, size_t n_slots,
+                        int ncol, int np, float *out, cudaStream_t st);
+cudaError_t launch_resample(const float *ell, const RoundPt *last, const AccState *acc, int np, float beta, int H,
+                            int *idx, cudaStream_t st);
+cudaError_t launch_tdraw(int K, int interp, const PointC *pts, int np, int max_npair, int max_M, const float2 *qa,
+                         const float4 *ca, const RoundPt *last, unsigned long long seed, int H, float *out,
+                         uint32_t *flags, cudaStream_t st);
 cudaError_t launch_tables_ctl(const unsigned long long *part, int hblocks, const RoundPt *rp, int n_points, int nb,
                               double floor_eps, const BatchCtl &B, const RoundCtl *ctl, cudaStream_t st);
 

@@ -89,7 +89,12 @@ def test_adam_step_on_device(lib, cuda):
     lib.rift_mdn_train(m, S, th, w, box, steps=1, batch=n, lr=1e-3)
     new = lib.rift_mdn_get_params(m, 0).astype(np.float64)
     want = prm.astype(np.float64) - 1e-3 * g / (np.abs(g) + 1e-8)     # Adam's first step
-    assert np.allclose(new, want, atol=2e-6)
+    # the gradient is summed with atomics, so its order varies between the two evaluations: a
+    # component within rounding of zero can change sign, which flips its first step (+-lr)
+    sure = np.abs(g) > 1e-5 * np.abs(g).max()
+    assert sure.mean() > 0.5
+    assert np.allclose(new[sure], want[sure], atol=2e-6)
+    assert np.all(np.abs(new - prm) <= 1e-3 + 2e-6)
 
 
 def _head(seed, pt):
