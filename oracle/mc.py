@@ -228,7 +228,8 @@ def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_tar
     adaptive=False: plain prior sampling.  adaptive=True: round 0 uses `tables`
     (default: the prior's own uniform tables); after round r < adapt_rounds (all rounds
     if adapt_rounds < 0) the tables are rebuilt from that round, otherwise kept.  Returns a dict with lnL_marg, n_eff, kish, sigma, n_evals,
-    rounds (and per-round data if keep)."""
+    rounds, with the adaptive proposal "tables_next" (the tables a further round would use: a
+    warm start for another point), and per-round data if keep."""
     acc = Accum()
     rnd = 0
     hist = []
@@ -256,6 +257,16 @@ def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_tar
                 tables[2] = uniform_time_table(n_bins)
     lnm, n_eff, kish, sig = acc.result()
     out = dict(lnL_marg=lnm, n_eff=n_eff, kish=kish, sigma=sig, n_evals=acc.n, rounds=rnd, acc=acc)
+    if adaptive:
+        # the proposal a further round would draw from (Sec. II.C: the integrator carried over to
+        # the next intrinsic point): the last round's rebuild when that round adapts
+        if adapt_rounds < 0 or rnd - 1 < adapt_rounds:
+            nxt, _ = rebuild_tables(ell, bins, n_bins, beta, floor_eps)
+            if time_marg:
+                nxt[2] = uniform_time_table(n_bins)
+            out["tables_next"] = nxt
+        else:
+            out["tables_next"] = tables.copy()
     if keep:
         out["history"] = hist
     return out
