@@ -229,6 +229,15 @@ typedef struct {
                             single-point calls and the batched runner; with the learned proposal
                             the mixture's time coordinate is integrated out (dropped from each
                             diagonal component) and the weight is that of the other four.        */
+  int tables_per_point;  /* adaptive, with `tables`: the tables are host [n_points][3][n_bins+1], one
+                            set per point (0: one set for every point).  With `tables_out` this
+                            warm-starts each intrinsic point from an earlier run's integrator
+                            (Sec. II.C and III.B: the adaptive integrator is reused from one intrinsic
+                            point to the next).                                                  */
+  float *tables_out;     /* adaptive, optional host [n_points][3][n_bins+1]: each point's proposal at
+                            return -- the tables rebuilt from its last round when that round adapted
+                            (adapt_rounds), else the tables that round used: the proposal its next
+                            round would draw from.  RIFT_EINVAL with other proposals.            */
 } rift_mc_opts;
 
 /* Size of the sampler-state blob of rift_mc_opts.resume / save (same library build and byte order). */

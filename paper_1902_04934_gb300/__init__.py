@@ -60,7 +60,8 @@ class McOpts(C.Structure):
                 ("floor_eps", C.c_double), ("adapt_rounds", C.c_int), ("tables", C.c_void_p),
                 ("mdn", C.c_void_p), ("dbg_ell", C.c_void_p), ("dbg_tables", C.c_void_p),
                 ("max_rounds", C.c_int), ("timing", C.c_int), ("strata", C.c_int * 3),
-                ("resume", C.c_void_p), ("save", C.c_void_p), ("time_marg", C.c_int)]
+                ("resume", C.c_void_p), ("save", C.c_void_p), ("time_marg", C.c_int),
+                ("tables_per_point", C.c_int), ("tables_out", C.c_void_p)]
 
 
 MC_STATE_BYTES = 8192   # RIFT_MC_STATE_BYTES
@@ -317,7 +318,7 @@ def rift_ile_check(h):
 def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target=1e300, d_lo=1.0,
           d_hi=1000.0, proposal="prior", n_bins=100, beta=0.3, floor_eps=0.1, adapt_rounds=-1,
           tables=None, mdn=None, dbg_ell=None, dbg_tables=None, max_rounds=0, timing=0, strata=(0, 0, 0),
-          resume=None, save=None, time_marg=0, keep=None):
+          resume=None, save=None, time_marg=0, tables_out=None, keep=None):
     o = McOpts()
     o.seed = int(seed)
     o.point_id = int(point_id)
@@ -336,6 +337,7 @@ def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target
         if keep is not None:
             keep.append(tb)
         o.tables = tb.ctypes.data
+        o.tables_per_point = 1 if tb.ndim == 3 else 0   # [n_points][3][n_bins+1]: one set per point
     o.mdn = mdn.ptr.value if mdn is not None else None
     o.dbg_ell = dbg_ell.data_ptr() if dbg_ell is not None else None
     o.dbg_tables = dbg_tables.data_ptr() if dbg_tables is not None else None
@@ -351,15 +353,27 @@ def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target
     if save is not None:
         keep.append(save)
         o.save = C.cast(save, C.c_void_p)
+    if tables_out is not None:
+        keep.append(tables_out)
+        o.tables_out = tables_out.ctypes.data
     return o
 
 
-def rift_ile_marginalize(h, save=False, **kw):
+def _tables_out(h, want, kw):
+    """Host buffer for each point's proposal tables at return (adaptive runs), or None."""
+    if not want:
+        return None
+    return np.zeros((h.n_points, 3, int(kw.get("n_bins", 100)) + 1), dtype=np.float32)
+
+
+def rift_ile_marginalize(h, save=False, want_tables=False, **kw):
     """One point's marginalisation (see the C header).  resume=<bytes> continues a run whose
-    state an earlier call returned with save=True (the dict's "state" entry)."""
+    state an earlier call returned with save=True (the dict's "state" entry); want_tables=True
+    returns the adapted proposal as "tables" ([3][n_bins+1], to warm-start another point)."""
     keep = []
     buf = C.create_string_buffer(MC_STATE_BYTES) if save else None
-    o = _opts(keep=keep, save=buf, **kw)
+    tout = _tables_out(h, want_tables, kw)
+    o = _opts(keep=keep, save=buf, tables_out=tout, **kw)
     r = McResult()
     st = _lib.rift_ile_marginalize(h.ptr, C.byref(o), C.byref(r))
     if st not in (0, 7):
@@ -367,6 +381,8 @@ def rift_ile_marginalize(h, save=False, **kw):
     d = r.as_dict()
     if save:
         d["state"] = buf.raw
+    if tout is not None:
+        d["tables"] = tout[0]
     return d
 
 
@@ -382,14 +398,21 @@ def rift_ile_marginalize_static(h, **kw):
     return r.as_dict()
 
 
-def rift_ile_batch_marginalize(h, **kw):
+def rift_ile_batch_marginalize(h, want_tables=False, **kw):
+    """Every point of a batch handle; tables=<[n_points][3][n_bins+1]> starts each point from its
+    own proposal, want_tables=True returns each point's adapted proposal as "tables"."""
     keep = []
-    o = _opts(keep=keep, **kw)
+    tout = _tables_out(h, want_tables, kw)
+    o = _opts(keep=keep, tables_out=tout, **kw)
     res = (McResult * h.n_points)()
     st = _lib.rift_ile_batch_marginalize(h.ptr, C.byref(o), res)
     if st not in (0, 7):
         _check(h, st)
-    return [r.as_dict() for r in res]
+    out = [r.as_dict() for r in res]
+    if tout is not None:
+        for p, d in enumerate(out):
+            d["tables"] = tout[p]
+    return out
 
 
 MDN_PARAMS = 105048

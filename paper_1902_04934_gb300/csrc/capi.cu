@@ -403,8 +403,9 @@ rift_status check_opts(rift_ile *h, const rift_mc_opts *o) {
     if (o->n_bins < 2 || o->n_bins > RIFT_MAXBINS) return fail(h, RIFT_EINVAL, "n_bins out of range [2, 256]");
     if (!(o->beta > 0) || !(o->floor_eps > 0) || !(o->floor_eps <= 1)) return fail(h, RIFT_EINVAL, "bad beta / floor_eps");
     if (o->tables) {
-      for (int d = 0; d < 3; ++d) {
-        const float *c = o->tables + d * (o->n_bins + 1);
+      const int sets = o->tables_per_point ? h->n_points : 1;
+      for (int q = 0; q < 3 * sets; ++q) {
+        const float *c = o->tables + (size_t)q * (o->n_bins + 1);
         if (c[0] != 0.f || c[o->n_bins] != 1.f) return fail(h, RIFT_EINVAL, "tables must start at 0 and end at 1");
         for (int b = 0; b < o->n_bins; ++b)
           if (!(c[b + 1] > c[b])) return fail(h, RIFT_EINVAL, "tables must be strictly increasing");
@@ -416,6 +417,8 @@ rift_status check_opts(rift_ile *h, const rift_mc_opts *o) {
   } else if (o->proposal != RIFT_PROPOSAL_PRIOR) {
     return fail(h, RIFT_EINVAL, "unknown proposal");
   }
+  if (o->tables_out && o->proposal != RIFT_PROPOSAL_ADAPTIVE)
+    return fail(h, RIFT_EINVAL, "tables_out needs the adaptive proposal");
   return RIFT_OK;
 }
 
@@ -620,8 +623,10 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
         for (int b = 0; b <= nb; ++b) u[d * (nb + 1) + b] = (float)((double)b / nb);
       src = u;
     }
-    for (int p = 0; p < np; ++p)
-      RIFT_CK(h, cudaMemcpyAsync(S.tables + p * tstride, src, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
+    for (int p = 0; p < np; ++p) {
+      const float *sp = (o->tables && o->tables_per_point) ? src + p * tstride : src;
+      RIFT_CK(h, cudaMemcpyAsync(S.tables + p * tstride, sp, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
+    }
     RIFT_CK(h, cudaStreamSynchronize(st));
     // lnw of the round-0 tables (every point): rp is only read for its flags with part == nullptr
     for (int p = 0; p < np; ++p) {
@@ -770,6 +775,13 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   }
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
+  if (o->tables_out && adaptive && status == RIFT_OK) {
+    // the buffer the next round would read: rebuilt from the last round if it adapted
+    for (int p = 0; p < np; ++p)
+      RIFT_CK(h, cudaMemcpyAsync(o->tables_out + p * tstride, S.tables + ((size_t)cur * np + p) * tstride,
+                                 sizeof(float) * tstride, cudaMemcpyDeviceToHost, st));
+    RIFT_CK(h, cudaStreamSynchronize(st));
+  }
   if (o->save && status == RIFT_OK) {
     McStateBlob outb = hdr;
     outb.rounds = (uint32_t)rounds[0];
@@ -1083,8 +1095,10 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
         for (int b = 0; b <= nb; ++b) u[d * (nb + 1) + b] = (float)((double)b / nb);
       src = u;
     }
-    for (int p = 0; p < np; ++p)
-      RIFT_CK(h, cudaMemcpyAsync(S.tables + p * tstride, src, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
+    for (int p = 0; p < np; ++p) {
+      const float *sp = (o->tables && o->tables_per_point) ? src + p * tstride : src;
+      RIFT_CK(h, cudaMemcpyAsync(S.tables + p * tstride, sp, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
+    }
     RIFT_CK(h, cudaStreamSynchronize(st));
     for (int p = 0; p < np; ++p) { S.rp_host[p].proposal = 1; S.rp_host[p].ncell = 1; }
     RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
@@ -1169,6 +1183,20 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   RIFT_CK(h, cudaMemcpyAsync(S.acc_host, S.acc, sizeof(AccState) * np, cudaMemcpyDeviceToHost, st));
   RIFT_CK(h, cudaMemcpyAsync(h->pst_host, h->pst, sizeof(PtState) * np, cudaMemcpyDeviceToHost, st));
   RIFT_CK(h, cudaStreamSynchronize(st));
+  if (o->tables_out && adaptive) {
+    // Round r reads table buffer (number of adapting rounds before r) mod 2 and an adapting round
+    // writes the other one, so after a point's last round its next proposal is in buffer
+    // min(rounds, adapt_rounds) mod 2; later rounds of other points do not touch its slot.
+    const size_t tstride = (size_t)3 * (nb + 1);
+    for (int p = 0; p < np; ++p) {
+      const long long rp_ = h->pst_host[p].rounds;
+      const long long na = (o->adapt_rounds < 0) ? rp_ : std::min<long long>(rp_, o->adapt_rounds);
+      const size_t buf = (size_t)(na & 1);
+      RIFT_CK(h, cudaMemcpyAsync(o->tables_out + p * tstride, S.tables + (buf * np + p) * tstride,
+                                 sizeof(float) * tstride, cudaMemcpyDeviceToHost, st));
+    }
+    RIFT_CK(h, cudaStreamSynchronize(st));
+  }
   rift_status fl = read_flags(h);
   rift_status overall = fl;
   for (int p = 0; p < np; ++p) {
@@ -1330,6 +1358,7 @@ rift_status rift_ile_autotune(rift_ile *h, const rift_mc_opts *o, int reps, rift
   t.max_rounds = reps;
   t.resume = nullptr;
   t.save = nullptr;
+  t.tables_out = nullptr;
   const int old_target = h->cell_target, old_ctas = h->smem_split;
   const int targets[3] = {320, 640, 1280}, splits[4] = {2, 3, 4, 6};
   std::vector<rift_mc_result> res((size_t)h->n_points);
