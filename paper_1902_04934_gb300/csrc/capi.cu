@@ -267,6 +267,30 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
         cv[c.uv_off + (size_t)pair_slot(a, b, M) * K + k] =
             make_float4((float)(f * u[0]), (float)(f * u[1]), (float)(f * v[0]), (float)(f * v[1]));
       }
+  c.coef_off = c.uv_off;
+  c.ncoef = c.npair * K;
+  // the grouped quadratic form is compiled for three detectors with cubic taps (kCanonPath)
+  c.canon_full = (c.canon_mask == (1u << RIFT_MAXM) - 1u && K == 3 && d->interp == 3) ? 1 : 0;
+  if (c.canon_full) {
+    // grouped layout of quad_canon: [U part | V part][slot][k], two pairs per float4 (modes are
+    // stored in canonical order, so canonical index = stored index)
+    c.coef_off = (long long)cv.size();
+    c.ncoef = 2 * kCanonSlots * K;
+    cv.resize(cv.size() + (size_t)c.ncoef, make_float4(0.f, 0.f, 0.f, 0.f));
+    float *g = reinterpret_cast<float *>(cv.data() + c.coef_off);
+    for (int part = 0; part < 2; ++part)
+      for (int i = 0; i < kCanonPairs; ++i) {
+        const int code = part ? canon_pair_B(i) : canon_pair_A(i);
+        const int a = (code >> 5) & 31, b = code & 31;
+        const bool conj = !part && canon_m(b) < canon_m(a);
+        for (int k = 0; k < K; ++k) {
+          const float4 pc = cv[c.uv_off + (size_t)pair_slot(a, b, M) * K + k];
+          float *o = g + 4 * ((size_t)(part * kCanonSlots + i / 2) * K + k) + 2 * (i & 1);
+          o[0] = part ? pc.z : pc.x;
+          o[1] = part ? pc.w : (conj ? -pc.y : pc.y);
+        }
+      }
+  }
   return RIFT_OK;
 }
 
@@ -339,7 +363,7 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
       return s;
     }
     h->max_M = std::max(h->max_M, h->pts[i].c.M);
-    h->max_pairK = std::max(h->max_pairK, h->pts[i].c.npair * h->K);
+    h->max_pairK = std::max(h->max_pairK, h->pts[i].c.ncoef);
     if (descs[i].interp != descs[0].interp) {
       rift_status s2 = fail(h, RIFT_EINVAL, "points differ in interp");
       rift_ile_destroy(h);

@@ -73,6 +73,17 @@ __device__ __forceinline__ void copy_words(const void *src, void *dst, int nbyte
   for (int i = threadIdx.x; i < nbytes / 4; i += blockDim.x) d[i] = s[i];
 }
 
+// Quadratic term of a drawn sample: the grouped form for points with all 21 canonical modes
+// (the kernels compiled with it), the pair form otherwise.  u_phi = n1 2^-24, n1 odd.
+template <int K, int NT>
+__device__ __forceinline__ float quad_cell(const PointC &P, const float4 *__restrict__ C, const SampleGeo &g,
+                                           const float2 *Ys, int ystride, float ch, float sh, float u_phi) {
+  if constexpr (kCanonPath<K, NT>) {
+    if (P.canon_full) return quad_canon<K>(P, C, g, ch, sh, (uint32_t)(u_phi * 16777216.f));
+  }
+  return quad_term<K>(P, C, g, Ys, ystride);
+}
+
 // Sky and time geometry of a drawn sample: cos/sin of (ra - GMST) and sin/cos dec.
 struct Sky { float ca, sa, cd; df sd; };
 
@@ -261,8 +272,8 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(C
       copy_words(L.pts + p, &P, sizeof(PointC));
       copy_words(L.rp + p, &sR, sizeof(RoundPt));
       __syncthreads();
-      const float4 *cg = L.ca + P.uv_off;
-      for (int j = threadIdx.x; j < P.npair * K; j += blockDim.x) C[j] = cg[j];
+      const float4 *cg = L.ca + P.coef_off;
+      for (int j = threadIdx.x; j < P.ncoef; j += blockDim.x) C[j] = cg[j];
       if (R.proposal == 1) {
         for (int j = threadIdx.x; j < 3 * (R.nb + 1); j += blockDim.x) tab[j] = R.tab[j];
         for (int j = threadIdx.x; j < 3 * R.nb; j += blockDim.x) lnw[j] = R.lnw[j];
@@ -395,14 +406,15 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(C
       g.x = d.xd;
       float sphi, cphi;
       sincospif(2.f * d.u_phi, &sphi, &cphi);
-      swsh_canonical(P, sqrtf(d.c_frac), sqrtf(1.f - d.c_frac), cphi, sphi, Ys, ystride);
+      const float ch = sqrtf(d.c_frac), sh = sqrtf(1.f - d.c_frac);   // cos, sin(incl/2)
+      swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
       float lnL;
       if (TMARG) {
-        const float quad = quad_term<K>(P, C, g, Ys, ystride);
+        const float quad = quad_cell<K, NT>(P, C, g, Ys, ystride, ch, sh, d.u_phi);
         lnL = tmarg_term<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
       } else {
         const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
-        const float quad = quad_term<K>(P, C, g, Ys, ystride);
+        const float quad = quad_cell<K, NT>(P, C, g, Ys, ystride, ch, sh, d.u_phi);
         lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
       }
       float ell = lnL + d.lpq;

@@ -6,6 +6,8 @@
 // Q oscillates at ~100 Hz, so 1e-9 s of time error is ~1e-4 in lnL at SNR 30.
 #pragma once
 #include <cstdint>
+#include <type_traits>
+#include <utility>
 #include <cuda_runtime.h>
 
 #define RIFT_MAXK 4
@@ -39,6 +41,8 @@ struct PointC {
   int J, pad1;        // J: points of the time quadrature, floor((t_hi - t_lo) fs)
   long long q_off;    // offset of this point's Q in the Q arena (float2 units), 16-byte aligned
   long long uv_off;   // offset of this point's pair coefficients (float4 units)
+  long long coef_off; // offset of the coefficients the quadratic form reads (uv_off, or the
+                      // grouped canonical array of a point with all 21 modes)
   float fs, dref;     // Q rate (Hz), D_ref (Mpc)
   float g_hi, g_lo;   // GMST / 2pi (turns), double-float
   float A, Alo;       // (t_hi - t_lo) fs, samples (double-float)
@@ -48,7 +52,10 @@ struct PointC {
   ModeC mode[RIFT_MAXM];
   // the same harmonics by canonical index j (l = 2..4, m = -l..l in order): bit j of canon_mask
   // is set when mode j is present; its terms r = r_min(j).. have coefficients ccoef[j][r - r_min(j)]
-  uint32_t canon_mask, pad2, pad3, pad4;
+  uint32_t canon_mask;
+  int ncoef;          // float4 entries at coef_off (staged into shared memory by the kernels)
+  int canon_full;     // all 21 canonical modes present: grouped quadratic form (quad_canon)
+  int pad4;
   float ccoef[RIFT_MAXM][RIFT_MAXTERM];
 };
 
@@ -167,6 +174,18 @@ __device__ __forceinline__ void response_delay(const PointC &P, float ca, float 
   }
 }
 
+// Real factor d_j(iota) of -2Y_lm = e^{i m phi} d_j for canonical mode j, from the powers
+// cp[k] = cos(iota/2)^k, sp[k] = sin(iota/2)^k (j compile-time after unrolling).
+__device__ __forceinline__ float canon_dval(const PointC &P, int j, const float (&cp)[9], const float (&sp)[9]) {
+  float v = 0.f;
+#pragma unroll
+  for (int r = canon_rmin(j); r <= canon_rmax(j); ++r) {
+    const int kc = 2 * r - 2 - canon_m(j);
+    v = fmaf(P.ccoef[j][r - canon_rmin(j)], cp[kc] * sp[2 * canon_l(j) - kc], v);
+  }
+  return v;
+}
+
 // -2Y_lm of the present modes, unrolled over the canonical table so every power index is a
 // compile-time constant; stored mode a = number of present canonical modes before j.
 __device__ __forceinline__ void swsh_canonical(const PointC &P, float c, float s, float cphi, float sphi,
@@ -185,12 +204,7 @@ __device__ __forceinline__ void swsh_canonical(const PointC &P, float c, float s
 #pragma unroll
   for (int j = 0; j < RIFT_MAXM; ++j) {
     if (mask & (1u << j)) {
-      float v = 0.f;
-#pragma unroll
-      for (int r = canon_rmin(j); r <= canon_rmax(j); ++r) {
-        const int kc = 2 * r - 2 - canon_m(j);
-        v = fmaf(P.ccoef[j][r - canon_rmin(j)], cp[kc] * sp[2 * canon_l(j) - kc], v);
-      }
+      const float v = canon_dval(P, j, cp, sp);
       const int am = canon_m(j) < 0 ? -canon_m(j) : canon_m(j);
       const float2 em = e[am];
       const int a = __popc(mask & ((1u << j) - 1u));
@@ -345,6 +359,136 @@ __device__ __forceinline__ float quad_term(const PointC &P, const float4 *__rest
   }
   return quad;
 }
+
+// ---------------------------------------------------------------------------
+// Quadratic term of a point with all 21 canonical modes.  With -2Y_lm(i, phi) = e^{i m phi} d_lm(i)
+// (d real), conj(Y_a) Y_b = d_a d_b e^{i (m_b - m_a) phi} and Y_a Y_b = d_a d_b e^{i (m_a + m_b) phi}, so
+//   A_k = sum_{D=0..8} Re(e^{i D phi} S_kD),   S_kD = sum_{a<=b, |m_b - m_a| = D} d_a d_b c_ab
+//   B_k = sum_{s=-8..8} e^{i s phi} T_ks,       T_ks = sum_{a<=b, m_a + m_b = s}  d_a d_b v_ab
+// with c_ab, v_ab the pair coefficients of quad_term (c_ab conjugated where m_b < m_a).  Each pair
+// costs one real product and two FMAs per detector and part instead of complex products.  The
+// pairs are enumerated at compile time in group order (canon_pair_A / canon_pair_B: group << 10 |
+// a << 5 | b); the grouped coefficients hold two pairs per float4 per detector: [slot][k] =
+// (c_{2s}, c_{2s+1}), the U part first, then the V part.
+// ---------------------------------------------------------------------------
+constexpr int kCanonPairs = RIFT_MAXM * (RIFT_MAXM + 1) / 2;
+constexpr int kCanonSlots = (kCanonPairs + 1) / 2;
+
+// Pair tables, built once at compile time: A[i], B[i] = group << 10 | a << 5 | b.
+struct CanonPairs {
+  int A[kCanonPairs];
+  int B[kCanonPairs];
+};
+
+__host__ __device__ constexpr CanonPairs make_canon_pairs() {
+  CanonPairs t{};
+  int n = 0;
+  for (int D = 0; D <= 8; ++D)
+    for (int a = 0; a < RIFT_MAXM; ++a)
+      for (int b = a; b < RIFT_MAXM; ++b) {
+        const int dm = canon_m(b) - canon_m(a);
+        if ((dm < 0 ? -dm : dm) == D) t.A[n++] = (D << 10) | (a << 5) | b;
+      }
+  n = 0;
+  for (int S = -8; S <= 8; ++S)
+    for (int a = 0; a < RIFT_MAXM; ++a)
+      for (int b = a; b < RIFT_MAXM; ++b)
+        if (canon_m(a) + canon_m(b) == S) t.B[n++] = ((S + 8) << 10) | (a << 5) | b;
+  return t;
+}
+
+// host copies (the coefficient layout is built on the host)
+constexpr CanonPairs kCanonPairTab = make_canon_pairs();
+constexpr int canon_pair_A(int i) { return kCanonPairTab.A[i]; }
+constexpr int canon_pair_B(int i) { return kCanonPairTab.B[i]; }
+
+// the pair tables as constant data (folded into immediates once the loops below are unrolled)
+__constant__ const CanonPairs kCanonPairDev = make_canon_pairs();
+
+__device__ __forceinline__ float2 eiphi_n(const float2 (&e)[9], int n) {
+  const float2 r = e[n < 0 ? -n : n];
+  return n < 0 ? make_float2(r.x, -r.y) : r;
+}
+
+// One part (U: B = false, V: B = true) over the 231 pairs in group order.
+template <int K, bool B>
+__device__ __forceinline__ void canon_part(const float4 *__restrict__ G, const float (&d)[RIFT_MAXM],
+                                           const float2 (&e)[9], float (&acc)[K][2]) {
+  float S[K][2];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { S[k][0] = 0.f; S[k][1] = 0.f; }
+#pragma unroll
+  for (int i = 0; i < kCanonPairs; ++i) {
+    const int code = B ? kCanonPairDev.B[i] : kCanonPairDev.A[i];
+    const int grp = code >> 10;
+    const float4 *c = G + (B ? kCanonSlots * K : 0) + (i >> 1) * K;
+    // d_a d_b; the V part forms it as an FMA with zero (the same value) so that the compiler does
+    // not keep the U part's 231 products alive for reuse
+    const float p = B ? __fmaf_rn(d[(code >> 5) & 31], d[code & 31], 0.f) : d[(code >> 5) & 31] * d[code & 31];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float4 ck = c[k];
+      S[k][0] = fmaf(p, (i & 1) ? ck.z : ck.x, S[k][0]);
+      if (B || grp != 0) S[k][1] = fmaf(p, (i & 1) ? ck.w : ck.y, S[k][1]);   // D = 0: only Re S counts
+    }
+    const bool last = (i + 1 == kCanonPairs) || ((B ? kCanonPairDev.B[i + 1] : kCanonPairDev.A[i + 1]) >> 10) != grp;
+    if (last) {
+      // the group ends: rotate its sum by e^{i n phi} into the part's total
+      const float2 r = eiphi_n(e, B ? grp - 8 : grp);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        acc[k][0] = fmaf(r.x, S[k][0], fmaf(-r.y, S[k][1], acc[k][0]));
+        if (B) acc[k][1] = fmaf(r.x, S[k][1], fmaf(r.y, S[k][0], acc[k][1]));
+        S[k][0] = 0.f;
+        S[k][1] = 0.f;
+      }
+    }
+  }
+}
+
+// Not inlined: one copy per translation unit instead of one per kernel keeps the build short.
+// c, s = cos, sin(iota/2): the d_j are evaluated here from the same sums as swsh_canonical.
+// phi = 2 pi n1 2^-24 with n1 odd (the sampler's lattice): e^{i D phi} = sincospi(D n1 2^-23),
+// reduced modulo 2 exactly in integers, so every rotation is good to an ulp (a product chain
+// from e^{i phi} would carry D times its rounding into whole group sums).
+template <int K>
+__device__ __noinline__ float quad_canon(const PointC &P, const float4 *__restrict__ G, const SampleGeo &g,
+                                         float c, float s, uint32_t n1) {
+  float2 e[9];
+  e[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int D = 1; D <= 8; ++D) {
+    const uint32_t r = ((uint32_t)D * n1) & 0xFFFFFFu;
+    sincospif((float)r * 1.1920928955078125e-07f, &e[D].y, &e[D].x);
+  }
+  float cp[9], sp[9];
+  cp[0] = 1.f; sp[0] = 1.f;
+#pragma unroll
+  for (int j = 1; j < 9; ++j) { cp[j] = cp[j - 1] * c; sp[j] = sp[j - 1] * s; }
+  float d[RIFT_MAXM];
+#pragma unroll
+  for (int j = 0; j < RIFT_MAXM; ++j) d[j] = canon_dval(P, j, cp, sp);
+  float A[K][2], Bc[K][2];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { A[k][0] = 0.f; A[k][1] = 0.f; Bc[k][0] = 0.f; Bc[k][1] = 0.f; }
+  canon_part<K, false>(G, d, e, A);
+  canon_part<K, true>(G, d, e, Bc);
+  float quad = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float2 F = g.F[k];
+    const float f2 = F.x * F.x + F.y * F.y;
+    const float gr = F.x * F.x - F.y * F.y, gi = -2.f * F.x * F.y;
+    quad += f2 * A[k][0] + (gr * Bc[k][0] - gi * Bc[k][1]);
+  }
+  return quad;
+}
+
+// Cell kernels compiled with the grouped form: three detectors and cubic taps (the full-size
+// workload); the host marks a point canon_full only for these, so that compile time stays short.
+// The other kernels read the pair layout (uv_off) and use quad_term for every point.
+template <int K, int NT>
+constexpr bool kCanonPath = (K == 3 && NT == 4);
 
 // ---------------------------------------------------------------------------
 // Time-marginalised likelihood, Eq. (lnL:tmarg): ln (1/J) sum_j exp(lnL(theta, t_j)) over the
