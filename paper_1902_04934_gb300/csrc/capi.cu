@@ -128,6 +128,9 @@ struct rift_ile {
   RoundPt *last = nullptr;    // [np]
   int *hidx = nullptr;        // harvest indices
   size_t cap_hidx = 0;
+  // single-point handle of a three-detector point with all 21 modes: its grouped coefficients,
+  // passed to the cell kernel as a parameter
+  CanonCoefParam *canon0 = nullptr;
 };
 
 namespace {
@@ -369,6 +372,11 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
       rift_ile_destroy(h);
       return s2;
     }
+  }
+  if (n == 1 && h->pts[0].c.canon_full) {
+    h->canon0 = new (std::nothrow) CanonCoefParam;
+    if (!h->canon0) { rift_status s1 = fail(h, RIFT_ENOMEM, "host allocation"); rift_ile_destroy(h); return s1; }
+    std::memcpy(h->canon0->g, cv.data() + h->pts[0].c.coef_off, sizeof(h->canon0->g));
   }
   if (fault_is("alloc")) {
     rift_status s0 = fail(h, RIFT_ENOMEM, "injected fault: device allocation failed");
@@ -760,7 +768,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     RIFT_CK(h, cudaMemcpyAsync(S.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
     const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(items, (uint32_t)(h->num_sms * bps)));
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev0, st));
-    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st));
+    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st, np == 1 ? h->canon0 : nullptr));
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev1, st));
     RIFT_CK(h, launch_merge_points(S.partials, S.rp, np, S.acc, st));
     launches += 2;
@@ -899,6 +907,7 @@ void rift_ile_destroy(rift_ile *h) {
   cudaFreeHost(h->ctl_host);
   cudaFreeHost(h->pst_host);
   if (h->gstream) cudaStreamDestroy(h->gstream);
+  delete h->canon0;
   delete h;
 }
 

@@ -75,9 +75,11 @@ __device__ __forceinline__ void copy_words(const void *src, void *dst, int nbyte
 
 // Quadratic term of a drawn sample: the grouped form for points with all 21 canonical modes
 // (the kernels compiled with it), the pair form otherwise.  u_phi = n1 2^-24, n1 odd.
-template <int K, int NT>
-__device__ __forceinline__ float quad_cell(const PointC &P, const float4 *__restrict__ C, const SampleGeo &g,
-                                           const float2 *Ys, int ystride, float ch, float sh, float u_phi) {
+template <int K, int NT, int CP>
+__device__ __forceinline__ float quad_cell(const PointC &P, const float4 *__restrict__ C,
+                                           const float4 *__restrict__ cpg, const SampleGeo &g, const float2 *Ys,
+                                           int ystride, float ch, float sh, float u_phi) {
+  if constexpr (CP) return quad_canon_body<K>(P, cpg, g, ch, sh, (uint32_t)(u_phi * 16777216.f));
   if constexpr (kCanonPath<K, NT>) {
     if (P.canon_full) return quad_canon<K>(P, C, g, ch, sh, (uint32_t)(u_phi * 16777216.f));
   }
@@ -211,8 +213,8 @@ __device__ __forceinline__ void delay_index(const PointC &P, const Sky &s, df ou
 // TMARG: the event time is marginalised by quadrature (Eq. lnL:tmarg) instead of sampled; the
 // sample's t uniform is unused, its Q rows span the whole time window (no staging), and the
 // likelihood is tmarg_term.
-template <int K, int NT, int LEARNED, int TMARG>
-__global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(CellLaunch L) {
+template <int K, int NT, int LEARNED, int TMARG, int CP>
+__device__ __forceinline__ void cells_body(const CellLaunch &L, const float4 *__restrict__ cpg) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_item, s_point;
@@ -272,8 +274,10 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(C
       copy_words(L.pts + p, &P, sizeof(PointC));
       copy_words(L.rp + p, &sR, sizeof(RoundPt));
       __syncthreads();
-      const float4 *cg = L.ca + P.coef_off;
-      for (int j = threadIdx.x; j < P.ncoef; j += blockDim.x) C[j] = cg[j];
+      if (!CP) {
+        const float4 *cg = L.ca + P.coef_off;
+        for (int j = threadIdx.x; j < P.ncoef; j += blockDim.x) C[j] = cg[j];
+      }
       if (R.proposal == 1) {
         for (int j = threadIdx.x; j < 3 * (R.nb + 1); j += blockDim.x) tab[j] = R.tab[j];
         for (int j = threadIdx.x; j < 3 * R.nb; j += blockDim.x) lnw[j] = R.lnw[j];
@@ -410,11 +414,11 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(C
       swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
       float lnL;
       if (TMARG) {
-        const float quad = quad_cell<K, NT>(P, C, g, Ys, ystride, ch, sh, d.u_phi);
+        const float quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
         lnL = tmarg_term<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
       } else {
         const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
-        const float quad = quad_cell<K, NT>(P, C, g, Ys, ystride, ch, sh, d.u_phi);
+        const float quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
         lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
       }
       float ell = lnL + d.lpq;
@@ -602,6 +606,17 @@ __global__ void tables_points_kernel(const unsigned long long *__restrict__ part
   }
 }
 
+template <int K, int NT, int LEARNED, int TMARG>
+__global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(CellLaunch L) {
+  cells_body<K, NT, LEARNED, TMARG, 0>(L, nullptr);
+}
+
+// One three-detector point with all 21 modes: its grouped coefficients come in the parameters.
+template <int K, int NT>
+__global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel_cp(CellLaunch L, const __grid_constant__ CanonCoefParam cc) {
+  cells_body<K, NT, 0, 0, 1>(L, cc.g);
+}
+
 // The samples of one round of point 0 in cell order (no evaluation).
 __global__ void draw_cells_kernel(CellLaunch L, DrawOut o, uint32_t n) {
   __shared__ __align__(16) PointC P;
@@ -768,7 +783,22 @@ cudaError_t cells_kl(const CellLaunch &L, int grid, int block, size_t smem, cuda
 }
 
 template <int K, int NT>
-cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
+cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,
+                    const CanonCoefParam *cc) {
+  if constexpr (kCanonPath<K, NT>) {
+    if (cc && !L.tmarg && !L.learned) {
+      static bool attr = false;
+      if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(cells_kernel_cp<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      cells_kernel_cp<K, NT><<<grid, block, smem, st>>>(L, *cc);
+      return cudaGetLastError();
+    }
+  }
+  (void)cc;
   if (L.tmarg) return L.learned ? cells_kl<K, NT, 1, 1>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 1>(L, grid, block, smem, st);
   return L.learned ? cells_kl<K, NT, 1, 0>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 0>(L, grid, block, smem, st);
 }
@@ -808,8 +838,9 @@ size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block) 
     default: break;                                                             \
   }
 
-cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st) {
-#define RIFT_C(KK, TT) cells_k<KK, TT>(L, grid, block, smem, st)
+cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,
+                         const CanonCoefParam *cc) {
+#define RIFT_C(KK, TT) cells_k<KK, TT>(L, grid, block, smem, st, cc)
   RIFT_CELLS_DISPATCH(K, ntap, RIFT_C)
 #undef RIFT_C
   return cudaErrorInvalidValue;

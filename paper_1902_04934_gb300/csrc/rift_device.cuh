@@ -446,14 +446,15 @@ __device__ __forceinline__ void canon_part(const float4 *__restrict__ G, const f
   }
 }
 
-// Not inlined: one copy per translation unit instead of one per kernel keeps the build short.
+// quad_canon is not inlined: one copy per translation unit instead of one per kernel keeps the
+// build short (the kernel that reads G from its parameters inlines the body instead).
 // c, s = cos, sin(iota/2): the d_j are evaluated here from the same sums as swsh_canonical.
 // phi = 2 pi n1 2^-24 with n1 odd (the sampler's lattice): e^{i D phi} = sincospi(D n1 2^-23),
 // reduced modulo 2 exactly in integers, so every rotation is good to an ulp (a product chain
 // from e^{i phi} would carry D times its rounding into whole group sums).
 template <int K>
-__device__ __noinline__ float quad_canon(const PointC &P, const float4 *__restrict__ G, const SampleGeo &g,
-                                         float c, float s, uint32_t n1) {
+__device__ __forceinline__ float quad_canon_body(const PointC &P, const float4 *__restrict__ G, const SampleGeo &g,
+                                                 float c, float s, uint32_t n1) {
   float2 e[9];
   e[0] = make_float2(1.f, 0.f);
 #pragma unroll
@@ -484,11 +485,24 @@ __device__ __noinline__ float quad_canon(const PointC &P, const float4 *__restri
   return quad;
 }
 
+template <int K>
+__device__ __noinline__ float quad_canon(const PointC &P, const float4 *__restrict__ G, const SampleGeo &g, float c,
+                                         float s, uint32_t n1) {
+  return quad_canon_body<K>(P, G, g, c, s, n1);
+}
+
 // Cell kernels compiled with the grouped form: three detectors and cubic taps (the full-size
 // workload); the host marks a point canon_full only for these, so that compile time stays short.
 // The other kernels read the pair layout (uv_off) and use quad_term for every point.
 template <int K, int NT>
 constexpr bool kCanonPath = (K == 3 && NT == 4);
+
+// The grouped coefficients of one three-detector point as a kernel parameter: single-point launches
+// pass them by value, so the quadratic form reads them from the parameter (constant) bank instead of
+// shared memory.
+struct CanonCoefParam {
+  float4 g[2 * kCanonSlots * 3];
+};
 
 // ---------------------------------------------------------------------------
 // Time-marginalised likelihood, Eq. (lnL:tmarg): ln (1/J) sum_j exp(lnL(theta, t_j)) over the
