@@ -293,6 +293,18 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
           o[1] = part ? pc.w : (conj ? -pc.y : pc.y);
         }
       }
+    // modes on one sign of frequency each (non-precessing): U vanishes between opposite-sign m,
+    // V between same-sign m; checked exactly, so skipping those pairs changes no bit
+    c.canon_sparse = 1;
+    for (int a = 0; a < M && c.canon_sparse; ++a)
+      for (int b = a; b < M; ++b) {
+        const int mm = canon_m(a) * canon_m(b);
+        if (mm == 0) continue;
+        for (int k = 0; k < K; ++k) {
+          const float4 pc = cv[c.uv_off + (size_t)pair_slot(a, b, M) * K + k];
+          if ((mm < 0 && (pc.x != 0.f || pc.y != 0.f)) || (mm > 0 && (pc.z != 0.f || pc.w != 0.f))) c.canon_sparse = 0;
+        }
+      }
   }
   return RIFT_OK;
 }
@@ -768,7 +780,8 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     RIFT_CK(h, cudaMemcpyAsync(S.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
     const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(items, (uint32_t)(h->num_sms * bps)));
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev0, st));
-    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st, np == 1 ? h->canon0 : nullptr));
+    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st, np == 1 ? h->canon0 : nullptr,
+                            h->pts[0].c.canon_sparse));
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev1, st));
     RIFT_CK(h, launch_merge_points(S.partials, S.rp, np, S.acc, st));
     launches += 2;

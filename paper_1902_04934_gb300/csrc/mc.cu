@@ -79,9 +79,11 @@ template <int K, int NT, int CP>
 __device__ __forceinline__ float quad_cell(const PointC &P, const float4 *__restrict__ C,
                                            const float4 *__restrict__ cpg, const SampleGeo &g, const float2 *Ys,
                                            int ystride, float ch, float sh, float u_phi) {
-  if constexpr (CP) return quad_canon_body<K>(P, cpg, g, ch, sh, (uint32_t)(u_phi * 16777216.f));
+  const uint32_t n1 = (uint32_t)(u_phi * 16777216.f);
+  if constexpr (CP) return quad_canon_body<K, CP == 2>(P, cpg, g, ch, sh, n1);
   if constexpr (kCanonPath<K, NT>) {
-    if (P.canon_full) return quad_canon<K>(P, C, g, ch, sh, (uint32_t)(u_phi * 16777216.f));
+    if (P.canon_full)
+      return P.canon_sparse ? quad_canon<K, true>(P, C, g, ch, sh, n1) : quad_canon<K, false>(P, C, g, ch, sh, n1);
   }
   return quad_term<K>(P, C, g, Ys, ystride);
 }
@@ -611,10 +613,11 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(C
   cells_body<K, NT, LEARNED, TMARG, 0>(L, nullptr);
 }
 
-// One three-detector point with all 21 modes: its grouped coefficients come in the parameters.
-template <int K, int NT>
+// One three-detector point with all 21 modes: its grouped coefficients come in the parameters
+// (SP: the pairs that vanish for modes on one sign of frequency are skipped).
+template <int K, int NT, int SP>
 __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel_cp(CellLaunch L, const __grid_constant__ CanonCoefParam cc) {
-  cells_body<K, NT, 0, 0, 1>(L, cc.g);
+  cells_body<K, NT, 0, 0, SP ? 2 : 1>(L, cc.g);
 }
 
 // The samples of one round of point 0 in cell order (no evaluation).
@@ -784,21 +787,25 @@ cudaError_t cells_kl(const CellLaunch &L, int grid, int block, size_t smem, cuda
 
 template <int K, int NT>
 cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,
-                    const CanonCoefParam *cc) {
+                    const CanonCoefParam *cc, int cc_sparse) {
   if constexpr (kCanonPath<K, NT>) {
     if (cc && !L.tmarg && !L.learned) {
       static bool attr = false;
       if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(cells_kernel_cp<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(cells_kernel_cp<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(cells_kernel_cp<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
       }
-      cells_kernel_cp<K, NT><<<grid, block, smem, st>>>(L, *cc);
+      if (cc_sparse) cells_kernel_cp<K, NT, 1><<<grid, block, smem, st>>>(L, *cc);
+      else cells_kernel_cp<K, NT, 0><<<grid, block, smem, st>>>(L, *cc);
       return cudaGetLastError();
     }
   }
   (void)cc;
+  (void)cc_sparse;
   if (L.tmarg) return L.learned ? cells_kl<K, NT, 1, 1>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 1>(L, grid, block, smem, st);
   return L.learned ? cells_kl<K, NT, 1, 0>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 0>(L, grid, block, smem, st);
 }
@@ -839,8 +846,8 @@ size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block) 
   }
 
 cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,
-                         const CanonCoefParam *cc) {
-#define RIFT_C(KK, TT) cells_k<KK, TT>(L, grid, block, smem, st, cc)
+                         const CanonCoefParam *cc, int cc_sparse) {
+#define RIFT_C(KK, TT) cells_k<KK, TT>(L, grid, block, smem, st, cc, cc_sparse)
   RIFT_CELLS_DISPATCH(K, ntap, RIFT_C)
 #undef RIFT_C
   return cudaErrorInvalidValue;

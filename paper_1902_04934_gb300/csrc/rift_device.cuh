@@ -55,7 +55,8 @@ struct PointC {
   uint32_t canon_mask;
   int ncoef;          // float4 entries at coef_off (staged into shared memory by the kernels)
   int canon_full;     // all 21 canonical modes present: grouped quadratic form (quad_canon)
-  int pad4;
+  int canon_sparse;   // and U vanishes exactly between modes of opposite-sign m, V between modes of
+                      // same-sign m (each h_lm on one sign of frequency): those pairs are skipped
   float ccoef[RIFT_MAXM][RIFT_MAXTERM];
 };
 
@@ -411,28 +412,38 @@ __device__ __forceinline__ float2 eiphi_n(const float2 (&e)[9], int n) {
 }
 
 // One part (U: B = false, V: B = true) over the 231 pairs in group order.
-template <int K, bool B>
+// SP: skip the pairs whose coefficient the host found to be exactly zero (canon_sparse); adding
+// p * 0 would leave the sums unchanged, so both variants give the same bits.
+template <int K, bool B, bool SP>
 __device__ __forceinline__ void canon_part(const float4 *__restrict__ G, const float (&d)[RIFT_MAXM],
                                            const float2 (&e)[9], float (&acc)[K][2]) {
   float S[K][2];
 #pragma unroll
   for (int k = 0; k < K; ++k) { S[k][0] = 0.f; S[k][1] = 0.f; }
+  bool any = false;   // the group has a pair that is not skipped (folded at compile time)
 #pragma unroll
   for (int i = 0; i < kCanonPairs; ++i) {
     const int code = B ? kCanonPairDev.B[i] : kCanonPairDev.A[i];
     const int grp = code >> 10;
-    const float4 *c = G + (B ? kCanonSlots * K : 0) + (i >> 1) * K;
-    // d_a d_b; the V part forms it as an FMA with zero (the same value) so that the compiler does
-    // not keep the U part's 231 products alive for reuse
-    const float p = B ? __fmaf_rn(d[(code >> 5) & 31], d[code & 31], 0.f) : d[(code >> 5) & 31] * d[code & 31];
+    const int a = (code >> 5) & 31, b = code & 31;
+    const int mm = canon_m(a) * canon_m(b);
+    const bool skip = SP && (B ? mm > 0 : mm < 0);
+    if (!skip) {
+      any = true;
+      const float4 *c = G + (B ? kCanonSlots * K : 0) + (i >> 1) * K;
+      // d_a d_b; the V part forms it as an FMA with zero (the same value) so that the compiler does
+      // not keep the U part's products alive for reuse
+      const float p = B ? __fmaf_rn(d[a], d[b], 0.f) : d[a] * d[b];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float4 ck = c[k];
-      S[k][0] = fmaf(p, (i & 1) ? ck.z : ck.x, S[k][0]);
-      if (B || grp != 0) S[k][1] = fmaf(p, (i & 1) ? ck.w : ck.y, S[k][1]);   // D = 0: only Re S counts
+      for (int k = 0; k < K; ++k) {
+        const float4 ck = c[k];
+        S[k][0] = fmaf(p, (i & 1) ? ck.z : ck.x, S[k][0]);
+        if (B || grp != 0) S[k][1] = fmaf(p, (i & 1) ? ck.w : ck.y, S[k][1]);   // D = 0: only Re S counts
+      }
     }
     const bool last = (i + 1 == kCanonPairs) || ((B ? kCanonPairDev.B[i + 1] : kCanonPairDev.A[i + 1]) >> 10) != grp;
-    if (last) {
+    if (last && any) {
+      any = false;
       // the group ends: rotate its sum by e^{i n phi} into the part's total
       const float2 r = eiphi_n(e, B ? grp - 8 : grp);
 #pragma unroll
@@ -452,7 +463,7 @@ __device__ __forceinline__ void canon_part(const float4 *__restrict__ G, const f
 // phi = 2 pi n1 2^-24 with n1 odd (the sampler's lattice): e^{i D phi} = sincospi(D n1 2^-23),
 // reduced modulo 2 exactly in integers, so every rotation is good to an ulp (a product chain
 // from e^{i phi} would carry D times its rounding into whole group sums).
-template <int K>
+template <int K, bool SP>
 __device__ __forceinline__ float quad_canon_body(const PointC &P, const float4 *__restrict__ G, const SampleGeo &g,
                                                  float c, float s, uint32_t n1) {
   float2 e[9];
@@ -472,8 +483,8 @@ __device__ __forceinline__ float quad_canon_body(const PointC &P, const float4 *
   float A[K][2], Bc[K][2];
 #pragma unroll
   for (int k = 0; k < K; ++k) { A[k][0] = 0.f; A[k][1] = 0.f; Bc[k][0] = 0.f; Bc[k][1] = 0.f; }
-  canon_part<K, false>(G, d, e, A);
-  canon_part<K, true>(G, d, e, Bc);
+  canon_part<K, false, SP>(G, d, e, A);
+  canon_part<K, true, SP>(G, d, e, Bc);
   float quad = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -485,10 +496,10 @@ __device__ __forceinline__ float quad_canon_body(const PointC &P, const float4 *
   return quad;
 }
 
-template <int K>
+template <int K, bool SP>
 __device__ __noinline__ float quad_canon(const PointC &P, const float4 *__restrict__ G, const SampleGeo &g, float c,
                                          float s, uint32_t n1) {
-  return quad_canon_body<K>(P, G, g, c, s, n1);
+  return quad_canon_body<K, SP>(P, G, g, c, s, n1);
 }
 
 // Cell kernels compiled with the grouped form: three detectors and cubic taps (the full-size
