@@ -43,6 +43,27 @@ def flops_per_sample(K: int, M: int, taps: int) -> int:
     return quad + lin + 14 * M + 60 + 40 * K + 60
 
 
+def grouped_quad_flops(K: int, sparse: bool) -> int:
+    """Flops the cell kernel executes for the quadratic forms of a point with all 21 (l <= 4) modes
+    (grouped form): per pair one product d_a d_b and per detector two FMAs per part (one for the
+    |m_b - m_a| = 0 group of the U part), one rotation per group and part, the F combination;
+    with `sparse` the pairs that vanish for one-sign modes are skipped."""
+    ms = [m for l in (2, 3, 4) for m in range(-l, l + 1)]
+    pairs = [(a, b) for a in range(21) for b in range(a, 21)]
+    u = [(a, b) for a, b in pairs if not (sparse and ms[a] * ms[b] < 0)]
+    v = [(a, b) for a, b in pairs if not (sparse and ms[a] * ms[b] > 0)]
+    fl = sum(1 + K * (2 if ms[a] == ms[b] else 4) for a, b in u) + sum(1 + 4 * K for _ in v)
+    fl += len({abs(ms[b] - ms[a]) for a, b in u}) * 4 * K + len({ms[a] + ms[b] for a, b in v}) * 8 * K
+    return fl + 8 * K
+
+
+def executed_flops_per_sample(K: int, M: int, taps: int, sparse: bool) -> int:
+    """flops_per_sample with the pair-form quadratic forms replaced by the grouped form the
+    kernel runs for a full 21-mode point."""
+    npair = M * (M + 1) // 2
+    return flops_per_sample(K, M, taps) - (npair * (12 + 12 * K) + 10 * K) + grouped_quad_flops(K, sparse)
+
+
 def measured_peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -340,8 +361,12 @@ def run_gpu(args, world, rank, local):
         "lnL_marg": r0["lnL_marg"], "n_eff": r0["n_eff"], "strata": list(r0["strata"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(),
-                     "kernel": "cells_kernel<3,4,0,0> (stratified cell: draw + staged Q window + likelihood + log-sum-exp)",
+                     "kernel": "cells_kernel_cp<3,4,1> (stratified cell: draw + staged Q window + likelihood with the "
+                               "grouped quadratic form, coefficients in the parameter bank + log-sum-exp)",
                      "kernel_ms": kmean, "flops_per_sample": flops_per_sample(K, M, taps),
+                     "executed_flops_per_sample": executed_flops_per_sample(K, M, taps, True),
+                     "executed_frac": executed_flops_per_sample(K, M, taps, True) * N_SAMPLES / (kmean * 1e-3) / 1e12
+                     / peak,
                      "peak_basis": f"FP32 FMA: 128 lanes/SM x {sms} SMs x 2 flop x median SM clock {f_mhz} MHz "
                                    "sampled during the run"},
         "gpu_launches": launches,
