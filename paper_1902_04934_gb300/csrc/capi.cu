@@ -128,7 +128,7 @@ struct rift_ile {
   RoundPt *last = nullptr;    // [np]
   int *hidx = nullptr;        // harvest indices
   size_t cap_hidx = 0;
-  // single-point handle of a three-detector point with all 21 modes: its grouped coefficients,
+  // single-point handle of a three-detector point in the grouped layout: its grouped coefficients,
   // passed to the cell kernel as a parameter
   CanonCoefParam *canon0 = nullptr;
 };
@@ -272,11 +272,16 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
       }
   c.coef_off = c.uv_off;
   c.ncoef = c.npair * K;
-  // the grouped quadratic form is compiled for three detectors with cubic taps (kCanonPath)
-  c.canon_full = (c.canon_mask == (1u << RIFT_MAXM) - 1u && K == 3 && d->interp == 3) ? 1 : 0;
-  if (c.canon_full) {
-    // grouped layout of quad_canon: [U part | V part][slot][k], two pairs per float4 (modes are
-    // stored in canonical order, so canonical index = stored index)
+  // the grouped quadratic form (compiled for three detectors with cubic taps, kCanonPath) over the
+  // 21 canonical modes, absent modes with zero coefficients; it pays from kCanonMinModes on
+  c.grouped = (K == 3 && d->interp == 3 && M >= kCanonMinModes) ? 1 : 0;
+  if (c.grouped) {
+    // grouped layout of quad_canon: [U part | V part][slot][k], two pairs per float4; modes are
+    // stored in canonical order, so a present canonical mode j is stored at the number of present
+    // modes before it
+    int stored[RIFT_MAXM];
+    for (int j = 0; j < RIFT_MAXM; ++j)
+      stored[j] = (c.canon_mask >> j & 1u) ? __builtin_popcount(c.canon_mask & ((1u << j) - 1u)) : -1;
     c.coef_off = (long long)cv.size();
     c.ncoef = 2 * kCanonSlots * K;
     cv.resize(cv.size() + (size_t)c.ncoef, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -284,8 +289,10 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
     for (int part = 0; part < 2; ++part)
       for (int i = 0; i < kCanonPairs; ++i) {
         const int code = part ? canon_pair_B(i) : canon_pair_A(i);
-        const int a = (code >> 5) & 31, b = code & 31;
-        const bool conj = !part && canon_m(b) < canon_m(a);
+        const int ja = (code >> 5) & 31, jb = code & 31;
+        const int a = stored[ja], b = stored[jb];
+        if (a < 0 || b < 0) continue;   // an absent mode: zero coefficient
+        const bool conj = !part && canon_m(jb) < canon_m(ja);
         for (int k = 0; k < K; ++k) {
           const float4 pc = cv[c.uv_off + (size_t)pair_slot(a, b, M) * K + k];
           float *o = g + 4 * ((size_t)(part * kCanonSlots + i / 2) * K + k) + 2 * (i & 1);
@@ -298,7 +305,7 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
     c.canon_sparse = 1;
     for (int a = 0; a < M && c.canon_sparse; ++a)
       for (int b = a; b < M; ++b) {
-        const int mm = canon_m(a) * canon_m(b);
+        const int mm = c.mode[a].m * c.mode[b].m;
         if (mm == 0) continue;
         for (int k = 0; k < K; ++k) {
           const float4 pc = cv[c.uv_off + (size_t)pair_slot(a, b, M) * K + k];
@@ -385,7 +392,7 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
       return s2;
     }
   }
-  if (n == 1 && h->pts[0].c.canon_full) {
+  if (n == 1 && h->pts[0].c.grouped) {
     h->canon0 = new (std::nothrow) CanonCoefParam;
     if (!h->canon0) { rift_status s1 = fail(h, RIFT_ENOMEM, "host allocation"); rift_ile_destroy(h); return s1; }
     std::memcpy(h->canon0->g, cv.data() + h->pts[0].c.coef_off, sizeof(h->canon0->g));

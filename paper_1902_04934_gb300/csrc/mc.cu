@@ -73,7 +73,7 @@ __device__ __forceinline__ void copy_words(const void *src, void *dst, int nbyte
   for (int i = threadIdx.x; i < nbytes / 4; i += blockDim.x) d[i] = s[i];
 }
 
-// Quadratic term of a drawn sample: the grouped form for points with all 21 canonical modes
+// Quadratic term of a drawn sample: the grouped form for points in the grouped layout
 // (the kernels compiled with it), the pair form otherwise.  u_phi = n1 2^-24, n1 odd.
 template <int K, int NT, int CP>
 __device__ __forceinline__ float quad_cell(const PointC &P, const float4 *__restrict__ C,
@@ -82,7 +82,7 @@ __device__ __forceinline__ float quad_cell(const PointC &P, const float4 *__rest
   const uint32_t n1 = (uint32_t)(u_phi * 16777216.f);
   if constexpr (CP) return quad_canon_body<K, CP == 2>(P, cpg, g, ch, sh, n1);
   if constexpr (kCanonPath<K, NT>) {
-    if (P.canon_full)
+    if (P.grouped)
       return P.canon_sparse ? quad_canon<K, true>(P, C, g, ch, sh, n1) : quad_canon<K, false>(P, C, g, ch, sh, n1);
   }
   return quad_term<K>(P, C, g, Ys, ystride);
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, TMARG ? 1 : 2) cells_kernel(C
   cells_body<K, NT, LEARNED, TMARG, 0>(L, nullptr);
 }
 
-// One three-detector point with all 21 modes: its grouped coefficients come in the parameters
+// One three-detector point in the grouped layout: its grouped coefficients come in the parameters
 // (SP: the pairs that vanish for modes on one sign of frequency are skipped).
 template <int K, int NT, int SP>
 __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel_cp(CellLaunch L, const __grid_constant__ CanonCoefParam cc) {

@@ -54,7 +54,8 @@ struct PointC {
   // is set when mode j is present; its terms r = r_min(j).. have coefficients ccoef[j][r - r_min(j)]
   uint32_t canon_mask;
   int ncoef;          // float4 entries at coef_off (staged into shared memory by the kernels)
-  int canon_full;     // all 21 canonical modes present: grouped quadratic form (quad_canon)
+  int grouped;        // grouped quadratic form (quad_canon) over the 21 canonical modes, absent
+                      // modes with zero coefficients (kCanonPath kernels, at least kCanonMinModes)
   int canon_sparse;   // and U vanishes exactly between modes of opposite-sign m, V between modes of
                       // same-sign m (each h_lm on one sign of frequency): those pairs are skipped
   float ccoef[RIFT_MAXM][RIFT_MAXTERM];
@@ -362,7 +363,8 @@ __device__ __forceinline__ float quad_term(const PointC &P, const float4 *__rest
 }
 
 // ---------------------------------------------------------------------------
-// Quadratic term of a point with all 21 canonical modes.  With -2Y_lm(i, phi) = e^{i m phi} d_lm(i)
+// Quadratic term over the 21 canonical modes (absent ones with zero coefficients).  With
+// -2Y_lm(i, phi) = e^{i m phi} d_lm(i)
 // (d real), conj(Y_a) Y_b = d_a d_b e^{i (m_b - m_a) phi} and Y_a Y_b = d_a d_b e^{i (m_a + m_b) phi}, so
 //   A_k = sum_{D=0..8} Re(e^{i D phi} S_kD),   S_kD = sum_{a<=b, |m_b - m_a| = D} d_a d_b c_ab
 //   B_k = sum_{s=-8..8} e^{i s phi} T_ks,       T_ks = sum_{a<=b, m_a + m_b = s}  d_a d_b v_ab
@@ -503,10 +505,15 @@ __device__ __noinline__ float quad_canon(const PointC &P, const float4 *__restri
 }
 
 // Cell kernels compiled with the grouped form: three detectors and cubic taps (the full-size
-// workload); the host marks a point canon_full only for these, so that compile time stays short.
+// workload); the host marks a point grouped only for these, so that compile time stays short.
 // The other kernels read the pair layout (uv_off) and use quad_term for every point.
 template <int K, int NT>
 constexpr bool kCanonPath = (K == 3 && NT == 4);
+
+// The grouped form runs over all 21 canonical modes whatever the point holds (291 pair-parts with
+// the one-sign pairs skipped, about 3.9 kflop at K = 3); the pair form costs about 22 flop per
+// pair-part, M (M + 1) of them, so the grouped form pays from 13 modes on.
+constexpr int kCanonMinModes = 13;
 
 // The grouped coefficients of one three-detector point as a kernel parameter: single-point launches
 // pass them by value, so the quadratic form reads them from the parameter (constant) bank instead of

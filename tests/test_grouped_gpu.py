@@ -1,6 +1,7 @@
-"""GPU: the grouped quadratic form of points carrying all 21 (l <= 4) modes, in its three forms:
-coefficients from kernel parameters (single-point runs) or shared memory (batched runs), with
-or without the pairs that vanish when each mode lives on one sign of frequency."""
+"""GPU: the grouped quadratic form (over the 21 canonical l <= 4 modes, absent ones with zero
+coefficients; used from 13 modes on), in its forms: coefficients from kernel parameters
+(single-point runs) or shared memory (batched runs), with or without the pairs that vanish when
+each mode lives on one sign of frequency."""
 from __future__ import annotations
 
 import numpy as np
@@ -97,6 +98,34 @@ def test_dense_grouped_form_matches_oracle(lib, cuda, p_full, path):
     pr = mc.Prior(pt["t_lo"], pt["t_hi"])
     S = tuple(res["strata"] if path == "single" else res[0]["strata"])
     th, _, lq = mc.draw(93, 0, 0, idx, pr, None, S, n)
+    want = mc.lnL_samples(pt, th) + lq
+    th64 = dict(ra=th["ra"], dec=np.arcsin(th["sindec"]), t=th["t"], psi=th["psi"], phi=th["phi"],
+                incl=np.arccos(th["cosi"]), dist=th["dist"])
+    err = np.abs(got[idx.astype(np.int64)] - want)
+    assert np.all(err <= _tol(pt, th64)), err.max()
+
+
+@pytest.mark.parametrize("path", ["single", "batched"])
+def test_partial_mode_set_matches_oracle(lib, cuda, path):
+    """15 of the 21 modes in a shuffled caller order (the layout zero-fills the six absent ones)."""
+    r = np.random.default_rng(8)
+    modes = [(l, m) for l in (2, 3, 4) for m in range(-l, l + 1)]
+    keep = [modes[i] for i in r.permutation(21)[:15]]
+    if (2, 2) not in keep:
+        keep[0] = (2, 2)
+    if (2, -2) not in keep:
+        keep[1] = (2, -2)
+    spec = W.cfg_full()
+    spec.modes = keep
+    pt = W.make_point(spec, 11)
+    assert len(np.asarray(pt["lm"])) == 15
+    n = 400_000
+    got, res = (_single if path == "single" else _batched)(lib, pt, n, 94)
+    got = got.astype(np.float64)
+    idx = np.unique(np.concatenate([np.argsort(got)[-200:], r.integers(0, n, 2000)])).astype(np.uint64)
+    pr = mc.Prior(pt["t_lo"], pt["t_hi"])
+    S = tuple(res["strata"] if path == "single" else res[0]["strata"])
+    th, _, lq = mc.draw(94, 0, 0, idx, pr, None, S, n)
     want = mc.lnL_samples(pt, th) + lq
     th64 = dict(ra=th["ra"], dec=np.arcsin(th["sindec"]), t=th["t"], psi=th["psi"], phi=th["phi"],
                 incl=np.arccos(th["cosi"]), dist=th["dist"])
