@@ -180,3 +180,67 @@ def test_posterior_rejects_bad_arguments(lib, cuda, p_small):
     with pytest.raises(lib.RiftError):
         lib.rift_ile_posterior(h, 0, seed=1, n_per_round=1000, max_evals=1000)
     lib.rift_ile_destroy(h)
+
+
+def _lnl_array(lib, h, rows, tmarg=False):
+    """lnL of exported parameter rows by the array kernels (an independent device path)."""
+    import torch
+    d = {k: torch.as_tensor(np.ascontiguousarray(rows[:, c]), device="cuda")
+         for c, k in enumerate(("ra", "dec", "t", "psi", "phi", "incl", "dist"))}
+    if tmarg:
+        out = lib.rift_ile_lnL_tmarg(h, d["ra"], d["dec"], d["psi"], d["phi"], d["incl"], d["dist"])
+    else:
+        out = lib.rift_ile_lnL(h, d["ra"], d["dec"], d["t"], d["psi"], d["phi"], d["incl"], d["dist"])
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("tmarg", [0, 1])
+def test_learned_proposal_rows_agree_with_the_array_kernels(lib, cuda, p_small, tmarg):
+    """Rows re-drawn from the learned proposal: their lnL column is what the array kernels give at
+    the exported parameters (the exported angles are the sampler's, rounded to float32)."""
+    import test_mdn_gpu as M
+    h = lib.rift_ile_create(p_small)
+    lib.rift_ile_set_proposal_head(h, M._head(11, p_small)[None])
+    n = 20000
+    rows, counts, _ = lib.rift_ile_samples(h, n, seed=66, n_per_round=n, max_evals=n, proposal="learned",
+                                          time_marg=tmarg)
+    g = rows[0].cpu().numpy()
+    assert counts == [n] and np.all(np.isfinite(g[:, [0, 1, 3, 4, 5, 6, 7, 8]]))
+    assert np.all(np.isnan(g[:, 2])) == bool(tmarg)
+    want = _lnl_array(lib, h, g.astype(np.float32), bool(tmarg))
+    cols = {k: g[:, c].astype(np.float64) for c, k in enumerate(("ra", "dec", "t", "psi", "phi", "incl", "dist"))}
+    if tmarg:
+        cols["t"] = np.zeros(n)
+    # float32 parameters move lnL by up to ~|d lnL / d theta| * ulp: a wider bar than the parity one
+    assert np.all(np.abs(g[:, 7] - want) <= 10 * _tol(p_small, cols)), np.max(np.abs(g[:, 7] - want))
+    lib.rift_ile_destroy(h)
+
+
+def test_batch_export_counts_follow_each_points_last_round(lib, cuda):
+    """Points stopping at different rounds: each exports the draws of its own last round."""
+    pts = [W.make_point(W.cfg_small(), 80 + i) for i in range(3)]
+    n = 8192
+    kw = dict(seed=67, n_per_round=n, max_evals=n * 6 - 100, n_eff_target=1.6, proposal="adaptive", n_bins=32,
+              strata=(2, 2, 2))
+    hb = lib.rift_ile_batch_create(pts)
+    rows, counts, res = lib.rift_ile_samples(hb, n, **kw)
+    for p in range(3):
+        want = n if res[p]["n_evals"] % n == 0 else res[p]["n_evals"] % n
+        assert counts[p] == want, (p, counts[p], res[p])
+        g = rows[p].cpu().numpy()
+        assert np.all(np.isfinite(g[:counts[p], 7])) and np.all(np.isnan(g[counts[p]:]))
+    lib.rift_ile_destroy(hb)
+
+
+def test_posterior_slot_counts_and_rejections(lib, cuda, p_small):
+    h = lib.rift_ile_create(p_small)
+    kw = dict(seed=68, n_per_round=1000, max_evals=1000)
+    rows, idx, _ = lib.rift_ile_posterior(h, 1, **kw)
+    assert 0 <= int(idx[0, 0]) < 1000
+    rows, idx, _ = lib.rift_ile_posterior(h, 5000, **kw)       # more slots than draws
+    gi = idx[0].cpu().numpy()
+    assert np.all((gi >= 0) & (gi < 1000)) and np.all(np.diff(gi) >= 0)
+    with pytest.raises(lib.RiftError):
+        lib.rift_ile_marginalize(h, want_tables=True, **kw)   # tables_out needs the adaptive proposal
+    lib.rift_ile_destroy(h)
