@@ -337,6 +337,15 @@ rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *opts, int H,
  * weight minus ln p - ln q, both as the sampler computed them in FP32.
  * Errors: RIFT_EINVAL for NULL or inconsistent arguments, the statuses of the marginalisation.
  */
+/*
+ * Device and pinned host buffers of handles are kept in a process-wide cache when a handle is
+ * destroyed and reused by later handles of the same sizes (a handle per intrinsic point then costs
+ * no device allocation).  rift_release_cached_memory gives every cached buffer back to CUDA (the
+ * cache also does so by itself when an allocation fails for lack of memory).  Buffers in use by live
+ * handles are not affected.
+ */
+void rift_release_cached_memory(void);
+
 #define RIFT_SAMPLE_COLS 9
 #define RIFT_POSTERIOR_COLS 8
 

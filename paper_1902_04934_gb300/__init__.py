@@ -120,6 +120,7 @@ def _load():
         "rift_ile_boxes": (I, [P, D, D, P]),
         "rift_ile_batch_harvest": (I, [P, C.POINTER(McOpts), I, D, P, C.POINTER(McResult)]),
         "rift_ile_samples": (I, [P, C.POINTER(McOpts), S, P, C.POINTER(U64), C.POINTER(McResult)]),
+        "rift_release_cached_memory": (None, []),
         "rift_ile_posterior": (I, [P, C.POINTER(McOpts), I, P, P, C.POINTER(McResult)]),
         "rift_ile_get_tune": (I, [P, C.POINTER(Tune)]),
         "rift_ile_set_tune": (I, [P, C.POINTER(Tune)]),
@@ -166,10 +167,10 @@ def _desc(pt, interp=3, stream=None, keep=None):
     Q = np.asarray(pt["Q"])
     M, T = Q.shape[1], Q.shape[2]
     arrs = dict(det_tensor=_f64(pt["det_tensor"]), det_pos=_f64(pt["det_pos"]), lm=lm,
-                Q=np.ascontiguousarray(Q.astype(np.complex128)).view(np.float64),
+                Q=np.ascontiguousarray(Q, dtype=np.complex128).view(np.float64),
                 q_t0_gps=_f64(pt["q_t0_gps"]),
-                U=np.ascontiguousarray(np.asarray(pt["U"]).astype(np.complex128)).view(np.float64),
-                V=np.ascontiguousarray(np.asarray(pt["V"]).astype(np.complex128)).view(np.float64))
+                U=np.ascontiguousarray(pt["U"], dtype=np.complex128).view(np.float64),
+                V=np.ascontiguousarray(pt["V"], dtype=np.complex128).view(np.float64))
     if keep is not None:
         keep.append(arrs)
     d = Desc()
@@ -554,6 +555,11 @@ def rift_ile_posterior(h, H, **kw):
     if st not in (0, 7):
         _check(h, st)
     return rows, idx, [r.as_dict() for r in res]
+
+
+def rift_release_cached_memory():
+    """Give the device and pinned buffers cached from destroyed handles back to CUDA."""
+    _lib.rift_release_cached_memory()
 
 
 def rift_ile_get_tune(h):

@@ -319,10 +319,10 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
 template <typename T>
 rift_status grow(rift_ile *h, T *&p, size_t &cap, size_t need) {
   if (need <= cap) return RIFT_OK;
-  if (p) cudaFree(p);
+  if (p) cache_dev_free(p);
   p = nullptr;
   cap = 0;
-  cudaError_t e = cudaMalloc(&p, sizeof(T) * need);
+  cudaError_t e = cache_dev_alloc((void **)&p, sizeof(T) * need);
   if (e != cudaSuccess) return fail(h, e == cudaErrorMemoryAllocation ? RIFT_ENOMEM : RIFT_ECUDA,
                                     std::string("scratch allocation: ") + cudaGetErrorString(e));
   cap = need;
@@ -335,16 +335,16 @@ rift_status ensure_scratch(rift_ile *h, int np, size_t max_items, size_t ebuf, i
   McScratch &S = h->sc;
   rift_status s;
   if (np > h->cap_np) {
-    cudaFree(S.acc); cudaFree(S.rp); cudaFree(S.counters);
-    cudaFreeHost(S.rp_host); cudaFreeHost(S.acc_host);
+    cache_dev_free(S.acc); cache_dev_free(S.rp); cache_dev_free(S.counters);
+    cache_host_free(S.rp_host); cache_host_free(S.acc_host);
     S.acc = nullptr; S.rp = nullptr; S.counters = nullptr; S.rp_host = nullptr; S.acc_host = nullptr;
     h->cap_np = 0;
     cudaError_t e;
-    if ((e = cudaMalloc(&S.acc, sizeof(AccState) * np)) != cudaSuccess ||
-        (e = cudaMalloc(&S.rp, sizeof(RoundPt) * np)) != cudaSuccess ||
-        (e = cudaMalloc(&S.counters, sizeof(uint32_t) * 2)) != cudaSuccess ||
-        (e = cudaMallocHost(&S.rp_host, sizeof(RoundPt) * np)) != cudaSuccess ||
-        (e = cudaMallocHost(&S.acc_host, sizeof(AccState) * np)) != cudaSuccess)
+    if ((e = cache_dev_alloc((void **)&S.acc, sizeof(AccState) * np)) != cudaSuccess ||
+        (e = cache_dev_alloc((void **)&S.rp, sizeof(RoundPt) * np)) != cudaSuccess ||
+        (e = cache_dev_alloc((void **)&S.counters, sizeof(uint32_t) * 2)) != cudaSuccess ||
+        (e = cache_host_alloc((void **)&S.rp_host, sizeof(RoundPt) * np)) != cudaSuccess ||
+        (e = cache_host_alloc((void **)&S.acc_host, sizeof(AccState) * np)) != cudaSuccess)
       return fail(h, RIFT_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
     h->cap_np = np;
   }
@@ -413,10 +413,10 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
   std::vector<PointC> pc(n);
   for (int i = 0; i < n; ++i) pc[i] = h->pts[i].c;
   rift_status s = RIFT_OK;
-  if ((e = cudaMalloc(&h->pts_dev, sizeof(PointC) * n)) != cudaSuccess ||
-      (e = cudaMalloc(&h->q_arena, sizeof(float2) * std::max<size_t>(qv.size(), 2))) != cudaSuccess ||
-      (e = cudaMalloc(&h->c_arena, sizeof(float4) * std::max<size_t>(cv.size(), 1))) != cudaSuccess ||
-      (e = cudaMalloc(&h->flags, sizeof(uint32_t))) != cudaSuccess ||
+  if ((e = cache_dev_alloc((void **)&h->pts_dev, sizeof(PointC) * n)) != cudaSuccess ||
+      (e = cache_dev_alloc((void **)&h->q_arena, sizeof(float2) * std::max<size_t>(qv.size(), 2))) != cudaSuccess ||
+      (e = cache_dev_alloc((void **)&h->c_arena, sizeof(float4) * std::max<size_t>(cv.size(), 1))) != cudaSuccess ||
+      (e = cache_dev_alloc((void **)&h->flags, sizeof(uint32_t))) != cudaSuccess ||
       (e = fault_is("h2d") ? cudaErrorInvalidValue : cudaSuccess) != cudaSuccess ||
       (e = cudaMemcpyAsync(h->pts_dev, pc.data(), sizeof(PointC) * n, cudaMemcpyHostToDevice, h->stream)) !=
           cudaSuccess ||
@@ -435,7 +435,7 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
     std::vector<double> t0((size_t)n * RIFT_MAX_DET, 0.0);
     for (int i = 0; i < n; ++i)
       for (int k = 0; k < descs[i].n_det; ++k) t0[(size_t)i * RIFT_MAX_DET + k] = descs[i].q_t0_gps[k] - descs[i].t_ref_gps;
-    if ((e = cudaMalloc(&h->tau0, sizeof(double) * t0.size())) != cudaSuccess ||
+    if ((e = cache_dev_alloc((void **)&h->tau0, sizeof(double) * t0.size())) != cudaSuccess ||
         (e = cudaMemcpy(h->tau0, t0.data(), sizeof(double) * t0.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
       fprintf(stderr, "rift_ile_create: %s\n", cudaGetErrorString(e));
       rift_ile_destroy(h);
@@ -542,10 +542,10 @@ int log2_pow2(int v) {
 rift_status ensure_learned(rift_ile *h) {
   const int np = h->n_points;
   if (!h->gmm) {
-    RIFT_CK(h, cudaMalloc(&h->gmm, sizeof(float) * (size_t)np * RIFT_GMM_FLOATS));
-    RIFT_CK(h, cudaMalloc(&h->gcst, sizeof(float) * (size_t)np * 4));
-    RIFT_CK(h, cudaMalloc(&h->head, sizeof(float) * (size_t)np * RIFT_MDN_HEAD));
-    RIFT_CK(h, cudaMalloc(&h->summ, sizeof(float) * (size_t)np * RIFT_MDN_SUMMARY));
+    RIFT_CK(h, cache_dev_alloc((void **)&h->gmm, sizeof(float) * (size_t)np * RIFT_GMM_FLOATS));
+    RIFT_CK(h, cache_dev_alloc((void **)&h->gcst, sizeof(float) * (size_t)np * 4));
+    RIFT_CK(h, cache_dev_alloc((void **)&h->head, sizeof(float) * (size_t)np * RIFT_MDN_HEAD));
+    RIFT_CK(h, cache_dev_alloc((void **)&h->summ, sizeof(float) * (size_t)np * RIFT_MDN_SUMMARY));
   }
   return RIFT_OK;
 }
@@ -897,35 +897,37 @@ rift_status rift_ile_batch_create(const rift_ile_desc *descs, int n_points, rift
 
 void rift_ile_destroy(rift_ile *h) {
   if (!h) return;
+  // the buffers go back to the cache for other handles: nothing of this handle may still run
   cudaStreamSynchronize(h->stream);
-  cudaFree(h->pts_dev);
-  cudaFree(h->q_arena);
-  cudaFree(h->c_arena);
-  cudaFree(h->flags);
+  if (h->gstream) cudaStreamSynchronize(h->gstream);
+  cache_dev_free(h->pts_dev);
+  cache_dev_free(h->q_arena);
+  cache_dev_free(h->c_arena);
+  cache_dev_free(h->flags);
   McScratch &S = h->sc;
-  cudaFree(S.acc);
-  cudaFree(S.partials);
-  cudaFree(S.rp);
-  cudaFree(S.counters);
-  cudaFree(S.ell);
-  cudaFree(S.bins);
-  cudaFree(S.hist);
-  cudaFree(S.tables);
-  cudaFree(S.lnw);
-  cudaFreeHost(S.rp_host);
-  cudaFreeHost(S.acc_host);
-  cudaFree(h->stage);
-  cudaFree(h->tau0);
-  cudaFree(h->head);
-  cudaFree(h->summ);
-  cudaFree(h->gmm);
-  cudaFree(h->gcst);
-  cudaFree(h->last);
-  cudaFree(h->hidx);
-  cudaFree(h->pst);
-  cudaFree(h->ctl);
-  cudaFreeHost(h->ctl_host);
-  cudaFreeHost(h->pst_host);
+  cache_dev_free(S.acc);
+  cache_dev_free(S.partials);
+  cache_dev_free(S.rp);
+  cache_dev_free(S.counters);
+  cache_dev_free(S.ell);
+  cache_dev_free(S.bins);
+  cache_dev_free(S.hist);
+  cache_dev_free(S.tables);
+  cache_dev_free(S.lnw);
+  cache_host_free(S.rp_host);
+  cache_host_free(S.acc_host);
+  cache_dev_free(h->stage);
+  cache_dev_free(h->tau0);
+  cache_dev_free(h->head);
+  cache_dev_free(h->summ);
+  cache_dev_free(h->gmm);
+  cache_dev_free(h->gcst);
+  cache_dev_free(h->last);
+  cache_dev_free(h->hidx);
+  cache_dev_free(h->pst);
+  cache_dev_free(h->ctl);
+  cache_host_free(h->ctl_host);
+  cache_host_free(h->pst_host);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   delete h->canon0;
   delete h;
@@ -965,10 +967,10 @@ rift_status rift_ile_lnL_host(rift_ile *h, size_t n, const float *ra, const floa
   if (n == 0) return RIFT_OK;
   if (!ra || !dec || !t || !psi || !phi || !incl || !dist || !lnL_out) return fail(h, RIFT_EINVAL, "null sample array");
   if (n > h->stage_n) {
-    cudaFree(h->stage);
+    cache_dev_free(h->stage);
     h->stage = nullptr;
     h->stage_n = 0;
-    RIFT_CK(h, cudaMalloc(&h->stage, sizeof(float) * 8 * n));
+    RIFT_CK(h, cache_dev_alloc((void **)&h->stage, sizeof(float) * 8 * n));
     h->stage_n = n;
   }
   float *s = h->stage;
@@ -1091,18 +1093,18 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   }
   const bool keep = adaptive || keep_ell;
   if ((s = ensure_scratch(h, np, items, keep ? (size_t)np * o->n_per_round : 0, nb, hb)) != RIFT_OK) return s;
-  if (keep_ell && !h->last) RIFT_CK(h, cudaMalloc(&h->last, sizeof(RoundPt) * np));
+  if (keep_ell && !h->last) RIFT_CK(h, cache_dev_alloc((void **)&h->last, sizeof(RoundPt) * np));
   McScratch &S = h->sc;
   if (np > h->cap_pst) {
-    cudaFree(h->pst); cudaFreeHost(h->pst_host);
+    cache_dev_free(h->pst); cache_host_free(h->pst_host);
     h->pst = nullptr; h->pst_host = nullptr; h->cap_pst = 0;
-    RIFT_CK(h, cudaMalloc(&h->pst, sizeof(PtState) * np));
-    RIFT_CK(h, cudaMallocHost(&h->pst_host, sizeof(PtState) * np));
+    RIFT_CK(h, cache_dev_alloc((void **)&h->pst, sizeof(PtState) * np));
+    RIFT_CK(h, cache_host_alloc((void **)&h->pst_host, sizeof(PtState) * np));
     h->cap_pst = np;
   }
   if (!h->ctl) {
-    RIFT_CK(h, cudaMalloc(&h->ctl, sizeof(RoundCtl)));
-    RIFT_CK(h, cudaMallocHost(&h->ctl_host, sizeof(RoundCtl)));
+    RIFT_CK(h, cache_dev_alloc((void **)&h->ctl, sizeof(RoundCtl)));
+    RIFT_CK(h, cache_host_alloc((void **)&h->ctl_host, sizeof(RoundCtl)));
   }
   if (!h->gstream) RIFT_CK(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
   cudaStream_t st = h->gstream;
@@ -1315,10 +1317,10 @@ rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *o, int H, do
   McScratch &S = h->sc;
   const size_t need = (size_t)np * H;
   if (need > h->cap_hidx) {
-    cudaFree(h->hidx);
+    cache_dev_free(h->hidx);
     h->hidx = nullptr;
     h->cap_hidx = 0;
-    RIFT_CK(h, cudaMalloc(&h->hidx, sizeof(int) * need));
+    RIFT_CK(h, cache_dev_alloc((void **)&h->hidx, sizeof(int) * need));
     h->cap_hidx = need;
   }
   cudaStream_t st = h->gstream;
@@ -1355,10 +1357,10 @@ rift_status rift_ile_posterior(rift_ile *h, const rift_mc_opts *o, int H, float 
   if (!idx) {
     const size_t need = (size_t)np * H;
     if (need > h->cap_hidx) {
-      cudaFree(h->hidx);
+      cache_dev_free(h->hidx);
       h->hidx = nullptr;
       h->cap_hidx = 0;
-      RIFT_CK(h, cudaMalloc(&h->hidx, sizeof(int) * need));
+      RIFT_CK(h, cache_dev_alloc((void **)&h->hidx, sizeof(int) * need));
       h->cap_hidx = need;
     }
     idx = h->hidx;

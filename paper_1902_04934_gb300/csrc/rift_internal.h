@@ -180,6 +180,13 @@ struct rift_mdn;
 cudaError_t launch_mdn_gmm(const rift_mdn *m, const float *summ, const float *cst, int np, float *head_scratch,
                            float *gmm, cudaStream_t st);
 cudaError_t launch_gmm_from_head(const float *head, const float *cst, int np, float *gmm, cudaStream_t st);
+// device and pinned host buffers of handles, recycled through a process-wide cache (cache.cu);
+// a buffer is given back only when no work in flight uses it
+cudaError_t cache_dev_alloc(void **p, size_t n);
+cudaError_t cache_host_alloc(void **p, size_t n);
+void cache_dev_free(void *p);
+void cache_host_free(void *p);
+
 // posterior samples (posterior.cu, kernels.cu)
 cudaError_t launch_rows(const CellLaunch &L, const RoundPt *last, const float *ell, const int *idx, size_t n_slots,
                         int ncol, int np, float *out, cudaStream_t st);

@@ -375,3 +375,26 @@ def test_marginalize_full_size_sampled(lib, cuda, p_full):
     a = mc.Accum.of(got[idx.astype(np.int64)][sel]).result()[0]
     b = mc.Accum.of(want[sel]).result()[0]
     assert abs(a - b) < TOL_MARG * 3, (a, b)
+
+
+def test_recycled_buffers_do_not_change_results(lib, cuda, p_small, p_full):
+    """Handles destroyed return their buffers to a process-wide cache that later handles reuse:
+    the results are the same bits with fresh, recycled and released buffers, whatever ran between."""
+    import torch
+    kw = dict(seed=51, n_per_round=200_000, max_evals=400_000, proposal="adaptive", n_bins=32)
+
+    def run(pt):
+        h = lib.rift_ile_create(pt)
+        dbg = torch.full((400_000,), float("nan"), dtype=torch.float32, device="cuda")
+        r = lib.rift_ile_marginalize(h, dbg_ell=dbg, **kw)
+        lib.rift_ile_destroy(h)
+        return r["lnL_marg"], r["n_eff"], dbg.cpu().numpy()
+
+    a = run(p_small)
+    run(p_full)                          # other sizes in between
+    b = run(p_small)                     # recycled buffers
+    lib.rift_release_cached_memory()
+    c = run(p_small)                     # fresh buffers again
+    for x in (b, c):
+        assert x[0] == a[0] and x[1] == a[1]
+        assert np.array_equal(x[2], a[2])
