@@ -198,3 +198,20 @@ def test_tmarg_resume_and_static_scratch(lib, cuda):
     st = lib.rift_ile_marginalize_static(h, **kw)
     assert st["lnL_marg"] == full["lnL_marg"] and st["n_evals"] == full["n_evals"]
     lib.rift_ile_destroy(h)
+
+
+def test_adaptive_time_marginalised_run_reaches_neff_target_on_a_physical_injection(lib, cuda):
+    """A physical injection (H1, L1, V1; l = 2; SNR 10): the time-marginalised estimator with the
+    adaptive (ra, sin dec) proposal reaches n_eff >= 1000, and independent runs agree to 0.05."""
+    from test_oracle_warm import phys_point
+    pt = phys_point(41, snr=10.0)
+    h = lib.rift_ile_create(pt)
+    kw = dict(n_per_round=1_000_000, max_evals=200_000_000, n_eff_target=1000, proposal="adaptive", n_bins=64,
+              beta=0.3, time_marg=1)
+    a = lib.rift_ile_marginalize(h, seed=5, **kw)
+    b = lib.rift_ile_marginalize(h, seed=6, **kw)
+    lib.rift_ile_destroy(h)
+    for r in (a, b):
+        assert r["n_eff"] >= 1000 and r["n_evals"] < 200_000_000, r
+    assert abs(a["lnL_marg"] - b["lnL_marg"]) < 0.05, (a["lnL_marg"], b["lnL_marg"])
+    assert abs(a["lnL_marg"] - b["lnL_marg"]) < 4 * np.hypot(a["sigma"], b["sigma"])
