@@ -392,7 +392,7 @@ rift_status rift_ile_posterior(rift_ile *h, const rift_mc_opts *opts, int H, flo
  */
 #define RIFT_STATIC_MAX_ROUND 131072
 #define RIFT_STATIC_MAX_PRIOR_ROUND 67108864
-#define RIFT_STATIC_SCRATCH_BYTES 4601088
+#define RIFT_STATIC_SCRATCH_BYTES 3552512
 rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
 
 /*

@@ -10,7 +10,7 @@ struct PointC;
 #define RIFT_MC_BLOCK 256
 // Threads per block of the cell kernel, and samples per work item at most.
 #define RIFT_CELL_BLOCK 256
-#define RIFT_CHUNK 1024
+#define RIFT_CHUNK 2048
 
 // Block partial of the log-sum-exp: max, sum e^{l-max}, sum e^{2(l-max)}, count.
 struct __align__(32) Part {
