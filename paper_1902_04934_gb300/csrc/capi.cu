@@ -691,7 +691,11 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   const int block = RIFT_CELL_BLOCK;
   int smem_sm = 0;
   RIFT_CK(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
-  const size_t fixed = cells_smem_fixed(K, h->max_M, h->max_pairK, nb, block);
+  // a single point in the grouped layout passes its coefficients as a kernel parameter (when the
+  // kernel has that variant): no shared-memory copy of them, so the Q windows get the room
+  const CanonCoefParam *cc = (np == 1 && h->canon0 && NT == 4 && !learned && !o->time_marg) ? h->canon0 : nullptr;
+  const int coef_f4 = cc ? 0 : h->max_pairK;
+  const size_t fixed = cells_smem_fixed(K, h->max_M, coef_f4, nb, block);
   long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
   budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
   const size_t smem = fixed + (size_t)budget;
@@ -715,7 +719,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.bin_buf = adaptive ? S.bins : nullptr;
   L.flags = h->flags;
   L.max_M = h->max_M;
-  L.max_pairK = h->max_pairK;
+  L.max_pairK = coef_f4;
   L.max_nb = nb;
   L.learned = learned ? 1 : 0;
   L.fault_nan = fault_is("nan_sample") ? 1 : 0;
@@ -787,8 +791,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     RIFT_CK(h, cudaMemcpyAsync(S.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
     const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(items, (uint32_t)(h->num_sms * bps)));
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev0, st));
-    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st, np == 1 ? h->canon0 : nullptr,
-                            h->pts[0].c.canon_sparse));
+    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st, cc, h->pts[0].c.canon_sparse));
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev1, st));
     RIFT_CK(h, launch_merge_points(S.partials, S.rp, np, S.acc, st));
     launches += 2;
@@ -1415,14 +1418,14 @@ rift_status rift_ile_autotune(rift_ile *h, const rift_mc_opts *o, int reps, rift
   t.save = nullptr;
   t.tables_out = nullptr;
   const int old_target = h->cell_target, old_ctas = h->smem_split;
-  const int targets[3] = {320, 640, 1280}, splits[4] = {2, 3, 4, 6};
+  const int targets[5] = {320, 640, 960, 1280, 2048}, splits[4] = {2, 3, 4, 6};
   std::vector<rift_mc_result> res((size_t)h->n_points);
   double best_ms = 1e300;
   rift_tune b{old_target, old_ctas, 0.0};
   cudaEvent_t e0, e1;
   RIFT_CK(h, cudaEventCreate(&e0));
   RIFT_CK(h, cudaEventCreate(&e1));
-  for (int ti = 0; ti < 3; ++ti)
+  for (int ti = 0; ti < 5; ++ti)
     for (int si = 0; si < 4; ++si) {
       const int c = splits[si];
       h->cell_target = targets[ti];
