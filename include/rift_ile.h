@@ -337,15 +337,6 @@ rift_status rift_ile_batch_harvest(rift_ile *h, const rift_mc_opts *opts, int H,
  * weight minus ln p - ln q, both as the sampler computed them in FP32.
  * Errors: RIFT_EINVAL for NULL or inconsistent arguments, the statuses of the marginalisation.
  */
-/*
- * Device and pinned host buffers of handles are kept in a process-wide cache when a handle is
- * destroyed and reused by later handles of the same sizes (a handle per intrinsic point then costs
- * no device allocation).  rift_release_cached_memory gives every cached buffer back to CUDA (the
- * cache also does so by itself when an allocation fails for lack of memory).  Buffers in use by live
- * handles are not affected.
- */
-void rift_release_cached_memory(void);
-
 #define RIFT_SAMPLE_COLS 9
 #define RIFT_POSTERIOR_COLS 8
 
@@ -364,11 +355,21 @@ rift_status rift_ile_samples(rift_ile *h, const rift_mc_opts *opts, size_t cap, 
  * without draws (its rows are NaN).  With time_marg, each resampled draw then gets its event time
  * from the conditional on the quadrature grid of Eq. (lnL:tmarg), P(t_j | rest) proportional to
  * L(t_j), t_j = t_lo + (j + 1/2)/fs: the first j whose cumulative probability exceeds u, u the
- * uniform of Philox block 3 of counter (h, 0, point id) (the sampler uses blocks 0-2); column 7 is
+ * uniform of Philox block 3 of counter (h, 0, point word: opts.point_id for a single-point handle,
+ * the point index in a batch) (the sampler uses blocks 0-2); column 7 is
  * then lnL(t_j).  A non-finite likelihood there gives RIFT_ENONFINITE, taps outside the Q window
  * RIFT_EWINDOW. */
 rift_status rift_ile_posterior(rift_ile *h, const rift_mc_opts *opts, int H, float *out_dev, int *idx_dev,
                                rift_mc_result *res);
+
+/*
+ * Device and pinned host buffers of handles are kept in a process-wide cache when a handle is
+ * destroyed and reused by later handles of the same sizes (a handle per intrinsic point then costs
+ * no device allocation).  rift_release_cached_memory gives every cached buffer back to CUDA (the
+ * cache also does so by itself when an allocation fails for lack of memory).  Buffers in use by live
+ * handles are not affected.
+ */
+void rift_release_cached_memory(void);
 
 /*
  * rift_ile_marginalize_static -- the same computation as rift_ile_marginalize (point 0,
