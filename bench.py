@@ -244,6 +244,39 @@ def cpu_oracle_throughput(target_s: float = 12.0):
     return v, op.cores, f"{n} prior samples of the full-size point (indices 0..{n - 1}, seed 31)", wall
 
 
+def precision_check(rift, pt, opts, tune):
+    """Per-sample lnL of the benchmark's own launch (same point, seed and launch shape) against the
+    FP64 oracle on the host: 2000 random draws and the 300 of highest weight, with the tolerance of
+    the parity tests, 1e-3 max(1, <h|h>/900); and lnL_marg restricted to the top 300 on both sides."""
+    import numpy as np
+    import torch
+    from oracle import likelihood as OL
+    from oracle import mc
+    h = rift.rift_ile_create(pt)
+    rift.rift_ile_set_tune(h, cell_samples=tune["cell_samples"], smem_split=tune["smem_split"])
+    n = opts["n_per_round"]
+    dbg = torch.empty(n, dtype=torch.float32, device="cuda")
+    res = rift.rift_ile_marginalize(h, dbg_ell=dbg, **opts)
+    rift.rift_ile_destroy(h)
+    got = dbg.cpu().numpy().astype(np.float64)
+    del dbg
+    top = np.argsort(got)[-300:]
+    r = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([top, r.integers(0, n, 2000)])).astype(np.uint64)
+    th, _, lq = mc.draw(opts["seed"], 0, 0, idx, mc.Prior(pt["t_lo"], pt["t_hi"]), None, tuple(res["strata"]), n)
+    want = mc.lnL_samples(pt, th) + lq
+    th64 = dict(ra=th["ra"], dec=np.arcsin(th["sindec"]), t=th["t"], psi=th["psi"], phi=th["phi"],
+                incl=np.arccos(th["cosi"]), dist=th["dist"])
+    hh = -2.0 * OL.lnL_factorised(dict(pt, Q=np.zeros_like(pt["Q"])), **th64)
+    tol = 1e-3 * np.maximum(1.0, hh / 900.0)
+    err = np.abs(got[idx.astype(np.int64)] - want)
+    sel = np.isin(idx.astype(np.int64), top)
+    a, b = mc.Accum.of(got[idx.astype(np.int64)][sel]).result()[0], mc.Accum.of(want[sel]).result()[0]
+    return {"samples": int(idx.size), "max_abs_dlnL": float(err.max()), "max_err_over_tol": float((err / tol).max()),
+            "mean_err_over_tol": float((err / tol).mean()), "dlnL_marg_top300": float(abs(a - b)),
+            "tolerance": "1e-3 max(1, <h|h>/900) per sample (FP64 oracle, same draws)"}
+
+
 # ---------------------------------------------------------------- GPU leg
 def run_gpu(args, world, rank, local):
     import numpy as np
@@ -332,10 +365,12 @@ def run_gpu(args, world, rank, local):
                "includes": "rift_ile_create from host FP64 arrays + rift_ile_marginalize + result read + destroy"}
 
     cpu = None
+    precision = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample, wall = cpu_oracle_throughput(args.cpu_seconds)
         cpu = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
                "wall_s": round(wall, 2)}
+        precision = precision_check(rift, pt, opts, tune)
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
@@ -374,6 +409,7 @@ def run_gpu(args, world, rank, local):
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "precision": precision,
         "wall_s": t_wall,
     }
     out.update(extras)
