@@ -155,46 +155,54 @@ __device__ __forceinline__ float linear_term_staged(const PointC &P, const float
                                                     const float4 *const win[K], const int wlo[K],
                                                     const int whi[K], uint32_t &flags) {
   constexpr int first = (NT == 4) ? -1 : 0;
-  float lin = 0.f;
   const int rs = P.Mp >> 1;
   const int npairs = (P.M + 1) >> 1;
+  // per detector: interpolation weights and the first tap row (staged window or global)
+  float w[K][NT];
+  const float4 *row[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     int i; float mu;
     df s = s_idx[k];
     if (NT == 1) s = df_add_f(s, 0.5f);
     df_floor(s, i, mu);
-    float w[NT];
-    interp_weights<NT>(mu, w);
+    interp_weights<NT>(mu, w[k]);
     int i0 = i + first;
     if (i0 < 0 || i0 + NT > P.T) {
       flags |= RIFT_FLAG_WINDOW;
       i0 = min(max(i0, 0), P.T - NT);
     }
     const bool in_win = win[k] != nullptr && i0 >= wlo[k] && i0 + NT - 1 <= whi[k];
-    const float4 *row = in_win ? win[k] + (size_t)(i0 - wlo[k]) * rs
-                               : reinterpret_cast<const float4 *>(Q + ((long long)k * P.T + i0) * P.Mp);
-    float zr = 0.f, zi = 0.f;
-#pragma unroll 2
-    for (int a2 = 0; a2 < npairs; ++a2) {
+    row[k] = in_win ? win[k] + (size_t)(i0 - wlo[k]) * rs
+                    : reinterpret_cast<const float4 *>(Q + ((long long)k * P.T + i0) * P.Mp);
+  }
+  // modes outside, detectors inside: each Y_lm is read from shared memory once
+  float zr[K], zi[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { zr[k] = 0.f; zi[k] = 0.f; }
+  for (int a2 = 0; a2 < npairs; ++a2) {
+    const float2 y0 = Ys[(2 * a2) * ystride];
+    const float2 y1 = (2 * a2 + 1 < P.M) ? Ys[(2 * a2 + 1) * ystride] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
       float4 q[NT];
 #pragma unroll
-      for (int r = 0; r < NT; ++r) q[r] = row[r * rs + a2];
+      for (int r = 0; r < NT; ++r) q[r] = row[k][r * rs + a2];
       float q0r = 0.f, q0i = 0.f, q1r = 0.f, q1i = 0.f;
 #pragma unroll
       for (int r = 0; r < NT; ++r) {
-        q0r = fmaf(w[r], q[r].x, q0r); q0i = fmaf(w[r], q[r].y, q0i);
-        q1r = fmaf(w[r], q[r].z, q1r); q1i = fmaf(w[r], q[r].w, q1i);
+        q0r = fmaf(w[k][r], q[r].x, q0r); q0i = fmaf(w[k][r], q[r].y, q0i);
+        q1r = fmaf(w[k][r], q[r].z, q1r); q1i = fmaf(w[k][r], q[r].w, q1i);
       }
-      const float2 y0 = Ys[(2 * a2) * ystride];
-      const float2 y1 = (2 * a2 + 1 < P.M) ? Ys[(2 * a2 + 1) * ystride] : make_float2(0.f, 0.f);
-      zr = fmaf(y0.x, q0r, fmaf(y0.y, q0i, zr));
-      zi = fmaf(y0.x, q0i, fmaf(-y0.y, q0r, zi));
-      zr = fmaf(y1.x, q1r, fmaf(y1.y, q1i, zr));
-      zi = fmaf(y1.x, q1i, fmaf(-y1.y, q1r, zi));
+      zr[k] = fmaf(y0.x, q0r, fmaf(y0.y, q0i, zr[k]));
+      zi[k] = fmaf(y0.x, q0i, fmaf(-y0.y, q0r, zi[k]));
+      zr[k] = fmaf(y1.x, q1r, fmaf(y1.y, q1i, zr[k]));
+      zi[k] = fmaf(y1.x, q1i, fmaf(-y1.y, q1r, zi[k]));
     }
-    lin += F[k].x * zr - F[k].y * zi;
   }
+  float lin = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) lin += F[k].x * zr[k] - F[k].y * zi[k];
   return lin;
 }
 
