@@ -553,15 +553,33 @@ __global__ void hist_points_kernel(const float *__restrict__ ell, const uint32_t
   __syncthreads();
   if (R.ncell > 0 && R.ell_off >= 0 && R.proposal == 1) {
     const float mx = (float)acc[p].round_max;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += gridDim.x * blockDim.x) {
-      const float l = ell[R.ell_off + i];
-      if (!isfinite(l)) continue;
-      const float w = expf(beta * (l - mx));
-      const unsigned long long q = __float2ull_rn(w * 4294967296.0f);
-      const uint32_t b = bins[R.ell_off + i];
-      atomicAdd(&h[b & 255u], q);
-      atomicAdd(&h[nb + ((b >> 8) & 255u)], q);
-      atomicAdd(&h[2 * nb + ((b >> 16) & 255u)], q);
+    const uint32_t lane = threadIdx.x & 31u;
+    // warp-uniform loop; adapted proposals put many samples of a warp in the same bin, so the
+    // lanes of one bin are summed first (exactly: the 2^32 fixed point in 1 + 24 + 8 bit parts,
+    // each part's warp sum fits 32 bits) and one atomic per distinct bin is issued
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < R.n; base += gridDim.x * blockDim.x) {
+      const uint32_t i = base + lane;
+      bool ok = false;
+      unsigned long long q = 0ull;
+      uint32_t b = 0u;
+      if (i < R.n) {
+        const float l = ell[R.ell_off + i];
+        if (isfinite(l)) {
+          ok = true;
+          q = __float2ull_rn(expf(beta * (l - mx)) * 4294967296.0f);
+          b = bins[R.ell_off + i];
+        }
+      }
+      const uint32_t qhi = (uint32_t)(q >> 32), qmid = (uint32_t)(q >> 8) & 0xFFFFFFu, qlo = (uint32_t)q & 0xFFu;
+#pragma unroll
+      for (int dd = 0; dd < 3; ++dd) {
+        const uint32_t key = ok ? ((b >> (8 * dd)) & 255u) : 0xFFFFFFFFu;
+        const unsigned grp = __match_any_sync(0xFFFFFFFFu, key);
+        const uint32_t shi = __reduce_add_sync(grp, qhi), smid = __reduce_add_sync(grp, qmid),
+                       slo = __reduce_add_sync(grp, qlo);
+        if (ok && lane == (uint32_t)(__ffs(grp) - 1))
+          atomicAdd(&h[dd * nb + key], ((unsigned long long)shi << 32) + ((unsigned long long)smid << 8) + slo);
+      }
     }
   }
   __syncthreads();
