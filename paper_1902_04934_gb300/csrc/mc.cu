@@ -421,14 +421,20 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const float4 *__
       float sphi, cphi;
       sincospif(2.f * d.u_phi, &sphi, &cphi);
       const float ch = sqrtf(d.c_frac), sh = sqrtf(1.f - d.c_frac);   // cos, sin(incl/2)
-      swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
+      float dj[RIFT_MAXM];   // d_lm(incl) for the grouped quadratic form (parameter-bank kernels)
+      if constexpr (CP != 0) swsh_canonical_t<true>(P, ch, sh, cphi, sphi, Ys, ystride, dj);
+      else swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
       float lnL;
       if (TMARG) {
         const float quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
         lnL = tmarg_term<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
       } else {
+        // the quadratic form first: the d_lm it takes from the harmonics are then dead before the
+        // linear term's taps are loaded
+        float quad;
+        if constexpr (CP != 0) quad = quad_canon_from_d<K, CP == 2>(cpg, g, dj, (uint32_t)(d.u_phi * 16777216.f));
+        else quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
         const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
-        const float quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
         lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
       }
       float ell = lnL + d.lpq;

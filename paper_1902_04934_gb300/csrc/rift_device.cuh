@@ -190,8 +190,11 @@ __device__ __forceinline__ float canon_dval(const PointC &P, int j, const float 
 
 // -2Y_lm of the present modes, unrolled over the canonical table so every power index is a
 // compile-time constant; stored mode a = number of present canonical modes before j.
-__device__ __forceinline__ void swsh_canonical(const PointC &P, float c, float s, float cphi, float sphi,
-                                               float2 *Ys, int stride) {
+// WITH_D: also d[j] = d_j(iota) for every canonical j (0 for absent modes), the real factors the
+// grouped quadratic form needs.
+template <bool WITH_D>
+__device__ __forceinline__ void swsh_canonical_t(const PointC &P, float c, float s, float cphi, float sphi,
+                                                 float2 *Ys, int stride, float *d) {
   float cp[9], sp[9];
   cp[0] = 1.f; sp[0] = 1.f;
 #pragma unroll
@@ -205,14 +208,21 @@ __device__ __forceinline__ void swsh_canonical(const PointC &P, float c, float s
   const uint32_t mask = P.canon_mask;
 #pragma unroll
   for (int j = 0; j < RIFT_MAXM; ++j) {
+    if (WITH_D) d[j] = 0.f;
     if (mask & (1u << j)) {
       const float v = canon_dval(P, j, cp, sp);
+      if (WITH_D) d[j] = v;
       const int am = canon_m(j) < 0 ? -canon_m(j) : canon_m(j);
       const float2 em = e[am];
       const int a = __popc(mask & ((1u << j) - 1u));
       Ys[a * stride] = make_float2(v * em.x, canon_m(j) < 0 ? -(v * em.y) : v * em.y);
     }
   }
+}
+
+__device__ __forceinline__ void swsh_canonical(const PointC &P, float c, float s, float cphi, float sphi,
+                                               float2 *Ys, int stride) {
+  swsh_canonical_t<false>(P, c, s, cphi, sphi, Ys, stride, nullptr);
 }
 
 // Lagrange interpolation weights on NT taps: i-1..i+2 (cubic), i..i+1 (linear), i (nearest).
@@ -466,8 +476,8 @@ __device__ __forceinline__ void canon_part(const float4 *__restrict__ G, const f
 // reduced modulo 2 exactly in integers, so every rotation is good to an ulp (a product chain
 // from e^{i phi} would carry D times its rounding into whole group sums).
 template <int K, bool SP>
-__device__ __forceinline__ float quad_canon_body(const PointC &P, const float4 *__restrict__ G, const SampleGeo &g,
-                                                 float c, float s, uint32_t n1) {
+__device__ __forceinline__ float quad_canon_from_d(const float4 *__restrict__ G, const SampleGeo &g,
+                                                   const float (&d)[RIFT_MAXM], uint32_t n1) {
   float2 e[9];
   e[0] = make_float2(1.f, 0.f);
 #pragma unroll
@@ -475,13 +485,6 @@ __device__ __forceinline__ float quad_canon_body(const PointC &P, const float4 *
     const uint32_t r = ((uint32_t)D * n1) & 0xFFFFFFu;
     sincospif((float)r * 1.1920928955078125e-07f, &e[D].y, &e[D].x);
   }
-  float cp[9], sp[9];
-  cp[0] = 1.f; sp[0] = 1.f;
-#pragma unroll
-  for (int j = 1; j < 9; ++j) { cp[j] = cp[j - 1] * c; sp[j] = sp[j - 1] * s; }
-  float d[RIFT_MAXM];
-#pragma unroll
-  for (int j = 0; j < RIFT_MAXM; ++j) d[j] = canon_dval(P, j, cp, sp);
   float A[K][2], Bc[K][2];
 #pragma unroll
   for (int k = 0; k < K; ++k) { A[k][0] = 0.f; A[k][1] = 0.f; Bc[k][0] = 0.f; Bc[k][1] = 0.f; }
@@ -496,6 +499,19 @@ __device__ __forceinline__ float quad_canon_body(const PointC &P, const float4 *
     quad += f2 * A[k][0] + (gr * Bc[k][0] - gi * Bc[k][1]);
   }
   return quad;
+}
+
+template <int K, bool SP>
+__device__ __forceinline__ float quad_canon_body(const PointC &P, const float4 *__restrict__ G, const SampleGeo &g,
+                                                 float c, float s, uint32_t n1) {
+  float cp[9], sp[9];
+  cp[0] = 1.f; sp[0] = 1.f;
+#pragma unroll
+  for (int j = 1; j < 9; ++j) { cp[j] = cp[j - 1] * c; sp[j] = sp[j - 1] * s; }
+  float d[RIFT_MAXM];
+#pragma unroll
+  for (int j = 0; j < RIFT_MAXM; ++j) d[j] = canon_dval(P, j, cp, sp);
+  return quad_canon_from_d<K, SP>(G, g, d, n1);
 }
 
 template <int K, bool SP>
