@@ -246,18 +246,27 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
         if (std::fabs(v1[0] - v2[0]) > 1e-10 * vmax || std::fabs(v1[1] - v2[1]) > 1e-10 * vmax)
           return fail(h, RIFT_EINVAL, "V is not symmetric");
       }
-  for (int i = 0; i < K * M * T * 2; ++i)
-    if (!std::isfinite(d->Q[i])) return fail(h, RIFT_EINVAL, "non-finite Q");
-  // Q arena block: [K][T][Mp] complex64, zero padded
+  // Q arena block: [K][T][Mp] complex64, zero padded; converted in blocks of 64 times so that the
+  // rows written stay in cache, with the finiteness check in the same pass (x - x is 0 only for
+  // finite x)
   c.q_off = (long long)qv.size();
   qv.resize(qv.size() + (size_t)K * T * c.Mp, make_float2(0.f, 0.f));
   float2 *qb = qv.data() + c.q_off;
+  bool finite = true;
   for (int k = 0; k < K; ++k)
-    for (int a = 0; a < M; ++a)
-      for (int j = 0; j < T; ++j) {
-        const double *q = d->Q + 2 * (((size_t)k * M + perm[a]) * T + j);
-        qb[((size_t)k * T + j) * c.Mp + a] = make_float2((float)q[0], (float)q[1]);
+    for (int j0 = 0; j0 < T; j0 += 64) {
+      const int j1 = std::min(T, j0 + 64);
+      for (int a = 0; a < M; ++a) {
+        const double *q = d->Q + 2 * (((size_t)k * M + perm[a]) * T);
+        float2 *out = qb + (size_t)k * T * c.Mp + a;
+        for (int j = j0; j < j1; ++j) {
+          const double re = q[2 * j], im = q[2 * j + 1];
+          finite &= (re - re == 0.0) & (im - im == 0.0);
+          out[(size_t)j * c.Mp] = make_float2((float)re, (float)im);
+        }
       }
+    }
+  if (!finite) return fail(h, RIFT_EINVAL, "non-finite Q");
   // pair coefficients [pair_slot(a, b)][K] = (U, V) upper triangle, off-diagonal doubled
   c.uv_off = (long long)cv.size();
   cv.resize(cv.size() + (size_t)c.npair * K);
