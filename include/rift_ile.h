@@ -367,7 +367,8 @@ rift_status rift_ile_posterior(rift_ile *h, const rift_mc_opts *opts, int H, flo
  * destroyed and reused by later handles of the same sizes (a handle per intrinsic point then costs
  * no device allocation).  rift_release_cached_memory gives every cached buffer back to CUDA (the
  * cache also does so by itself when an allocation fails for lack of memory).  Buffers in use by live
- * handles are not affected.
+ * handles are not affected.  Call it before cudaDeviceReset (which invalidates cached buffers) and
+ * before handing the memory to another allocator.
  */
 void rift_release_cached_memory(void);
 
