@@ -385,7 +385,8 @@ void rift_release_cached_memory(void);
  *    loads the library holds until the process exits.
  *  - The first call on a device resolves that array's device address (and may load the
  *    library's device code); make this first call before any stream capture.
- *  - Limits: n_per_round <= RIFT_STATIC_MAX_PRIOR_ROUND, and with the adaptive proposal
+ *  - Limits: n_per_round <= RIFT_STATIC_MAX_PRIOR_ROUND (time-marginalised rounds, whose work
+ *    items hold fewer draws: RIFT_STATIC_MAX_PRIOR_ROUND / 8), and with the adaptive proposal
  *    n_per_round <= RIFT_STATIC_MAX_ROUND; larger rounds are rejected with RIFT_EINVAL.
  *    opts->dbg_tables and opts->timing must be 0.
  *  - Every call on a device shares the array and resets what must start from zero; calls

@@ -781,8 +781,13 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
       R.tmarg = o->time_marg ? 1 : 0;
       R.lcorr0 = (float)std::log((double)n / ((double)C * (R.base + 1.0)));
       R.lcorr1 = R.base ? (float)std::log((double)n / ((double)C * R.base)) : 0.f;
-      R.chunks = (R.base + (R.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
-      R.nitem = C * R.chunks;
+      if (o->time_marg) {   // runs of consecutive draws across cells (chunks unused)
+        R.chunks = 0;
+        R.nitem = (n + RIFT_TMARG_CHUNK - 1) / RIFT_TMARG_CHUNK;
+      } else {
+        R.chunks = (R.base + (R.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
+        R.nitem = C * R.chunks;
+      }
       R.ell_off = adaptive ? (long long)p * npr : -1;
       R.dbg_off = (np == 1 && o->dbg_ell) ? (long long)rounds[p] * npr : -1;
       R.tab = adaptive ? S.tables + ((size_t)cur * np + p) * tstride : nullptr;
@@ -1062,7 +1067,7 @@ rift_status rift_ile_marginalize(rift_ile *h, const rift_mc_opts *o, rift_mc_res
   const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
   const int nb = adaptive ? o->n_bins : 0;
   const int hb = std::max(1, std::min(64, (int)(o->n_per_round / 8192)));
-  const size_t items = (size_t)RIFT_MAX_CELLS + o->n_per_round / RIFT_CHUNK + 1;
+  const size_t items = (size_t)RIFT_MAX_CELLS + o->n_per_round / (o->time_marg ? RIFT_TMARG_CHUNK : RIFT_CHUNK) + 1;
   if ((s = ensure_scratch(h, 1, items, adaptive ? o->n_per_round : 0, nb, hb)) != RIFT_OK) return s;
   return run_mc(h, o, 1, h->sc, res);
 }
@@ -1101,7 +1106,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
       if ((1 << (ls[0] + ls[1] + ls[2])) > RIFT_MAX_CELLS) return fail(h, RIFT_EINVAL, "more than RIFT_MAX_CELLS cells");
       if (o->time_marg && ls[2] != 0) return fail(h, RIFT_EINVAL, "time-marginalised rounds are not stratified in t");
     }
-    items += ((size_t)1 << (ls[0] + ls[1] + ls[2])) + o->n_per_round / RIFT_CHUNK + 1;
+    items += ((size_t)1 << (ls[0] + ls[1] + ls[2])) + o->n_per_round / (o->time_marg ? RIFT_TMARG_CHUNK : RIFT_CHUNK) + 1;
   }
   const bool keep = adaptive || keep_ell;
   if ((s = ensure_scratch(h, np, items, keep ? (size_t)np * o->n_per_round : 0, nb, hb)) != RIFT_OK) return s;

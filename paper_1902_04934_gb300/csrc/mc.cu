@@ -124,6 +124,12 @@ __device__ __forceinline__ uint32_t sample_index(const RoundPt &R, uint32_t cell
   return (cell < R.rem) ? cell * (R.base + 1u) + j : R.rem * (R.base + 1u) + (cell - R.rem) * R.base + j;
 }
 
+// Cell of global sample i (i < R.n, so R.base >= 1 whenever cells hold samples).
+__device__ __forceinline__ uint32_t cell_of(const RoundPt &R, uint32_t i) {
+  const uint32_t big = R.rem * (R.base + 1u);
+  return (i < big) ? i / (R.base + 1u) : R.rem + (i - big) / R.base;
+}
+
 __device__ __forceinline__ void lse_push(float l, float &m, float &s1, float &s2) {
   if (l > m) {
     const float e = expf(m - l);
@@ -298,10 +304,19 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const float4 *__
       cur = p;
     }
     const uint32_t local = item - R.item0;
-    const uint32_t cell = local / R.chunks;
-    const uint32_t j0 = (local - cell * R.chunks) * RIFT_CHUNK;
-    const uint32_t n_cell = R.base + (cell < R.rem ? 1u : 0u);
-    const uint32_t j_end = min(n_cell, j0 + RIFT_CHUNK);
+    uint32_t cell, j0, j_end;
+    if constexpr (TMARG) {
+      // a run of at most RIFT_TMARG_CHUNK consecutive draws of the point, one per thread (a draw
+      // costs about J samples, so every item is one full pass); each draw takes its own cell
+      cell = 0u;
+      j0 = local * RIFT_TMARG_CHUNK;
+      j_end = min(R.n, j0 + RIFT_TMARG_CHUNK);
+    } else {
+      cell = local / R.chunks;
+      j0 = (local - cell * R.chunks) * RIFT_CHUNK;
+      const uint32_t n_cell = R.base + (cell < R.rem ? 1u : 0u);
+      j_end = min(n_cell, j0 + RIFT_CHUNK);
+    }
     const float2 *Q = L.qa + P.q_off;
     constexpr int first = (NT == 4) ? -1 : 0;
 
@@ -388,8 +403,9 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const float4 *__
     // C. evaluate
     float m = kNegInf, s1 = 0.f, s2 = 0.f, cnt = 0.f;
     for (uint32_t j = j0 + threadIdx.x; j < j_end; j += blockDim.x) {
-      const uint32_t i = sample_index(R, cell, j);
-      const Drawn d = draw_any<LEARNED, TMARG>(L.seed, R, i, cell, tab, lnw, s_gmm, P.dref, L.d_lo3, L.d_span3);
+      const uint32_t i = TMARG ? j : sample_index(R, cell, j);
+      const Drawn d = draw_any<LEARNED, TMARG>(L.seed, R, i, TMARG ? cell_of(R, i) : cell, tab, lnw, s_gmm, P.dref,
+                                               L.d_lo3, L.d_span3);
       const Sky s = sky_of(P, d);
       df si[K];
       if (TMARG) delay_index<K>(P, s, si);
@@ -729,8 +745,13 @@ __global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState 
       N.ncell = C;
       N.base = n / C;
       N.rem = n % C;
-      N.chunks = (N.base + (N.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
-      N.nitem = C * N.chunks;
+      if (B.tmarg) {   // runs of consecutive draws across cells (chunks unused)
+        N.chunks = 0;
+        N.nitem = (n + RIFT_TMARG_CHUNK - 1) / RIFT_TMARG_CHUNK;
+      } else {
+        N.chunks = (N.base + (N.rem ? 1u : 0u) + RIFT_CHUNK - 1) / RIFT_CHUNK;
+        N.nitem = C * N.chunks;
+      }
       N.round = (uint32_t)st.rounds;
       N.point_id = (B.np == 1) ? B.point_id1 : (uint32_t)p;
       N.ls0 = l0; N.ls1 = l1; N.ls2 = l2;

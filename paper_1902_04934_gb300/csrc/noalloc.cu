@@ -29,7 +29,8 @@ namespace {
 constexpr int kHist = 64;          // histogram blocks per round
 // work items of one round: cells plus extra chunks of large cells (adaptive rounds are
 // capped at RIFT_STATIC_MAX_ROUND samples; prior rounds of any size use at most this many
-// items because the runner rejects more)
+// items because the runner rejects more; time-marginalised rounds, in items of at most
+// RIFT_TMARG_CHUNK = RIFT_CHUNK / 8 draws, are capped at an eighth of the prior-round limit)
 constexpr size_t kItems = (size_t)RIFT_MAX_CELLS + RIFT_STATIC_MAX_PRIOR_ROUND / RIFT_CHUNK + 1;
 constexpr size_t kAlign = 256;
 
@@ -47,6 +48,7 @@ constexpr size_t kOffEll = al(kOffLnw + sizeof(float) * 2 * 3 * RIFT_MAXBINS);
 constexpr size_t kOffBin = al(kOffEll + sizeof(float) * RIFT_STATIC_MAX_ROUND);
 constexpr size_t kBytes = al(kOffBin + sizeof(uint32_t) * RIFT_STATIC_MAX_ROUND);
 static_assert(kBytes == RIFT_STATIC_SCRATCH_BYTES, "scratch size in the header is out of date");
+static_assert(RIFT_CHUNK == 8 * RIFT_TMARG_CHUNK, "the time-marginalised round limit assumes items of RIFT_CHUNK / 8");
 
 }  // namespace
 
@@ -91,6 +93,10 @@ extern "C" rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_op
     return rift_internal_fail(h, RIFT_EINVAL,
                               "rift_ile_marginalize_static: n_per_round exceeds RIFT_STATIC_MAX_PRIOR_ROUND "
                               "(the static scratch holds the partials of at most that many samples per round)");
+  if (o->time_marg && o->n_per_round > (uint32_t)(RIFT_STATIC_MAX_PRIOR_ROUND / 8))
+    return rift_internal_fail(h, RIFT_EINVAL,
+                              "rift_ile_marginalize_static: time-marginalised rounds hold at most "
+                              "RIFT_STATIC_MAX_PRIOR_ROUND / 8 draws (work items of at most 256 draws)");
   if (o->dbg_tables || o->timing)
     return rift_internal_fail(h, RIFT_EINVAL, "rift_ile_marginalize_static: dbg_tables and timing are not supported");
   if (o->proposal == RIFT_PROPOSAL_ADAPTIVE && (o->n_bins < 2 || o->n_bins > RIFT_MAXBINS))

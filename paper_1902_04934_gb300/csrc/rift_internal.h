@@ -11,6 +11,10 @@ struct PointC;
 // Threads per block of the cell kernel, and samples per work item at most.
 #define RIFT_CELL_BLOCK 256
 #define RIFT_CHUNK 2048
+// Draws per work item in time-marginalised rounds: an item is a run of consecutive draws of a
+// point (across cells), one per thread, so every item but a point's last is one full pass of a CTA
+// (a draw costs about J samples; items of part-filled passes leave threads idle).
+#define RIFT_TMARG_CHUNK RIFT_CELL_BLOCK
 
 // Block partial of the log-sum-exp: max, sum e^{l-max}, sum e^{2(l-max)}, count.
 struct __align__(32) Part {
@@ -33,8 +37,8 @@ struct RoundPt {
   uint32_t ncell;          // cells: S_ra S_sd S_t, 0 if inactive
   uint32_t base, rem;      // n = base * ncell + rem; cells [0, rem) hold base + 1 samples
   uint32_t item0;          // first work item of this point in the round
-  uint32_t chunks;         // work items per cell (each at most RIFT_CHUNK samples)
-  uint32_t nitem;          // work items of this point: ncell * chunks
+  uint32_t chunks;         // work items per cell (each at most RIFT_CHUNK samples); 0 if tmarg
+  uint32_t nitem;          // work items of this point: ncell * chunks (tmarg: ceil(n / RIFT_TMARG_CHUNK))
   uint32_t round;          // Philox counter word 1
   uint32_t point_id;       // Philox counter word 3
   uint32_t ls0, ls1, ls2;  // log2 of the strata in effect
