@@ -304,8 +304,8 @@ def test_adaptive_fixed_tables_parity(lib, cuda, p_small):
 
 
 def test_adaptive_table_rebuild_parity(lib, cuda, p_small):
-    """One adaptive update from the prior: the device's round-1 tables vs the oracle's rebuild
-    from its own round-0 weights (same draws)."""
+    """One adaptive update from the prior: the tables the device draws its second Monte Carlo
+    round from vs the oracle's rebuild from its own first-round weights (same draws)."""
     import torch
     nb = 50
     n = 60000
