@@ -373,8 +373,16 @@ rift_status rift_ile_posterior(rift_ile *h, const rift_mc_opts *opts, int H, flo
 void rift_release_cached_memory(void);
 
 /*
+ * Counters of the buffer cache since the library was loaded (host array of 4, written):
+ * out[0] device-buffer requests, out[1] pinned-host-buffer requests (served from the cache or by
+ * a new allocation), out[2] cudaMalloc calls, out[3] cudaMallocHost calls those requests needed.
+ * Tracing only: a call that leaves all four unchanged made no handle allocation.
+ */
+void rift_cache_counters(unsigned long long out[4]);
+
+/*
  * rift_ile_marginalize_static -- the same computation as rift_ile_marginalize (point 0,
- * prior or adaptive proposal; same kernels, same results) for callers that cannot
+ * prior or adaptive proposal, sampled or marginalised time; same kernels, same results) for callers that cannot
  * allocate device memory when they marginalise: programs that give (nearly) all device
  * memory to another allocator at start-up, or that forbid device allocation after
  * initialisation.  The paper has no counterpart; it is a deployment variant.
@@ -383,12 +391,15 @@ void rift_release_cached_memory(void);
  *    partials, accumulator, adaptive histograms, tables, one round of per-sample weights)
  *    is a file-scope device array of RIFT_STATIC_SCRATCH_BYTES that every device which
  *    loads the library holds until the process exits.
- *  - The first call on a device resolves that array's device address (and may load the
- *    library's device code); make this first call before any stream capture.
+ *  - Every call looks that array's device address up (cudaGetSymbolAddress, with the
+ *    caller's device current), so the address stays right after cudaDeviceReset.  The first
+ *    call on a device is the set-up: the lookup may load the library's device code there;
+ *    make this first call before any stream capture.
  *  - Limits: n_per_round <= RIFT_STATIC_MAX_PRIOR_ROUND (time-marginalised rounds, whose work
  *    items hold fewer draws: RIFT_STATIC_MAX_PRIOR_ROUND / 8), and with the adaptive proposal
  *    n_per_round <= RIFT_STATIC_MAX_ROUND; larger rounds are rejected with RIFT_EINVAL.
- *    opts->dbg_tables and opts->timing must be 0.
+ *    The learned proposal (whose network buffers a handle allocates on first use) is rejected
+ *    with RIFT_EINVAL.  opts->dbg_tables and opts->timing must be 0.
  *  - Every call on a device shares the array and resets what must start from zero; calls
  *    whose GPU work overlaps (different streams or host threads) race and must not be issued.
  * The handle itself is created (and allocated) beforehand with rift_ile_create.

@@ -121,6 +121,7 @@ def _load():
         "rift_ile_batch_harvest": (I, [P, C.POINTER(McOpts), I, D, P, C.POINTER(McResult)]),
         "rift_ile_samples": (I, [P, C.POINTER(McOpts), S, P, C.POINTER(U64), C.POINTER(McResult)]),
         "rift_release_cached_memory": (None, []),
+        "rift_cache_counters": (None, [P]),
         "rift_ile_posterior": (I, [P, C.POINTER(McOpts), I, P, P, C.POINTER(McResult)]),
         "rift_ile_get_tune": (I, [P, C.POINTER(Tune)]),
         "rift_ile_set_tune": (I, [P, C.POINTER(Tune)]),
@@ -560,6 +561,14 @@ def rift_ile_posterior(h, H, **kw):
 def rift_release_cached_memory():
     """Give the device and pinned buffers cached from destroyed handles back to CUDA."""
     _lib.rift_release_cached_memory()
+
+
+def rift_cache_counters():
+    """Buffer-cache counters: (device requests, pinned host requests, cudaMalloc calls,
+    cudaMallocHost calls) since the library was loaded."""
+    out = (C.c_ulonglong * 4)()
+    _lib.rift_cache_counters(out)
+    return tuple(int(x) for x in out)
 
 
 def rift_ile_get_tune(h):

@@ -25,6 +25,8 @@ struct Cache {
   std::mutex mu;
   std::multimap<Key, void *> free_dev, free_host;
   std::unordered_map<void *, Key> live_dev, live_host;
+  // requests served (device, pinned host) and the CUDA allocations they needed
+  unsigned long long n_req_dev = 0, n_req_host = 0, n_malloc_dev = 0, n_malloc_host = 0;
 };
 
 Cache &cache() {
@@ -66,8 +68,10 @@ cudaError_t alloc(void **p, size_t n, bool host) {
   Cache &c = cache();
   std::lock_guard<std::mutex> lock(c.mu);
   Key k{host ? -1 : dev, rounded(n)};
+  (host ? c.n_req_host : c.n_req_dev) += 1;
   void *q = take(host ? c.free_host : c.free_dev, k);
   if (!q) {
+    (host ? c.n_malloc_host : c.n_malloc_dev) += 1;
     e = host ? cudaMallocHost(&q, k.size) : cudaMalloc(&q, k.size);
     if (e == cudaErrorMemoryAllocation) {
       cudaGetLastError();   // the failed call's error is not sticky; clear it before retrying
@@ -106,4 +110,14 @@ extern "C" void rift_release_cached_memory(void) {
   Cache &c = cache();
   std::lock_guard<std::mutex> lock(c.mu);
   release_locked(c);
+}
+
+extern "C" void rift_cache_counters(unsigned long long out[4]) {
+  if (!out) return;
+  Cache &c = cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  out[0] = c.n_req_dev;
+  out[1] = c.n_req_host;
+  out[2] = c.n_malloc_dev;
+  out[3] = c.n_malloc_host;
 }

@@ -44,6 +44,14 @@ struct Drawn {
   uint32_t bins;   // adapted bins, 8 bits each
 };
 
+// cos dec of a draw from its sin dec fraction x1 = (1 + sin dec) / 2 (double-float):
+// 2 sqrt(x1 (1 - x1)), with 1 - x1 formed from both words of x1.  Near the north pole, where
+// 1 - x1 ~ (pi/2 - dec)^2 / 4 is tiny, the high word alone would leave 1 - x1 with only a few
+// correct bits (a relative error in cos dec of several per cent within 1e-3 rad of the pole).
+__device__ __forceinline__ float cos_dec_of(df x1) {
+  return 2.f * sqrtf(x1.hi * __fsub_rn(__fsub_rn(1.f, x1.hi), x1.lo));
+}
+
 // Sample i (index in the point's round) of cell `cell`: Philox uniforms, stratified
 // (ra, sin dec, t) uniforms U_d = (c_d + u_d) / S_d (exact: S_d is a power of two),
 // prior or tabulated proposal.

@@ -100,7 +100,7 @@ __device__ __forceinline__ Sky sky_of(const PointC &P, const Drawn &d) {
   s.ca = c0 - s0 * ares;
   s.sa = s0 + c0 * ares;
   s.sd = df_add_f(df{2.f * d.x1.hi, 2.f * d.x1.lo}, -1.f);
-  s.cd = 2.f * sqrtf(d.x1.hi * (1.f - d.x1.hi));
+  s.cd = cos_dec_of(d.x1);
   return s;
 }
 

@@ -10,14 +10,18 @@
 //
 // The array below exists once per device that loads the library and stays allocated
 // until the process exits.  Host code cannot use the name `g_static_scratch` as a device
-// address (on the host it names a stand-in object); the device address is obtained with
-// cudaGetSymbolAddress, once per device, with that device current, by the first call made
-// on that device.  That first call should therefore come before any stream capture.
+// address (on the host it names a stand-in object); every call looks the device address up
+// with cudaGetSymbolAddress, with the caller's device current, and checks the result.  The
+// first call on a device is the set-up: the lookup may load the library's device code there
+// (which is when the array is allocated), so that first call should come before any stream
+// capture.  Later lookups only read the runtime's symbol table; looking the address up on
+// every call, rather than keeping it, keeps it valid after cudaDeviceReset, which unloads the
+// module and may place the array elsewhere when it is loaded again.
+// The learned proposal is refused: its per-handle network buffers would be allocated.
 // All calls on one device share the array: calls whose work overlaps on the GPU race.
 #include <cmath>
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "../../include/rift_ile.h"
@@ -56,24 +60,12 @@ static __device__ __align__(256) unsigned char g_static_scratch[kBytes];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (set-up on first use).
+// Device address of the scratch array on the current device.
 cudaError_t scratch_address(unsigned char **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<unsigned char *>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<unsigned char *>(p);
   return cudaSuccess;
 }
 
@@ -97,6 +89,10 @@ extern "C" rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_op
     return rift_internal_fail(h, RIFT_EINVAL,
                               "rift_ile_marginalize_static: time-marginalised rounds hold at most "
                               "RIFT_STATIC_MAX_PRIOR_ROUND / 8 draws (work items of at most 256 draws)");
+  if (o->proposal == RIFT_PROPOSAL_LEARNED)
+    return rift_internal_fail(h, RIFT_EINVAL,
+                              "rift_ile_marginalize_static: the learned proposal is not supported (its network "
+                              "buffers are allocated per handle)");
   if (o->dbg_tables || o->timing)
     return rift_internal_fail(h, RIFT_EINVAL, "rift_ile_marginalize_static: dbg_tables and timing are not supported");
   if (o->proposal == RIFT_PROPOSAL_ADAPTIVE && (o->n_bins < 2 || o->n_bins > RIFT_MAXBINS))

@@ -25,7 +25,7 @@ constexpr float kTwoPi = 6.283185307179586f;
 __device__ __forceinline__ void theta_of(const PointC &P, const Drawn &d, bool tmarg, float *o) {
   o[0] = kTwoPi * (d.x0.hi + d.x0.lo);
   const float sd = (2.f * d.x1.hi - 1.f) + 2.f * d.x1.lo;
-  const float cd = 2.f * sqrtf(d.x1.hi * (1.f - d.x1.hi));
+  const float cd = cos_dec_of(d.x1);
   o[1] = atan2f(sd, cd);
   o[2] = tmarg ? NAN : P.t_lo + P.t_span * (d.x2.hi + d.x2.lo);
   o[3] = kPi * d.u_psi;
