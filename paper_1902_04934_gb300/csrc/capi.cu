@@ -131,6 +131,8 @@ struct rift_ile {
   // single-point handle of a three-detector point in the grouped layout: its grouped coefficients,
   // passed to the cell kernel as a parameter
   CanonCoefParam *canon0 = nullptr;
+  // or, for a mirror-symmetric point, the coefficients of its positive quadratic form
+  MirrorCoefParam *mirror0 = nullptr;
 };
 
 namespace {
@@ -321,6 +323,68 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
           if ((mm < 0 && (pc.x != 0.f || pc.y != 0.f)) || (mm > 0 && (pc.z != 0.f || pc.w != 0.f))) c.canon_sparse = 0;
         }
       }
+    // reflection symmetry of non-precessing modes (quad_mirror): every mode's mirror present,
+    // conj(h_a(-f)) = sigma_a h_abar(f), read off the inputs as V_ab = sigma_a U_{abar b} for all b,
+    // with U zero between opposite-sign m and U_{abar bbar} = sigma_a sigma_b conj(U_ab); checked
+    // to 1e-10 of the largest |U|, |V| (FP64 inputs), so the positive form equals the general one
+    int mir[RIFT_MAXM];
+    bool ok = true;
+    for (int a = 0; a < M && ok; ++a) {
+      mir[a] = -1;
+      for (int b = 0; b < M; ++b)
+        if (c.mode[b].l == c.mode[a].l && c.mode[b].m == -c.mode[a].m) mir[a] = b;
+      ok = mir[a] >= 0;
+    }
+    const double tol = 1e-10 * std::max(umax, vmax);
+    // U, V of stored modes (a, b) of detector k
+    auto Uab = [&](int k, int a, int b, int comp) { return d->U[2 * ((k * M + perm[a]) * M + perm[b]) + comp]; };
+    auto Vab = [&](int k, int a, int b, int comp) { return d->V[2 * ((k * M + perm[a]) * M + perm[b]) + comp]; };
+    int sig[RIFT_MAXM];
+    for (int a = 0; a < M && ok; ++a) {
+      sig[a] = 0;
+      for (int sv = 1; sv >= -1 && !sig[a]; sv -= 2) {
+        bool match = true;
+        for (int k = 0; k < K && match; ++k)
+          for (int b = 0; b < M && match; ++b)
+            match = std::fabs(Vab(k, a, b, 0) - sv * Uab(k, mir[a], b, 0)) <= tol &&
+                    std::fabs(Vab(k, a, b, 1) - sv * Uab(k, mir[a], b, 1)) <= tol;
+        if (match) sig[a] = sv;
+      }
+      ok = sig[a] != 0;
+    }
+    for (int a = 0; a < M && ok; ++a) {
+      ok = sig[mir[a]] == sig[a];
+      for (int b = 0; b < M && ok; ++b)
+        for (int k = 0; k < K && ok; ++k) {
+          if ((long long)c.mode[a].m * c.mode[b].m < 0)
+            ok = std::fabs(Uab(k, a, b, 0)) <= tol && std::fabs(Uab(k, a, b, 1)) <= tol;
+          else
+            ok = std::fabs(Uab(k, mir[a], mir[b], 0) - sig[a] * sig[b] * Uab(k, a, b, 0)) <= tol &&
+                 std::fabs(Uab(k, mir[a], mir[b], 1) + sig[a] * sig[b] * Uab(k, a, b, 1)) <= tol;
+        }
+    }
+    if (ok) {
+      c.mirror = 1;
+      c.sigma_neg = 0u;
+      int stored[RIFT_MAXM];
+      for (int j = 0; j < RIFT_MAXM; ++j)
+        stored[j] = (c.canon_mask >> j & 1u) ? __builtin_popcount(c.canon_mask & ((1u << j) - 1u)) : -1;
+      for (int j = 0; j < RIFT_MAXM; ++j)
+        if (stored[j] >= 0 && sig[stored[j]] < 0) c.sigma_neg |= 1u << j;
+      c.coef_off = (long long)cv.size();
+      c.ncoef = (kMirrorPairs * K + 1) / 2;
+      cv.resize(cv.size() + (size_t)c.ncoef, make_float4(0.f, 0.f, 0.f, 0.f));
+      float2 *g = reinterpret_cast<float2 *>(cv.data() + c.coef_off);
+      for (int i = 0; i < kMirrorPairs; ++i) {
+        const int code = mirror_pair(i);
+        const int ja = (code >> 5) & 31, jb = code & 31;
+        const int a = stored[ja], b = stored[jb];
+        if (a < 0 || b < 0) continue;   // absent modes (their mirrors are absent too): zero
+        const double w = mirror_weight(ja, jb);
+        for (int k = 0; k < K; ++k)
+          g[(size_t)i * K + k] = make_float2((float)(w * Uab(k, a, b, 0)), (float)(w * Uab(k, a, b, 1)));
+      }
+    }
   }
   return RIFT_OK;
 }
@@ -401,7 +465,11 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
       return s2;
     }
   }
-  if (n == 1 && h->pts[0].c.grouped) {
+  if (n == 1 && h->pts[0].c.grouped && h->pts[0].c.mirror) {
+    h->mirror0 = new (std::nothrow) MirrorCoefParam;
+    if (!h->mirror0) { rift_status s1 = fail(h, RIFT_ENOMEM, "host allocation"); rift_ile_destroy(h); return s1; }
+    std::memcpy(h->mirror0->g, cv.data() + h->pts[0].c.coef_off, sizeof(h->mirror0->g));
+  } else if (n == 1 && h->pts[0].c.grouped) {
     h->canon0 = new (std::nothrow) CanonCoefParam;
     if (!h->canon0) { rift_status s1 = fail(h, RIFT_ENOMEM, "host allocation"); rift_ile_destroy(h); return s1; }
     std::memcpy(h->canon0->g, cv.data() + h->pts[0].c.coef_off, sizeof(h->canon0->g));
@@ -703,7 +771,8 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   // a single point in the grouped layout passes its coefficients as a kernel parameter (when the
   // kernel has that variant): no shared-memory copy of them, so the Q windows get the room
   const CanonCoefParam *cc = (np == 1 && h->canon0 && NT == 4 && !learned && !o->time_marg) ? h->canon0 : nullptr;
-  const int coef_f4 = cc ? 0 : h->max_pairK;
+  const MirrorCoefParam *mp = (np == 1 && h->mirror0 && NT == 4 && !learned && !o->time_marg) ? h->mirror0 : nullptr;
+  const int coef_f4 = (cc || mp) ? 0 : h->max_pairK;
   const size_t fixed = cells_smem_fixed(K, h->max_M, coef_f4, nb, block);
   long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
   budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
@@ -805,7 +874,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     RIFT_CK(h, cudaMemcpyAsync(S.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st));
     const int grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(items, (uint32_t)(h->num_sms * bps)));
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev0, st));
-    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st, cc, h->pts[0].c.canon_sparse));
+    RIFT_CK(h, launch_cells(K, NT, L, grid, block, smem, st, cc, h->pts[0].c.canon_sparse, mp));
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev1, st));
     RIFT_CK(h, launch_merge_points(S.partials, S.rp, np, S.acc, st));
     launches += 2;
@@ -947,6 +1016,7 @@ void rift_ile_destroy(rift_ile *h) {
   cache_host_free(h->pst_host);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   delete h->canon0;
+  delete h->mirror0;
   delete h;
 }
 

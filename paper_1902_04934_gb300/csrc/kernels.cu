@@ -20,6 +20,29 @@ __device__ __forceinline__ void load_point(const PointC *src, PointC *dst) {
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Stage the coefficients of the point's quadratic form into shared memory: the positive form's
+// table for a mirror-symmetric point (kernels compiled for three detectors and cubic taps), the
+// pair layout otherwise.  The region holds npair * K float4, at least the mirror table's ncoef.
+template <int K, int NT>
+__device__ __forceinline__ void stage_quad_coef(const PointC &P, const float4 *__restrict__ ca, float4 *C) {
+  const bool mir = kCanonPath<K, NT> && P.mirror;
+  const float4 *cg = ca + (mir ? P.coef_off : P.uv_off);
+  const int n = mir ? P.ncoef : P.npair * K;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) C[j] = cg[j];
+}
+
+// Quadratic form of a caller draw with harmonics Ys and real factors d (phi in radians).
+template <int K, int NT>
+__device__ __forceinline__ float quad_caller(const PointC &P, const float4 *C, const SampleGeo &g, const float2 *Ys,
+                                             int ystride, float phi, const float (&d)[RIFT_MAXM]) {
+  if constexpr (kCanonPath<K, NT>) {
+    if (P.mirror) return quad_mirror_at<K>(reinterpret_cast<const float2 *>(C), g, d, P.sigma_neg, phi);
+  }
+  (void)phi;
+  (void)d;
+  return quad_term<K>(P, C, g, Ys, ystride);
+}
+
 template <int K, int NT>
 __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict__ pts, const float2 *__restrict__ qa,
                                                          const float4 *__restrict__ ca, size_t n,
@@ -38,8 +61,7 @@ __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict
   off = align16(off + sizeof(float4) * (size_t)P.npair * K);
   float2 *Ys = reinterpret_cast<float2 *>(smem + off) + threadIdx.x;
   const int ystride = blockDim.x;
-  const float4 *cg = ca + P.uv_off;
-  for (int j = threadIdx.x; j < P.npair * K; j += blockDim.x) C[j] = cg[j];
+  stage_quad_coef<K, NT>(P, ca, C);
   __syncthreads();
   const float2 *Q = qa + P.q_off;
   uint32_t flags = 0u;
@@ -69,9 +91,10 @@ __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict
     float sphi, cphi, ch, sh;
     sincosf(phi[i], &sphi, &cphi);
     sincosf(0.5f * incl[i], &sh, &ch);
-    swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
+    float dj[RIFT_MAXM];
+    swsh_canonical_t<kCanonPath<K, NT>>(P, ch, sh, cphi, sphi, Ys, ystride, dj);
     const float lin = linear_term<K, NT>(P, Q, g, Ys, ystride, flags);
-    const float quad = quad_term<K>(P, C, g, Ys, ystride);
+    const float quad = quad_caller<K, NT>(P, C, g, Ys, ystride, phi[i], dj);
     const float lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
     if (!isfinite(lnL)) flags |= RIFT_FLAG_NONFINITE;
     out[i] = lnL;
@@ -82,7 +105,7 @@ __global__ void __launch_bounds__(128) lnl_array_kernel(const PointC *__restrict
 // Geometry, harmonics and quadratic form of a caller draw (ra, dec, psi, phi, incl, D) whose time
 // is integrated: g.s[k] is the Q index of the first quadrature time t_lo + 1/(2 fs) plus the time
 // of flight to detector k.  Returns the quadratic form.
-template <int K>
+template <int K, int NT>
 __device__ __forceinline__ float tmarg_setup(const PointC &P, const float4 *C, float r, float dec, float psi,
                                              float phi, float incl, float dist, SampleGeo &g, float2 *Ys,
                                              int ystride) {
@@ -105,8 +128,9 @@ __device__ __forceinline__ float tmarg_setup(const PointC &P, const float4 *C, f
   float sphi, cphi, ch, sh;
   sincosf(phi, &sphi, &cphi);
   sincosf(0.5f * incl, &sh, &ch);
-  swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
-  return quad_term<K>(P, C, g, Ys, ystride);
+  float dj[RIFT_MAXM];
+  swsh_canonical_t<kCanonPath<K, NT>>(P, ch, sh, cphi, sphi, Ys, ystride, dj);
+  return quad_caller<K, NT>(P, C, g, Ys, ystride, phi, dj);
 }
 
 // Time-marginalised likelihood of caller draws (ra, dec, psi, phi, incl, D): Eq. (lnL:tmarg)
@@ -126,15 +150,14 @@ __global__ void __launch_bounds__(128) lnl_tmarg_array_kernel(
   off = align16(off + sizeof(float4) * (size_t)P.npair * K);
   float2 *Ys = reinterpret_cast<float2 *>(smem + off) + threadIdx.x;
   const int ystride = blockDim.x;
-  const float4 *cg = ca + P.uv_off;
-  for (int j = threadIdx.x; j < P.npair * K; j += blockDim.x) C[j] = cg[j];
+  stage_quad_coef<K, NT>(P, ca, C);
   __syncthreads();
   const float2 *Q = qa + P.q_off;
   uint32_t flags = 0u;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     SampleGeo g;
-    const float quad = tmarg_setup<K>(P, C, ra[i], dec[i], psi[i], phi[i], incl[i], dist[i], g, Ys, ystride);
+    const float quad = tmarg_setup<K, NT>(P, C, ra[i], dec[i], psi[i], phi[i], incl[i], dist[i], g, Ys, ystride);
     const float lm = tmarg_term<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
     if (!isfinite(lm)) flags |= RIFT_FLAG_NONFINITE;
     out[i] = lm;
@@ -161,8 +184,7 @@ __global__ void __launch_bounds__(128) tdraw_kernel(const PointC *__restrict__ p
   off = align16(off + sizeof(float4) * (size_t)P.npair * K);
   float2 *Ys = reinterpret_cast<float2 *>(smem + off) + threadIdx.x;
   const int ystride = blockDim.x;
-  const float4 *cg = ca + P.uv_off;
-  for (int j = threadIdx.x; j < P.npair * K; j += blockDim.x) C[j] = cg[j];
+  stage_quad_coef<K, NT>(P, ca, C);
   __syncthreads();
   const float2 *Q = qa + P.q_off;
   uint32_t flags = 0u;
@@ -173,7 +195,7 @@ __global__ void __launch_bounds__(128) tdraw_kernel(const PointC *__restrict__ p
       const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
       const uint4 b = philox4x32_10(make_uint4((uint32_t)h, 0u, 3u, last[p].point_id), key);
       SampleGeo g;
-      const float quad = tmarg_setup<K>(P, C, o[0], o[1], o[3], o[4], o[5], o[6], g, Ys, ystride);
+      const float quad = tmarg_setup<K, NT>(P, C, o[0], o[1], o[3], o[4], o[5], o[6], g, Ys, ystride);
       float l;
       const int j = tmarg_pick<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, bits_to_u(b.x), l, flags);
       if (j < 0) {

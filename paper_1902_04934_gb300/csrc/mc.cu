@@ -73,17 +73,22 @@ __device__ __forceinline__ void copy_words(const void *src, void *dst, int nbyte
   for (int i = threadIdx.x; i < nbytes / 4; i += blockDim.x) d[i] = s[i];
 }
 
-// Quadratic term of a drawn sample: the grouped form for points in the grouped layout
-// (the kernels compiled with it), the pair form otherwise.  u_phi = n1 2^-24, n1 odd.
+// Quadratic term of a drawn sample: for points in the canonical layout (the kernels compiled with
+// it) the positive form of a mirror-symmetric point or the grouped form, the pair form otherwise.
+// CP: coefficients from the shared copy C (0) or the kernel parameters cpg: grouped dense (1),
+// grouped sparse (2), mirror (3).  u_phi = n1 2^-24, n1 odd.
 template <int K, int NT, int CP>
 __device__ __forceinline__ float quad_cell(const PointC &P, const float4 *__restrict__ C,
-                                           const float4 *__restrict__ cpg, const SampleGeo &g, const float2 *Ys,
+                                           const void *__restrict__ cpg, const SampleGeo &g, const float2 *Ys,
                                            int ystride, float ch, float sh, float u_phi) {
   const uint32_t n1 = (uint32_t)(u_phi * 16777216.f);
-  if constexpr (CP) return quad_canon_body<K, CP == 2>(P, cpg, g, ch, sh, n1);
+  if constexpr (CP == 3) return quad_mirror_body<K>(P, static_cast<const float2 *>(cpg), g, ch, sh, n1);
+  if constexpr (CP) return quad_canon_body<K, CP == 2>(P, static_cast<const float4 *>(cpg), g, ch, sh, n1);
   if constexpr (kCanonPath<K, NT>) {
-    if (P.grouped)
+    if (P.grouped) {
+      if (P.mirror) return quad_mirror<K>(P, reinterpret_cast<const float2 *>(C), g, ch, sh, n1);
       return P.canon_sparse ? quad_canon<K, true>(P, C, g, ch, sh, n1) : quad_canon<K, false>(P, C, g, ch, sh, n1);
+    }
   }
   return quad_term<K>(P, C, g, Ys, ystride);
 }
@@ -230,7 +235,7 @@ __device__ __forceinline__ void delay_index(const PointC &P, const Sky &s, df ou
 // sample's t uniform is unused, its Q rows span the whole time window (no staging), and the
 // likelihood is tmarg_term.
 template <int K, int NT, int LEARNED, int TMARG, int CP>
-__device__ __forceinline__ void cells_body(const CellLaunch &L, const float4 *__restrict__ cpg) {
+__device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__restrict__ cpg) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_item, s_point;
@@ -448,7 +453,11 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const float4 *__
         // the quadratic form first: the d_lm it takes from the harmonics are then dead before the
         // linear term's taps are loaded
         float quad;
-        if constexpr (CP != 0) quad = quad_canon_from_d<K, CP == 2>(cpg, g, dj, (uint32_t)(d.u_phi * 16777216.f));
+        if constexpr (CP == 3)
+          quad = quad_mirror_from_d<K>(static_cast<const float2 *>(cpg), g, dj, P.sigma_neg,
+                                       (uint32_t)(d.u_phi * 16777216.f));
+        else if constexpr (CP != 0)
+          quad = quad_canon_from_d<K, CP == 2>(static_cast<const float4 *>(cpg), g, dj, (uint32_t)(d.u_phi * 16777216.f));
         else quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
         const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
         lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
@@ -668,6 +677,13 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel_cp(CellLaunch
   cells_body<K, NT, 0, 0, SP ? 2 : 1>(L, cc.g);
 }
 
+// One mirror-symmetric three-detector point: the coefficients of its positive quadratic form come
+// in the parameters.
+template <int K, int NT>
+__global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel_mp(CellLaunch L, const __grid_constant__ MirrorCoefParam mc) {
+  cells_body<K, NT, 0, 0, 3>(L, mc.g);
+}
+
 // The samples of one round of point 0 in cell order (no evaluation).
 __global__ void draw_cells_kernel(CellLaunch L, DrawOut o, uint32_t n) {
   __shared__ __align__(16) PointC P;
@@ -840,8 +856,19 @@ cudaError_t cells_kl(const CellLaunch &L, int grid, int block, size_t smem, cuda
 
 template <int K, int NT>
 cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,
-                    const CanonCoefParam *cc, int cc_sparse) {
+                    const CanonCoefParam *cc, int cc_sparse, const MirrorCoefParam *mp) {
   if constexpr (kCanonPath<K, NT>) {
+    if (mp && !L.tmarg && !L.learned) {
+      static bool attr = false;
+      if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(cells_kernel_mp<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      cells_kernel_mp<K, NT><<<grid, block, smem, st>>>(L, *mp);
+      return cudaGetLastError();
+    }
     if (cc && !L.tmarg && !L.learned) {
       static bool attr = false;
       if (!attr) {
@@ -859,6 +886,7 @@ cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaS
   }
   (void)cc;
   (void)cc_sparse;
+  (void)mp;
   if (L.tmarg) return L.learned ? cells_kl<K, NT, 1, 1>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 1>(L, grid, block, smem, st);
   return L.learned ? cells_kl<K, NT, 1, 0>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 0>(L, grid, block, smem, st);
 }
@@ -899,8 +927,8 @@ size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block) 
   }
 
 cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,
-                         const CanonCoefParam *cc, int cc_sparse) {
-#define RIFT_C(KK, TT) cells_k<KK, TT>(L, grid, block, smem, st, cc, cc_sparse)
+                         const CanonCoefParam *cc, int cc_sparse, const MirrorCoefParam *mp) {
+#define RIFT_C(KK, TT) cells_k<KK, TT>(L, grid, block, smem, st, cc, cc_sparse, mp)
   RIFT_CELLS_DISPATCH(K, ntap, RIFT_C)
 #undef RIFT_C
   return cudaErrorInvalidValue;

@@ -58,6 +58,11 @@ struct PointC {
                       // modes with zero coefficients (kCanonPath kernels, at least kCanonMinModes)
   int canon_sparse;   // and U vanishes exactly between modes of opposite-sign m, V between modes of
                       // same-sign m (each h_lm on one sign of frequency): those pairs are skipped
+  int mirror;         // the modes satisfy the reflection symmetry checked on the host (every mode's
+                      // mirror (l, -m) present, V_ab = sigma_a U_{mirror(a) b}, U zero between
+                      // opposite-sign m): the quadratic form is the positive form of quad_mirror and
+                      // coef_off holds its coefficients [kMirrorPairs][K] float2 (grouped is set too)
+  uint32_t sigma_neg; // bit j: sigma = -1 for canonical mode j (mirror points)
   float ccoef[RIFT_MAXM][RIFT_MAXTERM];
 };
 
@@ -519,6 +524,175 @@ __device__ __noinline__ float quad_canon(const PointC &P, const float4 *__restri
                                          float s, uint32_t n1) {
   return quad_canon_body<K, SP>(P, G, g, c, s, n1);
 }
+
+// ---------------------------------------------------------------------------
+// Quadratic term of a point with the reflection symmetry of non-precessing modes.  When each mode's
+// mirror (l, -m) is present and the mirror of h_lm is a signed mode of the point,
+// conj(h_a(-f)) = sigma_a h_abar(f) with sigma_a = +-1 (which the host reads off V: V_ab =
+// sigma_a U_{abar b} for every b), the detector strain
+//   h_k = (x/2) sum_a [conj(F) Y_a h_a + F conj(Y_a) conj(h_a(-f))] = x sum_a beta_a h_a,
+//   beta_a = (conj(F) Y_a + sigma_a F conj(Y_abar)) / 2,
+// is a combination of the mode waveforms alone, and <h_k|h_k> = x^2 beta^H U beta, so the
+// |F|^2 conj(Y) U Y + Re(conj(F)^2 Y V Y) of Eq. (def:lnL:Decomposed) equals 2 beta^H U beta: a
+// positive form whose terms do not cancel.  The general form cancels where h_k is small against
+// |F|^2 conj(Y) U Y (nearly edge-on sources, whose strain is nearly linearly polarised): its FP32
+// sums then carry errors of a few ulp of the large terms into a small result.  Here the
+// cancellation happens in the two-term coefficients beta_a, each exact to an ulp of its terms.
+// With Y_a = d_a e^{i m_a phi} and sigma_abar = sigma_a, beta_a = e^{i m_a phi} (Fr p_a + i Fi q_a),
+// p_a = (d_a + sigma_a d_abar) / 2, q_a = (sigma_a d_abar - d_a) / 2, and beta_abar =
+// sigma_a conj(beta_a); with U zero between opposite-sign m and U_{abar bbar} = sigma_a sigma_b
+// conj(U_ab), the negative-m block of beta^H U beta is the conjugate of the positive-m block and
+// the (negative m, m = 0) block that of the (positive m, m = 0) block, so
+//   2 beta^H U beta = sum over pairs a <= b with m_a, m_b >= 0 (78 of them) of
+//                     w_ab Re( e^{i (m_b - m_a) phi} U_ab conj(g_a) g_b ),   g_a = Fr p_a + i Fi q_a,
+//   conj(g_a) g_b = Fr^2 p_a p_b + Fi^2 q_a q_b + i Fr Fi (p_a q_b - q_a p_b),
+// w_ab = 4 (a = b, m > 0), 8 (a < b, both m > 0, or one m = 0), 2 (a = b, m = 0), 4 (a < b, m = 0).
+// Coefficients c_ab = w_ab U_ab per detector: [pair][k] float2, pairs in group order of
+// D = m_b - m_a (-4..4); per group and detector three complex sums X = sum pp c, Y = sum qq c,
+// Z = sum (pq - qp) c, combined once: Re(e^{i D phi} (Fr^2 X + Fi^2 Y + i Fr Fi Z)).
+// ---------------------------------------------------------------------------
+constexpr int kMirrorModes = 12;   // canonical modes with m >= 0
+constexpr int kMirrorPairs = kMirrorModes * (kMirrorModes + 1) / 2;
+
+struct MirrorPairs {
+  int code[kMirrorPairs];   // (D + 4) << 10 | a << 5 | b, canonical a <= b
+};
+
+__host__ __device__ constexpr MirrorPairs make_mirror_pairs() {
+  MirrorPairs t{};
+  int n = 0;
+  for (int D = -4; D <= 4; ++D)
+    for (int a = 0; a < RIFT_MAXM; ++a)
+      for (int b = a; b < RIFT_MAXM; ++b)
+        if (canon_m(a) >= 0 && canon_m(b) >= 0 && canon_m(b) - canon_m(a) == D) t.code[n++] = ((D + 4) << 10) | (a << 5) | b;
+  return t;
+}
+
+constexpr MirrorPairs kMirrorPairTab = make_mirror_pairs();
+constexpr int mirror_pair(int i) { return kMirrorPairTab.code[i]; }
+// weight w_ab of canonical pair (a, b), a <= b, both m >= 0
+constexpr float mirror_weight(int a, int b) {
+  return (canon_m(a) > 0 && canon_m(b) > 0) ? (a == b ? 4.f : 8.f)
+                                            : ((canon_m(a) == 0 && canon_m(b) == 0) ? (a == b ? 2.f : 4.f) : 8.f);
+}
+__constant__ const MirrorPairs kMirrorPairDev = make_mirror_pairs();
+
+// e[D] = e^{i D phi}, D = 0..4.
+template <int K>
+__device__ __forceinline__ float quad_mirror_from_e(const float2 *__restrict__ G, const SampleGeo &g,
+                                                    const float (&d)[RIFT_MAXM], uint32_t sigma_neg,
+                                                    const float2 (&e)[5]) {
+  float p[RIFT_MAXM], q[RIFT_MAXM];
+#pragma unroll
+  for (int j = 0; j < RIFT_MAXM; ++j) {
+    if (canon_m(j) >= 0) {
+      const int jb = canon_index(canon_l(j), -canon_m(j));
+      const float sd = ((sigma_neg >> j) & 1u) ? -d[jb] : d[jb];
+      p[j] = 0.5f * (d[j] + sd);
+      q[j] = 0.5f * (sd - d[j]);
+    } else {
+      p[j] = 0.f;
+      q[j] = 0.f;
+    }
+  }
+  float fr2[K], fi2[K], fri[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    fr2[k] = g.F[k].x * g.F[k].x;
+    fi2[k] = g.F[k].y * g.F[k].y;
+    fri[k] = g.F[k].x * g.F[k].y;
+  }
+  float X[K][2], Y[K][2], Z[K][2];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { X[k][0] = X[k][1] = Y[k][0] = Y[k][1] = Z[k][0] = Z[k][1] = 0.f; }
+  float quad = 0.f;
+#pragma unroll
+  for (int i = 0; i < kMirrorPairs; ++i) {
+    const int code = kMirrorPairDev.code[i];
+    const int D = (code >> 10) - 4;
+    const int a = (code >> 5) & 31, b = code & 31;
+    const float pp = p[a] * p[b], qq = q[a] * q[b];
+    const float r = (a == b) ? 0.f : fmaf(p[a], q[b], -(q[a] * p[b]));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 c = G[i * K + k];
+      X[k][0] = fmaf(pp, c.x, X[k][0]);
+      Y[k][0] = fmaf(qq, c.x, Y[k][0]);
+      if (D != 0) {
+        X[k][1] = fmaf(pp, c.y, X[k][1]);
+        Y[k][1] = fmaf(qq, c.y, Y[k][1]);
+        Z[k][0] = fmaf(r, c.x, Z[k][0]);
+      }
+      if (a != b) Z[k][1] = fmaf(r, c.y, Z[k][1]);   // U_aa is real: diagonal pairs add no Im c
+    }
+    const bool last = (i + 1 == kMirrorPairs) || ((kMirrorPairDev.code[i + 1] >> 10) - 4 != D);
+    if (last) {
+      const float2 ed = e[D < 0 ? -D : D];
+      const float er = ed.x, ei = D < 0 ? -ed.y : ed.y;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float wr = fmaf(fr2[k], X[k][0], fmaf(fi2[k], Y[k][0], -fri[k] * Z[k][1]));
+        if (D == 0) {
+          quad += wr;
+        } else {
+          const float wi = fmaf(fr2[k], X[k][1], fmaf(fi2[k], Y[k][1], fri[k] * Z[k][0]));
+          quad += fmaf(er, wr, -ei * wi);
+        }
+        X[k][0] = X[k][1] = Y[k][0] = Y[k][1] = Z[k][0] = Z[k][1] = 0.f;
+      }
+    }
+  }
+  return quad;
+}
+
+// phi = 2 pi n1 2^-24 on the sampler's lattice: e^{i D phi} = sincospi(D n1 2^-23) reduced exactly.
+template <int K>
+__device__ __forceinline__ float quad_mirror_from_d(const float2 *__restrict__ G, const SampleGeo &g,
+                                                    const float (&d)[RIFT_MAXM], uint32_t sigma_neg, uint32_t n1) {
+  float2 e[5];
+  e[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int D = 1; D <= 4; ++D) {
+    const uint32_t r = ((uint32_t)D * n1) & 0xFFFFFFu;
+    sincospif((float)r * 1.1920928955078125e-07f, &e[D].y, &e[D].x);
+  }
+  return quad_mirror_from_e<K>(G, g, d, sigma_neg, e);
+}
+
+// Any phi (caller draws).
+template <int K>
+__device__ __forceinline__ float quad_mirror_at(const float2 *__restrict__ G, const SampleGeo &g,
+                                                const float (&d)[RIFT_MAXM], uint32_t sigma_neg, float phi) {
+  float2 e[5];
+  e[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int D = 1; D <= 4; ++D) sincosf((float)D * phi, &e[D].y, &e[D].x);
+  return quad_mirror_from_e<K>(G, g, d, sigma_neg, e);
+}
+
+template <int K>
+__device__ __forceinline__ float quad_mirror_body(const PointC &P, const float2 *__restrict__ G, const SampleGeo &g,
+                                                  float c, float s, uint32_t n1) {
+  float cp[9], sp[9];
+  cp[0] = 1.f; sp[0] = 1.f;
+#pragma unroll
+  for (int j = 1; j < 9; ++j) { cp[j] = cp[j - 1] * c; sp[j] = sp[j - 1] * s; }
+  float d[RIFT_MAXM];
+#pragma unroll
+  for (int j = 0; j < RIFT_MAXM; ++j) d[j] = canon_dval(P, j, cp, sp);
+  return quad_mirror_from_d<K>(G, g, d, P.sigma_neg, n1);
+}
+
+template <int K>
+__device__ __noinline__ float quad_mirror(const PointC &P, const float2 *__restrict__ G, const SampleGeo &g, float c,
+                                          float s, uint32_t n1) {
+  return quad_mirror_body<K>(P, G, g, c, s, n1);
+}
+
+// The mirror coefficients of one three-detector point as a kernel parameter (single-point launches).
+struct MirrorCoefParam {
+  float2 g[kMirrorPairs * 3];
+};
 
 // Cell kernels compiled with the grouped form: three detectors and cubic taps (the full-size
 // workload); the host marks a point grouped only for these, so that compile time stays short.

@@ -161,7 +161,7 @@ cudaError_t launch_lnl_tmarg(int K, const PointC *pt_dev, const PointC &ph, cons
 // Cell kernel (mc.cu)
 size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block);
 cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,
-                         const CanonCoefParam *cc = nullptr, int cc_sparse = 0);
+                         const CanonCoefParam *cc = nullptr, int cc_sparse = 0, const MirrorCoefParam *mp = nullptr);
 int cells_blocks_per_sm(int K, int ntap, size_t smem, int block, int tmarg = 0);
 cudaError_t launch_merge_points(const Part *partials, const RoundPt *rp, int n_points, AccState *acc,
                                 cudaStream_t st);
