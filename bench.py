@@ -31,37 +31,61 @@ WORKLOAD = "plain ILE full size: K=3 (H1,L1,V1), M=21 (2<=l<=4), Q +-0.1 s @ 163
 
 
 def flops_per_sample(K: int, M: int, taps: int) -> int:
-    """Algorithmic FP32 flops of one likelihood evaluation (FMA = 2).
+    """Algorithmic FP32 flops of one likelihood evaluation (FMA = 2), the count the roofline
+    fraction is reported on: response and time of flight 60 + 36 K; the harmonics 14 M; the Q
+    term K M (6 + 4 taps + 2) + 4 taps K (tap weights and gather, conj(F Y) Q); the U forms
+    3 M(M+1)/2 (products conj(Y_a) Y_b shared by the detectors) + 4 K M(M+1)/2; the V forms
+    3 M(M+1)/2 + 8 K M(M+1)/2; combine, log weight and log-sum-exp 40.  11,764 at K = 3, M = 21,
+    4 taps."""
+    npair = M * (M + 1) // 2
+    return (60 + 36 * K) + 14 * M + (K * M * (6 + 4 * taps + 2) + 4 * taps * K) + (3 * npair + 4 * K * npair) \
+        + (3 * npair + 8 * K * npair) + 40
 
-    quadratic forms over pairs a <= b: products conj(ya) yb and ya yb (12), then per
-    detector Re(P U) (4) and R V (8); linear term per (k, lm): F conj(Y) (6) and per tap
-    Re(c q) + weight (5); harmonics ~14 M; response + delay ~60 + 40 K; transforms,
-    combine and log-sum-exp ~60."""
+
+def pair_form_flops_per_sample(K: int, M: int, taps: int) -> int:
+    """A recount of the same arithmetic as the pair-form kernel code does it (FMA = 2): per pair
+    a <= b the products conj(ya) yb and ya yb (12), per detector Re(P U) (4) and R V (8); the
+    linear term per (k, lm) F conj(Y) (6) and per tap Re(c q) + weight (5); harmonics ~14 M;
+    response + delay ~60 + 40 K; transforms, combine and log-sum-exp ~60."""
     npair = M * (M + 1) // 2
     quad = npair * (12 + 12 * K) + 10 * K
     lin = K * M * (6 + 5 * taps) + 8 * K
     return quad + lin + 14 * M + 60 + 40 * K + 60
 
 
-def grouped_quad_flops(K: int, sparse: bool) -> int:
-    """Flops the cell kernel executes for the quadratic forms of a point with all 21 (l <= 4) modes
-    (grouped form): per pair one product d_a d_b and per detector two FMAs per part (one for the
-    |m_b - m_a| = 0 group of the U part), one rotation per group and part, the F combination;
-    with `sparse` the pairs that vanish for one-sign modes are skipped."""
+def mirror_quad_flops(K: int) -> int:
+    """Flops the cell kernel executes for the quadratic form of a mirror-symmetric point with all
+    21 (l <= 4) modes (the positive form over the 78 pairs of modes with m >= 0): per pair the
+    products p_a p_b, q_a q_b (2) and p_a q_b - q_a p_b (3, off-diagonal), per detector 2, 3 or 6
+    FMAs (diagonal, same m, other); per group and detector the combination (5 for D = 0, else 13);
+    p, q of the 12 modes (6 each) and |F| products (3 per detector)."""
     ms = [m for l in (2, 3, 4) for m in range(-l, l + 1)]
-    pairs = [(a, b) for a in range(21) for b in range(a, 21)]
-    u = [(a, b) for a, b in pairs if not (sparse and ms[a] * ms[b] < 0)]
-    v = [(a, b) for a, b in pairs if not (sparse and ms[a] * ms[b] > 0)]
-    fl = sum(1 + K * (2 if ms[a] == ms[b] else 4) for a, b in u) + sum(1 + 4 * K for _ in v)
-    fl += len({abs(ms[b] - ms[a]) for a, b in u}) * 4 * K + len({ms[a] + ms[b] for a, b in v}) * 8 * K
-    return fl + 8 * K
+    P = [j for j in range(21) if ms[j] >= 0]
+    fl, groups = 0, set()
+    for ia, a in enumerate(P):
+        for b in P[ia:]:
+            D = ms[b] - ms[a]
+            groups.add(D)
+            fl += (2 + 4 * K) if a == b else ((5 + 6 * K) if D == 0 else (5 + 12 * K))
+    return fl + K * (5 + 13 * (len(groups) - 1)) + 12 * 6 + 3 * K
 
 
-def executed_flops_per_sample(K: int, M: int, taps: int, sparse: bool) -> int:
-    """flops_per_sample with the pair-form quadratic forms replaced by the grouped form the
-    kernel runs for a full 21-mode point."""
+def executed_flops_per_sample(K: int, M: int, taps: int) -> int:
+    """pair_form_flops_per_sample with the pair-form quadratic forms replaced by the positive
+    form the cell kernel runs for the benchmark's point."""
     npair = M * (M + 1) // 2
-    return flops_per_sample(K, M, taps) - (npair * (12 + 12 * K) + 10 * K) + grouped_quad_flops(K, sparse)
+    return pair_form_flops_per_sample(K, M, taps) - (npair * (12 + 12 * K) + 10 * K) + mirror_quad_flops(K)
+
+
+def mdn_forward_flops(P: int) -> int:
+    """FP32 flops of the network forward pass for P points: 64 -> 256 -> 256 -> 88 (FMA = 2), plus
+    about 20 flops per GELU."""
+    return P * (2 * (64 * 256 + 256 * 256 + 256 * 88) + 20 * 512)
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 FMA issue peak: 128 lanes per SM x 2 flop per FMA x SMs x SM clock."""
+    return 2 * 128 * sms * mhz * 1e6 / 1e12
 
 
 def measured_peaks():
@@ -213,18 +237,21 @@ def _oracle_chunk(args):
 
 
 class OraclePool:
-    """The FP64 oracle on the host cores: one spawned worker process per core, each holding the
-    full-size point; timed on bounded samples of the same workload."""
+    """The FP64 oracle on the host cores: one spawned worker process per core (single-threaded
+    numerics), each holding the full-size point; timed on bounded samples of the same workload."""
 
-    def __init__(self):
+    def __init__(self, cores=None):
         import multiprocessing as mp
-        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        all_cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        self.cores = cores or all_cores
         self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init)
         cal = self.pool.map(_oracle_chunk, [(31, i * 2000, 2000) for i in range(self.cores)])
         self.per_sample = max(c[0] / c[1] for c in cal)
 
     def run(self, target_s: float, start: int = 0):
-        chunk = 20000
+        chunk = 20000 if target_s >= 2.0 else 5000
         n_chunks = max(self.cores, int(target_s / (self.per_sample * chunk)) * self.cores)
         t0 = time.perf_counter()
         res = self.pool.map(_oracle_chunk, [(31, start + i * chunk, chunk) for i in range(n_chunks)])
@@ -237,17 +264,38 @@ class OraclePool:
         self.pool.join()
 
 
-def cpu_oracle_throughput(target_s: float = 12.0):
+def cpu_oracle_throughput(target_s: float = 12.0, single_s: float = 4.0):
+    """The oracle on every host core, then on one core (one worker process)."""
     op = OraclePool()
     v, n, wall = op.run(target_s)
     op.close()
-    return v, op.cores, f"{n} prior samples of the full-size point (indices 0..{n - 1}, seed 31)", wall
+    one = OraclePool(cores=1)
+    v1, n1, wall1 = one.run(single_s)
+    one.close()
+    return {"value": v, "unit": "evals/s", "cores": op.cores, "kind": "oracle",
+            "sample": f"{n} prior samples of the full-size point (indices 0..{n - 1}, seed 31)",
+            "wall_s": round(wall, 2),
+            "single_core": {"value": v1, "unit": "evals/s", "cores": 1,
+                            "sample": f"{n1} prior samples of the same round (indices 0..{n1 - 1})",
+                            "wall_s": round(wall1, 2)}}
+
+
+def _oracle_round(args):
+    """The oracle's log-sum-exp state over samples [a, b) of a stratified round of n samples."""
+    seed, S, n, a, b = args
+    import numpy as np
+    from oracle import mc
+    pt = _ORACLE_PT
+    th, _, lq = mc.draw(seed, 0, 0, np.arange(a, b, dtype=np.uint64), mc.Prior(pt["t_lo"], pt["t_hi"]), None, S, n)
+    acc = mc.Accum.of(mc.lnL_samples(pt, th) + lq)
+    return acc.m, acc.s1, acc.s2, acc.n
 
 
 def precision_check(rift, pt, opts, tune):
-    """Per-sample lnL of the benchmark's own launch (same point, seed and launch shape) against the
-    FP64 oracle on the host: 2000 random draws and the 300 of highest weight, with the tolerance of
-    the parity tests, 1e-3 max(1, <h|h>/900); and lnL_marg restricted to the top 300 on both sides."""
+    """The benchmark's own launch (same point, seed and launch shape) against the FP64 oracle on the
+    host: lnL_marg of the whole round (the oracle evaluates every sample, on all host cores), and
+    per-sample lnL on 20000 random draws and the 1000 of highest weight with the tolerance of the
+    parity tests, 1e-3 max(1, <h|h>/900)."""
     import numpy as np
     import torch
     from oracle import likelihood as OL
@@ -260,21 +308,36 @@ def precision_check(rift, pt, opts, tune):
     rift.rift_ile_destroy(h)
     got = dbg.cpu().numpy().astype(np.float64)
     del dbg
-    top = np.argsort(got)[-300:]
+    S = tuple(res["strata"])
+    op = OraclePool()
+    t0 = time.perf_counter()
+    edges = np.linspace(0, n, 8 * op.cores + 1).astype(np.int64)
+    parts = op.pool.map(_oracle_round, [(opts["seed"], S, n, int(edges[i]), int(edges[i + 1]))
+                                        for i in range(len(edges) - 1)])
+    op.close()
+    acc = mc.Accum()
+    for m, s1, s2, c in parts:
+        acc = acc.merge(mc.Accum(m, s1, s2, c))
+    ref = acc.result()
+    t_full = time.perf_counter() - t0
+    top = np.argsort(got)[-1000:]
     r = np.random.default_rng(7)
-    idx = np.unique(np.concatenate([top, r.integers(0, n, 2000)])).astype(np.uint64)
-    th, _, lq = mc.draw(opts["seed"], 0, 0, idx, mc.Prior(pt["t_lo"], pt["t_hi"]), None, tuple(res["strata"]), n)
+    idx = np.unique(np.concatenate([top, r.integers(0, n, 20000)])).astype(np.uint64)
+    th, _, lq = mc.draw(opts["seed"], 0, 0, idx, mc.Prior(pt["t_lo"], pt["t_hi"]), None, S, n)
     want = mc.lnL_samples(pt, th) + lq
     th64 = dict(ra=th["ra"], dec=np.arcsin(th["sindec"]), t=th["t"], psi=th["psi"], phi=th["phi"],
                 incl=np.arccos(th["cosi"]), dist=th["dist"])
     hh = -2.0 * OL.lnL_factorised(dict(pt, Q=np.zeros_like(pt["Q"])), **th64)
     tol = 1e-3 * np.maximum(1.0, hh / 900.0)
     err = np.abs(got[idx.astype(np.int64)] - want)
-    sel = np.isin(idx.astype(np.int64), top)
-    a, b = mc.Accum.of(got[idx.astype(np.int64)][sel]).result()[0], mc.Accum.of(want[sel]).result()[0]
-    return {"samples": int(idx.size), "max_abs_dlnL": float(err.max()), "max_err_over_tol": float((err / tol).max()),
-            "mean_err_over_tol": float((err / tol).mean()), "dlnL_marg_top300": float(abs(a - b)),
-            "tolerance": "1e-3 max(1, <h|h>/900) per sample (FP64 oracle, same draws)"}
+    le30 = hh <= 900.0
+    return {"samples": int(idx.size), "max_err_over_tol": float((err / tol).max()),
+            "mean_err_over_tol": float((err / tol).mean()),
+            "max_abs_dlnL_template_snr_le_30": float(err[le30].max()) if le30.any() else None,
+            "dlnL_marg": float(res["lnL_marg"] - ref[0]), "lnL_marg_oracle": ref[0], "n_eff_oracle": ref[1],
+            "oracle_full_round_s": round(t_full, 2), "oracle_samples": int(acc.n),
+            "tolerance": "per sample 1e-3 max(1, <h|h>/900) (1e-3 absolute at template SNR <= 30); lnL_marg "
+                         "1e-4; FP64 oracle on the same draws"}
 
 
 # ---------------------------------------------------------------- GPU leg
@@ -333,13 +396,12 @@ def run_gpu(args, world, rank, local):
 
     # roofline of the likelihood kernel (FP32 ALU bound)
     taps = 4
-    fl = flops_per_sample(K, M, taps) * N_SAMPLES
     kmean = statistics.mean(kern_ms)
-    achieved = fl / (kmean * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     f_mhz = clk["sm_mhz"] or 1455.0
-    peak = 2 * 128 * sms * f_mhz * 1e6 / 1e12
+    peak = fp32_peak_tflops(sms, f_mhz)
+    achieved = flops_per_sample(K, M, taps) * N_SAMPLES / (kmean * 1e-3) / 1e12
 
     # end to end through the public API with host buffers: create (host Q/U/V -> device)
     # + marginalise + result back, every step
@@ -367,14 +429,12 @@ def run_gpu(args, world, rank, local):
     cpu = None
     precision = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, sample, wall = cpu_oracle_throughput(args.cpu_seconds)
-        cpu = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
-               "wall_s": round(wall, 2)}
+        cpu = cpu_oracle_throughput(args.cpu_seconds)
         precision = precision_check(rift, pt, opts, tune)
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = run_extras(args, rift, W)
+        extras = run_extras(args, rift, W, peak)
 
     r0 = results[-1]
     out = {
@@ -390,20 +450,21 @@ def run_gpu(args, world, rank, local):
         "vs_baseline": None,
         "dtype": "f32 (double-float time index; f64 accumulators)",
         "data": "synthetic: seeded chirp-like modes, analytic aLIGO PSD, Gaussian noise; samples drawn on device",
-        "config": {"workload": WORKLOAD, "global_batch": N_SAMPLES * world, "samples_per_point": N_SAMPLES,
-                   "points": world, "parallelism": f"independent points x{world}", "l2": "flushed between steps"},
+        "config": bench_config(world),
         "lnL_marg_per_s": world / (ms_per_step * 1e-3),
         "lnL_marg": r0["lnL_marg"], "n_eff": r0["n_eff"], "strata": list(r0["strata"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(),
-                     "kernel": "cells_kernel_cp<3,4,1> (stratified cell: draw + staged Q window + likelihood with the "
-                               "grouped quadratic form, coefficients in the parameter bank + log-sum-exp)",
+                     "kernel": "cells_kernel_mp<3,4> (stratified cell: draw + staged Q window + likelihood with the "
+                               "positive quadratic form of a mirror-symmetric point, coefficients in the parameter "
+                               "bank + log-sum-exp)",
                      "kernel_ms": kmean, "flops_per_sample": flops_per_sample(K, M, taps),
-                     "executed_flops_per_sample": executed_flops_per_sample(K, M, taps, True),
-                     "executed_frac": executed_flops_per_sample(K, M, taps, True) * N_SAMPLES / (kmean * 1e-3) / 1e12
-                     / peak,
+                     "pair_form_flops_per_sample": pair_form_flops_per_sample(K, M, taps),
+                     "pair_form_frac": pair_form_flops_per_sample(K, M, taps) * N_SAMPLES / (kmean * 1e-3) / 1e12 / peak,
+                     "executed_flops_per_sample": executed_flops_per_sample(K, M, taps),
+                     "executed_frac": executed_flops_per_sample(K, M, taps) * N_SAMPLES / (kmean * 1e-3) / 1e12 / peak,
                      "peak_basis": f"FP32 FMA: 128 lanes/SM x {sms} SMs x 2 flop x median SM clock {f_mhz} MHz "
-                                   "sampled during the run"},
+                                   "sampled during the run (no FP32 figure in the measured peaks)"},
         "gpu_launches": launches,
         "autotune": tune,
         "clocks": clk,
@@ -432,7 +493,7 @@ def make_points(specs, seed0):
         return pool.map(_make_point, [(s, seed0 + i) for i, s in enumerate(specs)], chunksize=4)
 
 
-def run_extras(args, rift, W):
+def run_extras(args, rift, W, peak):
     """The batched workload (many points, uneven mode counts and Q lengths, adaptive rounds,
     one graph-replayed launch sequence) against sequential per-point runs, and the learned
     proposal against the prior at equal evaluations."""
@@ -499,29 +560,90 @@ def run_extras(args, rift, W):
         "median_n_eff_prior": float(np.median([p["n_eff"] for p in prior])),
         "median_n_eff_learned": float(np.median([l["n_eff"] for l in learned])),
         "median_abs_dlnL_marg": float(np.median(dl)), "frac_within_0.05": float(np.mean(dl <= 0.05))}
-    out["time_marginalised"] = run_tmarg(rift, W, pts[:16])
-    out["quv"] = run_quv(rift, W)
+    out["time_marginalised"] = run_tmarg(rift, W, pts[:16], peak)
+    out["quv"] = run_quv(rift, W, peak)
+    out["mdn"] = run_mdn(rift, peak)
     return out
 
 
-def run_quv(rift, W):
-    """Eq. (QUV) on the device for the full-size point (direct sums over the band: no FFT), the
-    wall time of the C call including its uploads and downloads, after one warm call."""
+def run_quv(rift, W, peak):
+    """Eq. (QUV) on the device for the full-size point (direct sums over the band: no FFT): the wall
+    time of the C call (host preparation, uploads, kernels, downloads) and each kernel's CUDA-event
+    time, after one warm call."""
     pt = W.make_point(W.cfg_full(), point_seed(0))
     rift.rift_quv(pt)
-    times = []
+    times, qms, uvms = [], [], []
     for _ in range(3):
         t0 = time.perf_counter()
         rift.rift_quv(pt)
         times.append(time.perf_counter() - t0)
+        a, b = rift.rift_quv_kernel_ms()
+        qms.append(a)
+        uvms.append(b)
     K, M, T = pt["Q"].shape
     nb = int((pt["weight"] != 0).any(axis=0).sum())
+    q_flops = 8 * K * M * T * nb          # one complex multiply-add (4 FMA) per (k, mode, time, bin)
+    uv_flops = 2 * 8 * K * M * M * nb     # U and V: one complex multiply-add each per (k, a, b, bin)
+    q_ms, uv_ms = statistics.median(qms), statistics.median(uvms)
     return {"workload": f"K={K}, M={M}, n_t={T}, {nb} band bins of {len(pt['freqs'])}",
-            "ms_per_point": 1e3 * statistics.median(times),
-            "complex_macs": K * M * T * nb + 2 * K * M * M * nb}
+            "ms_per_point": 1e3 * statistics.median(times), "q_kernel_ms": q_ms, "uv_kernel_ms": uv_ms,
+            "complex_macs": K * M * T * nb + 2 * K * M * M * nb,
+            "roofline_q": {"bound": "alu", "kernel": "quv_q_kernel", "achieved": q_flops / (q_ms * 1e-3) / 1e12,
+                           "peak": peak, "unit": "TFLOP/s", "frac": q_flops / (q_ms * 1e-3) / 1e12 / peak,
+                           "flops": q_flops, "traffic": None},
+            "roofline_uv": {"bound": "alu", "kernel": "quv_uv_kernel", "achieved": uv_flops / (uv_ms * 1e-3) / 1e12,
+                            "peak": peak, "unit": "TFLOP/s", "frac": uv_flops / (uv_ms * 1e-3) / 1e12 / peak,
+                            "flops": uv_flops, "traffic": None}}
 
 
-def run_tmarg(rift, W, pts):
+def run_mdn(rift, peak):
+    """The network's forward kernel on 4096 points (CUDA events on the stream it runs on, the
+    default stream), and one training step on 256 points with 64 samples each (forward, loss,
+    backward, Adam)."""
+    import numpy as np
+    import torch
+    m = rift.rift_mdn_create(11)
+    P = 4096
+    g = torch.Generator(device="cuda").manual_seed(5)
+    S = torch.randn((P, 64), device="cuda", generator=g)
+    for _ in range(3):
+        rift.rift_mdn_forward(m, S)
+    torch.cuda.synchronize()
+    fw = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rift.rift_mdn_forward(m, S)
+        e1.record()
+        e1.synchronize()
+        fw.append(e0.elapsed_time(e1))
+    B, H = 256, 64
+    th = torch.rand((B, H, 5), device="cuda", generator=g) * 0.8 + 0.1
+    w = torch.full((B, H), 1.0 / H, device="cuda")
+    box = torch.as_tensor(np.tile(np.array([[0, 0, 0, 0, 0], [1, 1, 1, 1, 1]], dtype=np.float32), (B, 1, 1)),
+                          device="cuda")
+    rift.rift_mdn_train(m, S[:B], th, w, box, steps=3, batch=B, lr=1e-4)
+    torch.cuda.synchronize()
+    steps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rift.rift_mdn_train(m, S[:B], th, w, box, steps=steps, batch=B, lr=1e-4)
+    e1.record()
+    e1.synchronize()
+    tr = e0.elapsed_time(e1) / steps
+    rift.rift_mdn_destroy(m)
+    ms = statistics.median(fw)
+    fl = mdn_forward_flops(P)
+    return {"workload": f"forward on {P} points; training steps of {B} points x {H} samples",
+            "forward_ms": ms, "train_step_ms": tr,
+            "roofline_forward": {"bound": "alu", "kernel": "mdn_forward_kernel", "achieved": fl / (ms * 1e-3) / 1e12,
+                                 "peak": peak, "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / 1e12 / peak,
+                                 "flops": fl, "traffic": None,
+                                 "note": "BF16 weights on CUDA cores, FP32 accumulation"},
+            "train_step_note": "the step's time includes the per-step loss read back to the host"}
+
+
+def run_tmarg(rift, W, pts, peak):
     """Eq. (lnL:tmarg): the event time integrated by quadrature for each draw.  Throughput on the
     full-size point (draws/s and likelihood points/s, CUDA events around the kernel launch) and,
     on batched points, n_eff and lnL_marg against the sampled-time estimator at equal time."""
@@ -556,35 +678,49 @@ def run_tmarg(rift, W, pts):
                     "sampled-time evaluations per point",
         "kernel_ms": ms, "draws_per_s": n / (ms * 1e-3), "lnL_points_per_s": n * J / (ms * 1e-3),
         "tflops": flops / (ms * 1e-3) / 1e12, "flops_per_draw": flops / n,
+        "roofline": {"bound": "alu", "kernel": "cells_kernel<3,4,0,1>", "achieved": flops / (ms * 1e-3) / 1e12,
+                     "peak": peak, "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / peak, "traffic": None},
         "median_n_eff_tmarg": float(np.median(nt)), "median_n_eff_sampled_t": float(np.median(ns)),
         "median_lnL_marg_tmarg_minus_sampled": float(np.median(dl))}
 
 
 def run_reference(args, world, rank):
-    """The FP64 oracle timed as the reference arm on the host cores (rank 0 only)."""
+    """The FP64 oracle timed as the reference arm on the host cores (rank 0 only): each step draws
+    and evaluates a bounded sample of the same prior round (as many samples as the step's time
+    budget allows), and the line reports the samples it ran and the time it took."""
     if rank != 0:
         return
     op = OraclePool()
-    per_step, desc = [], None
+    per_step = max(1.0, min(args.ref_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    walls, ns, start = [], [], 0
     for s in range(args.warmup + args.steps):
-        v, n, wall = op.run(args.ref_seconds)
+        v, n, wall = op.run(per_step, start=start)
+        start += n
         if s >= args.warmup:
-            per_step.append(v)
-            desc = f"{n} prior samples of the full-size point per step (seed 31), {op.cores} worker processes"
+            walls.append(wall)
+            ns.append(n)
     op.close()
-    v = statistics.mean(per_step)
+    v = sum(ns) / sum(walls)
+    desc = (f"{statistics.mean(ns):.0f} prior samples of the full-size point per step (seed 31, consecutive "
+            f"indices), {op.cores} worker processes, about {per_step:.1f} s per step")
     out = {
         "impl": "reference",
         "metric": "extrinsic lnL evals/sec (and lnL_marg/sec) per GB300",
         "value": v, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": N_SAMPLES / v * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (same workload generator)",
-        "config": {"workload": WORKLOAD, "global_batch": N_SAMPLES, "points": 1,
-                   "parallelism": "host cores (spawned processes)"},
+        "ms_per_step": 1e3 * statistics.mean(walls), "samples_per_step": statistics.mean(ns),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic: seeded chirp-like modes, analytic aLIGO PSD, Gaussian noise",
+        "config": bench_config(1),
         "cpu_baseline": {"value": v, "unit": "evals/s", "cores": op.cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
+
+
+def bench_config(world):
+    """The workload the benchmark line is quoted on."""
+    return {"workload": WORKLOAD, "global_batch": N_SAMPLES * world, "samples_per_point": N_SAMPLES,
+            "points": world, "parallelism": f"independent points x{world}", "l2": "flushed between steps"}
 
 
 def main():

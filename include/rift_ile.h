@@ -167,6 +167,9 @@ typedef struct {
  */
 rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V);
 const char *rift_quv_last_error(void);
+/* Device time (ms, CUDA events on the call's stream) of the two kernels of the last successful
+ * rift_quv call of the calling thread: out[0] the Q sums, out[1] the U and V sums (host array of 2). */
+void rift_quv_kernel_ms(double out[2]);
 
 /* rift_quv followed by rift_ile_create on the result (U made exactly Hermitian and V exactly
  * symmetric by averaging each pair of transposed elements): a handle built from frequency-domain
@@ -408,6 +411,24 @@ void rift_cache_counters(unsigned long long out[4]);
 #define RIFT_STATIC_MAX_PRIOR_ROUND 67108864
 #define RIFT_STATIC_SCRATCH_BYTES 3552512
 rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_opts *opts, rift_mc_result *res);
+
+/*
+ * Detector-frame description of sources, for building physical injections (Sec. II.A: the
+ * response F_k = F_+ - i F_x of detector k to a source at (ra, dec, psi), its arrival time
+ * t_k = t + delay_k, delay_k = -(x_k . n)/c, and the harmonics -2Y_lm(incl, phi)): for source s
+ * and detector k
+ *   coef[s][k][a] = (D_ref / D) conj(F_k) Y_{l_a m_a}(incl, phi),   tk[s][k] = t + delay_k,
+ * so that the source's strain in detector k is Re sum_a coef[s][k][a] h_a(t - tk[s][k]) (times
+ * relative to t_ref_gps, at which GMST is taken).  Evaluated on the device with the likelihood
+ * kernels' own response, time-of-flight and harmonic arithmetic (FP32, times in double-float).
+ * Host arrays: det_tensor [K][3][3], det_pos [K][3] (m), lm [M][2]; src [n][7] float64 rows
+ * (ra, dec, t, psi, phi, incl, D in Mpc, D > 0); outputs coef [n][K][M] complex128 (modes in the
+ * caller's order) and tk [n][K] float64.  Synchronous on the legacy default stream; temporary
+ * device buffers are allocated and freed inside.  RIFT_EINVAL for bad sizes, modes or values.
+ */
+rift_status rift_source_frame(int n_det, const double *det_tensor, const double *det_pos, int n_modes,
+                              const int *lm, double t_ref_gps, double d_ref_mpc, size_t n, const double *src,
+                              double *coef, double *tk);
 
 /*
  * Launch shape of the Monte Carlo kernels: samples per stratification cell (sets the strata

@@ -102,6 +102,8 @@ def _load():
         "rift_ile_check": (I, [P]),
         "rift_quv": (I, [P, P, P, P]),
         "rift_quv_last_error": (C.c_char_p, []),
+        "rift_quv_kernel_ms": (None, [P]),
+        "rift_source_frame": (I, [I, P, P, I, P, D, D, S, P, P, P]),
         "rift_ile_create_fd": (I, [P, C.POINTER(P)]),
         "rift_ile_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
         "rift_ile_batch_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
@@ -234,6 +236,30 @@ def rift_quv(pt, stream=None):
     if st != 0:
         raise RiftError(st, (_lib.rift_quv_last_error() or b"").decode())
     return Q, U, V
+
+
+def rift_source_frame(det_tensor, det_pos, lm, t_ref_gps, d_ref_mpc, src):
+    """Detector-frame coefficients and arrival times of sources: src (n, 7) rows (ra, dec, t, psi,
+    phi, incl, D) -> coef (n, K, M) complex128 = (D_ref/D) conj(F_k) Y_lm, tk (n, K) = t + delay_k."""
+    tens = np.ascontiguousarray(det_tensor, dtype=np.float64)
+    pos = np.ascontiguousarray(det_pos, dtype=np.float64)
+    modes = np.ascontiguousarray(np.asarray(lm).reshape(-1, 2), dtype=np.int32)
+    s = np.ascontiguousarray(np.asarray(src, dtype=np.float64).reshape(-1, 7))
+    n, K, M = s.shape[0], tens.shape[0], modes.shape[0]
+    coef = np.empty((n, K, M), dtype=np.complex128)
+    tk = np.empty((n, K), dtype=np.float64)
+    st = _lib.rift_source_frame(K, tens.ctypes.data, pos.ctypes.data, M, modes.ctypes.data, float(t_ref_gps),
+                                float(d_ref_mpc), n, s.ctypes.data, coef.ctypes.data, tk.ctypes.data)
+    if st != 0:
+        raise RiftError(st, "rift_source_frame failed")
+    return coef, tk
+
+
+def rift_quv_kernel_ms():
+    """Device time (ms) of the Q kernel and of the U/V kernel of this thread's last rift_quv call."""
+    out = (C.c_double * 2)()
+    _lib.rift_quv_kernel_ms(out)
+    return float(out[0]), float(out[1])
 
 
 def rift_ile_create_fd(pt, interp=3, stream=None):

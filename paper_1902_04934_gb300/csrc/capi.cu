@@ -1470,6 +1470,91 @@ rift_status rift_ile_posterior(rift_ile *h, const rift_mc_opts *o, int H, float 
 }
 
 
+rift_status rift_source_frame(int n_det, const double *det_tensor, const double *det_pos, int n_modes, const int *lm,
+                              double t_ref_gps, double d_ref_mpc, size_t n, const double *src, double *coef,
+                              double *tk) {
+  const int K = n_det, M = n_modes;
+  if (K < 1 || K > RIFT_MAX_DET || M < 1 || M > RIFT_MAX_MODES) return RIFT_EINVAL;
+  if (!det_tensor || !det_pos || !lm || !(d_ref_mpc > 0) || !std::isfinite(t_ref_gps)) return RIFT_EINVAL;
+  if (n == 0) return RIFT_OK;
+  if (!src || !coef || !tk) return RIFT_EINVAL;
+  // the detectors and modes as the likelihood kernels hold them, with times in seconds
+  PointC c;
+  std::memset(&c, 0, sizeof(c));
+  c.K = K; c.M = M; c.fs = 1.f; c.dref = (float)d_ref_mpc;
+  split(gmst_rad(t_ref_gps) / (2.0 * kPi), c.g_hi, c.g_lo);
+  int perm[RIFT_MAX_MODES];
+  for (int a = 0; a < M; ++a) {
+    const int l = lm[2 * a], m = lm[2 * a + 1];
+    if (l < 2 || l > 4 || m < -l || m > l) return RIFT_EINVAL;
+    for (int b = 0; b < a; ++b)
+      if (lm[2 * b] == l && lm[2 * b + 1] == m) return RIFT_EINVAL;
+    perm[a] = a;
+  }
+  std::sort(perm, perm + M, [&](int x, int y) {
+    return lm[2 * x] != lm[2 * y] ? lm[2 * x] < lm[2 * y] : lm[2 * x + 1] < lm[2 * y + 1];
+  });
+  for (int a = 0; a < M; ++a) {
+    swsh_terms(lm[2 * perm[a]], lm[2 * perm[a] + 1], c.mode[a]);
+    c.canon_mask |= 1u << canon_index(c.mode[a].l, c.mode[a].m);
+  }
+  for (int j = 0; j < RIFT_MAXM; ++j) {
+    ModeC t;
+    swsh_terms(canon_l(j), canon_m(j), t);
+    for (int r = 0; r < t.nterm; ++r) c.ccoef[j][r] = t.coef[r];
+  }
+  for (int k = 0; k < K; ++k) {
+    const double *t = det_tensor + 9 * k;
+    DetC &D = c.det[k];
+    D.d[0] = (float)t[0]; D.d[1] = (float)t[1]; D.d[2] = (float)t[2];
+    D.d[3] = (float)t[4]; D.d[4] = (float)t[5]; D.d[5] = (float)t[8];
+    for (int i = 0; i < 3; ++i) split(det_pos[3 * k + i] / kC, D.P[i], D.Plo[i]);
+  }
+  std::vector<float> in(8 * n);
+  for (size_t i = 0; i < n; ++i) {
+    const double *q = src + 7 * i;
+    for (int j = 0; j < 7; ++j)
+      if (!std::isfinite(q[j])) return RIFT_EINVAL;
+    if (!(q[6] > 0)) return RIFT_EINVAL;
+    in[i] = (float)q[0];
+    in[n + i] = (float)q[1];
+    split(q[2], in[2 * n + i], in[3 * n + i]);
+    in[4 * n + i] = (float)q[3];
+    in[5 * n + i] = (float)q[4];
+    in[6 * n + i] = (float)q[5];
+    in[7 * n + i] = (float)q[6];
+  }
+  PointC *pd = nullptr;
+  float *sd = nullptr;
+  float2 *cd = nullptr, *td = nullptr;
+  std::vector<float2> cf(n * K * M), tf(n * K);
+  cudaError_t e;
+  if ((e = cudaMalloc(&pd, sizeof(PointC))) == cudaSuccess && (e = cudaMalloc(&sd, sizeof(float) * in.size())) == cudaSuccess &&
+      (e = cudaMalloc(&cd, sizeof(float2) * cf.size())) == cudaSuccess &&
+      (e = cudaMalloc(&td, sizeof(float2) * tf.size())) == cudaSuccess &&
+      (e = cudaMemcpy(pd, &c, sizeof(PointC), cudaMemcpyHostToDevice)) == cudaSuccess &&
+      (e = cudaMemcpy(sd, in.data(), sizeof(float) * in.size(), cudaMemcpyHostToDevice)) == cudaSuccess &&
+      (e = launch_source_frame(K, pd, n, sd, cd, td, nullptr)) == cudaSuccess &&
+      (e = cudaMemcpy(cf.data(), cd, sizeof(float2) * cf.size(), cudaMemcpyDeviceToHost)) == cudaSuccess)
+    e = cudaMemcpy(tf.data(), td, sizeof(float2) * tf.size(), cudaMemcpyDeviceToHost);
+  cudaFree(pd);
+  cudaFree(sd);
+  cudaFree(cd);
+  cudaFree(td);
+  if (e != cudaSuccess) return (e == cudaErrorMemoryAllocation) ? RIFT_ENOMEM : RIFT_ECUDA;
+  for (size_t i = 0; i < n; ++i)
+    for (int k = 0; k < K; ++k) {
+      tk[i * K + k] = (double)tf[i * K + k].x + (double)tf[i * K + k].y;
+      for (int a = 0; a < M; ++a) {   // stored (canonical) order -> the caller's order
+        const float2 v = cf[(i * K + k) * M + a];
+        double *o = coef + 2 * ((i * K + k) * M + perm[a]);
+        o[0] = v.x;
+        o[1] = v.y;
+      }
+    }
+  return RIFT_OK;
+}
+
 rift_status rift_ile_get_tune(const rift_ile *h, rift_tune *out) {
   if (!h || !out) return RIFT_EINVAL;
   out->cell_samples = h->cell_target;

@@ -262,7 +262,69 @@ cudaError_t tdraw_k(const PointC *pts, const float2 *qa, const float4 *ca, const
 
 int taps_of(int interp) { return interp == 3 ? 4 : (interp == 1 ? 2 : 1); }
 
+// Detector-frame coefficients and arrival times of sources (physical injections): for source i,
+// coef[i][k][a] = x conj(F_k) Y_a (stored modes a, canonical order) and tk[i][k] = t + delay_k as
+// (hi, lo) of a double-float, with the response, time of flight and harmonics of the likelihood
+// kernels.  P holds the detectors with P.det[k].P = x_k / c in seconds (a sampling rate of 1), so
+// the double-float "index" of response_delay is a time.  src: [8][n] = ra, dec, t (hi, lo), psi,
+// phi, incl, D.
+template <int K>
+__global__ void __launch_bounds__(128) source_frame_kernel(const PointC *__restrict__ pts, size_t n,
+                                                            const float *__restrict__ src, float2 *__restrict__ coef,
+                                                            float2 *__restrict__ tk) {
+  __shared__ __align__(16) PointC P;
+  load_point(pts, &P);
+  __syncthreads();
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float r = src[i], dec = src[n + i], psi = src[4 * n + i], phi = src[5 * n + i], incl = src[6 * n + i];
+  const float ph = __fmul_rn(r, 0.15915494309189535f);
+  const float pl = __fmaf_rn(r, 0.15915494309189535f, -ph) + r * 6.4206382e-09f;
+  const df v = df_add(fast_two_sum(ph, pl), df{-P.g_hi, -P.g_lo});
+  float s0, c0;
+  sincospif(2.f * v.hi, &s0, &c0);
+  const float ares = kTwoPi * v.lo;
+  const float cA = c0 - s0 * ares, sA = s0 + c0 * ares;
+  float sdh, cd, s2p, c2p;
+  sincosf(dec, &sdh, &cd);
+  sincosf(2.f * psi, &s2p, &c2p);
+  df base[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) base[k] = df{src[2 * n + i], src[3 * n + i]};
+  SampleGeo g;
+  response_delay<K>(P, cA, sA, df{sdh, 0.f}, cd, c2p, s2p, g, base);
+  const float x = __fdiv_rn(P.dref, src[7 * n + i]);
+  float sphi, cphi, ch, sh;
+  sincosf(phi, &sphi, &cphi);
+  sincosf(0.5f * incl, &sh, &ch);
+  float2 Y[RIFT_MAXM];
+  swsh_canonical(P, ch, sh, cphi, sphi, Y, 1);
+  for (int k = 0; k < K; ++k) {
+    const float2 F = g.F[k];
+    for (int a = 0; a < P.M; ++a) {
+      // x conj(F) Y
+      const float2 y = Y[a];
+      coef[(i * K + k) * P.M + a] = make_float2(x * (F.x * y.x + F.y * y.y), x * (F.x * y.y - F.y * y.x));
+    }
+    tk[i * K + k] = make_float2(g.s[k].hi, g.s[k].lo);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_source_frame(int K, const PointC *pt_dev, size_t n, const float *src, float2 *coef, float2 *tk,
+                                cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 127) / 128);
+  switch (K) {
+    case 1: source_frame_kernel<1><<<grid, 128, 0, st>>>(pt_dev, n, src, coef, tk); break;
+    case 2: source_frame_kernel<2><<<grid, 128, 0, st>>>(pt_dev, n, src, coef, tk); break;
+    case 3: source_frame_kernel<3><<<grid, 128, 0, st>>>(pt_dev, n, src, coef, tk); break;
+    case 4: source_frame_kernel<4><<<grid, 128, 0, st>>>(pt_dev, n, src, coef, tk); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 size_t rift_point_smem_bytes(int K, int npair, int nb, int block, int M) {
   size_t off = (sizeof(PointC) + 15) & ~size_t(15);

@@ -119,6 +119,7 @@ __global__ void quv_uv_kernel(const float2 *__restrict__ H, const float2 *__rest
 double unit_scale(double vmax) { return vmax > 0.0 && std::isfinite(vmax) ? std::ldexp(1.0, -std::ilogb(vmax)) : 1.0; }
 
 thread_local std::string g_quv_err;
+thread_local double g_quv_ms[2] = {0.0, 0.0};   // quv_q_kernel, quv_uv_kernel of the last call
 
 rift_status quv_fail(rift_status s, const std::string &m) {
   g_quv_err = m;
@@ -135,6 +136,12 @@ struct DevBuf {
 extern "C" {
 
 const char *rift_quv_last_error(void) { return g_quv_err.c_str(); }
+
+void rift_quv_kernel_ms(double out[2]) {
+  if (!out) return;
+  out[0] = g_quv_ms[0];
+  out[1] = g_quv_ms[1];
+}
 
 rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V) {
   if (!d || !Q || !U || !V) return quv_fail(RIFT_EINVAL, "null argument");
@@ -245,13 +252,31 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
       (e = cudaMalloc(&dU.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess ||
       (e = cudaMalloc(&dV.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess)
     return quv_fail(e == cudaErrorMemoryAllocation ? RIFT_ENOMEM : RIFT_ECUDA, cudaGetErrorString(e));
+  // CUDA events around each kernel on the call's stream (rift_quv_kernel_ms)
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  for (int i = 0; i < 3; ++i)
+    if ((e = cudaEventCreate(&ev[i])) != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+      return quv_fail(RIFT_ECUDA, cudaGetErrorString(e));
+    }
   dim3 gq((nt + kQThreads - 1) / kQThreads, (M + kQModes - 1) / kQModes, K);
+  cudaEventRecord(ev[0], st);
   quv_q_kernel<<<gq, kQThreads, 0, st>>>((const float2 *)dH.p, (const float2 *)dB.p, (const int *)dnu.p,
                                          (const int *)drun.p, nb, M, nt, (int)n, (double2 *)dQ.p);
+  cudaEventRecord(ev[1], st);
   dim3 guv((M * M + 127) / 128, K);
   quv_uv_kernel<<<guv, 128, 0, st>>>((const float2 *)dH.p, (const float2 *)dHm.p, (const float2 *)dHw.p, nb, M,
                                      (double2 *)dU.p, (double2 *)dV.p, (const double *)dsc.p);
-  if ((e = cudaGetLastError()) != cudaSuccess ||
+  cudaEventRecord(ev[2], st);
+  if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventSynchronize(ev[2])) == cudaSuccess) {
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    g_quv_ms[0] = a;
+    g_quv_ms[1] = b;
+  }
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess ||
       (e = cudaMemcpyAsync(Q, dQ.p, sizeof(double2) * (size_t)K * M * nt, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(U, dU.p, sizeof(double2) * (size_t)K * M * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(V, dV.p, sizeof(double2) * (size_t)K * M * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -158,6 +158,10 @@ cudaError_t launch_lnl_tmarg(int K, const PointC *pt_dev, const PointC &ph, cons
                              size_t n, const float *ra, const float *dec, const float *psi, const float *phi,
                              const float *incl, const float *dist, float *out, uint32_t *flags, cudaStream_t st);
 
+// Detector-frame coefficients and arrival times of sources (kernels.cu)
+cudaError_t launch_source_frame(int K, const PointC *pt_dev, size_t n, const float *src, float2 *coef, float2 *tk,
+                                cudaStream_t st);
+
 // Cell kernel (mc.cu)
 size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block);
 cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,

@@ -114,3 +114,47 @@ def test_summary_features_shape_and_physics():
     s2 = mdn.summary(pt2)
     assert abs((s2[0] - s[0]) - 3.0 / pt["fs"]) < 1e-12
     assert np.allclose(s2[1:5], s[1:5])
+
+
+def test_summary_closed_form_gaussian_envelope():
+    """Every summary feature on Q whose features are known in closed form: in each detector the
+    (2, 2) and (2, -2) modes are Gaussian envelopes A exp(-(tau - t0)^2 / (2 s^2)) of constant
+    phase theta, sampled far inside the window.  With w = |Q|^8 the weight is a Gaussian of
+    variance s^2 / 8, whose sampled moments equal the continuous ones to exponential accuracy
+    (Poisson summation, s >> 1/fs): mean time t0, spread s / sqrt(8), log of the mean |Q|^8 over
+    8 = ln A + ln(sqrt(2 pi) (s / sqrt(8)) fs / T) / 8, phase of sum w Q = theta; then
+    ln sqrt(U_aa) per detector and mode, and the differences of the (2, 2) mean times."""
+    fs, T, K = 4096.0, 1201, 3
+    t_ref = 1187008882.4
+    q_t0 = t_ref + np.array([-0.15, -0.148, -0.1505])
+    lm = [(2, -2), (2, 1), (2, 2)]
+    params = {  # (k, mode): (A, t0 relative to t_ref, s, theta)
+        (0, (2, 2)): (3.0, -0.0031, 12 / fs, 0.7), (0, (2, -2)): (0.5, -0.0027, 9 / fs, -2.1),
+        (1, (2, 2)): (2.0, 0.0043, 15 / fs, 2.9), (1, (2, -2)): (7.0, 0.0049, 10 / fs, 0.2),
+        (2, (2, 2)): (1.5, 0.0002, 11 / fs, -1.3), (2, (2, -2)): (4.0, -0.0003, 13 / fs, 1.1),
+    }
+    Q = np.zeros((K, len(lm), T), dtype=np.complex128)
+    for k in range(K):
+        tau = (q_t0[k] - t_ref) + np.arange(T) / fs
+        Q[k, lm.index((2, 1))] = 0.3 * np.exp(1j * 40.0 * tau)      # a mode the summary ignores
+        for mode in ((2, 2), (2, -2)):
+            A, t0, sg, th = params[(k, mode)]
+            Q[k, lm.index(mode)] = A * np.exp(-(tau - t0) ** 2 / (2 * sg * sg)) * np.exp(1j * th)
+    U = np.zeros((K, 3, 3), dtype=np.complex128)
+    for k in range(K):
+        U[k] = np.diag([5.0 + k, 1.0, 20.0 * (k + 1)])
+    pt = dict(Q=Q, U=U, lm=np.array(lm, dtype=np.int32), fs=fs, q_t0_gps=q_t0, t_ref_gps=t_ref)
+    s = mdn.summary(pt)
+    want = []
+    for k in range(K):
+        for mode in ((2, 2), (2, -2)):
+            A, t0, sg, th = params[(k, mode)]
+            sw = sg / math.sqrt(8.0)
+            want += [t0, sw, math.log(A) + math.log(math.sqrt(2 * math.pi) * sw * fs / T) / 8.0,
+                     math.cos(th), math.sin(th)]
+    for k in range(K):
+        want += [0.5 * math.log(20.0 * (k + 1)), 0.5 * math.log(5.0 + k)]
+    t22 = [params[(k, (2, 2))][1] for k in range(K)]
+    want += [t22[0] - t22[1], t22[0] - t22[2], t22[1] - t22[2]]
+    want += [0.0] * (64 - len(want))
+    assert np.allclose(s, np.array(want), rtol=0, atol=1e-12), np.max(np.abs(s - np.array(want)))

@@ -415,8 +415,28 @@ def test_rebuild_tables_properties():
         assert c[0] == 0.0 and c[-1] == 1.0 and np.all(np.diff(c) > 0)
         p = np.diff(c)
         assert np.all(p >= 0.1 / 20 * (1 - 1e-6))
-        want = 0.9 * h[d] / h[d].sum() + 0.1 / 20
-        assert np.allclose(p, want, atol=1e-7)
+
+
+def test_rebuild_tables_hand_computed():
+    """The adaptive rebuild (tempered weights exp(beta (l - max l)) summed per bin, floor-mixed
+    p_b = (1 - eps) h_b / sum h + eps / n_bins, float32 CDF) on five samples worked out by hand:
+    beta = 1/2, eps = 1/5, 4 bins, log weights 3000 + {2 ln 2, 0, 0, -2 ln 2, 2 ln 2}, so the
+    tempered weights are {1, 1/2, 1/2, 1/4, 1}.  The offset 3000 overflows exp(beta l) unless the
+    maximum is taken out first."""
+    l2 = math.log(2.0)
+    ell = 3000.0 + np.array([2 * l2, 0.0, 0.0, -2 * l2, 2 * l2])
+    bins = np.array([[0, 1, 1, 3, 0],      # ra: h = (2, 1, 0, 1/4)
+                     [2, 2, 2, 2, 2],      # sin dec: all in bin 2, h = (0, 0, 13/4, 0)
+                     [3, 0, 1, 2, 0]])     # t: h = (3/2, 1/2, 1/4, 1)
+    tab, _ = mc.rebuild_tables(ell, bins, 4, 0.5, 0.2)
+    # ra: p = (4/5) h / (13/4) + 1/20 = (141, 77, 13, 29) / 260
+    want0 = np.array([0, 141, 218, 231, 260]) / 260.0
+    # sin dec: p = (1/20, 1/20, 4/5 + 1/20, 1/20)
+    want1 = np.array([0, 1, 2, 19, 20]) / 20.0
+    # t: sum h = 13/4, p = (16/65)(3/2, 1/2, 1/4, 1) + 1/20 = (109, 45, 29, 77) / 260
+    want2 = np.array([0, 109, 154, 183, 260]) / 260.0
+    for d, want in enumerate((want0, want1, want2)):
+        assert np.array_equal(tab[d], want.astype(np.float32)), (d, tab[d], want)
 
 
 # ---------------------------------------------------------------- stratified rounds
@@ -467,3 +487,37 @@ def test_stratified_marginalisation_agrees_with_plain():
     strat = mc.marginalize(pt, 202, 0, pr, 100000, 300000, 1e300, strata=(16, 8, 8))
     s = math.hypot(plain["sigma"], strat["sigma"])
     assert abs(plain["lnL_marg"] - strat["lnL_marg"]) < 5 * s + 0.005
+
+
+# ---------------------------------------------------------------- reflection-symmetric modes
+def test_positive_quadratic_form_of_mirror_symmetric_modes():
+    """The identity the kernels use for points whose modes carry the reflection symmetry of
+    non-precessing sources, conj(h_a(-f)) = sigma_a h_mirror(a)(f): the detector strain is
+    x sum_a beta_a h_a with beta_a = (conj(F) Y_a + sigma_a F conj(Y_mirror(a))) / 2, so the
+    quadratic form of Eq. (def:lnL:Decomposed) is 2 beta^H U beta.  The synthetic full-size point
+    has the symmetry (sigma = -1 for odd l, m != 0; its m = 0 modes are real), which shows in its
+    inputs as V_ab = sigma_a U_mirror(a),b; on random draws the positive form equals the oracle's
+    general form (-4 lnL / x^2 with Q = 0) to 1e-12."""
+    pt = W.make_point(W.cfg_full(), 2)
+    modes = [tuple(x) for x in np.asarray(pt["lm"]).tolist()]
+    mir = np.array([modes.index((l, -m)) for l, m in modes])
+    sig = np.array([(-1.0 if (l % 2 and m != 0) else 1.0) for l, m in modes])
+    U, V = pt["U"], pt["V"]
+    scale = np.abs(U).max()
+    assert np.abs(V - sig[None, :, None] * U[:, mir, :]).max() < 1e-12 * scale
+    r = _rng(31)
+    n = 200
+    th = dict(ra=r.uniform(0, 2 * np.pi, n), dec=np.arcsin(r.uniform(-1, 1, n)), t=np.zeros(n),
+              psi=r.uniform(0, np.pi, n), phi=r.uniform(0, 2 * np.pi, n), incl=np.arccos(r.uniform(-1, 1, n)),
+              dist=np.full(n, 100.0))
+    silent = dict(pt, Q=np.zeros_like(pt["Q"]))
+    general = -4.0 * L.lnL_factorised(silent, **th)          # x = d_ref / D = 1
+    Y = S.ylm_m2(modes, th["incl"], th["phi"])                # (n, M)
+    gm = G.gmst_from_gps(pt["t_ref_gps"])
+    pos = np.zeros(n)
+    for k in range(U.shape[0]):
+        F = G.complex_antenna(pt["det_tensor"][k], th["ra"], th["dec"], th["psi"], gm)
+        beta = 0.5 * (np.conj(F)[:, None] * Y + sig[None, :] * F[:, None] * np.conj(Y[:, mir]))
+        pos += 2.0 * np.real(np.einsum("na,ab,nb->n", np.conj(beta), U[k], beta))
+    assert np.all(pos >= 0)
+    assert np.max(np.abs(pos - general)) < 1e-12 * np.max(np.abs(general))
