@@ -773,7 +773,9 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   const CanonCoefParam *cc = (np == 1 && h->canon0 && NT == 4 && !learned && !o->time_marg) ? h->canon0 : nullptr;
   const MirrorCoefParam *mp = (np == 1 && h->mirror0 && NT == 4 && !learned && !o->time_marg) ? h->mirror0 : nullptr;
   const int coef_f4 = (cc || mp) ? 0 : h->max_pairK;
-  const size_t fixed = cells_smem_fixed(K, h->max_M, coef_f4, nb, block);
+  // a mirror-symmetric point with all 21 modes keeps its harmonics in registers (no shared buffer)
+  const int ys_modes = (mp && h->pts[0].c.M == RIFT_MAXM) ? 0 : h->max_M;
+  const size_t fixed = cells_smem_fixed(K, ys_modes, coef_f4, nb, block);
   long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
   budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
   const size_t smem = fixed + (size_t)budget;
@@ -796,7 +798,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.ell_buf = adaptive ? S.ell : nullptr;
   L.bin_buf = adaptive ? S.bins : nullptr;
   L.flags = h->flags;
-  L.max_M = h->max_M;
+  L.max_M = ys_modes;
   L.max_pairK = coef_f4;
   L.max_nb = nb;
   L.learned = learned ? 1 : 0;

@@ -217,6 +217,66 @@ __device__ __forceinline__ float linear_term_staged(const PointC &P, const float
   return lin;
 }
 
+// The same linear term for a point holding all 21 canonical modes (stored order = canonical order),
+// with the harmonics formed in registers from their real factors d_j and e^{i m phi} instead of read
+// from a per-thread shared buffer; every operation is the one linear_term_staged performs on the
+// same values, so the results are the same bits.
+template <int K, int NT>
+__device__ __forceinline__ float linear_term_yreg(const PointC &P, const float2 *__restrict__ Q, const df s_idx[K],
+                                                  const float2 F[K], const float (&dj)[RIFT_MAXM],
+                                                  const float2 (&e)[5], const float4 *const win[K], const int wlo[K],
+                                                  const int whi[K], uint32_t &flags) {
+  constexpr int first = (NT == 4) ? -1 : 0;
+  constexpr int rs = (RIFT_MAXM + 1) / 2;   // row stride in float4 (Mp = 22)
+  float w[K][NT];
+  const float4 *row[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int i; float mu;
+    df s = s_idx[k];
+    if (NT == 1) s = df_add_f(s, 0.5f);
+    df_floor(s, i, mu);
+    interp_weights<NT>(mu, w[k]);
+    int i0 = i + first;
+    if (i0 < 0 || i0 + NT > P.T) {
+      flags |= RIFT_FLAG_WINDOW;
+      i0 = min(max(i0, 0), P.T - NT);
+    }
+    const bool in_win = win[k] != nullptr && i0 >= wlo[k] && i0 + NT - 1 <= whi[k];
+    row[k] = in_win ? win[k] + (size_t)(i0 - wlo[k]) * rs
+                    : reinterpret_cast<const float4 *>(Q + ((long long)k * P.T + i0) * (2 * rs));
+  }
+  float zr[K], zi[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { zr[k] = 0.f; zi[k] = 0.f; }
+#pragma unroll
+  for (int a2 = 0; a2 < rs; ++a2) {
+    const float2 y0 = canon_y(2 * a2, dj[2 * a2], e);
+    const float2 y1 = (2 * a2 + 1 < RIFT_MAXM) ? canon_y(2 * a2 + 1, dj[(2 * a2 + 1) % RIFT_MAXM], e)
+                                               : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float4 q[NT];
+#pragma unroll
+      for (int r = 0; r < NT; ++r) q[r] = row[k][r * rs + a2];
+      float q0r = 0.f, q0i = 0.f, q1r = 0.f, q1i = 0.f;
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        q0r = fmaf(w[k][r], q[r].x, q0r); q0i = fmaf(w[k][r], q[r].y, q0i);
+        q1r = fmaf(w[k][r], q[r].z, q1r); q1i = fmaf(w[k][r], q[r].w, q1i);
+      }
+      zr[k] = fmaf(y0.x, q0r, fmaf(y0.y, q0i, zr[k]));
+      zi[k] = fmaf(y0.x, q0i, fmaf(-y0.y, q0r, zi[k]));
+      zr[k] = fmaf(y1.x, q1r, fmaf(y1.y, q1i, zr[k]));
+      zi[k] = fmaf(y1.x, q1i, fmaf(-y1.y, q1r, zi[k]));
+    }
+  }
+  float lin = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) lin += F[k].x * zr[k] - F[k].y * zi[k];
+  return lin;
+}
+
 // Q index of t_0 + delay_k for the time quadrature: (t_lo - tau0_k) fs + 1/2 - fs x_k . n.
 template <int K>
 __device__ __forceinline__ void delay_index(const PointC &P, const Sky &s, df out[K]) {
@@ -234,7 +294,10 @@ __device__ __forceinline__ void delay_index(const PointC &P, const Sky &s, df ou
 // TMARG: the event time is marginalised by quadrature (Eq. lnL:tmarg) instead of sampled; the
 // sample's t uniform is unused, its Q rows span the whole time window (no staging), and the
 // likelihood is tmarg_term.
-template <int K, int NT, int LEARNED, int TMARG, int CP>
+// YR: a mirror-symmetric point with all 21 modes in the parameter bank (CP 3), harmonics in
+// registers (linear_term_yreg): no per-thread harmonics buffer in shared memory (L.max_M = 0), so
+// the room goes to the Q windows.
+template <int K, int NT, int LEARNED, int TMARG, int CP, int YR = 0>
 __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__restrict__ cpg) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
@@ -443,7 +506,8 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
       sincospif(2.f * d.u_phi, &sphi, &cphi);
       const float ch = sqrtf(d.c_frac), sh = sqrtf(1.f - d.c_frac);   // cos, sin(incl/2)
       float dj[RIFT_MAXM];   // d_lm(incl) for the grouped quadratic form (parameter-bank kernels)
-      if constexpr (CP != 0) swsh_canonical_t<true>(P, ch, sh, cphi, sphi, Ys, ystride, dj);
+      if constexpr (YR) canon_d_all(P, ch, sh, dj);
+      else if constexpr (CP != 0) swsh_canonical_t<true>(P, ch, sh, cphi, sphi, Ys, ystride, dj);
       else swsh_canonical(P, ch, sh, cphi, sphi, Ys, ystride);
       float lnL;
       if (TMARG) {
@@ -459,7 +523,14 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
         else if constexpr (CP != 0)
           quad = quad_canon_from_d<K, CP == 2>(static_cast<const float4 *>(cpg), g, dj, (uint32_t)(d.u_phi * 16777216.f));
         else quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
-        const float lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
+        float lin;
+        if constexpr (YR) {
+          float2 e[5];
+          eiphi_powers(cphi, sphi, e);
+          lin = linear_term_yreg<K, NT>(P, Q, g.s, g.F, dj, e, win, wlo, whi, flags);
+        } else {
+          lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
+        }
         lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
       }
       float ell = lnL + d.lpq;
@@ -679,9 +750,9 @@ __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel_cp(CellLaunch
 
 // One mirror-symmetric three-detector point: the coefficients of its positive quadratic form come
 // in the parameters.
-template <int K, int NT>
+template <int K, int NT, int YR>
 __global__ void __launch_bounds__(RIFT_CELL_BLOCK, 2) cells_kernel_mp(CellLaunch L, const __grid_constant__ MirrorCoefParam mc) {
-  cells_body<K, NT, 0, 0, 3>(L, mc.g);
+  cells_body<K, NT, 0, 0, 3, YR>(L, mc.g);
 }
 
 // The samples of one round of point 0 in cell order (no evaluation).
@@ -862,11 +933,15 @@ cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaS
       static bool attr = false;
       if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(cells_kernel_mp<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(cells_kernel_mp<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(cells_kernel_mp<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
       }
-      cells_kernel_mp<K, NT><<<grid, block, smem, st>>>(L, *mp);
+      // all 21 modes: harmonics in registers, and the launch reserves no harmonics buffer (max_M 0)
+      if (L.max_M == 0) cells_kernel_mp<K, NT, 1><<<grid, block, smem, st>>>(L, *mp);
+      else cells_kernel_mp<K, NT, 0><<<grid, block, smem, st>>>(L, *mp);
       return cudaGetLastError();
     }
     if (cc && !L.tmarg && !L.learned) {

@@ -197,6 +197,32 @@ __device__ __forceinline__ float canon_dval(const PointC &P, int j, const float 
 // compile-time constant; stored mode a = number of present canonical modes before j.
 // WITH_D: also d[j] = d_j(iota) for every canonical j (0 for absent modes), the real factors the
 // grouped quadratic form needs.
+// e^{i m phi}, m = 0..4, from (cos phi, sin phi): the factors the harmonics take.
+__device__ __forceinline__ void eiphi_powers(float cphi, float sphi, float2 (&e)[5]) {
+  e[0] = make_float2(1.f, 0.f);
+  e[1] = make_float2(cphi, sphi);
+  e[2] = make_float2(cphi * cphi - sphi * sphi, 2.f * cphi * sphi);
+  e[3] = make_float2(e[2].x * cphi - e[2].y * sphi, e[2].x * sphi + e[2].y * cphi);
+  e[4] = make_float2(e[2].x * e[2].x - e[2].y * e[2].y, 2.f * e[2].x * e[2].y);
+}
+
+// -2Y_lm of canonical mode j from its real factor d_j and the phase factors e (j compile-time).
+__device__ __forceinline__ float2 canon_y(int j, float dj, const float2 (&e)[5]) {
+  const int am = canon_m(j) < 0 ? -canon_m(j) : canon_m(j);
+  const float2 em = e[am];
+  return make_float2(dj * em.x, canon_m(j) < 0 ? -(dj * em.y) : dj * em.y);
+}
+
+// The real factors d_j(iota) of all 21 canonical modes (c, s = cos, sin(iota/2)).
+__device__ __forceinline__ void canon_d_all(const PointC &P, float c, float s, float (&d)[RIFT_MAXM]) {
+  float cp[9], sp[9];
+  cp[0] = 1.f; sp[0] = 1.f;
+#pragma unroll
+  for (int j = 1; j < 9; ++j) { cp[j] = cp[j - 1] * c; sp[j] = sp[j - 1] * s; }
+#pragma unroll
+  for (int j = 0; j < RIFT_MAXM; ++j) d[j] = canon_dval(P, j, cp, sp);
+}
+
 template <bool WITH_D>
 __device__ __forceinline__ void swsh_canonical_t(const PointC &P, float c, float s, float cphi, float sphi,
                                                  float2 *Ys, int stride, float *d) {
@@ -205,11 +231,7 @@ __device__ __forceinline__ void swsh_canonical_t(const PointC &P, float c, float
 #pragma unroll
   for (int j = 1; j < 9; ++j) { cp[j] = cp[j - 1] * c; sp[j] = sp[j - 1] * s; }
   float2 e[5];
-  e[0] = make_float2(1.f, 0.f);
-  e[1] = make_float2(cphi, sphi);
-  e[2] = make_float2(cphi * cphi - sphi * sphi, 2.f * cphi * sphi);
-  e[3] = make_float2(e[2].x * cphi - e[2].y * sphi, e[2].x * sphi + e[2].y * cphi);
-  e[4] = make_float2(e[2].x * e[2].x - e[2].y * e[2].y, 2.f * e[2].x * e[2].y);
+  eiphi_powers(cphi, sphi, e);
   const uint32_t mask = P.canon_mask;
 #pragma unroll
   for (int j = 0; j < RIFT_MAXM; ++j) {
@@ -217,10 +239,8 @@ __device__ __forceinline__ void swsh_canonical_t(const PointC &P, float c, float
     if (mask & (1u << j)) {
       const float v = canon_dval(P, j, cp, sp);
       if (WITH_D) d[j] = v;
-      const int am = canon_m(j) < 0 ? -canon_m(j) : canon_m(j);
-      const float2 em = e[am];
       const int a = __popc(mask & ((1u << j) - 1u));
-      Ys[a * stride] = make_float2(v * em.x, canon_m(j) < 0 ? -(v * em.y) : v * em.y);
+      Ys[a * stride] = canon_y(j, v, e);
     }
   }
 }
