@@ -481,58 +481,124 @@ def run_gpu(args, world, rank, local):
 
 def _make_point(args):
     import workload as W
-    spec, seed = args
-    return W.make_point(spec, seed)
+    spec, seed, inj = args
+    return W.make_point(spec, seed, injection=inj)
 
 
-def make_points(specs, seed0):
-    """Generate many points on the host cores (spawned processes, before heavy GPU work)."""
+def make_points(specs, seed0, injections=None):
+    """Generate many points on the host cores (spawned processes)."""
     import multiprocessing as mp
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     with mp.get_context("spawn").Pool(min(cores, 32)) as pool:
-        return pool.map(_make_point, [(s, seed0 + i) for i, s in enumerate(specs)], chunksize=4)
+        return pool.map(_make_point, [(s, seed0 + i, None if injections is None else injections[i])
+                                      for i, s in enumerate(specs)], chunksize=4)
 
 
-def run_extras(args, rift, W, peak):
-    """The batched workload (many points, uneven mode counts and Q lengths, adaptive rounds,
-    one graph-replayed launch sequence) against sequential per-point runs, and the learned
-    proposal against the prior at equal evaluations."""
+def physical_injections(rift, W, specs, seed):
+    """A physical source per point: seeded sky position, arrival time (inside the point's time
+    prior), polarisation, phase and inclination, at 400 Mpc (make_point rescales the waveform to
+    the point's SNR), turned into detector-frame coefficients and arrival times by the library's
+    own response and harmonics (rift_source_frame)."""
     import numpy as np
-    import torch
-    out = {}
-    t0 = time.perf_counter()
-    specs = W.batch_specs(args.batch_points, seed=5)
+    r = np.random.default_rng(np.random.SeedSequence([0x50485953, seed]))
+    out = []
+    for sp in specs:
+        tens = np.stack([W.detector(d)[0] for d in sp.dets])
+        pos = np.stack([W.detector(d)[1] for d in sp.dets])
+        src = np.array([[r.uniform(0, 2 * np.pi), np.arcsin(r.uniform(-1, 1)), r.uniform(-0.3, 0.3) * sp.t_half,
+                         r.uniform(0, np.pi), r.uniform(0, 2 * np.pi), np.arccos(r.uniform(-1, 1)), sp.d_inj]])
+        coef, tk = rift.rift_source_frame(tens, pos, sp.modes, sp.t_ref_gps, sp.d_ref, src)
+        out.append((coef[0], tk[0]))
+    return out
+
+
+def physical_batch(rift, W, n, seed, seed0):
+    import time as _t
+    t0 = _t.perf_counter()
+    specs = W.batch_specs(n, seed=seed)
     for sp in specs:
         sp.seg_len = 2.0
-    pts = make_points(specs, 1000)
-    gen_s = time.perf_counter() - t0
-    hb = rift.rift_ile_batch_create(pts)
-    kw = dict(seed=3, n_per_round=100000, max_evals=args.batch_evals, n_eff_target=1000.0, proposal="adaptive",
-              n_bins=100)
-    rift.rift_ile_batch_marginalize(hb, **kw)          # warm-up (graph instantiation, scratch)
+    pts = make_points(specs, seed0, physical_injections(rift, W, specs, seed))
+    return pts, _t.perf_counter() - t0
+
+
+def _timed_batch(rift, h, **kw):
+    import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = rift.rift_ile_batch_marginalize(hb, **kw)
+    res = rift.rift_ile_batch_marginalize(h, **kw)
     torch.cuda.synchronize()
-    bt = time.perf_counter() - t0
-    nseq = min(32, len(pts))
-    hs = [rift.rift_ile_create(p) for p in pts[:nseq]]
+    return res, time.perf_counter() - t0
+
+
+def _sequential(rift, pts, **kw):
+    """The same points marginalised one at a time (a handle each, created before timing)."""
+    import torch
+    hs = [rift.rift_ile_create(p) for p in pts]
     rift.rift_ile_marginalize(hs[0], point_id=0, **kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i, hh in enumerate(hs):
         rift.rift_ile_marginalize(hh, point_id=i, **kw)
     torch.cuda.synchronize()
-    st = time.perf_counter() - t0
-    ev = sum(r["n_evals"] for r in res)
+    dt = time.perf_counter() - t0
+    for hh in hs:
+        rift.rift_ile_destroy(hh)
+    return len(pts) / dt
+
+
+def run_extras(args, rift, W, peak):
+    """The batched workload (physical injections into points with uneven mode counts and Q lengths,
+    adaptive rounds, one graph-replayed launch sequence) against sequential per-point runs, with the
+    event time sampled and marginalised; the learned proposal trained on those points and judged on
+    held-out points against the adaptive sampler; the time quadrature, Q/U/V and network kernels."""
+    import numpy as np
+    import torch
+    out = {}
+    pts, gen_s = physical_batch(rift, W, args.batch_points, 5, 1000)
+    hb = rift.rift_ile_batch_create(pts)
+    wl = (f"{len(pts)} physical injections (seeded sky, time, polarisation, phase, inclination), 3 detectors, "
+          "M U{5..21}, Q U[800,3300] @ 16384 Hz, SNR U[8,30]")
+    # configured estimator: the event time sampled, adaptive (ra, sin dec, t), 1e5-sample rounds
+    kw = dict(seed=3, n_per_round=100000, max_evals=args.batch_evals, n_eff_target=1000.0, proposal="adaptive",
+              n_bins=100)
+    rift.rift_ile_batch_marginalize(hb, **kw)          # warm-up (graph instantiation, scratch)
+    res, bt = _timed_batch(rift, hb, **kw)
+    seq = _sequential(rift, pts[:32], **kw)
     out["batched"] = {
-        "workload": f"{len(pts)} points, 3 detectors, M U{{5..21}}, Q U[800,3300] @ 16384 Hz, SNR U[8,30]; adaptive "
-                    f"1e5-sample rounds until n_eff >= 1000 or {args.batch_evals} evaluations per point",
-        "points_per_s": len(pts) / bt, "evals_per_s": ev / bt, "seconds": bt,
-        "sequential_points_per_s": nseq / st, "speedup_vs_sequential": (len(pts) / bt) / (nseq / st),
+        "workload": wl + f"; adaptive 1e5-sample rounds until n_eff >= 1000 or {args.batch_evals} evaluations per point",
+        "points_per_s": len(pts) / bt, "evals_per_s": sum(r["n_evals"] for r in res) / bt, "seconds": bt,
+        "sequential_points_per_s": seq, "speedup_vs_sequential": (len(pts) / bt) / seq,
         "points_reaching_neff_1000": int(sum(r["n_eff"] >= 1000 for r in res)),
         "median_n_eff": float(np.median([r["n_eff"] for r in res])), "generation_s": gen_s}
-    # learned proposal: train on harvested samples of the batch, compare with the prior
+    # the paper's estimator: the event time integrated by quadrature, adaptive (ra, sin dec)
+    kt = dict(seed=4, n_per_round=20000, max_evals=args.tmarg_draws, n_eff_target=1000.0, proposal="adaptive",
+              n_bins=100, time_marg=1)
+    rift.rift_ile_batch_marginalize(hb, **dict(kt, max_evals=20000))
+    rt, tt = _timed_batch(rift, hb, **kt)
+    seq_t = _sequential(rift, pts[:16], **kt)
+    conv = [r for r in rt if r["n_eff"] >= 1000]
+    out["batched_time_marginalised"] = {
+        "workload": wl + f"; event time integrated by quadrature, adaptive (ra, sin dec), 2e4-draw rounds until "
+                         f"n_eff >= 1000 or {args.tmarg_draws} draws per point",
+        "points_per_s": len(pts) / tt, "draws_per_s": sum(r["n_evals"] for r in rt) / tt, "seconds": tt,
+        "sequential_points_per_s": seq_t, "speedup_vs_sequential": (len(pts) / tt) / seq_t,
+        "points_reaching_neff_1000": len(conv),
+        "median_draws_to_neff_1000": float(np.median([r["n_evals"] for r in conv])) if conv else None,
+        "median_n_eff": float(np.median([r["n_eff"] for r in rt]))}
+    out["learned"] = run_learned(args, rift, W, hb, pts, rt)
+    out["time_marginalised"] = run_tmarg(rift, W, peak)
+    out["quv"] = run_quv(rift, W, peak)
+    out["mdn"] = run_mdn(rift, peak)
+    return out
+
+
+def run_learned(args, rift, W, hb, pts, ad_train):
+    """The learned proposal: trained on samples harvested from the batch's points (the adaptive
+    sampler first, then its own proposal), then run on held-out physical points with the event time
+    integrated, against the adaptive sampler (its fallback and judge) at the same budget."""
+    import numpy as np
+    import torch
     t0 = time.perf_counter()
     S = rift.rift_ile_batch_summary(hb)
     box = torch.as_tensor(rift.rift_ile_boxes(hb), device="cuda")
@@ -548,22 +614,33 @@ def run_extras(args, rift, W, peak):
         rift.rift_mdn_train(m, S, theta, w, box, steps=800, batch=min(256, len(pts)), lr=1e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    ek = dict(seed=9, n_per_round=262144, max_evals=262144 * 4)
-    prior = rift.rift_ile_batch_marginalize(hb, **ek)
-    learned = rift.rift_ile_batch_marginalize(hb, proposal="learned", mdn=m, **ek)
-    gains = np.array([l["n_eff"] / p["n_eff"] for l, p in zip(learned, prior)])
-    dl = np.array([abs(l["lnL_marg"] - p["lnL_marg"]) for l, p in zip(learned, prior)])
-    out["learned"] = {
-        "workload": f"MDN trained in {train_s:.1f} s on samples harvested from the same {len(pts)} points "
-                    "(adaptive, then its own proposal, 3 stages); both proposals 1.05e6 evaluations per point",
-        "median_n_eff_gain": float(np.median(gains)), "mean_n_eff_gain": float(gains.mean()),
-        "median_n_eff_prior": float(np.median([p["n_eff"] for p in prior])),
-        "median_n_eff_learned": float(np.median([l["n_eff"] for l in learned])),
-        "median_abs_dlnL_marg": float(np.median(dl)), "frac_within_0.05": float(np.mean(dl <= 0.05))}
-    out["time_marginalised"] = run_tmarg(rift, W, pts[:16], peak)
-    out["quv"] = run_quv(rift, W, peak)
-    out["mdn"] = run_mdn(rift, peak)
-    return out
+    held, _ = physical_batch(rift, W, args.heldout_points, 6, 90000)
+    hh = rift.rift_ile_batch_create(held)
+    kt = dict(seed=8, n_per_round=20000, max_evals=args.tmarg_draws, n_eff_target=1000.0, n_bins=100, time_marg=1)
+    ad, t_ad = _timed_batch(rift, hh, proposal="adaptive", **kt)
+    le, t_le = _timed_batch(rift, hh, proposal="learned", mdn=m, fallback_neff=args.fallback_neff, **kt)
+    ln, _ = _timed_batch(rift, hh, proposal="learned", mdn=m, **kt)
+    rift.rift_ile_destroy(hh)
+    rift.rift_mdn_destroy(m)
+
+    def stats(rs):
+        return {"median_n_eff": float(np.median([r["n_eff"] for r in rs])),
+                "points_reaching_neff_1000": int(sum(r["n_eff"] >= 1000 for r in rs)),
+                "median_draws_per_point": float(np.median([r["n_evals"] for r in rs]))}
+    good = [i for i in range(len(held)) if ad[i]["n_eff"] >= 100 and le[i]["n_eff"] >= 100]
+    dl = np.array([abs(le[i]["lnL_marg"] - ad[i]["lnL_marg"]) for i in good])
+    return {
+        "workload": f"network trained in {train_s:.1f} s on samples harvested from the {len(pts)} batch points "
+                    f"(adaptive, then its own proposal, 3 stages); judged on {len(held)} held-out physical points, "
+                    "event time integrated, 2e4-draw rounds until n_eff >= 1000 or "
+                    f"{args.tmarg_draws} draws, against the adaptive (ra, sin dec) sampler",
+        "adaptive": stats(ad), "learned_with_fallback": stats(le), "learned_without_fallback": stats(ln),
+        "fallback_neff": args.fallback_neff,
+        "points_fallen_back": int(sum(r["fallback_round"] >= 0 for r in le)),
+        "points_compared": len(good),
+        "median_abs_dlnL_marg_vs_adaptive": float(np.median(dl)) if len(dl) else None,
+        "frac_within_0.05_of_adaptive": float(np.mean(dl <= 0.05)) if len(dl) else None,
+        "seconds_adaptive": t_ad, "seconds_learned_with_fallback": t_le}
 
 
 def run_quv(rift, W, peak):
@@ -643,10 +720,9 @@ def run_mdn(rift, peak):
             "train_step_note": "the step's time includes the per-step loss read back to the host"}
 
 
-def run_tmarg(rift, W, pts, peak):
+def run_tmarg(rift, W, peak):
     """Eq. (lnL:tmarg): the event time integrated by quadrature for each draw.  Throughput on the
-    full-size point (draws/s and likelihood points/s, CUDA events around the kernel launch) and,
-    on batched points, n_eff and lnL_marg against the sampled-time estimator at equal time."""
+    full-size point (draws/s and likelihood points/s, CUDA events around the kernel launch)."""
     import numpy as np
     import torch
     pt = W.make_point(W.cfg_full(), point_seed(0))
@@ -663,25 +739,13 @@ def run_tmarg(rift, W, pts, peak):
     # per (draw, t): per detector 8 M (conj(Y) Q row) + 4 taps x 4 (interpolation) + 4 (Re F Z); 12 for the
     # log-sum-exp step; per draw the quadratic forms and geometry of one sample
     flops = n * (J * (pt["Q"].shape[0] * (8 * pt["Q"].shape[1] + 4 * 4 + 4) + 12) + flops_per_sample(3, 21, 4))
-    ns, nt, dl = [], [], []
-    for i, p in enumerate(pts):
-        hh = rift.rift_ile_create(p)
-        a = rift.rift_ile_marginalize(hh, seed=3, point_id=i, n_per_round=100000, max_evals=2_000_000,
-                                      proposal="adaptive", n_bins=100)
-        b = rift.rift_ile_marginalize(hh, seed=3, point_id=i, n_per_round=20000, max_evals=400_000,
-                                      proposal="adaptive", n_bins=100, time_marg=1)
-        ns.append(a["n_eff"]); nt.append(b["n_eff"]); dl.append(b["lnL_marg"] - a["lnL_marg"])
-        rift.rift_ile_destroy(hh)
     return {
         "workload": f"full-size point, {n} draws per launch, each integrating J={J} times (midpoint rule on the "
-                    f"Q sampling interval); {len(pts)} batched points, adaptive (ra, sin dec), 4e5 draws vs 2e6 "
-                    "sampled-time evaluations per point",
+                    "Q sampling interval)",
         "kernel_ms": ms, "draws_per_s": n / (ms * 1e-3), "lnL_points_per_s": n * J / (ms * 1e-3),
         "tflops": flops / (ms * 1e-3) / 1e12, "flops_per_draw": flops / n,
         "roofline": {"bound": "alu", "kernel": "cells_kernel<3,4,0,1>", "achieved": flops / (ms * 1e-3) / 1e12,
-                     "peak": peak, "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / peak, "traffic": None},
-        "median_n_eff_tmarg": float(np.median(nt)), "median_n_eff_sampled_t": float(np.median(ns)),
-        "median_lnL_marg_tmarg_minus_sampled": float(np.median(dl))}
+                     "peak": peak, "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / peak, "traffic": None}}
 
 
 def run_reference(args, world, rank):
@@ -738,6 +802,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (profiling captures)")
     ap.add_argument("--batch-points", type=int, default=512)
     ap.add_argument("--batch-evals", type=int, default=2_000_000)
+    ap.add_argument("--tmarg-draws", type=int, default=1_000_000,
+                    help="draws per point at most in the time-marginalised batched runs")
+    ap.add_argument("--heldout-points", type=int, default=128)
+    ap.add_argument("--fallback-neff", type=float, default=10.0)
     ap.add_argument("--samples", type=int, default=N_SAMPLES,
                     help="samples per step (profiling captures use a smaller count of the same workload)")
     args = ap.parse_args()

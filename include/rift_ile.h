@@ -241,6 +241,14 @@ typedef struct {
                             return -- the tables rebuilt from its last round when that round adapted
                             (adapt_rounds), else the tables that round used: the proposal its next
                             round would draw from.  RIFT_EINVAL with other proposals.            */
+  double fallback_neff;  /* learned proposal: fallback to the adaptive sampler.  After a learned round
+                            whose own draws have n_eff = sum w / max w (over that round alone) below
+                            this value -- importance weights dominated by a few draws -- the point
+                            draws its remaining rounds from the adaptive proposal (n_bins, beta,
+                            floor_eps; starting from the prior's tables, unstratified like learned
+                            rounds) and rebuilds it from each of them.  Every round enters the
+                            estimate with its own q, so the pooled estimate stays unbiased.
+                            0 = no fallback; RIFT_EINVAL with other proposals or opts.tables.    */
 } rift_mc_opts;
 
 /* Size of the sampler-state blob of rift_mc_opts.resume / save (same library build and byte order). */
@@ -260,6 +268,8 @@ typedef struct {
   double kernel_ms;  /* with opts.timing: summed duration of the likelihood-kernel launches */
   int kernel_launches; /* likelihood + reduction + adaptive kernels launched by this call   */
   int strata[3];     /* strata used for rounds with n >= C                                     */
+  int fallback_round; /* learned proposal with fallback_neff: the first round drawn from the adaptive
+                         proposal, -1 if the point never fell back                                 */
 } rift_mc_result;
 
 /*

@@ -270,3 +270,53 @@ def marginalize(pt, seed, point, prior: Prior, n_per_round, max_evals, n_eff_tar
     if keep:
         out["history"] = hist
     return out
+
+
+def marginalize_learned(pt, seed, point, prior: Prior, head, n_per_round, max_evals, n_eff_target,
+                        fallback_neff=0.0, n_bins=100, beta=0.3, floor_eps=0.1, max_rounds=None,
+                        time_marg=False, interp=3):
+    """Round loop of Eq. (lnLmarg) with the learned proposal (oracle.mdn.sample, uniforms 0..9 of
+    each draw's stream) and its fallback to the adaptive sampler.
+
+    After a learned round whose own draws have n_eff = sum w / max w (that round alone) below
+    fallback_neff, the point's remaining rounds draw from the adaptive proposal, unstratified,
+    starting from the prior's tables and rebuilt from each adaptive round; every round enters the
+    pooled estimate with its own q.  Returns the marginalize() keys plus "fallback_round" (the first
+    adaptive round, -1 if none) and "round_neff" (each round's own n_eff)."""
+    from .mdn import sample
+    acc = Accum()
+    rnd, fb_round = 0, -1
+    learned = True
+    round_neff = []
+    tables = uniform_tables(n_bins)
+    head = np.atleast_2d(np.asarray(head, dtype=np.float64))
+    while True:
+        idx = np.arange(min(n_per_round, max_evals - acc.n), dtype=np.uint64)
+        if learned:
+            th, lpq = sample(uniforms(seed, point, rnd, idx, 10), head, prior, time_marg)
+            bins = None
+        else:
+            th, bins, lpq = draw(seed, point, rnd, idx, prior, tables, (1, 1, 1), len(idx))
+        if time_marg:
+            ell = lnL_tmarg(pt, th["ra"], np.arcsin(th["sindec"]), th["psi"], th["phi"], np.arccos(th["cosi"]),
+                            th["dist"], interp=interp) + lpq
+        else:
+            ell = lnL_samples(pt, th, interp) + lpq
+        this_round = Accum.of(ell)
+        round_neff.append(this_round.s1)
+        acc = acc.merge(this_round)
+        lnm, n_eff, kish, sig = acc.result()
+        rnd += 1
+        if n_eff >= n_eff_target or acc.n >= max_evals or (max_rounds and rnd >= max_rounds):
+            break
+        if learned:
+            if fallback_neff > 0.0 and this_round.s1 < fallback_neff:   # s1 = the round's sum w / max w
+                learned = False
+                fb_round = rnd
+        else:
+            tables, _ = rebuild_tables(ell, bins, n_bins, beta, floor_eps)
+            if time_marg:
+                tables[2] = uniform_time_table(n_bins)
+    lnm, n_eff, kish, sig = acc.result()
+    return dict(lnL_marg=lnm, n_eff=n_eff, kish=kish, sigma=sig, n_evals=acc.n, rounds=rnd, acc=acc,
+                fallback_round=fb_round, round_neff=round_neff)

@@ -118,6 +118,10 @@ struct rift_ile {
   int cap_pst = 0;
   cudaStream_t gstream = nullptr;
   int graph_rounds = 4;   // rounds per captured graph
+  // the instantiated graph of the last batched run and the launch arguments it was captured with:
+  // a call with the same arguments replays it without capturing again
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned char> gkey;
   // learned proposal
   double *tau0 = nullptr;     // [np][RIFT_MAXK] Q index origins (s), for the summary
   float *head = nullptr;      // [np][88] network heads (given or computed)
@@ -542,11 +546,19 @@ rift_status check_opts(rift_ile *h, const rift_mc_opts *o) {
   } else if (o->proposal == RIFT_PROPOSAL_LEARNED) {
     if (!o->mdn && !h->head_given)
       return fail(h, RIFT_EINVAL, "learned proposal needs opts.mdn or rift_ile_set_proposal_head");
+    if (o->fallback_neff > 0.0) {   // the adaptive sampler it falls back to
+      if (o->n_bins < 2 || o->n_bins > RIFT_MAXBINS) return fail(h, RIFT_EINVAL, "n_bins out of range [2, 256]");
+      if (!(o->beta > 0) || !(o->floor_eps > 0) || !(o->floor_eps <= 1)) return fail(h, RIFT_EINVAL, "bad beta / floor_eps");
+      if (o->tables) return fail(h, RIFT_EINVAL, "the fallback starts from the prior's tables (opts.tables must be NULL)");
+    }
   } else if (o->proposal != RIFT_PROPOSAL_PRIOR) {
     return fail(h, RIFT_EINVAL, "unknown proposal");
   }
   if (o->tables_out && o->proposal != RIFT_PROPOSAL_ADAPTIVE)
     return fail(h, RIFT_EINVAL, "tables_out needs the adaptive proposal");
+  if (!(o->fallback_neff >= 0.0)) return fail(h, RIFT_EINVAL, "fallback_neff must be >= 0");
+  if (o->fallback_neff > 0.0 && o->proposal != RIFT_PROPOSAL_LEARNED)
+    return fail(h, RIFT_EINVAL, "fallback_neff applies to the learned proposal only");
   return RIFT_OK;
 }
 
@@ -676,7 +688,7 @@ constexpr uint32_t kStateMagic = 0x53464952u;   // "RIFS"
 void state_header(const rift_ile *h, const rift_mc_opts *o, const int ls[3], McStateBlob &b) {
   std::memset(&b, 0, sizeof(b));
   b.magic = kStateMagic;
-  b.version = 1;
+  b.version = 2;
   b.seed = o->seed;
   b.point_id = o->point_id;
   b.n_per_round = o->n_per_round;
@@ -699,8 +711,10 @@ bool state_matches(const McStateBlob &a, const McStateBlob &b) {
 // The Monte Carlo round loop of Eq. (lnLmarg) for np points of the handle, with the scratch S.
 rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rift_mc_result *res) {
   const int K = h->K, NT = taps_of(h->interp);
-  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
   const bool learned = (o->proposal == RIFT_PROPOSAL_LEARNED);
+  const bool fallback = learned && o->fallback_neff > 0.0;
+  // table machinery: the adaptive proposal, or learned points that may fall back to it
+  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE) || fallback;
   const int nb = adaptive ? o->n_bins : 0;
   const uint32_t npr = o->n_per_round;
   std::vector<int> lsv(3 * np);
@@ -725,6 +739,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   cudaStream_t st = h->stream;
   if ((o->resume || o->save) && (np != 1 || h->n_points != 1))
     return fail(h, RIFT_EINVAL, "resume/save need a single-point handle");
+  if ((o->resume || o->save) && fallback) return fail(h, RIFT_EINVAL, "resume/save do not record a fallback");
   McStateBlob hdr, in{};
   if (o->resume || o->save) state_header(h, o, lsv.data(), hdr);
   if (o->resume) {
@@ -751,10 +766,14 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
         for (int b = 0; b <= nb; ++b) u[d * (nb + 1) + b] = (float)((double)b / nb);
       src = u;
     }
-    for (int p = 0; p < np; ++p) {
-      const float *sp = (o->tables && o->tables_per_point) ? src + p * tstride : src;
-      RIFT_CK(h, cudaMemcpyAsync(S.tables + p * tstride, sp, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
-    }
+    // (both buffers when learned points may fall back: a point that has not adapted yet reads
+    // whichever buffer the round reads)
+    for (int buf = 0; buf < (fallback ? 2 : 1); ++buf)
+      for (int p = 0; p < np; ++p) {
+        const float *sp = (o->tables && o->tables_per_point) ? src + p * tstride : src;
+        RIFT_CK(h, cudaMemcpyAsync(S.tables + ((size_t)buf * np + p) * tstride, sp, sizeof(float) * tstride,
+                                   cudaMemcpyHostToDevice, st));
+      }
     RIFT_CK(h, cudaStreamSynchronize(st));
     // lnw of the round-0 tables (every point): rp is only read for its flags with part == nullptr
     for (int p = 0; p < np; ++p) {
@@ -763,7 +782,9 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
       S.rp_host[p].ncell = 1;
     }
     RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
-    RIFT_CK(h, launch_tables_points(nullptr, 0, S.rp, np, nb, 0.0, S.tables, S.lnw, st));
+    for (int buf = 0; buf < (fallback ? 2 : 1); ++buf)
+      RIFT_CK(h, launch_tables_points(nullptr, 0, S.rp, np, nb, 0.0, S.tables + (size_t)buf * np * tstride,
+                                      S.lnw + (size_t)buf * np * wstride, st));
   }
   const int block = RIFT_CELL_BLOCK;
   int smem_sm = 0;
@@ -807,6 +828,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.tmarg = o->time_marg ? 1 : 0;
   std::vector<uint64_t> evals(np, 0);
   std::vector<int> rounds(np, 0), done(np, 0), nrun(np, 0);
+  std::vector<int> prop(np, learned ? 2 : (adaptive ? 1 : 0)), fb_round(np, -1);
   int r0 = 0;
   if (o->resume) {
     evals[0] = in.evals;
@@ -837,7 +859,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
       const uint32_t n = (uint32_t)std::min<uint64_t>(npr, o->max_evals - evals[p]);
       const int *ls = &lsv[3 * p];
       int l0 = ls[0], l1 = ls[1], l2 = ls[2];
-      if ((uint64_t)n < (1ull << (l0 + l1 + l2))) l0 = l1 = l2 = 0;
+      if ((uint64_t)n < (1ull << (l0 + l1 + l2))) l0 = l1 = l2 = 0;   // (learned points: lsv is 0)
       const uint32_t C = 1u << (l0 + l1 + l2);
       R.n = n;
       R.ncell = C;
@@ -846,9 +868,9 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
       R.round = (uint32_t)rounds[p];
       R.point_id = (np == 1) ? o->point_id : (uint32_t)p;
       R.ls0 = l0; R.ls1 = l1; R.ls2 = l2;
-      R.proposal = learned ? 2 : (adaptive ? 1 : 0);
+      R.proposal = prop[p];
       R.nb = nb;
-      R.gmm = learned ? h->gmm + (size_t)p * RIFT_GMM_FLOATS : nullptr;
+      R.gmm = (prop[p] == 2) ? h->gmm + (size_t)p * RIFT_GMM_FLOATS : nullptr;
       R.tmarg = o->time_marg ? 1 : 0;
       R.lcorr0 = (float)std::log((double)n / ((double)C * (R.base + 1.0)));
       R.lcorr1 = R.base ? (float)std::log((double)n / ((double)C * R.base)) : 0.f;
@@ -910,6 +932,12 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
         done[p] = 1;
       else
         any = true;
+      // fallback of the learned proposal: a learned round whose own draws have n_eff below the
+      // threshold (degenerate weights) hands the point to the adaptive sampler for its remaining rounds
+      if (!done[p] && fallback && prop[p] == 2 && a.round_neff < o->fallback_neff) {
+        prop[p] = 1;
+        fb_round[p] = rounds[p];
+      }
     }
     if (!any) break;
   }
@@ -941,6 +969,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   for (int p = 0; p < np; ++p) {
     fill_result(S.acc_host[p], &res[p]);
     res[p].rounds = rounds[p];
+    res[p].fallback_round = fb_round[p];
     res[p].kernel_ms = (p == 0) ? kms : 0.0;
     res[p].kernel_launches = (p == 0) ? launches : 0;
     for (int d = 0; d < 3; ++d) res[p].strata[d] = 1 << lsv[3 * p + d];
@@ -1016,6 +1045,7 @@ void rift_ile_destroy(rift_ile *h) {
   cache_dev_free(h->ctl);
   cache_host_free(h->ctl_host);
   cache_host_free(h->pst_host);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   delete h->canon0;
   delete h->mirror0;
@@ -1136,7 +1166,8 @@ rift_status rift_ile_marginalize(rift_ile *h, const rift_mc_opts *o, rift_mc_res
   rift_status s = check_opts(h, o);
   if (s != RIFT_OK) return s;
   std::memset(res, 0, sizeof(*res));
-  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
+  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE) ||
+                        (o->proposal == RIFT_PROPOSAL_LEARNED && o->fallback_neff > 0.0);
   const int nb = adaptive ? o->n_bins : 0;
   const int hb = std::max(1, std::min(64, (int)(o->n_per_round / 8192)));
   const size_t items = (size_t)RIFT_MAX_CELLS + o->n_per_round / (o->time_marg ? RIFT_TMARG_CHUNK : RIFT_CHUNK) + 1;
@@ -1159,8 +1190,10 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   if (o->resume || o->save) return fail(h, RIFT_EUNSUPPORTED, "resume/save: single-point marginalisation only");
   const int np = h->n_points;
   std::memset(res, 0, sizeof(*res) * np);
-  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE);
   const bool learned = (o->proposal == RIFT_PROPOSAL_LEARNED);
+  const bool fallback = learned && o->fallback_neff > 0.0;
+  // table machinery: the adaptive proposal, or learned points that may fall back to it
+  const bool adaptive = (o->proposal == RIFT_PROPOSAL_ADAPTIVE) || fallback;
   const int nb = adaptive ? o->n_bins : 0;
   const int hb = std::max(1, std::min(64, (int)(o->n_per_round / 8192)));
   std::vector<int> lsv(3 * np);
@@ -1206,6 +1239,8 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
     S.acc_host[p].m = -INFINITY;
     std::memset(&h->pst_host[p], 0, sizeof(PtState));
     for (int d = 0; d < 3; ++d) h->pst_host[p].ls[d] = lsv[3 * p + d];
+    h->pst_host[p].prop = learned ? 2 : (adaptive ? 1 : 0);
+    h->pst_host[p].fb_round = -1;
     std::memset(&S.rp_host[p], 0, sizeof(RoundPt));
   }
   std::memset(h->ctl_host, 0, sizeof(RoundCtl));
@@ -1231,6 +1266,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   B.last = keep_ell ? h->last : nullptr;
   B.tmarg = o->time_marg ? 1 : 0;
   B.point_id1 = o->point_id;
+  B.fallback_neff = fallback ? o->fallback_neff : 0.0;
   if (adaptive) {
     float u[3 * (RIFT_MAXBINS + 1)];
     const float *src = o->tables;
@@ -1239,14 +1275,20 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
         for (int b = 0; b <= nb; ++b) u[d * (nb + 1) + b] = (float)((double)b / nb);
       src = u;
     }
-    for (int p = 0; p < np; ++p) {
-      const float *sp = (o->tables && o->tables_per_point) ? src + p * tstride : src;
-      RIFT_CK(h, cudaMemcpyAsync(S.tables + p * tstride, sp, sizeof(float) * tstride, cudaMemcpyHostToDevice, st));
-    }
+    // both table buffers hold the round-0 tables when learned points may fall back: a point that
+    // has not adapted yet reads whichever buffer the round reads
+    for (int buf = 0; buf < (fallback ? 2 : 1); ++buf)
+      for (int p = 0; p < np; ++p) {
+        const float *sp = (o->tables && o->tables_per_point) ? src + p * tstride : src;
+        RIFT_CK(h, cudaMemcpyAsync(S.tables + ((size_t)buf * np + p) * tstride, sp, sizeof(float) * tstride,
+                                   cudaMemcpyHostToDevice, st));
+      }
     RIFT_CK(h, cudaStreamSynchronize(st));
     for (int p = 0; p < np; ++p) { S.rp_host[p].proposal = 1; S.rp_host[p].ncell = 1; }
     RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
-    RIFT_CK(h, launch_tables_points(nullptr, 0, S.rp, np, nb, 0.0, S.tables, S.lnw, st));
+    for (int buf = 0; buf < (fallback ? 2 : 1); ++buf)
+      RIFT_CK(h, launch_tables_points(nullptr, 0, S.rp, np, nb, 0.0, S.tables + (size_t)buf * np * tstride,
+                                      S.lnw + (size_t)buf * np * 3 * nb, st));
     for (int p = 0; p < np; ++p) { S.rp_host[p].proposal = 0; S.rp_host[p].ncell = 0; }
   }
   RIFT_CK(h, cudaMemcpyAsync(S.rp, S.rp_host, sizeof(RoundPt) * np, cudaMemcpyHostToDevice, st));
@@ -1286,27 +1328,50 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   const int grid = h->num_sms * bps;
   // capture G rounds: update -> cells -> merge -> (adaptive) hist -> tables
   const int G = std::max(1, h->graph_rounds);
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  RIFT_CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t ce = cudaSuccess;
-  for (int g = 0; g < G && ce == cudaSuccess; ++g) {
-    if ((ce = launch_round_update(B, h->pst, S.acc, S.rp, h->ctl, st)) != cudaSuccess) break;
-    if ((ce = launch_cells(K, NT, L, grid, block, smem, st)) != cudaSuccess) break;
-    if ((ce = launch_merge_points(S.partials, S.rp, np, S.acc, st)) != cudaSuccess) break;
-    if (adaptive) {
-      if ((ce = launch_hist_ctl(S.ell, S.bins, S.rp, np, S.acc, (float)o->beta, nb, S.hist, S.hblocks, h->ctl, st)) !=
-          cudaSuccess)
-        break;
-      if ((ce = launch_tables_ctl(S.hist, S.hblocks, S.rp, np, nb, o->floor_eps, B, h->ctl, st)) != cudaSuccess) break;
+  // every argument the captured launches take by value (pointers included): an equal key means the
+  // cached graph launches exactly these kernels with these arguments
+  std::vector<unsigned char> key;
+  auto put = [&key](const void *x, size_t nbytes) {
+    const unsigned char *c = static_cast<const unsigned char *>(x);
+    key.insert(key.end(), c, c + nbytes);
+  };
+  const float beta_f = (float)o->beta;
+  const double eps_d = o->floor_eps;
+  const int ints[9] = {K, NT, grid, block, (int)smem, G, adaptive ? 1 : 0, nb, S.hblocks};
+  put(&B, sizeof(B));
+  put(&L, sizeof(L));
+  put(ints, sizeof(ints));
+  put(&beta_f, sizeof(beta_f));
+  put(&eps_d, sizeof(eps_d));
+  const void *ptrs[7] = {h->pst, S.acc, S.rp, h->ctl, S.partials, S.ell, S.hist};
+  put(ptrs, sizeof(ptrs));
+  if (!h->gexec || key != h->gkey) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->gkey.clear();
+    cudaGraph_t graph = nullptr;
+    RIFT_CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int g = 0; g < G && ce == cudaSuccess; ++g) {
+      if ((ce = launch_round_update(B, h->pst, S.acc, S.rp, h->ctl, st)) != cudaSuccess) break;
+      if ((ce = launch_cells(K, NT, L, grid, block, smem, st)) != cudaSuccess) break;
+      if ((ce = launch_merge_points(S.partials, S.rp, np, S.acc, st)) != cudaSuccess) break;
+      if (adaptive) {
+        if ((ce = launch_hist_ctl(S.ell, S.bins, S.rp, np, S.acc, beta_f, nb, S.hist, S.hblocks, h->ctl, st)) !=
+            cudaSuccess)
+          break;
+        if ((ce = launch_tables_ctl(S.hist, S.hblocks, S.rp, np, nb, eps_d, B, h->ctl, st)) != cudaSuccess) break;
+      }
     }
+    cudaError_t ee = cudaStreamEndCapture(st, &graph);
+    if (ce != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(h, ce, "graph capture"); }
+    if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
+    ee = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ee != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, ee, "cudaGraphInstantiate"); }
+    h->gkey = key;
   }
-  cudaError_t ee = cudaStreamEndCapture(st, &graph);
-  if (ce != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(h, ce, "graph capture"); }
-  if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
-  ee = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaGraphInstantiate");
+  cudaGraphExec_t exec = h->gexec;
   // replay until a round update finds no active point (all results accounted)
   uint64_t max_np_evals = o->max_evals;
   const uint64_t rounds_cap = (max_np_evals + o->n_per_round - 1) / o->n_per_round + 2;
@@ -1322,7 +1387,6 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
     if (h->ctl_host->active == 0) break;
     if ((uint64_t)replays > replay_cap) { status = fail(h, RIFT_ETIMEOUT, "batched run did not terminate"); break; }
   }
-  cudaGraphExecDestroy(exec);
   if (status != RIFT_OK) return status;
   RIFT_CK(h, cudaMemcpyAsync(S.acc_host, S.acc, sizeof(AccState) * np, cudaMemcpyDeviceToHost, st));
   RIFT_CK(h, cudaMemcpyAsync(h->pst_host, h->pst, sizeof(PtState) * np, cudaMemcpyDeviceToHost, st));
@@ -1347,6 +1411,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
     fill_result(S.acc_host[p], &res[p]);
     res[p].rounds = h->pst_host[p].rounds;
     res[p].kernel_launches = (p == 0) ? replays * G * (adaptive ? 5 : 3) : 0;
+    res[p].fallback_round = h->pst_host[p].fb_round;
     for (int d = 0; d < 3; ++d) res[p].strata[d] = 1 << lsv[3 * p + d];
     rift_status sp = fl;
     if (sp == RIFT_OK && res[p].n_eff < o->n_eff_target) sp = RIFT_ENOTCONVERGED;

@@ -183,11 +183,13 @@ __device__ __forceinline__ Drawn draw_learned(unsigned long long seed, const Rou
   return d;
 }
 
+// LEARNED: the launch's points use learned proposals; each point's round says which proposal it
+// draws from (R.proposal 2, or 1 after a fallback to the adaptive tables).
 template <int LEARNED, int TM = 0>
 __device__ __forceinline__ Drawn draw_any(unsigned long long seed, const RoundPt &R, uint32_t i, uint32_t cell,
                                           const float *tab, const float *lnw, const float *G, float dref, float d_lo3,
                                           float d_span3) {
-  if (LEARNED) return draw_learned<TM>(seed, R, i, G, dref, d_lo3, d_span3);
+  if (LEARNED && R.proposal == 2) return draw_learned<TM>(seed, R, i, G, dref, d_lo3, d_span3);
   return draw_cell_sample(seed, R, i, cell, tab, lnw, dref, d_lo3, d_span3);
 }
 

@@ -629,6 +629,7 @@ __global__ void __launch_bounds__(256) merge_points_kernel(const Part *__restric
     double S1 = 0.0, S2 = 0.0, N = 0.0;
     for (int w = 0; w < nw; ++w) { S1 += sm[0][w]; S2 += sm[1][w]; N += sm[2][w]; }
     A.round_max = M;
+    A.round_neff = (N > 0.0 && M != -INFINITY) ? S1 : 0.0;   // the round's own sum w / max w
     if (N > 0.0 && M != -INFINITY) {
       if (M > A.m) {
         const double f = (A.m == -INFINITY) ? 0.0 : exp(A.m - M);
@@ -818,6 +819,12 @@ __global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState 
       const double n_eff = acc[p].s1 + acc[p].c1;
       if (n_eff >= B.n_eff_target || st.evals >= B.max_evals || (B.max_rounds > 0 && st.rounds >= B.max_rounds))
         st.done = 1;
+      // fallback of the learned proposal: a learned round whose own draws have n_eff below the
+      // threshold (degenerate weights) hands the point to the adaptive sampler for its remaining rounds
+      if (!st.done && st.prop == 2 && B.fallback_neff > 0.0 && acc[p].round_neff < B.fallback_neff) {
+        st.prop = 1;
+        st.fb_round = st.rounds;
+      }
     }
     RoundPt N;
     memset(&N, 0, sizeof(N));
@@ -826,6 +833,7 @@ __global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState 
     if (!st.done) {
       const uint32_t n = (uint32_t)min((unsigned long long)B.npr, B.max_evals - st.evals);
       int l0 = st.ls[0], l1 = st.ls[1], l2 = st.ls[2];
+      if (st.prop == 2) l0 = l1 = l2 = 0;   // learned rounds are not stratified
       if ((unsigned long long)n < (1ull << (l0 + l1 + l2))) l0 = l1 = l2 = 0;
       const uint32_t C = 1u << (l0 + l1 + l2);
       N.n = n;
@@ -842,12 +850,12 @@ __global__ void __launch_bounds__(1024) round_update_kernel(BatchCtl B, PtState 
       N.round = (uint32_t)st.rounds;
       N.point_id = (B.np == 1) ? B.point_id1 : (uint32_t)p;
       N.ls0 = l0; N.ls1 = l1; N.ls2 = l2;
-      N.proposal = B.learned ? 2 : (B.adaptive ? 1 : 0);
+      N.proposal = st.prop;
       N.nb = B.nb;
       N.lcorr0 = (float)log((double)n / ((double)C * (N.base + 1.0)));
       N.lcorr1 = N.base ? (float)log((double)n / ((double)C * N.base)) : 0.f;
       N.ell_off = (B.adaptive || B.keep_ell) ? (long long)p * B.npr : -1;
-      if (B.learned) N.gmm = B.gmm + (size_t)p * RIFT_GMM_FLOATS;
+      if (N.proposal == 2) N.gmm = B.gmm + (size_t)p * RIFT_GMM_FLOATS;
       N.tmarg = B.tmarg;
       if (B.adaptive) {
         N.tab = B.tables + ((size_t)tabbuf * B.np + p) * tstride;

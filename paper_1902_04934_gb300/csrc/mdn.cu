@@ -166,21 +166,19 @@ __global__ void __launch_bounds__(128) mdn_loss_kernel(const float *__restrict__
   }
 }
 
-// Backpropagation of dL/dhead through the MLP; weight gradients accumulated with atomics.
+// Backpropagation of dL/dhead through the MLP to the pre-activation gradients of both hidden layers
+// of point p: ga[p][0..NH) = dL/da1, ga[p][NH..2NH) = dL/da2 (the weight gradients are the sums over
+// points of their outer products, formed by mdn_wgrad_kernel in a fixed order).
 __global__ void __launch_bounds__(256) mdn_backward_kernel(const __nv_bfloat16 *__restrict__ W,
-                                                           const float *__restrict__ S,
                                                            const float *__restrict__ cache,
                                                            const float *__restrict__ gout, int P,
-                                                           float *__restrict__ grad) {
+                                                           float *__restrict__ ga) {
   const int p = blockIdx.x;
   if (p >= P) return;
-  __shared__ float s[NI], h1[NH], h2[NH], ga1[NH], ga2[NH], go[NO];
+  __shared__ float ga2[NH], go[NO];
   const int t = threadIdx.x;
-  if (t < NI) s[t] = S[(size_t)p * NI + t];
   if (t < NO) go[t] = gout[(size_t)p * NO + t];
   const float a1 = cache[(size_t)p * 2 * NH + t], a2 = cache[(size_t)p * 2 * NH + NH + t];
-  h1[t] = gelu(a1);
-  h2[t] = gelu(a2);
   __syncthreads();
   float gh2 = 0.f;
   for (int o = 0; o < NO; ++o) gh2 = fmaf(go[o], bf(W, OFF_W3 + o * NH + t), gh2);
@@ -188,14 +186,41 @@ __global__ void __launch_bounds__(256) mdn_backward_kernel(const __nv_bfloat16 *
   __syncthreads();
   float gh1 = 0.f;
   for (int j = 0; j < NH; ++j) gh1 = fmaf(ga2[j], bf(W, OFF_W2 + j * NH + t), gh1);
-  ga1[t] = gh1 * gelu_grad(a1);
-  __syncthreads();
-  for (int o = 0; o < NO; ++o) atomicAdd(grad + OFF_W3 + o * NH + t, go[o] * h2[t]);
-  if (t < NO) atomicAdd(grad + OFF_B3 + t, go[t]);
-  for (int j = 0; j < NH; ++j) atomicAdd(grad + OFF_W2 + j * NH + t, ga2[j] * h1[t]);
-  atomicAdd(grad + OFF_B2 + t, ga2[t]);
-  for (int e = t; e < NH * NI; e += blockDim.x) atomicAdd(grad + OFF_W1 + e, ga1[e / NI] * s[e % NI]);
-  atomicAdd(grad + OFF_B1 + t, ga1[t]);
+  ga[(size_t)p * 2 * NH + t] = gh1 * gelu_grad(a1);
+  ga[(size_t)p * 2 * NH + NH + t] = ga2[t];
+}
+
+// Weight gradients as sums over the P points, each parameter by one thread in point order (the
+// same bits on every run): W3[o][t] += go[p][o] h2[p][t], b3[o] += go[p][o], W2[j][t] += ga2[p][j]
+// h1[p][t], b2[j] += ga2[p][j], W1[j][i] += ga1[p][j] s[p][i], b1[j] += ga1[p][j], with h = GELU(a)
+// recomputed from the cached pre-activations.
+__global__ void __launch_bounds__(256) mdn_wgrad_kernel(const float *__restrict__ S, const float *__restrict__ cache,
+                                                        const float *__restrict__ gout,
+                                                        const float *__restrict__ ga, int P,
+                                                        float *__restrict__ grad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NPARAM) return;
+  float acc = 0.f;
+  if (e >= OFF_B3) {
+    const int o = e - OFF_B3;
+    for (int p = 0; p < P; ++p) acc += gout[(size_t)p * NO + o];
+  } else if (e >= OFF_W3) {
+    const int o = (e - OFF_W3) / NH, t = (e - OFF_W3) % NH;
+    for (int p = 0; p < P; ++p) acc = fmaf(gout[(size_t)p * NO + o], gelu(cache[(size_t)p * 2 * NH + NH + t]), acc);
+  } else if (e >= OFF_B2) {
+    const int j = e - OFF_B2;
+    for (int p = 0; p < P; ++p) acc += ga[(size_t)p * 2 * NH + NH + j];
+  } else if (e >= OFF_W2) {
+    const int j = (e - OFF_W2) / NH, t = (e - OFF_W2) % NH;
+    for (int p = 0; p < P; ++p) acc = fmaf(ga[(size_t)p * 2 * NH + NH + j], gelu(cache[(size_t)p * 2 * NH + t]), acc);
+  } else if (e >= OFF_B1) {
+    const int j = e - OFF_B1;
+    for (int p = 0; p < P; ++p) acc += ga[(size_t)p * 2 * NH + j];
+  } else {
+    const int j = (e - OFF_W1) / NI, i = (e - OFF_W1) % NI;
+    for (int p = 0; p < P; ++p) acc = fmaf(ga[(size_t)p * 2 * NH + j], S[(size_t)p * NI + i], acc);
+  }
+  grad[e] += acc;
 }
 
 // Adam (Kingma & Ba 2015) on the float32 master copy, bfloat16 weights refreshed, gradient cleared.
@@ -378,7 +403,7 @@ struct rift_mdn {
   int step = 0;
   std::string err;
   // training scratch
-  float *head = nullptr, *cache = nullptr, *gout = nullptr, *loss = nullptr;
+  float *head = nullptr, *cache = nullptr, *gout = nullptr, *loss = nullptr, *ga = nullptr;
   int cap = 0;
 };
 
@@ -397,11 +422,12 @@ rift_status mfail(rift_mdn *m, rift_status s, const std::string &msg) {
 
 rift_status mdn_scratch(rift_mdn *m, int P) {
   if (P <= m->cap) return RIFT_OK;
-  cudaFree(m->head); cudaFree(m->cache); cudaFree(m->gout); cudaFree(m->loss);
-  m->head = m->cache = m->gout = m->loss = nullptr;
+  cudaFree(m->head); cudaFree(m->cache); cudaFree(m->gout); cudaFree(m->loss); cudaFree(m->ga);
+  m->head = m->cache = m->gout = m->loss = m->ga = nullptr;
   m->cap = 0;
   MCK(m, cudaMalloc(&m->head, sizeof(float) * (size_t)P * NO));
   MCK(m, cudaMalloc(&m->cache, sizeof(float) * (size_t)P * 2 * NH));
+  MCK(m, cudaMalloc(&m->ga, sizeof(float) * (size_t)P * 2 * NH));
   MCK(m, cudaMalloc(&m->gout, sizeof(float) * (size_t)P * NO));
   MCK(m, cudaMalloc(&m->loss, sizeof(float) * (size_t)P));
   m->cap = P;
@@ -466,7 +492,7 @@ rift_status rift_mdn_create(uint64_t seed, rift_mdn **out) {
 void rift_mdn_destroy(rift_mdn *m) {
   if (!m) return;
   cudaFree(m->master); cudaFree(m->m); cudaFree(m->v); cudaFree(m->grad); cudaFree(m->w);
-  cudaFree(m->head); cudaFree(m->cache); cudaFree(m->gout); cudaFree(m->loss);
+  cudaFree(m->head); cudaFree(m->cache); cudaFree(m->gout); cudaFree(m->loss); cudaFree(m->ga);
   delete m;
 }
 
@@ -513,7 +539,8 @@ rift_status rift_mdn_loss_grad(rift_mdn *m, int n, const float *summ_dev, const 
   MCK(m, cudaMemset(m->grad, 0, sizeof(float) * NPARAM));
   mdn_forward_kernel<<<n, 256>>>(m->w, summ_dev, n, m->head, m->cache);
   mdn_loss_kernel<<<n, 128>>>(m->head, theta_dev, w_dev, box_dev, H, 1.f / n, m->gout, m->loss);
-  mdn_backward_kernel<<<n, 256>>>(m->w, summ_dev, m->cache, m->gout, n, m->grad);
+  mdn_backward_kernel<<<n, 256>>>(m->w, m->cache, m->gout, n, m->ga);
+  mdn_wgrad_kernel<<<(NPARAM + 255) / 256, 256>>>(summ_dev, m->cache, m->gout, m->ga, n, m->grad);
   MCK(m, cudaGetLastError());
   std::vector<float> l(n);
   MCK(m, cudaMemcpy(l.data(), m->loss, sizeof(float) * n, cudaMemcpyDeviceToHost));
@@ -541,7 +568,8 @@ rift_status rift_mdn_train(rift_mdn *m, int n, const float *summ_dev, const floa
     const float *bx = box_dev + (size_t)p0 * 10;
     mdn_forward_kernel<<<nb, 256>>>(m->w, S, nb, m->head, m->cache);
     mdn_loss_kernel<<<nb, 128>>>(m->head, th, w, bx, H, 1.f / nb, m->gout, m->loss);
-    mdn_backward_kernel<<<nb, 256>>>(m->w, S, m->cache, m->gout, nb, m->grad);
+    mdn_backward_kernel<<<nb, 256>>>(m->w, m->cache, m->gout, nb, m->ga);
+    mdn_wgrad_kernel<<<(NPARAM + 255) / 256, 256>>>(S, m->cache, m->gout, m->ga, nb, m->grad);
     m->step += 1;
     const float bc1 = 1.f - std::pow(0.9f, (float)m->step), bc2 = 1.f - std::pow(0.999f, (float)m->step);
     mdn_adam_kernel<<<(NPARAM + 255) / 256, 256>>>(m->master, m->w, m->grad, m->m, m->v, NPARAM, (float)lr, bc1, bc2);

@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
 #pragma unroll
   for (int a = 0; a < kQModes; ++a) { accr[a] = df{0.f, 0.f}; acci[a] = df{0.f, 0.f}; }
   const float inv_n2 = 2.0f / (float)n;
+  float sts, stc;   // exp(2 pi i j / n), the twiddle's step between consecutive bins of a run
+  sincospif((float)(j % n) * inv_n2, &sts, &stc);
   int idx = 0;
   for (int b0 = 0; b0 < nb; b0 += kChunk) {
     const int cb = min(kChunk, nb - b0);
@@ -60,11 +62,20 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
     float pr[kQModes], pi[kQModes];
 #pragma unroll
     for (int a = 0; a < kQModes; ++a) { pr[a] = 0.f; pi[a] = 0.f; }
+    float sn = 0.f, cs = 1.f;
     for (int b = 0; b < cb; ++b) {
+      // the twiddle exp(2 pi i (nu_b j mod n) / n): exact (integer index into sincospi) at the start
+      // of a run of consecutive bins and every 16 bins; in between rotated by the thread's step
+      // exp(2 pi i j / n), so its error stays within about 16 roundings
       if (b == 0 || sRun[b]) idx = (int)(((long long)sNu[b] * j) % n);
       else { idx += j; if (idx >= n) idx -= n; }
-      float sn, cs;
-      sincospif((float)idx * inv_n2, &sn, &cs);
+      if (b == 0 || sRun[b] || (b & 15) == 0) {
+        sincospif((float)idx * inv_n2, &sn, &cs);
+      } else {
+        const float c2 = fmaf(cs, stc, -sn * sts);
+        sn = fmaf(sn, stc, cs * sts);
+        cs = c2;
+      }
 #pragma unroll
       for (int a = 0; a < kQModes; ++a) {
         const float2 x = sX[a][b];
@@ -86,33 +97,52 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
   }
 }
 
-// U and V of detector blockIdx.y, pair (a, b) over a flat thread index: Hw[k][b] = h_b w_k (formed on
-// the host in FP64, so the size of 1/S stays out of FP32), Hm[a] = h_a(-f); scale[k] undoes the
-// power-of-two scalings and carries 2 df.
-__global__ void quv_uv_kernel(const float2 *__restrict__ H, const float2 *__restrict__ Hm, const float2 *__restrict__ Hw,
-                              int nb, int M, double2 *__restrict__ U, double2 *__restrict__ V,
-                              const double *__restrict__ scale) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
-  if (p >= M * M) return;
-  const int a = p / M, b = p - a * M;
-  df ur{0.f, 0.f}, ui{0.f, 0.f}, vr{0.f, 0.f}, vi{0.f, 0.f};
-  float pur = 0.f, pui = 0.f, pvr = 0.f, pvi = 0.f;
+// U and V of detector blockIdx.y, pair (a, b) = blockIdx.x: the block's threads stride over the band
+// bins (coalesced loads), each keeping FP32 sums of its bins, then a block reduction in
+// double-float.  Hw[k][b] = h_b w_k (formed on the host in FP64, so the size of 1/S stays out of
+// FP32), Hm[a] = h_a(-f); scale[k] undoes the power-of-two scalings and carries 2 df.
+constexpr int kUVThreads = 256;
+
+__device__ __forceinline__ df df_shfl_down(df v, int o) {
+  return df{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+
+__global__ void __launch_bounds__(kUVThreads) quv_uv_kernel(const float2 *__restrict__ H, const float2 *__restrict__ Hm,
+                                                            const float2 *__restrict__ Hw, int nb, int M,
+                                                            double2 *__restrict__ U, double2 *__restrict__ V,
+                                                            const double *__restrict__ scale) {
+  __shared__ df sred[4][kUVThreads / 32];
+  const int pidx = blockIdx.x, k = blockIdx.y;
+  const int a = pidx / M, b = pidx - a * M;
   const float2 *ha = H + (size_t)a * nb, *hma = Hm + (size_t)a * nb, *yb = Hw + ((size_t)k * M + b) * nb;
-  for (int i = 0; i < nb; ++i) {
+  float pur = 0.f, pui = 0.f, pvr = 0.f, pvi = 0.f;
+  for (int i = threadIdx.x; i < nb; i += kUVThreads) {
     const float2 x = ha[i], y = yb[i], z = hma[i];
     pur = fmaf(x.x, y.x, fmaf(x.y, y.y, pur));     // conj(x) y
     pui = fmaf(x.x, y.y, fmaf(-x.y, y.x, pui));
     pvr = fmaf(z.x, y.x, fmaf(-z.y, y.y, pvr));    // z y
     pvi = fmaf(z.x, y.y, fmaf(z.y, y.x, pvi));
-    if ((i & 31) == 31 || i == nb - 1) {
-      df_acc(ur, pur); df_acc(ui, pui); df_acc(vr, pvr); df_acc(vi, pvi);
-      pur = pui = pvr = pvi = 0.f;
-    }
   }
-  const size_t o = ((size_t)k * M + a) * M + b;
-  const double sc = scale[k];
-  U[o] = make_double2(sc * ((double)ur.hi + ur.lo), sc * ((double)ui.hi + ui.lo));
-  V[o] = make_double2(sc * ((double)vr.hi + vr.lo), sc * ((double)vi.hi + vi.lo));
+  df v[4] = {df{pur, 0.f}, df{pui, 0.f}, df{pvr, 0.f}, df{pvi, 0.f}};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = df_add(v[c], df_shfl_down(v[c], o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sred[c][wid] = v[c];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    df t[4] = {df{0.f, 0.f}, df{0.f, 0.f}, df{0.f, 0.f}, df{0.f, 0.f}};
+    for (int w = 0; w < kUVThreads / 32; ++w)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) t[c] = df_add(t[c], sred[c][w]);
+    const size_t o = ((size_t)k * M + a) * M + b;
+    const double sc = scale[k];
+    U[o] = make_double2(sc * ((double)t[0].hi + t[0].lo), sc * ((double)t[1].hi + t[1].lo));
+    V[o] = make_double2(sc * ((double)t[2].hi + t[2].lo), sc * ((double)t[3].hi + t[3].lo));
+  }
 }
 
 // Power of two that brings the largest magnitude of a set near 1 (1 for an all-zero set).
@@ -264,9 +294,9 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   quv_q_kernel<<<gq, kQThreads, 0, st>>>((const float2 *)dH.p, (const float2 *)dB.p, (const int *)dnu.p,
                                          (const int *)drun.p, nb, M, nt, (int)n, (double2 *)dQ.p);
   cudaEventRecord(ev[1], st);
-  dim3 guv((M * M + 127) / 128, K);
-  quv_uv_kernel<<<guv, 128, 0, st>>>((const float2 *)dH.p, (const float2 *)dHm.p, (const float2 *)dHw.p, nb, M,
-                                     (double2 *)dU.p, (double2 *)dV.p, (const double *)dsc.p);
+  dim3 guv(M * M, K);
+  quv_uv_kernel<<<guv, kUVThreads, 0, st>>>((const float2 *)dH.p, (const float2 *)dHm.p, (const float2 *)dHw.p, nb,
+                                            M, (double2 *)dU.p, (double2 *)dV.p, (const double *)dsc.p);
   cudaEventRecord(ev[2], st);
   if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventSynchronize(ev[2])) == cudaSuccess) {
     float a = 0.f, b = 0.f;

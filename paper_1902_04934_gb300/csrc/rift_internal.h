@@ -29,6 +29,7 @@ struct AccState {
   double round_max; // max log weight of the last round (adaptive histograms)
   unsigned long long n;
   unsigned long long pad;
+  double round_neff;  // n_eff of the last round's draws alone: sum w / max w over the round
 };
 
 // One point's part of a Monte Carlo round (device array over points).
@@ -79,7 +80,8 @@ struct CellLaunch {
   int max_M;                   // largest mode count over the points (shared-memory layout)
   int max_pairK;               // largest npair * K over the points
   int max_nb;                  // largest bin count (0 if no point uses tables)
-  int learned;                 // every point samples from its learned proposal
+  int learned;                 // points sample from their learned proposal (R.proposal 2; a point that
+                               // fell back to the adaptive proposal draws from its tables)
   int fault_nan;               // injected fault: sample 0 of round 0 of every point has a NaN log weight
   int fault_stall;             // injected fault: window copies announced on the mbarrier but never issued
   int tmarg;                   // the event time is marginalised by quadrature (Eq. lnL:tmarg)
@@ -102,6 +104,8 @@ struct PtState {
   int rounds;
   int done;
   int ls[3];
+  int prop;       // proposal of the point's next round (learned points may fall back to adaptive)
+  int fb_round;   // first round on the adaptive proposal after a fallback, -1 if none
   int pad;
 };
 
@@ -123,6 +127,8 @@ struct BatchCtl {
   RoundPt *last;            // [np] the last round each point ran (harvest)
   int tmarg;                // the event time is marginalised by quadrature
   uint32_t point_id1;       // Philox point word of a single-point handle (batches use the point index)
+  double fallback_neff;     // learned points switch to the adaptive proposal after a round whose own
+                            // n_eff is below this (0: never)
 };
 
 // Scratch of the Monte Carlo runner (device pointers unless noted).

@@ -74,3 +74,20 @@ def test_batch_fixed_tables_matches_oracle(lib, cuda, batch_points):
         ref = mc.marginalize(pt, 14, p, mc.Prior(pt["t_lo"], pt["t_hi"]), 20000, 40000, 1e300, adaptive=True,
                              n_bins=nb, tables=tab, adapt_rounds=0, strata=(2, 2, 2))
         assert abs(res[p]["lnL_marg"] - ref["lnL_marg"]) < TOL_MARG
+
+
+def test_batch_graph_is_reused_and_recaptured(lib, cuda, batch_points):
+    """The handle keeps the instantiated graph of its last batched run: a second call with the same
+    options replays it (same results, bit for bit), other options capture a new one (the results of
+    those options), and going back gives the first results again."""
+    h = lib.rift_ile_batch_create(batch_points)
+    kw = dict(seed=12, n_per_round=20000, max_evals=60000, proposal="adaptive", n_bins=32)
+    a = lib.rift_ile_batch_marginalize(h, **kw)
+    b = lib.rift_ile_batch_marginalize(h, **kw)
+    assert a == b
+    c = lib.rift_ile_batch_marginalize(h, **dict(kw, seed=13))
+    fresh = lib.rift_ile_batch_create(batch_points)
+    assert c == lib.rift_ile_batch_marginalize(fresh, **dict(kw, seed=13))
+    assert a == lib.rift_ile_batch_marginalize(h, **kw)
+    lib.rift_ile_destroy(fresh)
+    lib.rift_ile_destroy(h)

@@ -201,3 +201,65 @@ def test_training_improves_on_the_prior(lib, cuda):
     learned = lib.rift_ile_batch_marginalize(ht, proposal="learned", mdn=m, **kw)
     gain = np.median([l["n_eff"] / p["n_eff"] for l, p in zip(learned, prior)])
     assert gain > 2.0, gain
+
+
+def _far_head():
+    """Every mixture component at the corner of the box with narrow widths: only the defensive prior
+    component of the proposal covers the likelihood, so the learned rounds' weights degenerate."""
+    head = np.zeros(mdn.N_OUT, dtype=np.float32)
+    head[mdn.N_COMP:mdn.N_COMP + 40] = 4.0
+    head[mdn.N_COMP + 40:] = -3.0
+    return head
+
+
+@pytest.mark.parametrize("path", ["single", "batched"])
+def test_learned_fallback_matches_oracle(lib, cuda, pts, path):
+    """The fallback to the adaptive sampler: a learned round whose own n_eff is below fallback_neff
+    hands the point to the adaptive proposal.  With the threshold just above the oracle's round-0
+    value the device falls back at round 1, as the oracle does, and the pooled lnL_marg (a learned
+    round, then an adaptive round from the prior's tables) agrees at 1e-4; with the threshold below
+    every learned round's n_eff the point stays learned."""
+    pt = pts[2]
+    pr = mc.Prior(pt["t_lo"], pt["t_hi"])
+    head = _far_head()
+    n = 20000
+    ref0 = mc.marginalize_learned(pt, 61, 0, pr, head.astype(np.float64), n, 2 * n, 1e300)
+    rn = ref0["round_neff"]
+    h = lib.rift_ile_create(pt) if path == "single" else lib.rift_ile_batch_create([pt])
+    lib.rift_ile_set_proposal_head(h, head[None])
+    run = lib.rift_ile_marginalize if path == "single" else (lambda hh, **kw: lib.rift_ile_batch_marginalize(hh, **kw)[0])
+    kw = dict(seed=61, n_per_round=n, max_evals=2 * n, proposal="learned", n_bins=32)
+    stay = run(h, fallback_neff=0.5 * min(rn), **kw)
+    assert stay["fallback_round"] == -1
+    assert abs(stay["lnL_marg"] - ref0["lnL_marg"]) < 1e-4
+    ref = mc.marginalize_learned(pt, 61, 0, pr, head.astype(np.float64), n, 2 * n, 1e300,
+                                 fallback_neff=1.01 * rn[0], n_bins=32)
+    assert ref["fallback_round"] == 1
+    got = run(h, fallback_neff=1.01 * rn[0], **kw)
+    assert got["fallback_round"] == 1 and got["n_evals"] == 2 * n and got["rounds"] == 2
+    assert abs(got["lnL_marg"] - ref["lnL_marg"]) < 1e-4, (got["lnL_marg"], ref["lnL_marg"])
+    assert abs(got["n_eff"] - ref["n_eff"]) <= 1e-3 * ref["n_eff"] + 1e-3
+    with pytest.raises(lib.RiftError):
+        lib.rift_ile_marginalize(lib.rift_ile_create(pt), seed=1, n_per_round=n, max_evals=n, fallback_neff=5.0)
+
+
+def test_training_is_deterministic(lib, cuda, pts):
+    """Weight gradients are sums over the batch's points in a fixed order (no float atomics): two
+    trainings from the same initial parameters on the same data give the same parameters, bit for
+    bit (the device gradient against the oracle is test_loss_and_gradient_match_oracle)."""
+    import torch
+    h = lib.rift_ile_batch_create(pts)
+    S = lib.rift_ile_batch_summary(h)
+    box = torch.as_tensor(lib.rift_ile_boxes(h), device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(4)
+    H = 32
+    theta = box[:, 0:1, :] + (box[:, 1:2, :] - box[:, 0:1, :]) * (0.05 + 0.9 * torch.rand((len(pts), H, 5), device="cuda",
+                                                                                         generator=g))
+    w = torch.full((len(pts), H), 1.0 / H, device="cuda")
+    out = []
+    for _ in range(2):
+        m = lib.rift_mdn_create(21)
+        lib.rift_mdn_train(m, S, theta, w, box, steps=50, batch=len(pts), lr=1e-3)
+        out.append(lib.rift_mdn_get_params(m))
+        lib.rift_mdn_destroy(m)
+    assert np.array_equal(out[0], out[1])

@@ -158,3 +158,42 @@ def test_summary_closed_form_gaussian_envelope():
     want += [t22[0] - t22[1], t22[0] - t22[2], t22[1] - t22[2]]
     want += [0.0] * (64 - len(want))
     assert np.allclose(s, np.array(want), rtol=0, atol=1e-12), np.max(np.abs(s - np.array(want)))
+
+
+def _far_head():
+    """A proposal head far from any posterior: every component at the corner of the box with
+    narrow widths, so that only the defensive prior component covers the likelihood."""
+    head = np.zeros(mdn.N_OUT)
+    head[mdn.N_COMP:mdn.N_COMP + 40] = 4.0
+    head[mdn.N_COMP + 40:] = -3.0
+    return head
+
+
+def _weak_point():
+    spec = W.PointSpec(dets=("H1", "L1", "V1"), modes=list(W.L2_MODES), fs=4096.0, snr=4.0, t_half=0.02,
+                       seg_len=4.0)
+    return W.make_point(spec, 41)
+
+
+def test_learned_fallback_switches_on_a_degenerate_round_and_stays_unbiased():
+    """The fallback of the learned proposal: with a head far from the posterior the learned rounds'
+    own n_eff (sum w / max w over a round) is small; a threshold below every learned round's keeps
+    the point learned, one just above round 0's hands it to the adaptive sampler from round 1 on.
+    The pooled estimate with the switch agrees with plain prior sampling within the Monte Carlo
+    errors (each round enters with its own q)."""
+    pt = _weak_point()
+    pr = mc.Prior(pt["t_lo"], pt["t_hi"])
+    head = _far_head()
+    n = 20000
+    learned = mc.marginalize_learned(pt, 3, 0, pr, head, n, 3 * n, 1e300)
+    rn = learned["round_neff"]
+    assert len(rn) == 3 and learned["fallback_round"] == -1
+    assert 1.0 < min(rn) and max(rn) < 0.2 * n
+    keep = mc.marginalize_learned(pt, 3, 0, pr, head, n, 3 * n, 1e300, fallback_neff=0.99 * min(rn))
+    assert keep["fallback_round"] == -1 and keep["lnL_marg"] == learned["lnL_marg"]
+    fb = mc.marginalize_learned(pt, 3, 0, pr, head, n, 8 * n, 1e300, fallback_neff=1.01 * rn[0], n_bins=32)
+    assert fb["fallback_round"] == 1 and fb["rounds"] == 8 and fb["acc"].n == 8 * n
+    assert fb["round_neff"][0] == rn[0]
+    plain = mc.marginalize(pt, 5, 0, pr, 100000, 400000, 1e300)
+    s = math.hypot(plain["sigma"], fb["sigma"])
+    assert abs(plain["lnL_marg"] - fb["lnL_marg"]) < 5 * s + 0.005, (plain["lnL_marg"], fb["lnL_marg"], s)
