@@ -26,15 +26,21 @@ constexpr int kChunk = 256;      // band bins staged per pass
 
 __device__ __forceinline__ void df_acc(df &acc, float v) { acc = df_add_f(acc, v); }
 
-// Q of detector blockIdx.z, modes [blockIdx.y * kQModes, +kQModes), times [blockIdx.x * kQThreads, +).
-// X[a][b] = conj(h_a(f_b)) B_k(f_b) is formed per staged chunk; the twiddle index nu_b j mod n
-// advances by j between consecutive bins of the same run and is recomputed at run starts.
+// Partial Q of detector blockIdx.z / slices over bin slice blockIdx.z % slices, modes
+// [blockIdx.y * kQModes, +kQModes), times [blockIdx.x * kQThreads, +): the band is cut into slices
+// of whole chunks so that enough CTAs run (one thread per grid time would leave the SMs nearly
+// idle); quv_q_reduce_kernel adds the slices.  X[a][b] = conj(h_a(f_b)) B_k(f_b) is formed per
+// staged chunk; the twiddle index nu_b j mod n advances by j between consecutive bins of the same
+// run and is recomputed at run starts.  Qp: [slices][K][M][nt] complex double.
 __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restrict__ H, const float2 *__restrict__ Bk,
                                                           const int *__restrict__ nu, const int *__restrict__ run_start,
-                                                          int nb, int M, int nt, int n, double2 *__restrict__ Q) {
+                                                          int nb, int M, int nt, int n, int slices,
+                                                          double2 *__restrict__ Qp) {
   __shared__ float2 sX[kQModes][kChunk];
   __shared__ int sNu[kChunk], sRun[kChunk];
-  const int k = blockIdx.z, a0 = blockIdx.y * kQModes;
+  const int k = blockIdx.z / slices, slice = blockIdx.z % slices, a0 = blockIdx.y * kQModes;
+  const int nchunk = (nb + kChunk - 1) / kChunk, per = (nchunk + slices - 1) / slices;
+  const int b_begin = min(nb, slice * per * kChunk), b_end = min(nb, (slice + 1) * per * kChunk);
   const int j = blockIdx.x * kQThreads + threadIdx.x;
   const int ma = min(kQModes, M - a0);
   df accr[kQModes], acci[kQModes];
@@ -44,8 +50,8 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
   float sts, stc;   // exp(2 pi i j / n), the twiddle's step between consecutive bins of a run
   sincospif((float)(j % n) * inv_n2, &sts, &stc);
   int idx = 0;
-  for (int b0 = 0; b0 < nb; b0 += kChunk) {
-    const int cb = min(kChunk, nb - b0);
+  for (int b0 = b_begin; b0 < b_end; b0 += kChunk) {
+    const int cb = min(kChunk, b_end - b0);
     __syncthreads();
     for (int t = threadIdx.x; t < cb * kQModes; t += blockDim.x) {
       const int a = t / cb, b = t - a * cb;
@@ -92,9 +98,22 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
 #pragma unroll
     for (int a = 0; a < kQModes; ++a)
       if (a < ma)
-        Q[((size_t)k * M + a0 + a) * nt + j] =
+        Qp[(((size_t)slice * (gridDim.z / slices) + k) * M + a0 + a) * nt + j] =
             make_double2((double)accr[a].hi + (double)accr[a].lo, (double)acci[a].hi + (double)acci[a].lo);
   }
+}
+
+// Q[k][m][j] = the sum over the slices of Qp, in slice order (FP64).
+__global__ void quv_q_reduce_kernel(const double2 *__restrict__ Qp, int slices, size_t count, double2 *__restrict__ Q) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < slices; ++s) {
+    const double2 v = Qp[(size_t)s * count + i];
+    re += v.x;
+    im += v.y;
+  }
+  Q[i] = make_double2(re, im);
 }
 
 // U and V of detector blockIdx.y, pair (a, b) = blockIdx.x: the block's threads stride over the band
@@ -264,7 +283,14 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
     }
   }
   cudaStream_t st = (cudaStream_t)d->cuda_stream;
-  DevBuf dH, dHm, dB, dHw, dnu, drun, dQ, dU, dV, dsc;
+  DevBuf dH, dHm, dB, dHw, dnu, drun, dQ, dU, dV, dsc, dQp;
+  // bin slices: about four CTAs per SM in all
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int ctas = ((nt + kQThreads - 1) / kQThreads) * ((M + kQModes - 1) / kQModes) * K;
+  const int nchunk = (nb + kChunk - 1) / kChunk;
+  const int slices = std::max(1, std::min(nchunk, (4 * nsm + ctas - 1) / ctas));
   cudaError_t e;
   auto up = [&](DevBuf &buf, const void *src, size_t bytes) {
     cudaError_t r = cudaMalloc(&buf.p, bytes);
@@ -279,6 +305,7 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
       (e = up(dnu, nuv.data(), sizeof(int) * nuv.size())) != cudaSuccess ||
       (e = up(drun, run.data(), sizeof(int) * run.size())) != cudaSuccess ||
       (e = cudaMalloc(&dQ.p, sizeof(double2) * (size_t)K * M * nt)) != cudaSuccess ||
+      (e = cudaMalloc(&dQp.p, sizeof(double2) * (size_t)slices * K * M * nt)) != cudaSuccess ||
       (e = cudaMalloc(&dU.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess ||
       (e = cudaMalloc(&dV.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess)
     return quv_fail(e == cudaErrorMemoryAllocation ? RIFT_ENOMEM : RIFT_ECUDA, cudaGetErrorString(e));
@@ -289,10 +316,13 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
       for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
       return quv_fail(RIFT_ECUDA, cudaGetErrorString(e));
     }
-  dim3 gq((nt + kQThreads - 1) / kQThreads, (M + kQModes - 1) / kQModes, K);
+  dim3 gq((nt + kQThreads - 1) / kQThreads, (M + kQModes - 1) / kQModes, K * slices);
   cudaEventRecord(ev[0], st);
   quv_q_kernel<<<gq, kQThreads, 0, st>>>((const float2 *)dH.p, (const float2 *)dB.p, (const int *)dnu.p,
-                                         (const int *)drun.p, nb, M, nt, (int)n, (double2 *)dQ.p);
+                                         (const int *)drun.p, nb, M, nt, (int)n, slices, (double2 *)dQp.p);
+  const size_t qcount = (size_t)K * M * nt;
+  quv_q_reduce_kernel<<<(unsigned)((qcount + 255) / 256), 256, 0, st>>>((const double2 *)dQp.p, slices, qcount,
+                                                                        (double2 *)dQ.p);
   cudaEventRecord(ev[1], st);
   dim3 guv(M * M, K);
   quv_uv_kernel<<<guv, kUVThreads, 0, st>>>((const float2 *)dH.p, (const float2 *)dHm.p, (const float2 *)dHw.p, nb,
