@@ -94,6 +94,16 @@ const char *rift_status_str(rift_status s);
 const char *rift_ile_last_error(const rift_ile *h);
 int rift_ile_n_points(const rift_ile *h);
 
+/* Forms the kernels take for point `point` of the handle, as bits of the return value (0 for a
+ * null handle or a point out of range): 1 the grouped quadratic form over the 21 canonical
+ * modes (Eq. (def:lnL:Decomposed) regrouped by m_b - m_a), 2 with the pairs skipped that vanish
+ * when each mode lives on one sign of frequency, 4 the positive form 2 beta^H U beta of a
+ * point whose modes have the reflection symmetry conj(h_a(-f)) = sigma_a h_abar(f), 8 the half
+ * rows of the time quadrature (Eq. (lnL:tmarg)): Q_abar(t) = sigma_a conj(Q_a(t)) holds at every
+ * sample (real data), so only the modes with m >= 0 are read.  Every form gives the same
+ * likelihood up to rounding; the flags only say which one runs. */
+unsigned rift_ile_forms(const rift_ile *h, int point);
+
 /*
  * Per-sample log-likelihood, Eq. (def:lnL:Decomposed), at caller-supplied samples
  * (point 0 of the handle).  Device pointers, float32, each of length n:

@@ -97,6 +97,7 @@ def _load():
         "rift_status_str": (C.c_char_p, [I]),
         "rift_ile_last_error": (C.c_char_p, [P]),
         "rift_ile_n_points": (I, [P]),
+        "rift_ile_forms": (C.c_uint, [P, I]),
         "rift_ile_lnL": (I, [P, S] + [P] * 8),
         "rift_ile_lnL_host": (I, [P, S] + [P] * 8),
         "rift_ile_lnL_tmarg": (I, [P, S] + [P] * 7),
@@ -298,6 +299,14 @@ def rift_ile_destroy(h):
     if h is not None and h.ptr:
         _lib.rift_ile_destroy(h.ptr)
         h.ptr = C.c_void_p(None)
+
+
+FORM_GROUPED, FORM_SPARSE, FORM_MIRROR, FORM_QHALF = 1, 2, 4, 8
+
+
+def rift_ile_forms(h, point=0):
+    """Bits of the forms the kernels take for `point` (FORM_* above; 0 for a bad index)."""
+    return int(_lib.rift_ile_forms(h.ptr, int(point)))
 
 
 def _dptr(t, n):

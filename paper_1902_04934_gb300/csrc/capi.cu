@@ -107,6 +107,7 @@ struct rift_ile {
   float *stage = nullptr;   // lnL_host staging [8][n]
   size_t stage_n = 0;
   int max_M = 0, max_pairK = 0;
+  int all_qhalf = 0;        // every point has the half rows of the time quadrature
   int interp = 3;
   int cell_target = 640;    // samples per stratification cell (autotuned)
   int smem_split = 3;       // shared-memory split of the cell kernel (sets the window budget; autotuned)
@@ -273,6 +274,67 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
       }
     }
   if (!finite) return fail(h, RIFT_EINVAL, "non-finite Q");
+  // merged rows for the time quadrature (tgrid_scan_half): for real data and modes with
+  // conj(h_a(-f)) = sigma_a h_abar(f), Eq. (QUV) gives Q_abar(t) = sigma_a conj(Q_a(t)); each pair
+  // (a, abar), m > 0, present with that relation at every sample (checked on the FP64 inputs to
+  // 1e-10 of the largest |Q|) is read from the row of a alone.  The slots are the stored modes
+  // but the merged m < 0 ones, in stored order; taken when at least one pair merges
+  {
+    double qmax = 0.0;
+    for (size_t i = 0; i < (size_t)2 * K * M * T; ++i) qmax = std::max(qmax, std::fabs(d->Q[i]));
+    const double tol = 1e-10 * qmax;
+    int mate[RIFT_MAXM], sg[RIFT_MAXM];   // mate[a]: the merged partner's stored index, else a
+    int merged = 0;
+    for (int a = 0; a < M; ++a) { mate[a] = a; sg[a] = 1; }
+    for (int a = 0; a < M; ++a) {
+      if (c.mode[a].m <= 0) continue;
+      int b = -1;
+      for (int e = 0; e < M; ++e)
+        if (c.mode[e].l == c.mode[a].l && c.mode[e].m == -c.mode[a].m) b = e;
+      if (b < 0) continue;
+      for (int sv = 1; sv >= -1; sv -= 2) {
+        bool match = true;
+        for (int k = 0; k < K && match; ++k) {
+          const double *qa = d->Q + 2 * (((size_t)k * M + perm[a]) * T);
+          const double *qb = d->Q + 2 * (((size_t)k * M + perm[b]) * T);
+          for (int j = 0; j < T && match; ++j)
+            match = std::fabs(qb[2 * j] - sv * qa[2 * j]) <= tol && std::fabs(qb[2 * j + 1] + sv * qa[2 * j + 1]) <= tol;
+        }
+        if (match) {
+          mate[a] = b;
+          mate[b] = a;
+          sg[a] = sv;
+          ++merged;
+          break;
+        }
+      }
+    }
+    int Mh = 0;
+    for (int a = 0; a < M; ++a)
+      if (!(c.mode[a].m < 0 && mate[a] != a)) ++Mh;
+    if (merged > 0 && Mh <= RIFT_MAXMH) {
+      Mh = 0;
+      for (int a = 0; a < M; ++a) {
+        if (c.mode[a].m < 0 && mate[a] != a) continue;
+        c.h_a[Mh] = (unsigned char)a;
+        c.h_b[Mh] = (unsigned char)mate[a];
+        if (sg[a] < 0) c.h_neg |= 1u << Mh;
+        ++Mh;
+      }
+      c.qhalf = 1;
+      c.Mh = Mh;
+      c.Mhp = (Mh + 1) & ~1;
+      const long long qh_off = (long long)qv.size();
+      c.qh_rel = qh_off - c.q_off;
+      qv.resize(qv.size() + (size_t)K * T * c.Mhp, make_float2(0.f, 0.f));
+      float2 *hb = qv.data() + qh_off;
+      const float2 *fb = qv.data() + c.q_off;
+      for (int k = 0; k < K; ++k)
+        for (int j = 0; j < T; ++j)
+          for (int hh = 0; hh < Mh; ++hh)
+            hb[((size_t)k * T + j) * c.Mhp + hh] = fb[((size_t)k * T + j) * c.Mp + c.h_a[hh]];
+    }
+  }
   // pair coefficients [pair_slot(a, b)][K] = (U, V) upper triangle, off-diagonal doubled
   c.uv_off = (long long)cv.size();
   cv.resize(cv.size() + (size_t)c.npair * K);
@@ -463,6 +525,7 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
     }
     h->max_M = std::max(h->max_M, h->pts[i].c.M);
     h->max_pairK = std::max(h->max_pairK, h->pts[i].c.ncoef);
+    h->all_qhalf = (i == 0 || h->all_qhalf) && h->pts[i].c.qhalf;
     if (descs[i].interp != descs[0].interp) {
       rift_status s2 = fail(h, RIFT_EINVAL, "points differ in interp");
       rift_ile_destroy(h);
@@ -620,6 +683,39 @@ void choose_strata_sky(uint32_t n, int ls[3], int target) {
   ls[1] = L / 2;
   ls[0] = L - ls[1];
   ls[2] = 0;
+}
+
+// Launch shape of the cell kernel: tm (0 sampled time, 1 time quadrature, 2 the quadrature's GEMM
+// form, taken when every point has merged rows and the block holds the GEMM's arrays with the
+// harmonics of the setup), the harmonics rows reserved in shared memory, the window budget and the
+// dynamic shared memory of a block.
+struct CellShape {
+  int tm, ys_modes;
+  long long budget;
+  size_t smem;
+};
+CellShape cell_shape(const rift_ile *h, int K, int NT, int time_marg, int ys_modes, int coef_f4, int nb, int smem_sm) {
+  const int block = RIFT_CELL_BLOCK;
+  CellShape c{};
+  if (time_marg && h->all_qhalf) {
+    const size_t fixed = cells_smem_fixed(K, 0, coef_f4, nb, block);
+    const long long budget = ((long long)RIFT_CELLS_MAX_DYN_SMEM - (long long)fixed) & ~15ll;
+    const TgLayout T = tg_layout(K, NT, RIFT_MAXMH, (unsigned)std::max(0ll, budget));
+    if (budget > 0 && T.rmax >= 64 && (long long)(T.end - T.S) >= 8ll * h->max_M * block) {
+      c.tm = 2;
+      c.ys_modes = 0;
+      c.budget = budget;
+      c.smem = fixed + (size_t)budget;
+      return c;
+    }
+  }
+  c.tm = time_marg ? 1 : 0;
+  c.ys_modes = ys_modes;
+  const size_t fixed = cells_smem_fixed(K, ys_modes, coef_f4, nb, block);
+  long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
+  c.budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
+  c.smem = fixed + (size_t)c.budget;
+  return c;
 }
 
 int log2_pow2(int v) {
@@ -795,12 +891,12 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   const MirrorCoefParam *mp = (np == 1 && h->mirror0 && NT == 4 && !learned && !o->time_marg) ? h->mirror0 : nullptr;
   const int coef_f4 = (cc || mp) ? 0 : h->max_pairK;
   // a mirror-symmetric point with all 21 modes keeps its harmonics in registers (no shared buffer)
-  const int ys_modes = (mp && h->pts[0].c.M == RIFT_MAXM) ? 0 : h->max_M;
-  const size_t fixed = cells_smem_fixed(K, ys_modes, coef_f4, nb, block);
-  long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
-  budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
-  const size_t smem = fixed + (size_t)budget;
-  int bps = cells_blocks_per_sm(K, NT, smem, block, o->time_marg ? 1 : 0);
+  const CellShape shp = cell_shape(h, K, NT, o->time_marg, (mp && h->pts[0].c.M == RIFT_MAXM) ? 0 : h->max_M,
+                                   coef_f4, nb, smem_sm);
+  const int ys_modes = shp.ys_modes, tm = shp.tm;
+  const long long budget = shp.budget;
+  const size_t smem = shp.smem;
+  int bps = cells_blocks_per_sm(K, NT, smem, block, tm);
   if (bps < 1) return fail(h, RIFT_EUNSUPPORTED, "cell kernel does not fit on an SM");
   CellLaunch L{};
   L.seed = o->seed;
@@ -825,7 +921,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.learned = learned ? 1 : 0;
   L.fault_nan = fault_is("nan_sample") ? 1 : 0;
   L.fault_stall = fault_is("stage_timeout") ? 1 : 0;
-  L.tmarg = o->time_marg ? 1 : 0;
+  L.tmarg = tm;
   std::vector<uint64_t> evals(np, 0);
   std::vector<int> rounds(np, 0), done(np, 0), nrun(np, 0);
   std::vector<int> prop(np, learned ? 2 : (adaptive ? 1 : 0)), fb_round(np, -1);
@@ -1005,6 +1101,12 @@ const char *rift_status_str(rift_status s) {
 
 const char *rift_ile_last_error(const rift_ile *h) { return h ? h->err.c_str() : "null handle"; }
 int rift_ile_n_points(const rift_ile *h) { return h ? h->n_points : 0; }
+
+unsigned rift_ile_forms(const rift_ile *h, int point) {
+  if (!h || point < 0 || point >= h->n_points) return 0u;
+  const PointC &c = h->pts[point].c;
+  return (c.grouped ? 1u : 0u) | (c.canon_sparse ? 2u : 0u) | (c.mirror ? 4u : 0u) | (c.qhalf ? 8u : 0u);
+}
 
 rift_status rift_ile_create(const rift_ile_desc *desc, rift_ile **out) { return create_impl(desc, 1, out); }
 
@@ -1296,11 +1398,11 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   const int block = RIFT_CELL_BLOCK;
   int smem_sm = 0;
   RIFT_CK(h, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
-  const size_t fixed = cells_smem_fixed(K, h->max_M, h->max_pairK, nb, block);
-  long long budget = ((long long)smem_sm / h->smem_split - (long long)fixed - 2048) & ~15ll;
-  budget = std::max(16ll * 1024, std::min(160ll * 1024, budget));
-  const size_t smem = fixed + (size_t)budget;
-  const int bps = cells_blocks_per_sm(K, NT, smem, block, o->time_marg ? 1 : 0);
+  const CellShape shp = cell_shape(h, K, NT, o->time_marg, h->max_M, h->max_pairK, nb, smem_sm);
+  const int tm = shp.tm;
+  const long long budget = shp.budget;
+  const size_t smem = shp.smem;
+  const int bps = cells_blocks_per_sm(K, NT, smem, block, tm);
   if (bps < 1) return fail(h, RIFT_EUNSUPPORTED, "cell kernel does not fit on an SM");
   CellLaunch L{};
   L.seed = o->seed;
@@ -1318,13 +1420,13 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   L.ell_buf = keep ? S.ell : nullptr;
   L.bin_buf = keep ? S.bins : nullptr;
   L.flags = h->flags;
-  L.max_M = h->max_M;
+  L.max_M = shp.ys_modes;
   L.max_pairK = h->max_pairK;
   L.max_nb = nb;
   L.learned = learned ? 1 : 0;
   L.fault_nan = fault_is("nan_sample") ? 1 : 0;
   L.fault_stall = fault_is("stage_timeout") ? 1 : 0;
-  L.tmarg = o->time_marg ? 1 : 0;
+  L.tmarg = tm;
   const int grid = h->num_sms * bps;
   // capture G rounds: update -> cells -> merge -> (adaptive) hist -> tables
   const int G = std::max(1, h->graph_rounds);

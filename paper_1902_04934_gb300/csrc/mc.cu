@@ -291,9 +291,329 @@ __device__ __forceinline__ void delay_index(const PointC &P, const Sky &s, df ou
   }
 }
 
+// Antenna patterns F_k = F+ - i Fx of a draw: the pattern at psi = 0 rotated by e^{2 i psi},
+// 2 psi = 2 pi u_psi.
+template <int K>
+__device__ __forceinline__ void antenna_of(const PointC &P, const Sky &s, float u_psi, SampleGeo &g) {
+  float s2p, c2p;
+  sincospif(2.f * u_psi, &s2p, &c2p);
+  const float ex = -s.sa, ey = s.ca;
+  const float fx = -s.sd.hi * s.ca, fy = -s.sd.hi * s.sa, fz = s.cd;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float *dd = P.det[k].d;
+    const float dex = dd[0] * ex + dd[1] * ey;
+    const float dey = dd[1] * ex + dd[3] * ey;
+    const float dez = dd[2] * ex + dd[4] * ey;
+    const float ee = ex * dex + ey * dey;
+    const float ff = fx * (dd[0] * fx + dd[1] * fy + dd[2] * fz) + fy * (dd[1] * fx + dd[3] * fy + dd[4] * fz) +
+                     fz * (dd[2] * fx + dd[4] * fy + dd[5] * fz);
+    const float ef = fx * dex + fy * dey + fz * dez;
+    const float fr = ee - ff, fi = 2.f * ef;
+    g.F[k] = make_float2(c2p * fr - s2p * fi, s2p * fr + c2p * fi);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Time quadrature of an item as a GEMM (Eq. (lnL:tmarg)).  The item's draws (one per thread) are
+// set up first: harmonics, quadratic form, merged-row coefficients G (tmarg_prep), weights and
+// first rows.  They are sorted by a key of their first rows, so that each group of 32 consecutive
+// slots comes from a small patch of sky, and each group is scanned in chunks of the time grid: for
+// every detector the union of the group's rows of the chunk is staged in shared memory
+// (cp.async.bulk, double buffered), the row sums S[row][draw] = sum_e Q[row][e] G[e][draw] are
+// formed by all threads in tiles of 8 rows x 4 draws (each row and coefficient loaded once per
+// tile), and each draw then interpolates its own rows of S into lin_j.  A Q row is thus read once
+// per group instead of once per draw.  Items whose groups spread over more rows than the block
+// holds take the per-draw scan (tgrid_rows) instead.
+// ---------------------------------------------------------------------------
+constexpr int kTgLin = 32;   // time points per epilogue thread per chunk (chunks of at most 8 kTgLin)
+
+__device__ __forceinline__ uint32_t spread_bits16(uint32_t v) {
+  v &= 0xFFFFu;
+  v = (v | (v << 8)) & 0x00FF00FFu;
+  v = (v | (v << 4)) & 0x0F0F0F0Fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+template <int K, int NT, int LEARNED>
+__device__ __forceinline__ void tmarg_gemm_item(const CellLaunch &L, const PointC &P, const RoundPt &R,
+                                                const float4 *C, const float *tab, const float *lnw,
+                                                const float *s_gmm, unsigned char *wbuf, uint64_t *tbar,
+                                                uint32_t &tph, uint32_t j0, uint32_t j_end, float &m, float &s1,
+                                                float &s2, float &cnt, uint32_t &flags, bool &ok) {
+  constexpr int B = RIFT_CELL_BLOCK;
+  constexpr int HP = RIFT_MAXMH / 2;
+  const TgLayout T = tg_layout(K, NT, RIFT_MAXMH, (unsigned)L.win_budget);
+  float4 *G = reinterpret_cast<float4 *>(wbuf + T.G);   // [K][HP][B]
+  float *W = reinterpret_cast<float *>(wbuf + T.W);       // [K][NT][B]
+  int *R0 = reinterpret_cast<int *>(wbuf + T.R0);         // [K][B]
+  float *CX = reinterpret_cast<float *>(wbuf + T.CX);
+  float *XX = reinterpret_cast<float *>(wbuf + T.XX);
+  uint2 *KEY = reinterpret_cast<uint2 *>(wbuf + T.KEY);
+  int *POS = reinterpret_cast<int *>(wbuf + T.POS);
+  float2 *LT = reinterpret_cast<float2 *>(wbuf + T.LT);
+  float *LN = reinterpret_cast<float *>(wbuf + T.LN);
+  int *GM = reinterpret_cast<int *>(wbuf + T.GM);         // [2][K][B / 32]: min, max of r0 per group
+  float *S = reinterpret_cast<float *>(wbuf + T.S);       // [rmax][RIFT_TG_SROW]
+  float2 *QS = reinterpret_cast<float2 *>(wbuf + T.QS);   // [2][rmax][RIFT_MAXMH]
+  float2 *Ys = reinterpret_cast<float2 *>(wbuf + T.S) + threadIdx.x;   // harmonics, setup only
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int n_it = (int)(j_end - j0);
+  const int J = P.J;
+  const float2 *Qh = L.qa + P.q_off + P.qh_rel;
+
+  // 1. setup of draw j0 + t
+  float4 g[K][HP];
+  float w[K][NT];
+  int r0[K];
+  float x = 0.f, quad = 0.f, lpq = 0.f;
+  uint32_t bins = 0u, i = 0u, key = 0xFFFFFFFFu;
+  const bool valid = t < n_it;
+  if (valid) {
+    i = j0 + (uint32_t)t;
+    const Drawn d = draw_any<LEARNED, 1>(L.seed, R, i, cell_of(R, i), tab, lnw, s_gmm, P.dref, L.d_lo3, L.d_span3);
+    const Sky s = sky_of(P, d);
+    SampleGeo gg;
+    {
+      df si[K];
+      delay_index<K>(P, s, si);
+#pragma unroll
+      for (int k = 0; k < K; ++k) gg.s[k] = si[k];
+    }
+    antenna_of<K>(P, s, d.u_psi, gg);
+    gg.x = d.xd;
+    float sphi, cphi;
+    sincospif(2.f * d.u_phi, &sphi, &cphi);
+    const float ch = sqrtf(d.c_frac), sh = sqrtf(1.f - d.c_frac);
+    swsh_canonical(P, ch, sh, cphi, sphi, Ys, B);
+    quad = quad_cell<K, NT, 0>(P, C, nullptr, gg, Ys, B, ch, sh, d.u_phi);
+    tmarg_prep<K, NT>(P, gg.s, gg.F, Ys, B, g, w, r0, flags);
+    x = gg.x;
+    lpq = d.lpq;
+    bins = d.bins;
+    const uint32_t k0 = (uint32_t)min(r0[0], 0xFFFF), k1 = (K > 1) ? (uint32_t)min(r0[K > 1 ? 1 : 0], 0xFFFF) : 0u;
+    key = min(spread_bits16(k0) | (spread_bits16(k1) << 1), 0xFFFFFFFEu);
+  }
+  // 2. sort the draws by key (bitonic, ties by thread): slot POS[t] of thread t
+  KEY[t] = make_uint2(key, (uint32_t)t);
+  __syncthreads();
+  for (int size = 2; size <= B; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int b = t ^ stride;
+      if (b > t) {
+        const uint2 ka = KEY[t], kb = KEY[b];
+        const bool gt = ka.x > kb.x || (ka.x == kb.x && ka.y > kb.y);
+        if (gt == ((t & size) == 0)) { KEY[t] = kb; KEY[b] = ka; }
+      }
+      __syncthreads();
+    }
+  POS[KEY[t].y] = t;
+  __syncthreads();
+  const int slot = POS[t];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int h2 = 0; h2 < HP; ++h2) G[(k * HP + h2) * B + slot] = valid ? g[k][h2] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < NT; ++r) W[(k * NT + r) * B + slot] = valid ? w[k][r] : 0.f;
+    R0[k * B + slot] = valid ? r0[k] : 0;
+  }
+  CX[slot] = valid ? -0.25f * x * quad : 0.f;
+  XX[slot] = valid ? x : 0.f;
+  __syncthreads();
+  // 3. row span of each group of 32 slots (invalid slots sort last and are left out)
+  const int ngroups = (n_it + 31) >> 5;
+  if (wid < ngroups) {
+    const bool v = 32 * wid + lane < n_it;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int r = R0[k * B + 32 * wid + lane];
+      const int mn = __reduce_min_sync(0xffffffffu, v ? r : INT_MAX);
+      const int mx = __reduce_max_sync(0xffffffffu, v ? r : INT_MIN);
+      if (lane == 0) { GM[k * (B / 32) + wid] = mn; GM[(K + k) * (B / 32) + wid] = mx; }
+    }
+  }
+  __syncthreads();
+  // chunk of the time grid of group wg: the union of its rows for a chunk of cj points, cj + NT - 1
+  // + (spread of its first rows), fits the block, and preferably B rows (one tile per thread); at
+  // most 8 kTgLin, a multiple of 8
+  auto chunk_of = [&](int wg) {
+    int sp = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sp = max(sp, GM[(K + k) * (B / 32) + wg] - GM[k * (B / 32) + wg]);
+    const int one = (min(T.rmax, B) - (NT - 1) - sp) & ~7;
+    return min(one >= 64 ? one : ((T.rmax - (NT - 1) - sp) & ~7), 8 * kTgLin);
+  };
+  bool gemm = T.rmax >= 64;
+  for (int wg = 0; wg < ngroups && gemm; ++wg) gemm = chunk_of(wg) >= 32;
+
+  float lnL = NAN;
+  if (!gemm) {
+    // 4a. per-draw scan over the cached rows
+    if (valid) {
+      float em = -INFINITY, es = 0.f;
+      tgrid_rows<K, NT>(P, Qh, g, w, r0, x, quad, [&](int, float l) {
+        if (l > em) { es = fmaf(es, expf(em - l), 1.f); em = l; }
+        else es += expf(l - em);
+      });
+      lnL = em + logf(es) - logf((float)J);
+    }
+  } else {
+    // 4b. stages (group, chunk, detector) in order; stage q fills buffer q & 1, issued two ahead by
+    // thread 0 once the buffer is free
+    const int rs = P.Mhp >> 1, npairs = (P.Mh + 1) >> 1;
+    int iw = 0, ijc = 0, ik = 0;   // next stage to issue (thread 0)
+    int issued = 0, consumed = 0;
+    auto issue_next = [&]() {
+      if (iw >= ngroups) return;
+      const int buf = issued & 1;
+      const int cj = min(chunk_of(iw), J - ijc);
+      const int gmn = GM[ik * (B / 32) + iw];
+      const int nrows = cj + NT - 1 + (GM[(K + ik) * (B / 32) + iw] - gmn);
+      const uint32_t bytes = (uint32_t)nrows * (uint32_t)P.Mhp * 8u;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&tbar[buf], bytes);
+      bulk_g2s(QS + (size_t)buf * T.rmax * RIFT_MAXMH, Qh + ((long long)ik * P.T + gmn + ijc) * P.Mhp, bytes,
+               &tbar[buf]);
+      ++issued;
+      if (++ik == K) {
+        ik = 0;
+        ijc += chunk_of(iw);
+        if (ijc >= J) { ijc = 0; ++iw; }
+      }
+    };
+    if (t == 0) { issue_next(); issue_next(); }
+    const int dl = lane, jq = wid;
+    for (int wg = 0; wg < ngroups && ok; ++wg) {
+      const int cjg = chunk_of(wg);
+      const int pslot = 32 * wg + dl;
+      const bool pv = pslot < n_it;
+      float em = -INFINITY, es = 0.f;
+      for (int jc = 0; jc < J && ok; jc += cjg) {
+        const int cj = min(cjg, J - jc);
+        const int jlo = (jq * cj) >> 3, nj = (((jq + 1) * cj) >> 3) - jlo;
+        float lin[kTgLin];
+#pragma unroll
+        for (int jj = 0; jj < kTgLin; ++jj) lin[jj] = 0.f;
+        for (int k = 0; k < K; ++k) {
+          const int buf = consumed & 1;
+          const uint32_t par = (tph >> buf) & 1u;
+          ok = __syncthreads_and(mbar_wait(&tbar[buf], par) ? 1 : 0) != 0;
+          if (!ok) { flags |= RIFT_FLAG_TIMEOUT_BIT; break; }
+          tph ^= 1u << buf;
+          ++consumed;
+          const int gmn = GM[k * (B / 32) + wg];
+          const int nrows = cj + NT - 1 + (GM[(K + k) * (B / 32) + wg] - gmn);
+          const int ntask = ((nrows + 7) >> 3) * 8;
+          const float4 *Qb = reinterpret_cast<const float4 *>(QS + (size_t)buf * T.rmax * RIFT_MAXMH);
+          const float4 *Gk = G + (size_t)k * HP * B + 32 * wg;
+          for (int task = t; task < ntask; task += B) {
+            const int rt = task >> 3, td = task & 7;
+            float acc[8][4];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+#pragma unroll
+            for (int e4 = 0; e4 < HP; ++e4) {
+              if (e4 < npairs) {
+                float4 gv[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) gv[c] = Gk[e4 * B + td + 8 * c];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                  const float4 qv = Qb[(8 * rt + q) * rs + e4];
+#pragma unroll
+                  for (int c = 0; c < 4; ++c)
+                    acc[q][c] = fmaf(qv.x, gv[c].x, fmaf(qv.y, gv[c].y, fmaf(qv.z, gv[c].z, fmaf(qv.w, gv[c].w, acc[q][c]))));
+                }
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) S[(8 * rt + q) * RIFT_TG_SROW + td + 8 * c] = acc[q][c];
+          }
+          __syncthreads();
+          if (t == 0) issue_next();   // buffer `buf` is free again
+          if (pv) {
+            const int off = R0[k * B + pslot] - gmn + jlo;
+            float wk[NT], tap[NT];
+#pragma unroll
+            for (int r = 0; r < NT; ++r) wk[r] = W[(k * NT + r) * B + pslot];
+#pragma unroll
+            for (int r = 0; r < NT - 1; ++r) tap[r] = S[(off + r) * RIFT_TG_SROW + dl];
+#pragma unroll
+            for (int jj = 0; jj < kTgLin; ++jj) {
+              if (jj < nj) {
+                tap[NT - 1] = S[(off + jj + NT - 1) * RIFT_TG_SROW + dl];
+                float v = 0.f;
+#pragma unroll
+                for (int r = 0; r < NT; ++r) v = fmaf(wk[r], tap[r], v);
+                lin[jj] += v;
+#pragma unroll
+                for (int r = 0; r < NT - 1; ++r) tap[r] = tap[r + 1];
+              }
+            }
+          }
+          __syncthreads();   // S is rewritten by the next stage
+        }
+        if (ok && pv) {
+          const float xx = XX[pslot], cc = CX[pslot];
+#pragma unroll
+          for (int jj = 0; jj < kTgLin; ++jj) {
+            if (jj < nj) {
+              const float l = xx * (lin[jj] + cc);
+              if (l > em) { es = fmaf(es, expf(em - l), 1.f); em = l; }
+              else es += expf(l - em);
+            }
+          }
+        }
+      }
+      if (!ok) break;
+      LT[t] = make_float2(em, es);
+      __syncthreads();
+      if (t < 32 && 32 * wg + t < n_it) {
+        float M = -INFINITY;
+        for (int q = 0; q < B / 32; ++q) M = fmaxf(M, LT[q * 32 + t].x);
+        float sum = 0.f;
+        for (int q = 0; q < B / 32; ++q) {
+          const float2 e = LT[q * 32 + t];
+          if (e.y != 0.f) sum += e.y * expf(e.x - M);
+        }
+        LN[32 * wg + t] = M + logf(sum) - logf((float)J);
+      }
+      __syncthreads();
+    }
+    if (!ok) {
+      // copies still in flight into this CTA's shared memory: wait for them (bounded) before the
+      // caller stops
+      for (; consumed < issued; ++consumed) {
+        const int buf = consumed & 1;
+        mbar_wait(&tbar[buf], (tph >> buf) & 1u);
+        tph ^= 1u << buf;
+      }
+      return;
+    }
+    if (valid) lnL = LN[slot];
+  }
+  // 5. the draw's log weight
+  if (valid) {
+    float ell = lnL + lpq;
+    if (L.fault_nan && i == 0u && R.round == 0u) ell = __int_as_float(0x7fc00000);   // injected (host-requested) fault
+    if (L.dbg_ell && R.dbg_off >= 0) L.dbg_ell[R.dbg_off + i] = ell;
+    if (L.ell_buf && R.ell_off >= 0) { L.ell_buf[R.ell_off + i] = ell; L.bin_buf[R.ell_off + i] = bins; }
+    if (isfinite(ell)) { lse_push(ell, m, s1, s2); cnt += 1.f; }
+    else flags |= RIFT_FLAG_NONFINITE;
+  }
+}
+
 // TMARG: the event time is marginalised by quadrature (Eq. lnL:tmarg) instead of sampled; the
 // sample's t uniform is unused, its Q rows span the whole time window (no staging), and the
-// likelihood is tmarg_term.
+// likelihood is tmarg_term: each point reads its half rows (tgrid_scan_half) when it has them, and
+// TMARG 2, for launches whose points all have them, compiles only that path (fewer registers).
 // YR: a mirror-symmetric point with all 21 modes in the parameter bank (CP 3), harmonics in
 // registers (linear_term_yreg): no per-thread harmonics buffer in shared memory (L.max_M = 0), so
 // the room goes to the Q windows.
@@ -301,6 +621,7 @@ template <int K, int NT, int LEARNED, int TMARG, int CP, int YR = 0>
 __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__restrict__ cpg) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t tbar[2];   // staged Q rows of the time-quadrature GEMM (TMARG 2)
   __shared__ int s_item, s_point;
   __shared__ RoundPt sR;
   __shared__ float s_gmm[RIFT_GMM_FLOATS];
@@ -324,11 +645,12 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
+    if (TMARG == 2) { mbar_init(&tbar[0], 1); mbar_init(&tbar[1], 1); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_point = -1;
   }
   __syncthreads();
-  uint32_t phase = 0;
+  uint32_t phase = 0, tph = 0;
   int cur = -1;
   uint32_t flags = 0u;
   const uint32_t n_items = *L.n_items;
@@ -470,6 +792,10 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
 
     // C. evaluate
     float m = kNegInf, s1 = 0.f, s2 = 0.f, cnt = 0.f;
+    if constexpr (TMARG == 2) {
+      tmarg_gemm_item<K, NT, LEARNED>(L, P, R, C, tab, lnw, s_gmm, wbuf, tbar, tph, j0, j_end, m, s1, s2, cnt, flags,
+                                      ok);
+    } else {
     for (uint32_t j = j0 + threadIdx.x; j < j_end; j += blockDim.x) {
       const uint32_t i = TMARG ? j : sample_index(R, cell, j);
       const Drawn d = draw_any<LEARNED, TMARG>(L.seed, R, i, TMARG ? cell_of(R, i) : cell, tab, lnw, s_gmm, P.dref,
@@ -478,29 +804,10 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
       df si[K];
       if (TMARG) delay_index<K>(P, s, si);
       else time_index<K>(P, d, s, si);
-      float s2p, c2p;
-      sincospif(2.f * d.u_psi, &s2p, &c2p);   // 2 psi = 2 pi u_psi
       SampleGeo g;
 #pragma unroll
       for (int k = 0; k < K; ++k) g.s[k] = si[k];
-      // antenna pattern at psi = 0 rotated by e^{2 i psi}
-      {
-        const float ex = -s.sa, ey = s.ca;
-        const float fx = -s.sd.hi * s.ca, fy = -s.sd.hi * s.sa, fz = s.cd;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float *dd = P.det[k].d;
-          const float dex = dd[0] * ex + dd[1] * ey;
-          const float dey = dd[1] * ex + dd[3] * ey;
-          const float dez = dd[2] * ex + dd[4] * ey;
-          const float ee = ex * dex + ey * dey;
-          const float ff = fx * (dd[0] * fx + dd[1] * fy + dd[2] * fz) + fy * (dd[1] * fx + dd[3] * fy + dd[4] * fz) +
-                           fz * (dd[2] * fx + dd[4] * fy + dd[5] * fz);
-          const float ef = fx * dex + fy * dey + fz * dez;
-          const float fr = ee - ff, fi = 2.f * ef;
-          g.F[k] = make_float2(c2p * fr - s2p * fi, s2p * fr + c2p * fi);
-        }
-      }
+      antenna_of<K>(P, s, d.u_psi, g);
       g.x = d.xd;
       float sphi, cphi;
       sincospif(2.f * d.u_phi, &sphi, &cphi);
@@ -512,7 +819,7 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
       float lnL;
       if (TMARG) {
         const float quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
-        lnL = tmarg_term<K, NT>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
+        lnL = tmarg_term<K, NT, TMARG == 2 ? 1 : -1>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
       } else {
         // the quadratic form first: the d_lm it takes from the harmonics are then dead before the
         // linear term's taps are loaded
@@ -539,6 +846,7 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
       if (L.ell_buf && R.ell_off >= 0) { L.ell_buf[R.ell_off + i] = ell; L.bin_buf[R.ell_off + i] = d.bins; }
       if (isfinite(ell)) { lse_push(ell, m, s1, s2); cnt += 1.f; }
       else flags |= RIFT_FLAG_NONFINITE;
+    }
     }
     // D. one partial per cell
 #pragma unroll
@@ -567,8 +875,9 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
     __syncthreads();   // windows, partial slots and the point cache are reused by the next item
     if (!ok) {
       // the copies did not complete in time: wait once more (bounded) so none is left in
-      // flight into this CTA's shared memory, then stop; the flag reports the failure
-      mbar_wait(&bar, phase);
+      // flight into this CTA's shared memory, then stop; the flag reports the failure (the
+      // time-quadrature GEMM has waited for its own copies)
+      if (TMARG != 2) mbar_wait(&bar, phase);
       break;
     }
   }
@@ -925,7 +1234,7 @@ cudaError_t cells_kl(const CellLaunch &L, int grid, int block, size_t smem, cuda
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED, TMARG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -941,9 +1250,9 @@ cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaS
       static bool attr = false;
       if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(cells_kernel_mp<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(cells_kernel_mp<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
         if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(cells_kernel_mp<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+          e = cudaFuncSetAttribute(cells_kernel_mp<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
       }
@@ -956,9 +1265,9 @@ cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaS
       static bool attr = false;
       if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(cells_kernel_cp<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            cudaFuncSetAttribute(cells_kernel_cp<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
         if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(cells_kernel_cp<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+          e = cudaFuncSetAttribute(cells_kernel_cp<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
       }
@@ -970,6 +1279,8 @@ cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaS
   (void)cc;
   (void)cc_sparse;
   (void)mp;
+  if (L.tmarg == 2)
+    return L.learned ? cells_kl<K, NT, 1, 2>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 2>(L, grid, block, smem, st);
   if (L.tmarg) return L.learned ? cells_kl<K, NT, 1, 1>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 1>(L, grid, block, smem, st);
   return L.learned ? cells_kl<K, NT, 1, 0>(L, grid, block, smem, st) : cells_kl<K, NT, 0, 0>(L, grid, block, smem, st);
 }
@@ -977,13 +1288,14 @@ cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaS
 template <int K, int NT, int LEARNED, int TMARG>
 int cells_occ1(size_t smem, int block) {
   int nb = 0;
-  cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED, TMARG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(cells_kernel<K, NT, LEARNED, TMARG>, cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_kernel<K, NT, LEARNED, TMARG>, block, smem);
   return nb;
 }
 
 template <int K, int NT>
 int cells_occ(size_t smem, int block, int tmarg) {
+  if (tmarg == 2) return std::min(cells_occ1<K, NT, 0, 2>(smem, block), cells_occ1<K, NT, 1, 2>(smem, block));
   if (tmarg) return std::min(cells_occ1<K, NT, 0, 1>(smem, block), cells_occ1<K, NT, 1, 1>(smem, block));
   const int a = cells_occ1<K, NT, 0, 0>(smem, block), b = cells_occ1<K, NT, 1, 0>(smem, block);
   return a < b ? a : b;

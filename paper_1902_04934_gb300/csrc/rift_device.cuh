@@ -13,6 +13,7 @@
 #define RIFT_MAXK 4
 #define RIFT_MAXM 21
 #define RIFT_MAXPAIR (RIFT_MAXM * (RIFT_MAXM + 1) / 2)
+#define RIFT_MAXMH 12   // modes with m >= 0 among 2 <= l <= 4
 #define RIFT_MAXTERM 5
 #define RIFT_MAXBINS 256
 
@@ -64,6 +65,15 @@ struct PointC {
                       // coef_off holds its coefficients [kMirrorPairs][K] float2 (grouped is set too)
   uint32_t sigma_neg; // bit j: sigma = -1 for canonical mode j (mirror points)
   float ccoef[RIFT_MAXM][RIFT_MAXTERM];
+  // merged rows for the time quadrature: with real data and the reflection symmetry of the modes,
+  // Eq. (QUV) gives Q_abar(t) = sigma_a conj(Q_a(t)) (checked per pair on the host), so a pair
+  // (a, abar) is read from the row of a alone.  [K][T][Mhp] complex64 at q_off + qh_rel, Mhp = Mh
+  // rounded up to even: slot h holds the row of stored mode h_a[h], whose merged mirror is stored
+  // mode h_b[h] (h_a[h] when it has none), with sigma = -1 where bit h of h_neg is set
+  int qhalf, Mh, Mhp, pad2;
+  long long qh_rel;
+  unsigned char h_a[RIFT_MAXMH], h_b[RIFT_MAXMH];
+  uint32_t h_neg, pad3;
 };
 
 // Canonical mode index j <-> (l, m) and the Goldberg terms of -2Y_lm present for it:
@@ -760,10 +770,132 @@ __device__ __forceinline__ float2 z_row(const float4 *__restrict__ row, const fl
   return make_float2(zr, zi);
 }
 
+// Merged rows (P.qhalf): lin_j = sum_k sum_r w_kr s_k[r0_k + j + r] with the real row sums
+// s_k[i] = Re sum_h gamma_kh Qh_k,h[i] over the slots, where F_k is taken into the coefficients,
+// gamma_kh = F_k conj(Y_a) + sigma_a conj(F_k) Y_abar (F_k conj(Y_a) for a mode without a merged
+// mirror): the pair (a, abar) contributes Re[F_k (conj(Y_a) Q_a + conj(Y_abar) sigma_a conj(Q_a))],
+// which is Re[gamma_kh Q_a].  Each row costs 2 Mh FMAs on 8 Mh bytes instead of 4 M on 8 M (all 21
+// modes: Mh = 12).
+__device__ __forceinline__ float s_row(const float4 *__restrict__ row, const float4 (&g)[RIFT_MAXMH / 2], int npairs) {
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int a2 = 0; a2 < RIFT_MAXMH / 2; ++a2) {
+    if (a2 < npairs) {
+      const float4 q = row[a2];
+      s0 = fmaf(g[a2].x, q.x, fmaf(g[a2].y, q.y, s0));
+      s1 = fmaf(g[a2].z, q.z, fmaf(g[a2].w, q.w, s1));
+    }
+  }
+  return s0 + s1;
+}
+
+// The draw's part of the merged-row scan: (Re gamma, -Im gamma) of slots 2 h2 and 2 h2 + 1 of
+// each detector (so that Re(gamma q) is a dot product with the row), the interpolation weights and
+// the first row r0_k (clamped into the window, with the flag set, as the full-row scan does).
+template <int K, int NT>
+__device__ __forceinline__ void tmarg_prep(const PointC &P, const df s0[K], const float2 F[K], const float2 *Ys,
+                                           int ystride, float4 (&g)[K][RIFT_MAXMH / 2], float (&w)[K][NT],
+                                           int (&r0)[K], uint32_t &flags) {
+  constexpr int first = (NT == 4) ? -1 : 0;
+#pragma unroll
+  for (int h2 = 0; h2 < RIFT_MAXMH / 2; ++h2) {
+    float2 ya[2], yb[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int h = 2 * h2 + e;
+      ya[e] = make_float2(0.f, 0.f);
+      yb[e] = make_float2(0.f, 0.f);
+      if (h < P.Mh) {
+        ya[e] = Ys[P.h_a[h] * ystride];
+        if (P.h_b[h] != P.h_a[h]) {
+          yb[e] = Ys[P.h_b[h] * ystride];
+          if (P.h_neg >> h & 1u) yb[e] = make_float2(-yb[e].x, -yb[e].y);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float c[4];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        // F conj(ya) + conj(F) yb
+        const float gr = F[k].x * ya[e].x + F[k].y * ya[e].y + F[k].x * yb[e].x + F[k].y * yb[e].y;
+        const float gi = F[k].y * ya[e].x - F[k].x * ya[e].y + F[k].x * yb[e].y - F[k].y * yb[e].x;
+        c[2 * e] = gr;
+        c[2 * e + 1] = -gi;
+      }
+      g[k][h2] = make_float4(c[0], c[1], c[2], c[3]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int i; float mu;
+    df sk = s0[k];
+    if (NT == 1) sk = df_add_f(sk, 0.5f);
+    df_floor(sk, i, mu);
+    interp_weights<NT>(mu, w[k]);
+    r0[k] = i + first;
+    if (r0[k] < 0 || r0[k] + P.J - 1 + NT > P.T) {
+      flags |= RIFT_FLAG_WINDOW;
+      r0[k] = min(max(r0[k], 0), P.T - NT - (P.J - 1));
+      if (r0[k] < 0) r0[k] = 0;
+    }
+  }
+}
+
+// The scan of one draw over its own merged rows (read from Qh = Q + P.qh_rel through the cache).
 template <int K, int NT, class Visit>
+__device__ __forceinline__ void tgrid_rows(const PointC &P, const float2 *__restrict__ Qh,
+                                           const float4 (&g)[K][RIFT_MAXMH / 2], const float (&w)[K][NT],
+                                           const int (&r0)[K], float x, float quad, Visit &&visit) {
+  const int rs = P.Mhp >> 1, npairs = (P.Mh + 1) >> 1;
+  float z[K][NT];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float4 *base = reinterpret_cast<const float4 *>(Qh + ((long long)k * P.T + r0[k]) * P.Mhp);
+#pragma unroll
+    for (int r = 0; r < NT - 1; ++r) z[k][r] = s_row(base + (size_t)r * rs, g[k], npairs);
+  }
+  const float c = -0.25f * x * quad;
+  const int J = P.J;
+  for (int j = 0; j < J; ++j) {
+    float lin = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int row = min(r0[k] + j + NT - 1, P.T - 1);
+      z[k][NT - 1] = s_row(reinterpret_cast<const float4 *>(Qh + ((long long)k * P.T + row) * P.Mhp), g[k], npairs);
+#pragma unroll
+      for (int r = 0; r < NT; ++r) lin = fmaf(w[k][r], z[k][r], lin);
+#pragma unroll
+      for (int r = 0; r < NT - 1; ++r) z[k][r] = z[k][r + 1];
+    }
+    visit(j, x * (lin + c));
+  }
+}
+
+template <int K, int NT, class Visit>
+__device__ __forceinline__ void tgrid_scan_half(const PointC &P, const float2 *__restrict__ Q, const df s0[K],
+                                                const float2 F[K], const float2 *Ys, int ystride, float x, float quad,
+                                                uint32_t &flags, Visit &&visit) {
+  float4 g[K][RIFT_MAXMH / 2];
+  float w[K][NT];
+  int r0[K];
+  tmarg_prep<K, NT>(P, s0, F, Ys, ystride, g, w, r0, flags);
+  tgrid_rows<K, NT>(P, Q + P.qh_rel, g, w, r0, x, quad, visit);
+}
+
+// HALF: 1 the half rows (the point must have them), 0 the full rows, -1 chosen by P.qhalf
+template <int K, int NT, int HALF = -1, class Visit>
 __device__ __forceinline__ void tgrid_scan(const PointC &P, const float2 *__restrict__ Q, const df s0[K],
                                            const float2 F[K], const float2 *Ys, int ystride, float x, float quad,
                                            uint32_t &flags, Visit &&visit) {
+  if constexpr (HALF != 0) {
+    if (HALF == 1 || P.qhalf) {
+      tgrid_scan_half<K, NT>(P, Q, s0, F, Ys, ystride, x, quad, flags, visit);
+      return;
+    }
+  }
+  if constexpr (HALF == 1) return;
   constexpr int first = (NT == 4) ? -1 : 0;
   float2 y[RIFT_MAXM + 1];
 #pragma unroll
@@ -808,12 +940,12 @@ __device__ __forceinline__ void tgrid_scan(const PointC &P, const float2 *__rest
   }
 }
 
-template <int K, int NT>
+template <int K, int NT, int HALF = -1>
 __device__ __forceinline__ float tmarg_term(const PointC &P, const float2 *__restrict__ Q, const df s0[K],
                                             const float2 F[K], const float2 *Ys, int ystride, float x, float quad,
                                             uint32_t &flags) {
   float m = -INFINITY, s = 0.f;
-  tgrid_scan<K, NT>(P, Q, s0, F, Ys, ystride, x, quad, flags, [&](int, float l) {
+  tgrid_scan<K, NT, HALF>(P, Q, s0, F, Ys, ystride, x, quad, flags, [&](int, float l) {
     if (l > m) { s = fmaf(s, expf(m - l), 1.f); m = l; }
     else s += expf(l - m);
   });

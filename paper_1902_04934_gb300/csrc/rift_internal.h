@@ -15,6 +15,41 @@ struct PointC;
 // point (across cells), one per thread, so every item but a point's last is one full pass of a CTA
 // (a draw costs about J samples; items of part-filled passes leave threads idle).
 #define RIFT_TMARG_CHUNK RIFT_CELL_BLOCK
+// Dynamic shared memory the cell kernels may take (their attribute).
+#define RIFT_CELLS_MAX_DYN_SMEM (220 * 1024)
+
+// Shared-memory layout of the time-quadrature GEMM of the cell kernel (time-marginalised rounds
+// whose points all have merged rows) inside its window buffer of `budget` bytes: byte offsets,
+// 16-byte aligned, of the per-draw arrays of an item (RIFT_CELL_BLOCK draws) and the rows `rmax`
+// (a multiple of 8) of the row-sum block S ([rmax][33] floats) and of each of the two staged Q
+// buffers ([rmax][maxmh] complex64).  The draws' harmonics share the S and Q space during setup.
+#define RIFT_TG_SROW 33
+struct TgLayout {
+  unsigned G, W, R0, CX, XX, KEY, POS, LT, LN, GM, S, QS, end;
+  int rmax;
+};
+inline __host__ __device__ unsigned tg_al16(unsigned x) { return (x + 15u) & ~15u; }
+inline __host__ __device__ TgLayout tg_layout(int K, int NT, int maxmh, unsigned budget) {
+  const unsigned B = RIFT_CELL_BLOCK;
+  TgLayout t;
+  unsigned o = 0;
+  t.G = o;   o = tg_al16(o + 16u * (unsigned)K * (unsigned)(maxmh / 2) * B);   // float4 [K][maxmh/2][B]
+  t.W = o;   o = tg_al16(o + 4u * (unsigned)(K * NT) * B);                    // float [K][NT][B]
+  t.R0 = o;  o = tg_al16(o + 4u * (unsigned)K * B);                           // int [K][B]
+  t.CX = o;  o = tg_al16(o + 4u * B);                                          // -x quad / 4
+  t.XX = o;  o = tg_al16(o + 4u * B);                                          // x = D_ref / D
+  t.KEY = o; o = tg_al16(o + 8u * B);                                          // (sort key, thread)
+  t.POS = o; o = tg_al16(o + 4u * B);                                          // slot of each thread
+  t.LT = o;  o = tg_al16(o + 8u * B);                                          // (max, sum) per thread
+  t.LN = o;  o = tg_al16(o + 4u * B);                                          // lnL per slot
+  t.GM = o;  o = tg_al16(o + 8u * (unsigned)K * (B / 32u));                     // group min, max of r0
+  const unsigned row = 4u * RIFT_TG_SROW + 2u * 8u * (unsigned)maxmh;
+  t.rmax = (budget > o) ? (int)(((budget - o) / row) & ~7u) : 0;
+  t.S = o;   o = tg_al16(o + 4u * RIFT_TG_SROW * (unsigned)(t.rmax > 0 ? t.rmax : 0));
+  t.QS = o;  o = tg_al16(o + 2u * 8u * (unsigned)maxmh * (unsigned)(t.rmax > 0 ? t.rmax : 0));
+  t.end = o;
+  return t;
+}
 
 // Block partial of the log-sum-exp: max, sum e^{l-max}, sum e^{2(l-max)}, count.
 struct __align__(32) Part {

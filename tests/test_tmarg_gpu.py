@@ -40,12 +40,51 @@ def _gpu(lib, h, th):
     return out.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("which,n,interp", [("small", 1500, 3), ("small", 400, 1), ("small", 400, 0),
-                                            ("full", 160, 3)])
-def test_tmarg_array_parity(lib, cuda, which, n, interp):
+def _break_q(pt, modes=None):
+    """The point with the Q of each listed mode (default: every m < 0 mode) in detector 0 changed by
+    1e-6 of the largest |Q| at one sample: Q_abar = sigma conj(Q_a) no longer holds for those pairs,
+    so the kernels read them from their own rows (all of them: the full rows)."""
+    Q = pt["Q"].copy()
+    lm = [tuple(x) for x in np.asarray(pt["lm"]).tolist()]
+    for mode in (modes if modes is not None else [x for x in lm if x[1] < 0]):
+        Q[0, lm.index(mode), Q.shape[2] // 2] += 1e-6 * np.abs(Q).max()
+    return dict(pt, Q=Q)
+
+
+def test_merged_rows_are_taken_exactly_when_a_pair_is_reflection_symmetric(lib, cuda):
+    """Real data and mirror-symmetric modes give Q_abar(t) = sigma_a conj(Q_a(t)) (Eq. (QUV)): the
+    workload's points read merged rows; a perturbed Q whose only pair is (2, +-2), or a mode set
+    without any mirror pair, does not."""
+    for spec in (W.cfg_small(), W.cfg_full()):
+        pt = W.make_point(spec, 8)
+        h = lib.rift_ile_create(pt)
+        assert lib.rift_ile_forms(h) & lib.FORM_QHALF
+        lib.rift_ile_destroy(h)
+    for modes, want in (([(2, -2), (2, 1), (2, 2)], False), ([(2, -2), (2, 1), (2, 2), (3, -3), (3, 3)], True)):
+        spec = W.cfg_small()
+        spec.modes = modes
+        h = lib.rift_ile_create(_break_q(W.make_point(spec, 8), [(2, -2)]))
+        assert bool(lib.rift_ile_forms(h) & lib.FORM_QHALF) == want, modes
+        lib.rift_ile_destroy(h)
+    spec = W.cfg_small()
+    spec.modes = [(2, 1), (2, 2), (3, 3)]
+    h = lib.rift_ile_create(W.make_point(spec, 8))
+    assert not lib.rift_ile_forms(h) & lib.FORM_QHALF
+    lib.rift_ile_destroy(h)
+
+
+@pytest.mark.parametrize("which,n,interp,broken", [("small", 1500, 3, False), ("small", 400, 1, False),
+                                                   ("small", 400, 0, False), ("full", 160, 3, False),
+                                                   ("small", 400, 3, True), ("full", 160, 3, True)])
+def test_tmarg_array_parity(lib, cuda, which, n, interp, broken):
+    """Per draw against the oracle, with the half rows (the workload's points) and with the full
+    rows (broken: Q no longer reflection symmetric)."""
     spec = W.cfg_small() if which == "small" else W.cfg_full()
     pt = W.make_point(spec, 8)
+    if broken:
+        pt = _break_q(pt)
     h = lib.rift_ile_create(pt, interp=interp)
+    assert bool(lib.rift_ile_forms(h) & lib.FORM_QHALF) != broken
     th = _draws(n, 9)
     th64 = {k: v.astype(np.float64) for k, v in th.items()}
     got = _gpu(lib, h, th)
@@ -54,6 +93,21 @@ def test_tmarg_array_parity(lib, cuda, which, n, interp):
     tol = _tol(pt, th64)
     i = int(np.argmax(err / tol))
     assert np.all(err <= tol), (float(err[i]), float(tol[i]), float(want[i]), i)
+    lib.rift_ile_destroy(h)
+
+
+def test_tmarg_partly_merged_rows_match_oracle(lib, cuda):
+    """A point whose (3, +-3) pair merges and whose (2, -2) keeps its own row (slots of both kinds),
+    per draw against the oracle."""
+    spec = W.cfg_small()
+    spec.modes = [(2, -2), (2, 1), (2, 2), (3, -3), (3, 3)]
+    pt = _break_q(W.make_point(spec, 8), [(2, -2)])
+    h = lib.rift_ile_create(pt)
+    assert lib.rift_ile_forms(h) & lib.FORM_QHALF
+    th = _draws(600, 11)
+    th64 = {k: v.astype(np.float64) for k, v in th.items()}
+    err = np.abs(_gpu(lib, h, th) - TM.lnL_tmarg(pt, **th64))
+    assert np.all(err <= _tol(pt, th64)), float(err.max())
     lib.rift_ile_destroy(h)
 
 
@@ -80,11 +134,14 @@ def _marg(lib, h, n, **kw):
     return r, dbg.cpu().numpy().astype(np.float64)
 
 
-def test_tmarg_marginalize_matches_oracle(lib, cuda):
+@pytest.mark.parametrize("broken", [False, True])
+def test_tmarg_marginalize_matches_oracle(lib, cuda, broken):
     """Same Philox draws on both sides (the t uniform unused), sky strata 4 x 2: per-draw log weights
-    within the per-draw tolerance, lnL_marg within 1e-4."""
+    within the per-draw tolerance, lnL_marg within 1e-4 (half rows, and full rows when broken)."""
     from oracle import mc
     pt = W.make_point(W.cfg_small(), 8)
+    if broken:
+        pt = _break_q(pt)
     h = lib.rift_ile_create(pt)
     n, S = 1500, (4, 2, 1)
     res, ell = _marg(lib, h, n, seed=71, max_evals=2 * n, strata=S)
@@ -146,6 +203,7 @@ def test_tmarg_batch_equals_single_point_runs(lib, cuda):
     specs = W.batch_specs(3, seed=8, t_range=(800, 1200))
     pts = [W.make_point(sp, 20 + i) for i, sp in enumerate(specs)]
     hb = lib.rift_ile_batch_create(pts)
+    assert all(lib.rift_ile_forms(hb, i) & lib.FORM_QHALF for i in range(3))
     kw = dict(seed=81, n_per_round=4000, max_evals=12000, n_eff_target=1e300, time_marg=1, proposal="adaptive",
               n_bins=32)
     batch = lib.rift_ile_batch_marginalize(hb, **kw)
@@ -154,6 +212,30 @@ def test_tmarg_batch_equals_single_point_runs(lib, cuda):
         one = lib.rift_ile_marginalize(h, point_id=i, **kw)
         assert batch[i]["n_evals"] == one["n_evals"] and batch[i]["rounds"] == one["rounds"]
         assert batch[i]["lnL_marg"] == one["lnL_marg"], (i, batch[i]["lnL_marg"], one["lnL_marg"])
+        lib.rift_ile_destroy(h)
+    lib.rift_ile_destroy(hb)
+
+
+def test_tmarg_mixed_batch_equals_single_point_runs(lib, cuda):
+    """A batch whose points do not all have merged rows runs the kernel that chooses per point and
+    scans each draw's own rows: the point without them gets exactly its single-point result, the
+    others theirs within 1e-4 (alone they take the GEMM form of the scan, which sums in another
+    order)."""
+    specs = W.batch_specs(3, seed=9, t_range=(800, 1200))
+    pts = [W.make_point(sp, 30 + i) for i, sp in enumerate(specs)]
+    pts[1] = _break_q(pts[1])
+    hb = lib.rift_ile_batch_create(pts)
+    assert [bool(lib.rift_ile_forms(hb, i) & lib.FORM_QHALF) for i in range(3)] == [True, False, True]
+    kw = dict(seed=82, n_per_round=3000, max_evals=6000, n_eff_target=1e300, time_marg=1, proposal="adaptive",
+              n_bins=32)
+    batch = lib.rift_ile_batch_marginalize(hb, **kw)
+    for i, p in enumerate(pts):
+        h = lib.rift_ile_create(p)
+        one = lib.rift_ile_marginalize(h, point_id=i, **kw)
+        if i == 1:
+            assert batch[i]["lnL_marg"] == one["lnL_marg"], (i, batch[i]["lnL_marg"], one["lnL_marg"])
+        else:
+            assert abs(batch[i]["lnL_marg"] - one["lnL_marg"]) < 1e-4, (i, batch[i]["lnL_marg"], one["lnL_marg"])
         lib.rift_ile_destroy(h)
     lib.rift_ile_destroy(hb)
 
