@@ -916,6 +916,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.bin_buf = adaptive ? S.bins : nullptr;
   L.flags = h->flags;
   L.max_M = ys_modes;
+  L.merged = (mp && ys_modes == 0 && h->pts[0].c.qhalf && h->pts[0].c.Mh == RIFT_MAXMH) ? 1 : 0;
   L.max_pairK = coef_f4;
   L.max_nb = nb;
   L.learned = learned ? 1 : 0;

@@ -277,6 +277,86 @@ __device__ __forceinline__ float linear_term_yreg(const PointC &P, const float2 
   return lin;
 }
 
+// The linear term of a point with all 21 modes whose 9 mirror pairs all merge (P.qhalf, P.Mh = 12):
+// rows of the 12 modes with m >= 0 (merged rows, Mhp = 12), in the canonical order, slot h holding
+// canonical mode kMergedA[h] and its mirror kMergedB[h] (itself for m = 0).  With Y_a = d_a e^{i m
+// phi} and Y_abar = d_abar e^{-i m phi}, the coefficient of the pair's row is
+// gamma_k = F_k conj(Y_a) + sigma conj(F_k) Y_abar = (fr p c + fi q s, fi q c - fr p s), where
+// p = d_a + sigma d_abar, q = d_a - sigma d_abar, (c, s) = (cos m phi, sin m phi) and F_k = fr + i fi;
+// for m = 0, gamma_k = F_k d_a.  lin = sum_k sum_r w_kr sum_h Re(gamma_kh Q_kh[i_k + r]): each tap
+// row is dotted with (Re gamma, -Im gamma) and the NT row sums are interpolated.
+__device__ constexpr int kMergedA[RIFT_MAXMH] = {2, 3, 4, 8, 9, 10, 11, 16, 17, 18, 19, 20};
+__device__ constexpr int kMergedB[RIFT_MAXMH] = {2, 1, 0, 8, 7, 6, 5, 16, 15, 14, 13, 12};
+
+template <int K, int NT>
+__device__ __forceinline__ float linear_term_merged(const PointC &P, const float2 *__restrict__ Qh, const df s_idx[K],
+                                                    const float2 F[K], const float (&dj)[RIFT_MAXM],
+                                                    const float2 (&e)[5], const float4 *const win[K],
+                                                    const int wlo[K], const int whi[K], uint32_t &flags) {
+  constexpr int first = (NT == 4) ? -1 : 0;
+  constexpr int rs = RIFT_MAXMH / 2;   // merged row stride in float4
+  float w[K][NT];
+  const float4 *row[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int i; float mu;
+    df s = s_idx[k];
+    if (NT == 1) s = df_add_f(s, 0.5f);
+    df_floor(s, i, mu);
+    interp_weights<NT>(mu, w[k]);
+    int i0 = i + first;
+    if (i0 < 0 || i0 + NT > P.T) {
+      flags |= RIFT_FLAG_WINDOW;
+      i0 = min(max(i0, 0), P.T - NT);
+    }
+    const bool in_win = win[k] != nullptr && i0 >= wlo[k] && i0 + NT - 1 <= whi[k];
+    row[k] = in_win ? win[k] + (size_t)(i0 - wlo[k]) * rs
+                    : reinterpret_cast<const float4 *>(Qh + ((long long)k * P.T + i0) * (2 * rs));
+  }
+  float sr[K][NT];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int r = 0; r < NT; ++r) sr[k][r] = 0.f;
+#pragma unroll
+  for (int h2 = 0; h2 < rs; ++h2) {
+    // per slot of the pair: (fr, fi) -> (Re gamma, -Im gamma) = (fr A + fi B, fr C + fi D)
+    float A[2], Bc[2], Cc[2], D[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int h = 2 * h2 + u;
+      const int ja = kMergedA[h], jb = kMergedB[h];
+      const int m = canon_m(ja);
+      const float da = dj[ja];
+      if (m == 0) {
+        A[u] = da; Bc[u] = 0.f; Cc[u] = 0.f; D[u] = -da;
+      } else {
+        const float db = (P.h_neg >> h & 1u) ? -dj[jb] : dj[jb];
+        const float pp = da + db, qq = da - db;
+        const float c = e[m].x, sn = e[m].y;
+        A[u] = pp * c; Bc[u] = qq * sn; Cc[u] = pp * sn; D[u] = -qq * c;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float fr = F[k].x, fi = F[k].y;
+      const float4 gk = make_float4(fmaf(fr, A[0], fi * Bc[0]), fmaf(fr, Cc[0], fi * D[0]),
+                                    fmaf(fr, A[1], fi * Bc[1]), fmaf(fr, Cc[1], fi * D[1]));
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        const float4 q = row[k][r * rs + h2];
+        sr[k][r] = fmaf(gk.x, q.x, fmaf(gk.y, q.y, fmaf(gk.z, q.z, fmaf(gk.w, q.w, sr[k][r]))));
+      }
+    }
+  }
+  float lin = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int r = 0; r < NT; ++r) lin = fmaf(w[k][r], sr[k][r], lin);
+  return lin;
+}
+
 // Q index of t_0 + delay_k for the time quadrature: (t_lo - tau0_k) fs + 1/2 - fs x_k . n.
 template <int K>
 __device__ __forceinline__ void delay_index(const PointC &P, const Sky &s, df out[K]) {
@@ -519,16 +599,28 @@ __device__ __forceinline__ void tmarg_gemm_item(const CellLaunch &L, const Point
 #pragma unroll
             for (int e4 = 0; e4 < HP; ++e4) {
               if (e4 < npairs) {
-                float4 gv[4];
+                // all operands of the step first, then four passes of 32 independent FMAs
+                float4 gv[4], qv[8];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) gv[c] = Gk[e4 * B + td + 8 * c];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                  const float4 qv = Qb[(8 * rt + q) * rs + e4];
+                for (int q = 0; q < 8; ++q) qv[q] = Qb[(8 * rt + q) * rs + e4];
 #pragma unroll
-                  for (int c = 0; c < 4; ++c)
-                    acc[q][c] = fmaf(qv.x, gv[c].x, fmaf(qv.y, gv[c].y, fmaf(qv.z, gv[c].z, fmaf(qv.w, gv[c].w, acc[q][c]))));
-                }
+                for (int q = 0; q < 8; ++q)
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(qv[q].x, gv[c].x, acc[q][c]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(qv[q].y, gv[c].y, acc[q][c]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(qv[q].z, gv[c].z, acc[q][c]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(qv[q].w, gv[c].w, acc[q][c]);
               }
             }
 #pragma unroll
@@ -539,23 +631,20 @@ __device__ __forceinline__ void tmarg_gemm_item(const CellLaunch &L, const Point
           __syncthreads();
           if (t == 0) issue_next();   // buffer `buf` is free again
           if (pv) {
+            // the draw's rows of S for its time points, loaded before use (rows past the chunk are
+            // clamped into the block and not used)
             const int off = R0[k * B + pslot] - gmn + jlo;
-            float wk[NT], tap[NT];
+            float wk[NT], rowv[kTgLin + NT - 1];
 #pragma unroll
             for (int r = 0; r < NT; ++r) wk[r] = W[(k * NT + r) * B + pslot];
 #pragma unroll
-            for (int r = 0; r < NT - 1; ++r) tap[r] = S[(off + r) * RIFT_TG_SROW + dl];
+            for (int e = 0; e < kTgLin + NT - 1; ++e) rowv[e] = S[min(off + e, T.rmax - 1) * RIFT_TG_SROW + dl];
 #pragma unroll
             for (int jj = 0; jj < kTgLin; ++jj) {
-              if (jj < nj) {
-                tap[NT - 1] = S[(off + jj + NT - 1) * RIFT_TG_SROW + dl];
-                float v = 0.f;
+              float v = 0.f;
 #pragma unroll
-                for (int r = 0; r < NT; ++r) v = fmaf(wk[r], tap[r], v);
-                lin[jj] += v;
-#pragma unroll
-                for (int r = 0; r < NT - 1; ++r) tap[r] = tap[r + 1];
-              }
+              for (int r = 0; r < NT; ++r) v = fmaf(wk[r], rowv[jj + r], v);
+              if (jj < nj) lin[jj] += v;
             }
           }
           __syncthreads();   // S is rewritten by the next stage
@@ -616,7 +705,8 @@ __device__ __forceinline__ void tmarg_gemm_item(const CellLaunch &L, const Point
 // TMARG 2, for launches whose points all have them, compiles only that path (fewer registers).
 // YR: a mirror-symmetric point with all 21 modes in the parameter bank (CP 3), harmonics in
 // registers (linear_term_yreg): no per-thread harmonics buffer in shared memory (L.max_M = 0), so
-// the room goes to the Q windows.
+// the room goes to the Q windows; YR 2: the same with all 9 mirror pairs of Q merged
+// (linear_term_merged), the windows staged from the merged rows.
 template <int K, int NT, int LEARNED, int TMARG, int CP, int YR = 0>
 __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__restrict__ cpg) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -747,7 +837,7 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
     // B. stage the windows that fit
     if (threadIdx.x == 0) {
       uint32_t bytes = 0;
-      const int rowb = P.Mp * 8;
+      const int rowb = (YR == 2 ? P.Mhp : P.Mp) * 8;   // staged rows: merged rows for YR 2
       for (int k = 0; k < K; ++k) {
         int a = INT_MAX, b = INT_MIN;
         for (int w = 0; w < nw; ++w) { a = min(a, s_red[2 * k][w]); b = max(b, s_red[2 * k + 1][w]); }
@@ -769,7 +859,8 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
         mbar_expect_tx(&bar, bytes);
         for (int k = 0; k < K; ++k)
           if (s_woff[k] >= 0 && !L.fault_stall) {   // (an injected fault leaves the announced bytes unissued)
-            const float2 *src = Q + ((long long)k * P.T + s_wlo[k]) * P.Mp;
+            const float2 *src = (YR == 2) ? Q + P.qh_rel + ((long long)k * P.T + s_wlo[k]) * P.Mhp
+                                          : Q + ((long long)k * P.T + s_wlo[k]) * P.Mp;
             bulk_g2s(wbuf + s_woff[k], src, (uint32_t)(s_whi[k] - s_wlo[k] + 1) * rowb, &bar);
           }
       }
@@ -831,7 +922,11 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
           quad = quad_canon_from_d<K, CP == 2>(static_cast<const float4 *>(cpg), g, dj, (uint32_t)(d.u_phi * 16777216.f));
         else quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
         float lin;
-        if constexpr (YR) {
+        if constexpr (YR == 2) {
+          float2 e[5];
+          eiphi_powers(cphi, sphi, e);
+          lin = linear_term_merged<K, NT>(P, Q + P.qh_rel, g.s, g.F, dj, e, win, wlo, whi, flags);
+        } else if constexpr (YR) {
           float2 e[5];
           eiphi_powers(cphi, sphi, e);
           lin = linear_term_yreg<K, NT>(P, Q, g.s, g.F, dj, e, win, wlo, whi, flags);
@@ -1253,11 +1348,15 @@ cudaError_t cells_k(const CellLaunch &L, int grid, int block, size_t smem, cudaS
             cudaFuncSetAttribute(cells_kernel_mp<K, NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
         if (e == cudaSuccess)
           e = cudaFuncSetAttribute(cells_kernel_mp<K, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(cells_kernel_mp<K, NT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, RIFT_CELLS_MAX_DYN_SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
       }
-      // all 21 modes: harmonics in registers, and the launch reserves no harmonics buffer (max_M 0)
-      if (L.max_M == 0) cells_kernel_mp<K, NT, 1><<<grid, block, smem, st>>>(L, *mp);
+      // all 21 modes: harmonics in registers, and the launch reserves no harmonics buffer (max_M 0);
+      // merged rows when all 9 mirror pairs of Q merge
+      if (L.max_M == 0 && L.merged) cells_kernel_mp<K, NT, 2><<<grid, block, smem, st>>>(L, *mp);
+      else if (L.max_M == 0) cells_kernel_mp<K, NT, 1><<<grid, block, smem, st>>>(L, *mp);
       else cells_kernel_mp<K, NT, 0><<<grid, block, smem, st>>>(L, *mp);
       return cudaGetLastError();
     }

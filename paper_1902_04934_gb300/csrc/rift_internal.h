@@ -120,6 +120,8 @@ struct CellLaunch {
   int fault_nan;               // injected fault: sample 0 of round 0 of every point has a NaN log weight
   int fault_stall;             // injected fault: window copies announced on the mbarrier but never issued
   int tmarg;                   // the event time is marginalised by quadrature (Eq. lnL:tmarg)
+  int merged;                  // single mirror-symmetric point with all 21 modes whose 9 mirror
+                               // pairs of Q merge (P.qhalf, P.Mh = 12): merged rows (cells_kernel_mp)
 };
 
 // Device-side round control of a batched run replayed as a CUDA graph.
