@@ -260,6 +260,7 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
   qv.resize(qv.size() + (size_t)K * T * c.Mp, make_float2(0.f, 0.f));
   float2 *qb = qv.data() + c.q_off;
   bool finite = true;
+  double qmax = 0.0;
   for (int k = 0; k < K; ++k)
     for (int j0 = 0; j0 < T; j0 += 64) {
       const int j1 = std::min(T, j0 + 64);
@@ -269,6 +270,7 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
         for (int j = j0; j < j1; ++j) {
           const double re = q[2 * j], im = q[2 * j + 1];
           finite &= (re - re == 0.0) & (im - im == 0.0);
+          qmax = std::max(qmax, std::max(std::fabs(re), std::fabs(im)));
           out[(size_t)j * c.Mp] = make_float2((float)re, (float)im);
         }
       }
@@ -280,8 +282,6 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
   // 1e-10 of the largest |Q|) is read from the row of a alone.  The slots are the stored modes
   // but the merged m < 0 ones, in stored order; taken when at least one pair merges
   {
-    double qmax = 0.0;
-    for (size_t i = 0; i < (size_t)2 * K * M * T; ++i) qmax = std::max(qmax, std::fabs(d->Q[i]));
     const double tol = 1e-10 * qmax;
     int mate[RIFT_MAXM], sg[RIFT_MAXM];   // mate[a]: the merged partner's stored index, else a
     int merged = 0;
@@ -321,18 +321,11 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
         if (sg[a] < 0) c.h_neg |= 1u << Mh;
         ++Mh;
       }
+      // the rows themselves are gathered on the device from the uploaded Q block (create_impl
+      // places the merged blocks after all points' Q blocks and sets qh_rel)
       c.qhalf = 1;
       c.Mh = Mh;
       c.Mhp = (Mh + 1) & ~1;
-      const long long qh_off = (long long)qv.size();
-      c.qh_rel = qh_off - c.q_off;
-      qv.resize(qv.size() + (size_t)K * T * c.Mhp, make_float2(0.f, 0.f));
-      float2 *hb = qv.data() + qh_off;
-      const float2 *fb = qv.data() + c.q_off;
-      for (int k = 0; k < K; ++k)
-        for (int j = 0; j < T; ++j)
-          for (int hh = 0; hh < Mh; ++hh)
-            hb[((size_t)k * T + j) * c.Mhp + hh] = fb[((size_t)k * T + j) * c.Mp + c.h_a[hh]];
     }
   }
   // pair coefficients [pair_slot(a, b)][K] = (U, V) upper triangle, off-diagonal doubled
@@ -554,11 +547,20 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
     rift_ile_destroy(h);
     return RIFT_ECUDA;
   }
+  // merged-row blocks after all Q blocks (16-byte aligned: every block holds an even number of rows
+  // of an even width); only the Q blocks travel from the host
+  size_t qtot = qv.size(), qmerged = 0;
+  for (int i = 0; i < n; ++i) {
+    PointC &c = h->pts[i].c;
+    if (!c.qhalf) continue;
+    c.qh_rel = (long long)(qtot + qmerged) - c.q_off;
+    qmerged += (size_t)c.K * c.T * c.Mhp;
+  }
   std::vector<PointC> pc(n);
   for (int i = 0; i < n; ++i) pc[i] = h->pts[i].c;
   rift_status s = RIFT_OK;
   if ((e = cache_dev_alloc((void **)&h->pts_dev, sizeof(PointC) * n)) != cudaSuccess ||
-      (e = cache_dev_alloc((void **)&h->q_arena, sizeof(float2) * std::max<size_t>(qv.size(), 2))) != cudaSuccess ||
+      (e = cache_dev_alloc((void **)&h->q_arena, sizeof(float2) * std::max<size_t>(qtot + qmerged, 2))) != cudaSuccess ||
       (e = cache_dev_alloc((void **)&h->c_arena, sizeof(float4) * std::max<size_t>(cv.size(), 1))) != cudaSuccess ||
       (e = cache_dev_alloc((void **)&h->flags, sizeof(uint32_t))) != cudaSuccess ||
       (e = fault_is("h2d") ? cudaErrorInvalidValue : cudaSuccess) != cudaSuccess ||
@@ -568,6 +570,7 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
           cudaSuccess ||
       (e = cudaMemcpyAsync(h->c_arena, cv.data(), sizeof(float4) * cv.size(), cudaMemcpyHostToDevice, h->stream)) !=
           cudaSuccess ||
+      (e = qmerged ? launch_merge_rows(h->pts_dev, n, h->q_arena, h->stream) : cudaSuccess) != cudaSuccess ||
       (e = cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), h->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
     s = (e == cudaErrorMemoryAllocation) ? RIFT_ENOMEM : RIFT_ECUDA;

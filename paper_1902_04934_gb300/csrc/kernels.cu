@@ -353,6 +353,27 @@ cudaError_t launch_lnl_array(int K, const PointC *pt_dev, const PointC &ph, cons
 #undef RIFT_LA
 }
 
+// Merged rows (grid: blocks x points): row (k, t) of point p, slot h < Mh, is its Q row's entry for
+// stored mode h_a[h]; slots up to Mhp are zero.
+__global__ void __launch_bounds__(256) merge_rows_kernel(const PointC *__restrict__ pts, float2 *__restrict__ qa) {
+  const PointC &P = pts[blockIdx.y];
+  if (!P.qhalf) return;
+  const long long n = (long long)P.K * P.T * P.Mhp;
+  float2 *out = qa + P.q_off + P.qh_rel;
+  const float2 *in = qa + P.q_off;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int hh = (int)(i % P.Mhp);
+    const long long row = i / P.Mhp;
+    out[i] = (hh < P.Mh) ? in[row * P.Mp + P.h_a[hh]] : make_float2(0.f, 0.f);
+  }
+}
+
+cudaError_t launch_merge_rows(const PointC *pts, int np, float2 *qa, cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  merge_rows_kernel<<<dim3(32, (unsigned)np), 256, 0, st>>>(pts, qa);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lnl_tmarg(int K, const PointC *pt_dev, const PointC &ph, const float2 *qa, const float4 *ca,
                              size_t n, const float *ra, const float *dec, const float *psi, const float *phi,
                              const float *incl, const float *dist, float *out, uint32_t *flags, cudaStream_t st) {

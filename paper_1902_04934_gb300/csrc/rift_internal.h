@@ -210,6 +210,8 @@ size_t cells_smem_fixed(int K, int max_M, int max_pairK, int max_nb, int block);
 cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int block, size_t smem, cudaStream_t st,
                          const CanonCoefParam *cc = nullptr, int cc_sparse = 0, const MirrorCoefParam *mp = nullptr);
 int cells_blocks_per_sm(int K, int ntap, size_t smem, int block, int tmarg = 0);
+// Merged Q rows of every point that has them, gathered from the point's uploaded Q block.
+cudaError_t launch_merge_rows(const PointC *pts, int np, float2 *qa, cudaStream_t st);
 cudaError_t launch_merge_points(const Part *partials, const RoundPt *rp, int n_points, AccState *acc,
                                 cudaStream_t st);
 cudaError_t launch_hist_points(const float *ell, const uint32_t *bins, const RoundPt *rp, int n_points,

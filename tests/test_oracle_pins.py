@@ -521,3 +521,34 @@ def test_positive_quadratic_form_of_mirror_symmetric_modes():
         pos += 2.0 * np.real(np.einsum("na,ab,nb->n", np.conj(beta), U[k], beta))
     assert np.all(pos >= 0)
     assert np.max(np.abs(pos - general)) < 1e-12 * np.max(np.abs(general))
+
+
+def test_merged_rows_of_real_data():
+    """Real data and modes with conj(h_a(-f)) = sigma h_abar(f) give Q_abar(t) = sigma conj(Q_a(t))
+    from Eq. (QUV) (the direct sums of the oracle), so the likelihood is unchanged when every m < 0
+    row is replaced by sigma conj(row of its mirror); data made complex break the relation."""
+    from oracle import quv as QUV
+    pt = W.make_point(W.cfg_small(), 8)
+    Q = QUV.quv(pt)[0]
+    lm = [tuple(x) for x in np.asarray(pt["lm"]).tolist()]
+    qmax = np.abs(Q).max()
+    Q2 = Q.copy()
+    for i, (l, m) in enumerate(lm):
+        if m < 0:
+            continue
+        j = lm.index((l, -m))
+        errs = [np.abs(Q[:, j] - s * np.conj(Q[:, i])).max() for s in (1.0, -1.0)]
+        assert min(errs) <= 1e-12 * qmax, (l, m, errs)
+        if m > 0:
+            Q2[:, j] = (1.0, -1.0)[int(np.argmin(errs))] * np.conj(Q[:, i])
+    r = np.random.default_rng(3)
+    n = 200
+    th = dict(ra=r.uniform(0, 2 * np.pi, n), dec=np.arcsin(r.uniform(-1, 1, n)), t=r.uniform(-0.04, 0.04, n),
+              psi=r.uniform(0, np.pi, n), phi=r.uniform(0, 2 * np.pi, n), incl=np.arccos(r.uniform(-1, 1, n)),
+              dist=r.uniform(50.0, 500.0, n))
+    a = L.lnL_factorised(dict(pt, Q=Q), **th)
+    b = L.lnL_factorised(dict(pt, Q=Q2), **th)
+    assert np.max(np.abs(a - b)) <= 1e-9 * max(1.0, np.max(np.abs(a)))
+    Qc = QUV.quv(dict(pt, data=pt["data"] * np.exp(0.3j)))[0]
+    i, j = lm.index((2, 2)), lm.index((2, -2))
+    assert min(np.abs(Qc[:, j] - s * np.conj(Qc[:, i])).max() for s in (1.0, -1.0)) > 1e-3 * np.abs(Qc).max()
