@@ -259,7 +259,22 @@ typedef struct {
                             rounds) and rebuilds it from each of them.  Every round enters the
                             estimate with its own q, so the pooled estimate stays unbiased.
                             0 = no fallback; RIFT_EINVAL with other proposals or opts.tables.    */
+  int refine;            /* nonzero: the heaviest samples of each sampled-time round from the prior or
+                            the adaptive proposal are evaluated again in FP64 (draw, response,
+                            harmonics, interpolation, Eq. (def:lnL:Decomposed) with U, V kept in
+                            FP64; Q from its FP32 copy), and the estimate uses those values.  Per
+                            round: the samples within B nats of the running maximum, B the largest of
+                            1..24 that keeps them at RIFT_REFINE_CAP at most (none if more than that
+                            lie within one nat), taken from the two largest log weights of every warp
+                            of every work item.  This removes the FP32 floor of estimates that rest
+                            on a few samples (n_eff ~ 1: the heaviest sample's FP32 error).  Rounds
+                            of the learned proposal and time-marginalised rounds are not refined.
+                            Single-point and batched calls; RIFT_EINVAL with resume, save or the
+                            allocation-free entry point.                                        */
 } rift_mc_opts;
+
+/* Samples refined per point and round at most (rift_mc_opts.refine). */
+#define RIFT_REFINE_CAP 64
 
 /* Size of the sampler-state blob of rift_mc_opts.resume / save (same library build and byte order). */
 #define RIFT_MC_STATE_BYTES 8192
@@ -280,6 +295,7 @@ typedef struct {
   int strata[3];     /* strata used for rounds with n >= C                                     */
   int fallback_round; /* learned proposal with fallback_neff: the first round drawn from the adaptive
                          proposal, -1 if the point never fell back                                 */
+  int n_refined;      /* opts.refine: samples evaluated again in FP64 over the call               */
 } rift_mc_result;
 
 /*

@@ -61,10 +61,12 @@ class McOpts(C.Structure):
                 ("mdn", C.c_void_p), ("dbg_ell", C.c_void_p), ("dbg_tables", C.c_void_p),
                 ("max_rounds", C.c_int), ("timing", C.c_int), ("strata", C.c_int * 3),
                 ("resume", C.c_void_p), ("save", C.c_void_p), ("time_marg", C.c_int),
-                ("tables_per_point", C.c_int), ("tables_out", C.c_void_p), ("fallback_neff", C.c_double)]
+                ("tables_per_point", C.c_int), ("tables_out", C.c_void_p), ("fallback_neff", C.c_double),
+                ("refine", C.c_int)]
 
 
 MC_STATE_BYTES = 8192   # RIFT_MC_STATE_BYTES
+REFINE_CAP = 64         # RIFT_REFINE_CAP
 
 
 class McResult(C.Structure):
@@ -72,7 +74,7 @@ class McResult(C.Structure):
                 ("sigma", C.c_double), ("n_evals", C.c_uint64), ("rounds", C.c_int), ("status", C.c_int),
                 ("acc_max", C.c_double), ("acc_s1", C.c_double), ("acc_s2", C.c_double),
                 ("kernel_ms", C.c_double), ("kernel_launches", C.c_int), ("strata", C.c_int * 3),
-                ("fallback_round", C.c_int)]
+                ("fallback_round", C.c_int), ("n_refined", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -356,7 +358,7 @@ def rift_ile_check(h):
 def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target=1e300, d_lo=1.0,
           d_hi=1000.0, proposal="prior", n_bins=100, beta=0.3, floor_eps=0.1, adapt_rounds=-1,
           tables=None, mdn=None, dbg_ell=None, dbg_tables=None, max_rounds=0, timing=0, strata=(0, 0, 0),
-          resume=None, save=None, time_marg=0, tables_out=None, fallback_neff=0.0, keep=None):
+          resume=None, save=None, time_marg=0, tables_out=None, fallback_neff=0.0, refine=0, keep=None):
     o = McOpts()
     o.seed = int(seed)
     o.point_id = int(point_id)
@@ -385,6 +387,7 @@ def _opts(seed=1, point_id=0, n_per_round=100000, max_evals=100000, n_eff_target
         o.strata[d] = int(strata[d])
     o.time_marg = int(time_marg)
     o.fallback_neff = float(fallback_neff)
+    o.refine = int(refine)
     if resume is not None:
         rb = C.create_string_buffer(bytes(resume), MC_STATE_BYTES)
         keep.append(rb)

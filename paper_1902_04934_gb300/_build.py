@@ -17,7 +17,7 @@ CSRC = PKG / "csrc"
 LIBDIR = PKG / "_lib"
 LIB = LIBDIR / "librift_ile.so"
 INCLUDE = PKG.parent / "include"
-SOURCES = ["kernels.cu", "mc.cu", "capi.cu", "noalloc.cu", "mdn.cu", "quv.cu", "posterior.cu", "cache.cu"]
+SOURCES = ["kernels.cu", "mc.cu", "capi.cu", "noalloc.cu", "mdn.cu", "quv.cu", "posterior.cu", "cache.cu", "refine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -67,6 +67,24 @@ void swsh_terms(int l, int m, ModeC &out) {
   }
 }
 
+// The same terms in FP64 (refinement of heavy samples).
+void swsh_terms_d(int l, int m, PointD &pd, int a) {
+  const int s = -2;
+  const double pref = ((m & 1) ? -1.0 : 1.0) *
+                      std::sqrt(fact(l + m) * fact(l - m) * (2 * l + 1) / (4.0 * kPi * fact(l + s) * fact(l - s)));
+  pd.ml[a] = l; pd.mm[a] = m; pd.nterm[a] = 0;
+  for (int r = 0; r <= l - s; ++r) {
+    const int j = r + s - m;
+    if (j < 0 || j > l + s) continue;
+    const double sign = ((l - r - s) & 1) ? -1.0 : 1.0;
+    if (pd.nterm[a] < RIFT_MAXTERM) {
+      pd.coef[a][pd.nterm[a]] = pref * binom(l - s, r) * binom(l + s, j) * sign;
+      pd.kc[a][pd.nterm[a]] = 2 * r + s - m;
+      pd.nterm[a]++;
+    }
+  }
+}
+
 // Host-side fault injection for tests of the error paths: RIFT_FAULT names one fault.
 //   alloc       device allocation in rift_ile_create fails (before any CUDA call)      -> RIFT_ENOMEM
 //   h2d         the host-to-device upload in rift_ile_create fails                     -> RIFT_ECUDA
@@ -83,6 +101,7 @@ bool fault_is(const char *name) {
 
 struct Point {
   PointC c;
+  PointD d;   // FP64 constants (refinement of heavy samples)
   double t_lo, t_hi;
 };
 
@@ -108,6 +127,15 @@ struct rift_ile {
   size_t stage_n = 0;
   int max_M = 0, max_pairK = 0;
   int all_qhalf = 0;        // every point has the half rows of the time quadrature
+  // refinement of heavy samples: FP64 point constants and U, V; candidates, scratch, state
+  PointD *pd_dev = nullptr;
+  double2 *uv64 = nullptr;
+  float2 *cand = nullptr;
+  size_t cap_cand = 0;
+  unsigned char *rscratch = nullptr;
+  size_t cap_rscratch = 0;
+  RefineState *rstate = nullptr, *rstate_host = nullptr;
+  int cap_rstate = 0;
   int interp = 3;
   int cell_target = 640;    // samples per stratification cell (autotuned)
   int smem_split = 3;       // shared-memory split of the cell kernel (sets the window budget; autotuned)
@@ -159,7 +187,7 @@ rift_status cuda_fail(rift_ile *h, cudaError_t e, const char *where) {
 
 // Build the device constants of one point from its descriptor (FP64 on the host).
 rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vector<float2> &qv,
-                        std::vector<float4> &cv) {
+                        std::vector<float4> &cv, std::vector<double2> &uv64) {
   if (!d) return fail(h, RIFT_EINVAL, "null descriptor");
   const int K = d->n_det, M = d->n_modes, T = d->n_t;
   if (K < 1 || K > RIFT_MAX_DET) return fail(h, RIFT_EINVAL, "n_det out of range");
@@ -276,6 +304,33 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
       }
     }
   if (!finite) return fail(h, RIFT_EINVAL, "non-finite Q");
+  // FP64 constants and U, V (stored mode order) for the refinement of heavy samples
+  {
+    PointD &D = P.d;
+    std::memset(&D, 0, sizeof(D));
+    D.K = K; D.M = M; D.T = T; D.Mp = c.Mp; D.interp = d->interp;
+    D.q_off = c.q_off;
+    D.g = gmst_rad(d->t_ref_gps) / (2.0 * kPi);
+    D.A = (d->t_hi - d->t_lo) * d->fs;
+    D.t_lo = d->t_lo; D.t_span = d->t_hi - d->t_lo; D.fs = d->fs; D.dref = d->d_ref_mpc;
+    for (int k = 0; k < K; ++k) {
+      const double *t = d->det_tensor + 9 * k;
+      D.d[k][0] = t[0]; D.d[k][1] = t[1]; D.d[k][2] = t[2]; D.d[k][3] = t[4]; D.d[k][4] = t[5]; D.d[k][5] = t[8];
+      for (int i = 0; i < 3; ++i) D.P[k][i] = d->fs * d->det_pos[3 * k + i] / kC;
+      D.c0[k] = (d->t_lo - (d->q_t0_gps[k] - d->t_ref_gps)) * d->fs;
+    }
+    for (int a = 0; a < M; ++a) swsh_terms_d(d->lm[2 * perm[a]], d->lm[2 * perm[a] + 1], D, a);
+    D.uv_off = (long long)uv64.size();
+    uv64.resize(uv64.size() + (size_t)2 * K * M * M);
+    double2 *u = uv64.data() + D.uv_off;
+    for (int w = 0; w < 2; ++w)
+      for (int k = 0; k < K; ++k)
+        for (int a = 0; a < M; ++a)
+          for (int b = 0; b < M; ++b) {
+            const double *x = (w ? d->V : d->U) + 2 * ((k * M + perm[a]) * M + perm[b]);
+            u[(((size_t)w * K + k) * M + a) * M + b] = make_double2(x[0], x[1]);
+          }
+  }
   // merged rows for the time quadrature (tgrid_scan_half): for real data and modes with
   // conj(h_a(-f)) = sigma_a h_abar(f), Eq. (QUV) gives Q_abar(t) = sigma_a conj(Q_a(t)); each pair
   // (a, abar), m > 0, present with that relation at every sample (checked on the FP64 inputs to
@@ -495,6 +550,32 @@ rift_status ensure_scratch(rift_ile *h, int np, size_t max_items, size_t ebuf, i
   return RIFT_OK;
 }
 
+// Refinement of heavy samples: candidate and scratch buffers for np points and max_items work
+// items per round, and each point's state reset (no correction yet).
+rift_status ensure_refine(rift_ile *h, int np, size_t max_items, cudaStream_t st) {
+  rift_status s;
+  if ((s = grow(h, h->cand, h->cap_cand, max_items * RIFT_CAND_PER_ITEM)) != RIFT_OK) return s;
+  if ((s = grow(h, h->rscratch, h->cap_rscratch, refine_scratch_bytes(np))) != RIFT_OK) return s;
+  if (np > h->cap_rstate) {
+    cache_dev_free(h->rstate);
+    cache_host_free(h->rstate_host);
+    h->rstate = nullptr;
+    h->rstate_host = nullptr;
+    h->cap_rstate = 0;
+    cudaError_t e;
+    if ((e = cache_dev_alloc((void **)&h->rstate, sizeof(RefineState) * np)) != cudaSuccess ||
+        (e = cache_host_alloc((void **)&h->rstate_host, sizeof(RefineState) * np)) != cudaSuccess)
+      return fail(h, RIFT_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+    h->cap_rstate = np;
+  }
+  for (int p = 0; p < np; ++p) {
+    std::memset(&h->rstate_host[p], 0, sizeof(RefineState));
+    h->rstate_host[p].mref = -INFINITY;
+  }
+  RIFT_CK(h, cudaMemcpyAsync(h->rstate, h->rstate_host, sizeof(RefineState) * np, cudaMemcpyHostToDevice, st));
+  return RIFT_OK;
+}
+
 rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
   if (!out) return RIFT_EINVAL;
   *out = nullptr;
@@ -507,10 +588,11 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
   h->stream = (cudaStream_t)descs[0].cuda_stream;
   std::vector<float2> qv;
   std::vector<float4> cv;
+  std::vector<double2> uv64;
   h->pts.resize(n);
   for (int i = 0; i < n; ++i) {
     if (descs[i].n_det != h->K) { rift_status s = fail(h, RIFT_EINVAL, "points differ in n_det"); rift_ile_destroy(h); return s; }
-    rift_status s = build_point(h, &descs[i], h->pts[i], qv, cv);
+    rift_status s = build_point(h, &descs[i], h->pts[i], qv, cv, uv64);
     if (s != RIFT_OK) {
       fprintf(stderr, "rift_ile_create: point %d: %s\n", i, h->err.c_str());
       rift_ile_destroy(h);
@@ -557,7 +639,8 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
     qmerged += (size_t)c.K * c.T * c.Mhp;
   }
   std::vector<PointC> pc(n);
-  for (int i = 0; i < n; ++i) pc[i] = h->pts[i].c;
+  std::vector<PointD> pdv(n);
+  for (int i = 0; i < n; ++i) { pc[i] = h->pts[i].c; pdv[i] = h->pts[i].d; }
   rift_status s = RIFT_OK;
   if ((e = cache_dev_alloc((void **)&h->pts_dev, sizeof(PointC) * n)) != cudaSuccess ||
       (e = cache_dev_alloc((void **)&h->q_arena, sizeof(float2) * std::max<size_t>(qtot + qmerged, 2))) != cudaSuccess ||
@@ -571,6 +654,12 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
       (e = cudaMemcpyAsync(h->c_arena, cv.data(), sizeof(float4) * cv.size(), cudaMemcpyHostToDevice, h->stream)) !=
           cudaSuccess ||
       (e = qmerged ? launch_merge_rows(h->pts_dev, n, h->q_arena, h->stream) : cudaSuccess) != cudaSuccess ||
+      (e = cache_dev_alloc((void **)&h->pd_dev, sizeof(PointD) * n)) != cudaSuccess ||
+      (e = cache_dev_alloc((void **)&h->uv64, sizeof(double2) * std::max<size_t>(uv64.size(), 1))) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->pd_dev, pdv.data(), sizeof(PointD) * n, cudaMemcpyHostToDevice, h->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(h->uv64, uv64.data(), sizeof(double2) * uv64.size(), cudaMemcpyHostToDevice, h->stream)) !=
+          cudaSuccess ||
       (e = cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), h->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
     s = (e == cudaErrorMemoryAllocation) ? RIFT_ENOMEM : RIFT_ECUDA;
@@ -622,24 +711,38 @@ rift_status check_opts(rift_ile *h, const rift_mc_opts *o) {
   }
   if (o->tables_out && o->proposal != RIFT_PROPOSAL_ADAPTIVE)
     return fail(h, RIFT_EINVAL, "tables_out needs the adaptive proposal");
+  if (o->refine && (o->resume || o->save)) return fail(h, RIFT_EINVAL, "refine does not combine with resume or save");
   if (!(o->fallback_neff >= 0.0)) return fail(h, RIFT_EINVAL, "fallback_neff must be >= 0");
   if (o->fallback_neff > 0.0 && o->proposal != RIFT_PROPOSAL_LEARNED)
     return fail(h, RIFT_EINVAL, "fallback_neff applies to the learned proposal only");
   return RIFT_OK;
 }
 
-void fill_result(const AccState &a, rift_mc_result *r) {
+// rs (optional): the refinement of heavy samples, whose corrections replace the FP32 log weights of
+// the refined samples by their FP64 values in the sums; the largest weight is then the largest
+// refined one when the sample at the maximum was refined.
+void fill_result(const AccState &a, rift_mc_result *r, const RefineState *rs = nullptr) {
   r->acc_max = a.m;
   r->acc_s1 = a.s1 + a.c1;
   r->acc_s2 = a.s2 + a.c2;
   r->n_evals = a.n;
+  r->n_refined = 0;
+  double wmax = 1.0;
+  if (rs && rs->n > 0 && a.n > 0) {
+    const double f = std::exp(rs->mref - a.m);
+    r->acc_s1 += rs->d1 * f;
+    r->acc_s2 += rs->d2 * f * f;
+    const double w64 = std::exp(rs->l64max - a.m);
+    wmax = (rs->l32max == a.m) ? w64 : std::max(1.0, w64);
+    r->n_refined = (int)rs->n;
+  }
   const double n = (double)a.n;
   if (a.n == 0 || !(r->acc_s1 > 0)) {
     r->lnL_marg = -INFINITY; r->n_eff = 0; r->n_eff_kish = 0; r->sigma = INFINITY;
     return;
   }
   r->lnL_marg = a.m + std::log(r->acc_s1) - std::log(n);
-  r->n_eff = r->acc_s1;
+  r->n_eff = r->acc_s1 / wmax;
   r->n_eff_kish = r->acc_s1 * r->acc_s1 / r->acc_s2;
   r->sigma = (a.n > 1) ? std::sqrt(std::max(n * r->acc_s2 / (r->acc_s1 * r->acc_s1) - 1.0, 0.0) / (n - 1.0)) : INFINITY;
 }
@@ -920,6 +1023,13 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
   L.flags = h->flags;
   L.max_M = ys_modes;
   L.merged = (mp && ys_modes == 0 && h->pts[0].c.qhalf && h->pts[0].c.Mh == RIFT_MAXMH) ? 1 : 0;
+  const bool refine = o->refine && !o->time_marg;
+  if (refine) {
+    rift_status rs0 = ensure_refine(h, np, S.max_items, st);
+    if (rs0 != RIFT_OK) return rs0;
+    L.cand = h->cand;
+  }
+  const double lo3 = o->d_lo * o->d_lo * o->d_lo, span3 = o->d_hi * o->d_hi * o->d_hi - lo3;
   L.max_pairK = coef_f4;
   L.max_nb = nb;
   L.learned = learned ? 1 : 0;
@@ -1002,6 +1112,11 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     if (o->timing) RIFT_CK(h, cudaEventRecord(ev1, st));
     RIFT_CK(h, launch_merge_points(S.partials, S.rp, np, S.acc, st));
     launches += 2;
+    if (refine) {
+      RIFT_CK(h, launch_refine(h->pts_dev, h->pd_dev, h->uv64, h->q_arena, S.rp, S.acc, h->cand, np, o->seed, lo3,
+                               span3, h->rscratch, h->rstate, h->flags, st));
+      launches += 3;
+    }
     const bool adapt_now = adaptive && (o->adapt_rounds < 0 || r < o->adapt_rounds);
     if (adapt_now) {
       RIFT_CK(h, launch_hist_points(S.ell, S.bins, S.rp, np, S.acc, (float)o->beta, nb, S.hist, S.hblocks, st));
@@ -1065,9 +1180,13 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     std::memset(o->save, 0, RIFT_MC_STATE_BYTES);
     std::memcpy(o->save, &outb, sizeof(outb));
   }
+  if (refine) {
+    RIFT_CK(h, cudaMemcpyAsync(h->rstate_host, h->rstate, sizeof(RefineState) * np, cudaMemcpyDeviceToHost, st));
+    RIFT_CK(h, cudaStreamSynchronize(st));
+  }
   rift_status fl = read_flags(h);
   for (int p = 0; p < np; ++p) {
-    fill_result(S.acc_host[p], &res[p]);
+    fill_result(S.acc_host[p], &res[p], refine ? &h->rstate_host[p] : nullptr);
     res[p].rounds = rounds[p];
     res[p].fallback_round = fb_round[p];
     res[p].kernel_ms = (p == 0) ? kms : 0.0;
@@ -1151,6 +1270,12 @@ void rift_ile_destroy(rift_ile *h) {
   cache_dev_free(h->ctl);
   cache_host_free(h->ctl_host);
   cache_host_free(h->pst_host);
+  cache_dev_free(h->pd_dev);
+  cache_dev_free(h->uv64);
+  cache_dev_free(h->cand);
+  cache_dev_free(h->rscratch);
+  cache_dev_free(h->rstate);
+  cache_host_free(h->rstate_host);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   delete h->canon0;
@@ -1431,8 +1556,15 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   L.fault_nan = fault_is("nan_sample") ? 1 : 0;
   L.fault_stall = fault_is("stage_timeout") ? 1 : 0;
   L.tmarg = tm;
+  const bool refine = o->refine && !o->time_marg;
+  if (refine) {
+    rift_status rs0 = ensure_refine(h, np, S.max_items, st);
+    if (rs0 != RIFT_OK) return rs0;
+    L.cand = h->cand;
+  }
+  const double lo3 = o->d_lo * o->d_lo * o->d_lo, span3 = o->d_hi * o->d_hi * o->d_hi - lo3;
   const int grid = h->num_sms * bps;
-  // capture G rounds: update -> cells -> merge -> (adaptive) hist -> tables
+  // capture G rounds: update -> cells -> merge -> (refine) -> (adaptive) hist -> tables
   const int G = std::max(1, h->graph_rounds);
   // every argument the captured launches take by value (pointers included): an equal key means the
   // cached graph launches exactly these kernels with these arguments
@@ -1449,8 +1581,11 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   put(ints, sizeof(ints));
   put(&beta_f, sizeof(beta_f));
   put(&eps_d, sizeof(eps_d));
-  const void *ptrs[7] = {h->pst, S.acc, S.rp, h->ctl, S.partials, S.ell, S.hist};
+  const void *ptrs[12] = {h->pst, S.acc, S.rp, h->ctl, S.partials, S.ell, S.hist,
+                          refine ? h->rscratch : nullptr, refine ? h->rstate : nullptr, h->pd_dev, h->uv64, h->flags};
   put(ptrs, sizeof(ptrs));
+  const double refd[2] = {refine ? lo3 : 0.0, refine ? span3 : 0.0};
+  put(refd, sizeof(refd));
   if (!h->gexec || key != h->gkey) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
@@ -1462,6 +1597,9 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
       if ((ce = launch_round_update(B, h->pst, S.acc, S.rp, h->ctl, st)) != cudaSuccess) break;
       if ((ce = launch_cells(K, NT, L, grid, block, smem, st)) != cudaSuccess) break;
       if ((ce = launch_merge_points(S.partials, S.rp, np, S.acc, st)) != cudaSuccess) break;
+      if (refine && (ce = launch_refine(h->pts_dev, h->pd_dev, h->uv64, h->q_arena, S.rp, S.acc, h->cand, np, o->seed,
+                                        lo3, span3, h->rscratch, h->rstate, h->flags, st)) != cudaSuccess)
+        break;
       if (adaptive) {
         if ((ce = launch_hist_ctl(S.ell, S.bins, S.rp, np, S.acc, beta_f, nb, S.hist, S.hblocks, h->ctl, st)) !=
             cudaSuccess)
@@ -1496,6 +1634,8 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   if (status != RIFT_OK) return status;
   RIFT_CK(h, cudaMemcpyAsync(S.acc_host, S.acc, sizeof(AccState) * np, cudaMemcpyDeviceToHost, st));
   RIFT_CK(h, cudaMemcpyAsync(h->pst_host, h->pst, sizeof(PtState) * np, cudaMemcpyDeviceToHost, st));
+  if (refine)
+    RIFT_CK(h, cudaMemcpyAsync(h->rstate_host, h->rstate, sizeof(RefineState) * np, cudaMemcpyDeviceToHost, st));
   RIFT_CK(h, cudaStreamSynchronize(st));
   if (o->tables_out && adaptive) {
     // Round r reads table buffer (number of adapting rounds before r) mod 2 and an adapting round
@@ -1514,9 +1654,9 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
   rift_status fl = read_flags(h);
   rift_status overall = fl;
   for (int p = 0; p < np; ++p) {
-    fill_result(S.acc_host[p], &res[p]);
+    fill_result(S.acc_host[p], &res[p], refine ? &h->rstate_host[p] : nullptr);
     res[p].rounds = h->pst_host[p].rounds;
-    res[p].kernel_launches = (p == 0) ? replays * G * (adaptive ? 5 : 3) : 0;
+    res[p].kernel_launches = (p == 0) ? replays * G * ((adaptive ? 5 : 3) + (refine ? 3 : 0)) : 0;
     res[p].fallback_round = h->pst_host[p].fb_round;
     for (int d = 0; d < 3; ++d) res[p].strata[d] = 1 << lsv[3 * p + d];
     rift_status sp = fl;

@@ -719,6 +719,8 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
   __shared__ int s_red[2 * K][RIFT_CELL_BLOCK / 32];
   __shared__ float4 s_wpart[RIFT_CELL_BLOCK / 32];
   __shared__ uint32_t s_wflag[RIFT_CELL_BLOCK / 32];
+  __shared__ float s_tmax[RIFT_CELL_BLOCK];
+  __shared__ uint32_t s_timax[RIFT_CELL_BLOCK];
 
   PointC &P = *reinterpret_cast<PointC *>(smem);
   size_t off = al16(sizeof(PointC));
@@ -883,6 +885,10 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
 
     // C. evaluate
     float m = kNegInf, s1 = 0.f, s2 = 0.f, cnt = 0.f;
+    // this thread's largest log weight of the item and its sample (candidates), kept in shared
+    // memory so that the sample loop holds no more registers
+    s_tmax[threadIdx.x] = kNegInf;
+    s_timax[threadIdx.x] = 0u;
     if constexpr (TMARG == 2) {
       tmarg_gemm_item<K, NT, LEARNED>(L, P, R, C, tab, lnw, s_gmm, wbuf, tbar, tph, j0, j_end, m, s1, s2, cnt, flags,
                                       ok);
@@ -941,9 +947,27 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
       if (L.ell_buf && R.ell_off >= 0) { L.ell_buf[R.ell_off + i] = ell; L.bin_buf[R.ell_off + i] = d.bins; }
       if (isfinite(ell)) { lse_push(ell, m, s1, s2); cnt += 1.f; }
       else flags |= RIFT_FLAG_NONFINITE;
+      if (L.cand && ell > s_tmax[threadIdx.x]) { s_tmax[threadIdx.x] = ell; s_timax[threadIdx.x] = i; }
     }
     }
-    // D. one partial per cell
+    // D. one partial per cell; the two largest log weights of each warp as candidates
+    if (L.cand) {
+      float v = s_tmax[threadIdx.x];
+      uint32_t ix = s_timax[threadIdx.x];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float bv = v;
+        uint32_t bi = ix;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const uint32_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) L.cand[(size_t)item * RIFT_CAND_PER_ITEM + 2 * wid + r] = make_float2(bv, __uint_as_float(bi));
+        if (v == bv && ix == bi) v = kNegInf;
+      }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float m2 = __shfl_xor_sync(0xffffffffu, m, o);

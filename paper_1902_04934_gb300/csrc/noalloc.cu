@@ -95,6 +95,10 @@ extern "C" rift_status rift_ile_marginalize_static(rift_ile *h, const rift_mc_op
                               "buffers are allocated per handle)");
   if (o->dbg_tables || o->timing)
     return rift_internal_fail(h, RIFT_EINVAL, "rift_ile_marginalize_static: dbg_tables and timing are not supported");
+  if (o->refine)
+    return rift_internal_fail(h, RIFT_EINVAL,
+                              "rift_ile_marginalize_static: refine is not supported (its candidate buffers are "
+                              "allocated per handle)");
   if (o->proposal == RIFT_PROPOSAL_ADAPTIVE && (o->n_bins < 2 || o->n_bins > RIFT_MAXBINS))
     return rift_internal_fail(h, RIFT_EINVAL, "n_bins out of range [2, 256]");
   unsigned char *base = nullptr;

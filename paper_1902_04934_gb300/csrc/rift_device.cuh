@@ -76,6 +76,23 @@ struct PointC {
   uint32_t h_neg, pad3;
 };
 
+// FP64 constants of one point for the refinement of heavy samples (refine.cu): the same quantities
+// as PointC, unrounded, and the offset of the point's U, V in the FP64 pair arena.
+struct PointD {
+  int K, M, T, Mp, interp, pad;
+  long long q_off;           // the point's FP32 Q block (float2 units)
+  long long uv_off;          // U [K][M][M] then V [K][M][M] complex128 in the FP64 arena (double2 units)
+  double g;                  // GMST / 2pi (turns)
+  double A;                  // (t_hi - t_lo) fs
+  double t_lo, t_span, fs, dref;
+  double d[RIFT_MAXK][6];    // response tensors xx xy xz yy yz zz
+  double P[RIFT_MAXK][3];    // fs x_k / c (samples)
+  double c0[RIFT_MAXK];      // (t_lo - tau0_k) fs
+  int ml[RIFT_MAXM], mm[RIFT_MAXM], nterm[RIFT_MAXM];
+  int kc[RIFT_MAXM][RIFT_MAXTERM];
+  double coef[RIFT_MAXM][RIFT_MAXTERM];
+};
+
 // Canonical mode index j <-> (l, m) and the Goldberg terms of -2Y_lm present for it:
 // r from max(0, m + 2) to min(l + 2, l + m), exponent of cos(theta/2) k = 2 r - 2 - m.
 __host__ __device__ constexpr int canon_l(int j) { return j < 5 ? 2 : (j < 12 ? 3 : 4); }

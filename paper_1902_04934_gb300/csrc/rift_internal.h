@@ -56,6 +56,17 @@ struct __align__(32) Part {
   double m, s1, s2, n;
 };
 
+// Refinement of heavy samples (rift_mc_opts.refine), per point: the corrections of the sums,
+// sum over refined samples of e^{l64 - mref} - e^{l32 - mref} (and of the squares), relative to
+// mref, the running maximum when they were last folded; the largest refined FP64 log weight and the
+// FP32 value it replaced; the number of refined samples.
+struct RefineState {
+  double mref, d1, d2, l64max, l32max;
+  unsigned long long n;
+};
+// Candidates kept per work item: the two largest log weights of each warp.
+#define RIFT_CAND_PER_ITEM (2 * (RIFT_CELL_BLOCK / 32))
+
 // Running log-sum-exp state of one point (FP64, Neumaier-compensated sums).
 struct AccState {
   double m;       // max log weight so far
@@ -122,6 +133,8 @@ struct CellLaunch {
   int tmarg;                   // the event time is marginalised by quadrature (Eq. lnL:tmarg)
   int merged;                  // single mirror-symmetric point with all 21 modes whose 9 mirror
                                // pairs of Q merge (P.qhalf, P.Mh = 12): merged rows (cells_kernel_mp)
+  float2 *cand;                // optional [items][RIFT_CAND_PER_ITEM]: (log weight, sample index bits)
+                               // of the two largest log weights of each warp of each item
 };
 
 // Device-side round control of a batched run replayed as a CUDA graph.
@@ -212,6 +225,15 @@ cudaError_t launch_cells(int K, int ntap, const CellLaunch &L, int grid, int blo
 int cells_blocks_per_sm(int K, int ntap, size_t smem, int block, int tmarg = 0);
 // Merged Q rows of every point that has them, gathered from the point's uploaded Q block.
 cudaError_t launch_merge_rows(const PointC *pts, int np, float2 *qa, cudaStream_t st);
+// Refinement of heavy samples after a round's merge: choose each point's samples from the items'
+// candidates, evaluate them in FP64, fold the corrections into RefineState.  `scratch` holds
+// np * RIFT_REFINE_CAP uint2 + np int + np * RIFT_REFINE_CAP double2 (refine_scratch_bytes).
+struct PointD;
+size_t refine_scratch_bytes(int np);
+cudaError_t launch_refine(const PointC *pts, const PointD *pd, const double2 *uv64, const float2 *qa,
+                          const RoundPt *rp, const AccState *acc, const float2 *cand, int np,
+                          unsigned long long seed, double d_lo3, double d_span3, void *scratch,
+                          RefineState *rs, uint32_t *flags, cudaStream_t st);
 cudaError_t launch_merge_points(const Part *partials, const RoundPt *rp, int n_points, AccState *acc,
                                 cudaStream_t st);
 cudaError_t launch_hist_points(const float *ell, const uint32_t *bins, const RoundPt *rp, int n_points,
