@@ -132,6 +132,8 @@ struct rift_ile {
   double2 *uv64 = nullptr;
   float2 *cand = nullptr;
   size_t cap_cand = 0;
+  float *cmax = nullptr;
+  size_t cap_cmax = 0;
   unsigned char *rscratch = nullptr;
   size_t cap_rscratch = 0;
   RefineState *rstate = nullptr, *rstate_host = nullptr;
@@ -555,6 +557,7 @@ rift_status ensure_scratch(rift_ile *h, int np, size_t max_items, size_t ebuf, i
 rift_status ensure_refine(rift_ile *h, int np, size_t max_items, cudaStream_t st) {
   rift_status s;
   if ((s = grow(h, h->cand, h->cap_cand, max_items * RIFT_CAND_PER_ITEM)) != RIFT_OK) return s;
+  if ((s = grow(h, h->cmax, h->cap_cmax, max_items)) != RIFT_OK) return s;
   if ((s = grow(h, h->rscratch, h->cap_rscratch, refine_scratch_bytes(np))) != RIFT_OK) return s;
   if (np > h->cap_rstate) {
     cache_dev_free(h->rstate);
@@ -1028,6 +1031,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     rift_status rs0 = ensure_refine(h, np, S.max_items, st);
     if (rs0 != RIFT_OK) return rs0;
     L.cand = h->cand;
+    L.cmax = h->cmax;
   }
   const double lo3 = o->d_lo * o->d_lo * o->d_lo, span3 = o->d_hi * o->d_hi * o->d_hi - lo3;
   L.max_pairK = coef_f4;
@@ -1113,7 +1117,7 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     RIFT_CK(h, launch_merge_points(S.partials, S.rp, np, S.acc, st));
     launches += 2;
     if (refine) {
-      RIFT_CK(h, launch_refine(h->pts_dev, h->pd_dev, h->uv64, h->q_arena, S.rp, S.acc, h->cand, np, o->seed, lo3,
+      RIFT_CK(h, launch_refine(h->pts_dev, h->pd_dev, h->uv64, h->q_arena, S.rp, S.acc, h->cmax, h->cand, np, o->seed, lo3,
                                span3, h->rscratch, h->rstate, h->flags, st));
       launches += 3;
     }
@@ -1273,6 +1277,7 @@ void rift_ile_destroy(rift_ile *h) {
   cache_dev_free(h->pd_dev);
   cache_dev_free(h->uv64);
   cache_dev_free(h->cand);
+  cache_dev_free(h->cmax);
   cache_dev_free(h->rscratch);
   cache_dev_free(h->rstate);
   cache_host_free(h->rstate_host);
@@ -1561,6 +1566,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
     rift_status rs0 = ensure_refine(h, np, S.max_items, st);
     if (rs0 != RIFT_OK) return rs0;
     L.cand = h->cand;
+    L.cmax = h->cmax;
   }
   const double lo3 = o->d_lo * o->d_lo * o->d_lo, span3 = o->d_hi * o->d_hi * o->d_hi - lo3;
   const int grid = h->num_sms * bps;
@@ -1597,7 +1603,7 @@ rift_status batch_run(rift_ile *h, const rift_mc_opts *o, rift_mc_result *res, b
       if ((ce = launch_round_update(B, h->pst, S.acc, S.rp, h->ctl, st)) != cudaSuccess) break;
       if ((ce = launch_cells(K, NT, L, grid, block, smem, st)) != cudaSuccess) break;
       if ((ce = launch_merge_points(S.partials, S.rp, np, S.acc, st)) != cudaSuccess) break;
-      if (refine && (ce = launch_refine(h->pts_dev, h->pd_dev, h->uv64, h->q_arena, S.rp, S.acc, h->cand, np, o->seed,
+      if (refine && (ce = launch_refine(h->pts_dev, h->pd_dev, h->uv64, h->q_arena, S.rp, S.acc, h->cmax, h->cand, np, o->seed,
                                         lo3, span3, h->rscratch, h->rstate, h->flags, st)) != cudaSuccess)
         break;
       if (adaptive) {

@@ -988,6 +988,7 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
         F |= s_wflag[w];
       }
       L.partials[item] = Part{(double)M, (double)S1, (double)S2, (double)N};
+      if (L.cand) L.cmax[item] = M;
       if (F) atomicOr(L.flags, F);
     }
     flags = 0u;

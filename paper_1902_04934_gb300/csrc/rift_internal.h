@@ -135,6 +135,7 @@ struct CellLaunch {
                                // pairs of Q merge (P.qhalf, P.Mh = 12): merged rows (cells_kernel_mp)
   float2 *cand;                // optional [items][RIFT_CAND_PER_ITEM]: (log weight, sample index bits)
                                // of the two largest log weights of each warp of each item
+  float *cmax;                 // with cand: [items] the item's largest log weight
 };
 
 // Device-side round control of a batched run replayed as a CUDA graph.
@@ -231,7 +232,7 @@ cudaError_t launch_merge_rows(const PointC *pts, int np, float2 *qa, cudaStream_
 struct PointD;
 size_t refine_scratch_bytes(int np);
 cudaError_t launch_refine(const PointC *pts, const PointD *pd, const double2 *uv64, const float2 *qa,
-                          const RoundPt *rp, const AccState *acc, const float2 *cand, int np,
+                          const RoundPt *rp, const AccState *acc, const float *cmax, const float2 *cand, int np,
                           unsigned long long seed, double d_lo3, double d_span3, void *scratch,
                           RefineState *rs, uint32_t *flags, cudaStream_t st);
 cudaError_t launch_merge_points(const Part *partials, const RoundPt *rp, int n_points, AccState *acc,
