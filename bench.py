@@ -306,6 +306,7 @@ def precision_check(rift, pt, opts, tune):
     n = opts["n_per_round"]
     dbg = torch.empty(n, dtype=torch.float32, device="cuda")
     res = rift.rift_ile_marginalize(h, dbg_ell=dbg, **opts)
+    plain = rift.rift_ile_marginalize(h, **dict(opts, refine=0))   # the same round, FP32 only
     rift.rift_ile_destroy(h)
     got = dbg.cpu().numpy().astype(np.float64)
     del dbg
@@ -335,7 +336,9 @@ def precision_check(rift, pt, opts, tune):
     return {"samples": int(idx.size), "max_err_over_tol": float((err / tol).max()),
             "mean_err_over_tol": float((err / tol).mean()),
             "max_abs_dlnL_template_snr_le_30": float(err[le30].max()) if le30.any() else None,
-            "dlnL_marg": float(res["lnL_marg"] - ref[0]), "lnL_marg_oracle": ref[0], "n_eff_oracle": ref[1],
+            "dlnL_marg": float(res["lnL_marg"] - ref[0]), "refined_samples": res["n_refined"],
+            "dlnL_marg_fp32_only": float(plain["lnL_marg"] - ref[0]),
+            "lnL_marg_oracle": ref[0], "n_eff_oracle": ref[1],
             "oracle_full_round_s": round(t_full, 2), "oracle_samples": int(acc.n),
             "tolerance": "per sample 1e-3 max(1, <h|h>/900) (1e-3 absolute at template SNR <= 30); lnL_marg "
                          "1e-4; FP64 oracle on the same draws"}
@@ -412,6 +415,23 @@ def run_gpu(args, world, rank, local):
 
     # end to end through the public API with host buffers: create (host Q/U/V -> device)
     # + marginalise + result back, every step
+    # the same step without the FP64 refinement of the heaviest samples (the bulk and those samples
+    # both in FP32): its time is the cost of the refinement
+    fp32_only = None
+    if opts.get("refine"):
+        pl = []
+        for _ in range(5):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rift.rift_ile_marginalize(h, **dict(opts, refine=0))
+            e1.record()
+            e1.synchronize()
+            pl.append(e0.elapsed_time(e1))
+        fp32_only = {"ms_per_step": statistics.median(pl), "value": N_SAMPLES / (statistics.median(pl) * 1e-3),
+                     "unit": "evals/s", "note": "same step with refine=0 (no FP64 re-evaluation)"}
+
     e2e = None
     if not args.no_e2e:
         h2d = K * T * ((M + 1) // 2 * 2) * 8 + (M * (M + 1) // 2) * K * 16 + 2048
@@ -476,6 +496,7 @@ def run_gpu(args, world, rank, local):
         "autotune": tune,
         "clocks": clk,
         "e2e": e2e,
+        "fp32_only": fp32_only,
         "cpu_baseline": cpu,
         "precision": precision,
         "wall_s": t_wall,
