@@ -78,10 +78,9 @@ def executed_flops_per_sample(K: int, M: int, taps: int) -> int:
     return pair_form_flops_per_sample(K, M, taps) - (npair * (12 + 12 * K) + 10 * K) + mirror_quad_flops(K)
 
 
-def mdn_forward_flops(P: int) -> int:
-    """FP32 flops of the network forward pass for P points: 64 -> 256 -> 256 -> 88 (FMA = 2), plus
-    about 20 flops per GELU."""
-    return P * (2 * (64 * 256 + 256 * 256 + 256 * 88) + 20 * 512)
+def mdn_forward_mma_flops(P: int) -> int:
+    """Flops of the network's three matrix products for P points (FMA = 2)."""
+    return P * 2 * (64 * 256 + 256 * 256 + 256 * 88)
 
 
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
@@ -444,6 +443,7 @@ def run_gpu(args, world, rank, local):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h2 = rift.rift_ile_create(pt)
+            rift.rift_ile_set_tune(h2, tune["cell_samples"], tune["smem_split"])   # the cached launch shape
             r = rift.rift_ile_marginalize(h2, **opts)
             rift.rift_ile_destroy(h2)
             times.append(time.perf_counter() - t0)
@@ -451,7 +451,8 @@ def run_gpu(args, world, rank, local):
         e2e_s = max_over_ranks(world, statistics.mean(times))
         e2e = {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 64 * rounds + 4,
-               "includes": "rift_ile_create from host FP64 arrays + rift_ile_marginalize + result read + destroy"}
+               "includes": "rift_ile_create from host FP64 arrays + rift_ile_set_tune (cached launch shape) + "
+                           "rift_ile_marginalize + result read + destroy"}
 
     cpu = None
     precision = None
@@ -769,9 +770,9 @@ def run_quv(rift, W, peak):
 
 
 def run_mdn(rift, peak):
-    """The network's forward kernel on 4096 points (CUDA events on the stream it runs on, the
-    default stream), and one training step on 256 points with 64 samples each (forward, loss,
-    backward, Adam)."""
+    """The network's forward kernel on 4096 points (tensor cores; CUDA events around the kernel on
+    the stream it runs on, the default stream), and one training step on 256 points with 64
+    samples each (forward, loss, backward, Adam)."""
     import numpy as np
     import torch
     m = rift.rift_mdn_create(11)
@@ -783,12 +784,8 @@ def run_mdn(rift, peak):
     torch.cuda.synchronize()
     fw = []
     for _ in range(5):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
         rift.rift_mdn_forward(m, S)
-        e1.record()
-        e1.synchronize()
-        fw.append(e0.elapsed_time(e1))
+        fw.append(rift.rift_mdn_forward_ms())
     B, H = 256, 64
     th = torch.rand((B, H, 5), device="cuda", generator=g) * 0.8 + 0.1
     w = torch.full((B, H), 1.0 / H, device="cuda")
@@ -805,13 +802,19 @@ def run_mdn(rift, peak):
     tr = e0.elapsed_time(e1) / steps
     rift.rift_mdn_destroy(m)
     ms = statistics.median(fw)
-    fl = mdn_forward_flops(P)
+    fl = mdn_forward_mma_flops(P)
+    mp = measured_peaks() or {}
+    tpeak = mp.get("bf16_tflops") or 1900.0
     return {"workload": f"forward on {P} points; training steps of {B} points x {H} samples",
             "forward_ms": ms, "train_step_ms": tr,
-            "roofline_forward": {"bound": "alu", "kernel": "mdn_forward_kernel", "achieved": fl / (ms * 1e-3) / 1e12,
-                                 "peak": peak, "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / 1e12 / peak,
+            "roofline_forward": {"bound": "tensor", "kernel": "mdn_forward_tc_kernel", "achieved": fl / (ms * 1e-3) / 1e12,
+                                 "peak": tpeak, "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / 1e12 / tpeak,
                                  "flops": fl, "traffic": None,
-                                 "note": "BF16 weights on CUDA cores, FP32 accumulation"},
+                                 "peak_basis": "measured cuBLAS bf16 burst" if mp.get("bf16_tflops") else
+                                               "fallback bf16 burst (no measured peaks)",
+                                 "note": "tcgen05 BF16 products with FP32 accumulators in tensor memory, 128 points "
+                                         "per CTA; flops are the network's (the kernel issues twice as many: each "
+                                         "layer input is split into two BF16 terms); GELU on the CUDA cores"},
             "train_step_note": "the step's time includes the per-step loss read back to the host"}
 
 

@@ -335,8 +335,14 @@ const char *rift_mdn_last_error(const rift_mdn *m);
  * get: which = 0 the float32 master copy, 1 the bfloat16 weights the kernels use. */
 rift_status rift_mdn_set_params(rift_mdn *m, const float *host);
 rift_status rift_mdn_get_params(rift_mdn *m, float *host, int which);
-/* head_dev[n][88] = network(summ_dev[n][64]) (device pointers). */
+/* head_dev[n][88] = network(summ_dev[n][64]) (device pointers; the device's default stream).
+ * The three layers run on the tensor cores (tcgen05 BF16 products, FP32 accumulators in tensor
+ * memory), 128 points per CTA; each layer's FP32 input is split into two BF16 terms, so inputs
+ * keep about 16 significant bits and the weights are exactly their BF16 values.  Synchronises the
+ * device; RIFT_ETIMEOUT if a bounded wait for the tensor core expired. */
 rift_status rift_mdn_forward(rift_mdn *m, int n, const float *summ_dev, float *head_dev);
+/* Device time (ms, CUDA events around the kernel) of the last rift_mdn_forward of this thread. */
+double rift_mdn_forward_ms(void);
 /* Mean over the n points of the weighted negative log likelihood
  *   -sum_j w[p][j] ln q_MDN(theta[p][j] | summ[p]),
  * theta_dev [n][H][5] = (ra, sin dec, t, cos incl, ln D), w_dev [n][H], box_dev [n][2][5] the

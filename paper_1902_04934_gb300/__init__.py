@@ -107,6 +107,7 @@ def _load():
         "rift_quv": (I, [P, P, P, P]),
         "rift_quv_last_error": (C.c_char_p, []),
         "rift_quv_kernel_ms": (None, [P]),
+        "rift_mdn_forward_ms": (D, []),
         "rift_source_frame": (I, [I, P, P, I, P, D, D, S, P, P, P]),
         "rift_ile_create_fd": (I, [P, C.POINTER(P)]),
         "rift_ile_marginalize": (I, [P, C.POINTER(McOpts), C.POINTER(McResult)]),
@@ -513,6 +514,11 @@ def rift_mdn_forward(m, summ):
     out = torch.empty((n, MDN_HEAD), dtype=torch.float32, device=summ.device)
     _mcheck(m, _lib.rift_mdn_forward(m.ptr, n, summ.data_ptr(), out.data_ptr()))
     return out
+
+
+def rift_mdn_forward_ms():
+    """Device time (ms) of the kernel of this thread's last rift_mdn_forward call."""
+    return float(_lib.rift_mdn_forward_ms())
 
 
 def rift_mdn_loss_grad(m, summ, theta, w, box):

@@ -12,6 +12,7 @@
 #include "../../include/rift_ile.h"
 #include "rift_device.cuh"
 #include "rift_internal.h"
+#include "host_par.h"
 
 namespace {
 
@@ -29,6 +30,20 @@ double gmst_rad(double gps) {
   sec = std::fmod(sec, 86400.0);
   if (sec < 0) sec += 86400.0;
   return sec / 86400.0 * 2.0 * kPi;
+}
+
+// |x| as the integer bit pattern of an IEEE 754 double: magnitudes compare like their patterns,
+// and patterns at or above kInfBits are infinities and NaNs.
+constexpr uint64_t kInfBits = 0x7FF0000000000000ull;
+inline uint64_t abs_bits(double x) {
+  uint64_t u;
+  std::memcpy(&u, &x, sizeof u);
+  return u & 0x7FFFFFFFFFFFFFFFull;
+}
+inline double bits_double(uint64_t u) {
+  double x;
+  std::memcpy(&x, &u, sizeof x);
+  return x;
 }
 
 void split(double v, float &hi, float &lo) {
@@ -188,7 +203,16 @@ rift_status cuda_fail(rift_ile *h, cudaError_t e, const char *where) {
   } while (0)
 
 // Build the device constants of one point from its descriptor (FP64 on the host).
-rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vector<float2> &qv,
+// Q block of a point in the arena layout [K][T][Mp]: n_det x n_t x (n_modes rounded up to even)
+// complex64, or 0 for sizes that the point's validation refuses.
+size_t q_block_size(const rift_ile_desc &d) {
+  if (d.n_det < 1 || d.n_det > RIFT_MAX_DET || d.n_modes < 1 || d.n_modes > RIFT_MAX_MODES || d.n_t < 4) return 0;
+  return (size_t)d.n_det * d.n_t * ((d.n_modes + 1) & ~1);
+}
+
+// One point's constants; its Q block is written to qb (q_block_size(*d) entries), which sits at
+// entry q_off of the arena.
+rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, float2 *qb, long long q_off,
                         std::vector<float4> &cv, std::vector<double2> &uv64) {
   if (!d) return fail(h, RIFT_EINVAL, "null descriptor");
   const int K = d->n_det, M = d->n_modes, T = d->n_t;
@@ -283,29 +307,67 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
         if (std::fabs(v1[0] - v2[0]) > 1e-10 * vmax || std::fabs(v1[1] - v2[1]) > 1e-10 * vmax)
           return fail(h, RIFT_EINVAL, "V is not symmetric");
       }
-  // Q arena block: [K][T][Mp] complex64, zero padded; converted in blocks of 64 times so that the
-  // rows written stay in cache, with the finiteness check in the same pass (x - x is 0 only for
-  // finite x)
-  c.q_off = (long long)qv.size();
-  qv.resize(qv.size() + (size_t)K * T * c.Mp, make_float2(0.f, 0.f));
-  float2 *qb = qv.data() + c.q_off;
-  bool finite = true;
-  double qmax = 0.0;
-  for (int k = 0; k < K; ++k)
-    for (int j0 = 0; j0 < T; j0 += 64) {
-      const int j1 = std::min(T, j0 + 64);
+  // mirror pairs (a, b) of stored modes, m_a > 0 and b = (l_a, -m_a), for the merged rows below:
+  // their largest deviations from Q_b = conj(Q_a) (dev_p) and from Q_b = -conj(Q_a) (dev_m) over
+  // every detector and time are taken in the conversion pass
+  int pa[RIFT_MAXM], pb[RIFT_MAXM], npr = 0;
+  for (int a = 0; a < M; ++a) {
+    if (c.mode[a].m <= 0) continue;
+    for (int e = 0; e < M; ++e)
+      if (c.mode[e].l == c.mode[a].l && c.mode[e].m == -c.mode[a].m) { pa[npr] = a; pb[npr] = e; ++npr; }
+  }
+  // Q arena block: [K][T][Mp] complex64, the pad column (odd M) zero; converted in tasks of 64
+  // times of one detector, in parallel over host threads, so that the rows written stay in cache.
+  // Magnitudes are compared as the integer bit patterns of |x| (ordered like |x|; at or above
+  // kInfBits for an infinity or a NaN), so the largest |Q| and the finiteness check are one maximum
+  c.q_off = q_off;
+  constexpr int kParts = 8;
+  struct QPart {
+    uint64_t mx = 0, dp[RIFT_MAXM] = {}, dm[RIFT_MAXM] = {};
+  };
+  QPart qp[kParts];
+  const int nblk = (T + 63) / 64;
+  parallel_parts(K * nblk, 8, kParts, [&](int part, int task0, int task1) {
+    QPart &r = qp[part];
+    for (int task = task0; task < task1; ++task) {
+      const int k = task / nblk, j0 = (task % nblk) * 64, j1 = std::min(T, j0 + 64);
+      uint64_t mx = r.mx;
       for (int a = 0; a < M; ++a) {
         const double *q = d->Q + 2 * (((size_t)k * M + perm[a]) * T);
-        float2 *out = qb + (size_t)k * T * c.Mp + a;
+        float2 *outq = qb + (size_t)k * T * c.Mp + a;
         for (int j = j0; j < j1; ++j) {
           const double re = q[2 * j], im = q[2 * j + 1];
-          finite &= (re - re == 0.0) & (im - im == 0.0);
-          qmax = std::max(qmax, std::max(std::fabs(re), std::fabs(im)));
-          out[(size_t)j * c.Mp] = make_float2((float)re, (float)im);
+          mx = std::max(mx, std::max(abs_bits(re), abs_bits(im)));
+          outq[(size_t)j * c.Mp] = make_float2((float)re, (float)im);
         }
       }
+      r.mx = mx;
+      if (c.Mp > M)
+        for (int j = j0; j < j1; ++j) qb[((size_t)k * T + j) * c.Mp + M] = make_float2(0.f, 0.f);
+      for (int p = 0; p < npr; ++p) {
+        const double *qa = d->Q + 2 * (((size_t)k * M + perm[pa[p]]) * T);
+        const double *qm = d->Q + 2 * (((size_t)k * M + perm[pb[p]]) * T);
+        uint64_t dp = r.dp[p], dm = r.dm[p];
+        for (int j = j0; j < j1; ++j) {
+          const double ar = qa[2 * j], ai = qa[2 * j + 1], br = qm[2 * j], bi = qm[2 * j + 1];
+          dp = std::max(dp, std::max(abs_bits(br - ar), abs_bits(bi + ai)));
+          dm = std::max(dm, std::max(abs_bits(br + ar), abs_bits(bi - ai)));
+        }
+        r.dp[p] = dp;
+        r.dm[p] = dm;
+      }
     }
-  if (!finite) return fail(h, RIFT_EINVAL, "non-finite Q");
+  });
+  uint64_t qmax_bits = 0, dpb[RIFT_MAXM] = {}, dmb[RIFT_MAXM] = {};
+  for (int t = 0; t < kParts; ++t) {
+    qmax_bits = std::max(qmax_bits, qp[t].mx);
+    for (int p = 0; p < npr; ++p) {
+      dpb[p] = std::max(dpb[p], qp[t].dp[p]);
+      dmb[p] = std::max(dmb[p], qp[t].dm[p]);
+    }
+  }
+  if (qmax_bits >= kInfBits) return fail(h, RIFT_EINVAL, "non-finite Q");
+  const double qmax = bits_double(qmax_bits);
   // FP64 constants and U, V (stored mode order) for the refinement of heavy samples
   {
     PointD &D = P.d;
@@ -343,28 +405,13 @@ rift_status build_point(rift_ile *h, const rift_ile_desc *d, Point &P, std::vect
     int mate[RIFT_MAXM], sg[RIFT_MAXM];   // mate[a]: the merged partner's stored index, else a
     int merged = 0;
     for (int a = 0; a < M; ++a) { mate[a] = a; sg[a] = 1; }
-    for (int a = 0; a < M; ++a) {
-      if (c.mode[a].m <= 0) continue;
-      int b = -1;
-      for (int e = 0; e < M; ++e)
-        if (c.mode[e].l == c.mode[a].l && c.mode[e].m == -c.mode[a].m) b = e;
-      if (b < 0) continue;
-      for (int sv = 1; sv >= -1; sv -= 2) {
-        bool match = true;
-        for (int k = 0; k < K && match; ++k) {
-          const double *qa = d->Q + 2 * (((size_t)k * M + perm[a]) * T);
-          const double *qb = d->Q + 2 * (((size_t)k * M + perm[b]) * T);
-          for (int j = 0; j < T && match; ++j)
-            match = std::fabs(qb[2 * j] - sv * qa[2 * j]) <= tol && std::fabs(qb[2 * j + 1] + sv * qa[2 * j + 1]) <= tol;
-        }
-        if (match) {
-          mate[a] = b;
-          mate[b] = a;
-          sg[a] = sv;
-          ++merged;
-          break;
-        }
-      }
+    for (int p = 0; p < npr; ++p) {
+      const int sv = bits_double(dpb[p]) <= tol ? 1 : (bits_double(dmb[p]) <= tol ? -1 : 0);
+      if (!sv) continue;
+      mate[pa[p]] = pb[p];
+      mate[pb[p]] = pa[p];
+      sg[pa[p]] = sv;
+      ++merged;
     }
     int Mh = 0;
     for (int a = 0; a < M; ++a)
@@ -579,6 +626,55 @@ rift_status ensure_refine(rift_ile *h, int np, size_t max_items, cudaStream_t st
   return RIFT_OK;
 }
 
+// Host staging of create(): pinned memory from the buffer cache up to kPinnedStageMax bytes,
+// pageable beyond.  Pinned memory goes back to the cache only once the stream that reads it has
+// drained (sync_on names that stream).
+constexpr size_t kPinnedStageMax = size_t(256) << 20;
+struct HostStage {
+  unsigned char *p = nullptr;
+  bool pinned = false;
+  cudaStream_t st = nullptr;
+  bool reading = false;
+  std::vector<unsigned char> pageable;
+  cudaError_t get(size_t bytes) {
+    if (bytes <= kPinnedStageMax) {
+      void *q = nullptr;
+      cudaError_t e = cache_host_alloc(&q, bytes);
+      if (e == cudaSuccess) {
+        p = static_cast<unsigned char *>(q);
+        pinned = true;
+        return e;
+      }
+      cudaGetLastError();
+    }
+    try {
+      pageable.resize(bytes);
+    } catch (...) {
+      return cudaErrorMemoryAllocation;
+    }
+    p = pageable.data();
+    return cudaSuccess;
+  }
+  void sync_on(cudaStream_t s) { st = s; reading = true; }
+  void release() {
+    if (pinned && p) {
+      if (reading) cudaStreamSynchronize(st);
+      cache_host_free(p);
+    }
+    p = nullptr;
+    pinned = false;
+  }
+  ~HostStage() { release(); }
+};
+
+// Time origins tau0 = q_t0_gps - t_ref_gps of every point's detectors, [n][RIFT_MAX_DET] (FP64).
+const double *fill_tau0(const rift_ile_desc *descs, int n, double *t0) {
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < RIFT_MAX_DET; ++k)
+      t0[(size_t)i * RIFT_MAX_DET + k] = k < descs[i].n_det ? descs[i].q_t0_gps[k] - descs[i].t_ref_gps : 0.0;
+  return t0;
+}
+
 rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
   if (!out) return RIFT_EINVAL;
   *out = nullptr;
@@ -589,13 +685,30 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
   h->K = descs[0].n_det;
   h->interp = descs[0].interp;
   h->stream = (cudaStream_t)descs[0].cuda_stream;
-  std::vector<float2> qv;
   std::vector<float4> cv;
   std::vector<double2> uv64;
+  // host copy of the arena's Q blocks followed by the points' time origins tau0: pinned (from the
+  // buffer cache), so the upload is one asynchronous DMA, up to kPinnedStageMax bytes; pageable
+  // beyond that (large batches)
+  std::vector<long long> qoff(n);
+  size_t qtot = 0;
+  for (int i = 0; i < n; ++i) {
+    qoff[i] = (long long)qtot;
+    qtot += q_block_size(descs[i]);
+  }
+  HostStage stage;
+  const size_t q_bytes = sizeof(float2) * std::max<size_t>(qtot, 2);
+  if (stage.get(q_bytes + sizeof(double) * (size_t)n * RIFT_MAX_DET) != cudaSuccess) {
+    rift_status s = fail(h, RIFT_ENOMEM, "host staging buffer");
+    rift_ile_destroy(h);
+    return s;
+  }
+  float2 *qh = reinterpret_cast<float2 *>(stage.p);
+  double *t0h = reinterpret_cast<double *>(stage.p + q_bytes);
   h->pts.resize(n);
   for (int i = 0; i < n; ++i) {
     if (descs[i].n_det != h->K) { rift_status s = fail(h, RIFT_EINVAL, "points differ in n_det"); rift_ile_destroy(h); return s; }
-    rift_status s = build_point(h, &descs[i], h->pts[i], qv, cv, uv64);
+    rift_status s = build_point(h, &descs[i], h->pts[i], qh + qoff[i], qoff[i], cv, uv64);
     if (s != RIFT_OK) {
       fprintf(stderr, "rift_ile_create: point %d: %s\n", i, h->err.c_str());
       rift_ile_destroy(h);
@@ -634,52 +747,57 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
   }
   // merged-row blocks after all Q blocks (16-byte aligned: every block holds an even number of rows
   // of an even width); only the Q blocks travel from the host
-  size_t qtot = qv.size(), qmerged = 0;
+  size_t qmerged = 0;
   for (int i = 0; i < n; ++i) {
     PointC &c = h->pts[i].c;
     if (!c.qhalf) continue;
     c.qh_rel = (long long)(qtot + qmerged) - c.q_off;
     qmerged += (size_t)c.K * c.T * c.Mhp;
   }
-  std::vector<PointC> pc(n);
-  std::vector<PointD> pdv(n);
+  // the per-point constants and coefficients in a second staging buffer (sizes known only now)
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_pc = sizeof(PointC) * n, b_pd = sizeof(PointD) * n, b_cv = sizeof(float4) * cv.size(),
+               b_uv = sizeof(double2) * uv64.size();
+  HostStage small;
+  if (small.get(al(b_pc) + al(b_pd) + al(b_cv) + al(b_uv)) != cudaSuccess) {
+    rift_status s1 = fail(h, RIFT_ENOMEM, "host staging buffer");
+    rift_ile_destroy(h);
+    return s1;
+  }
+  PointC *pc = reinterpret_cast<PointC *>(small.p);
+  PointD *pdv = reinterpret_cast<PointD *>(small.p + al(b_pc));
+  float4 *cvh = reinterpret_cast<float4 *>(small.p + al(b_pc) + al(b_pd));
+  double2 *uvh = reinterpret_cast<double2 *>(small.p + al(b_pc) + al(b_pd) + al(b_cv));
   for (int i = 0; i < n; ++i) { pc[i] = h->pts[i].c; pdv[i] = h->pts[i].d; }
+  if (b_cv) std::memcpy(cvh, cv.data(), b_cv);
+  if (b_uv) std::memcpy(uvh, uv64.data(), b_uv);
   rift_status s = RIFT_OK;
+  stage.sync_on(h->stream);   // the copies below read the staging buffers
+  small.sync_on(h->stream);
   if ((e = cache_dev_alloc((void **)&h->pts_dev, sizeof(PointC) * n)) != cudaSuccess ||
       (e = cache_dev_alloc((void **)&h->q_arena, sizeof(float2) * std::max<size_t>(qtot + qmerged, 2))) != cudaSuccess ||
       (e = cache_dev_alloc((void **)&h->c_arena, sizeof(float4) * std::max<size_t>(cv.size(), 1))) != cudaSuccess ||
       (e = cache_dev_alloc((void **)&h->flags, sizeof(uint32_t))) != cudaSuccess ||
       (e = fault_is("h2d") ? cudaErrorInvalidValue : cudaSuccess) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h->pts_dev, pc.data(), sizeof(PointC) * n, cudaMemcpyHostToDevice, h->stream)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(h->q_arena, qv.data(), sizeof(float2) * qv.size(), cudaMemcpyHostToDevice, h->stream)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(h->c_arena, cv.data(), sizeof(float4) * cv.size(), cudaMemcpyHostToDevice, h->stream)) !=
-          cudaSuccess ||
+      (e = cudaMemcpyAsync(h->pts_dev, pc, b_pc, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->q_arena, qh, sizeof(float2) * qtot, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->c_arena, cvh, b_cv, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
       (e = qmerged ? launch_merge_rows(h->pts_dev, n, h->q_arena, h->stream) : cudaSuccess) != cudaSuccess ||
       (e = cache_dev_alloc((void **)&h->pd_dev, sizeof(PointD) * n)) != cudaSuccess ||
       (e = cache_dev_alloc((void **)&h->uv64, sizeof(double2) * std::max<size_t>(uv64.size(), 1))) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h->pd_dev, pdv.data(), sizeof(PointD) * n, cudaMemcpyHostToDevice, h->stream)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(h->uv64, uv64.data(), sizeof(double2) * uv64.size(), cudaMemcpyHostToDevice, h->stream)) !=
-          cudaSuccess ||
+      (e = cudaMemcpyAsync(h->pd_dev, pdv, b_pd, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->uv64, uvh, b_uv, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), h->stream)) != cudaSuccess ||
+      (e = cache_dev_alloc((void **)&h->tau0, sizeof(double) * (size_t)n * RIFT_MAX_DET)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->tau0, fill_tau0(descs, n, t0h), sizeof(double) * (size_t)n * RIFT_MAX_DET,
+                           cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
     s = (e == cudaErrorMemoryAllocation) ? RIFT_ENOMEM : RIFT_ECUDA;
     fprintf(stderr, "rift_ile_create: %s\n", cudaGetErrorString(e));
+    stage.release();   // after the handle's stream has drained
+    small.release();
     rift_ile_destroy(h);
     return s;
-  }
-  {
-    std::vector<double> t0((size_t)n * RIFT_MAX_DET, 0.0);
-    for (int i = 0; i < n; ++i)
-      for (int k = 0; k < descs[i].n_det; ++k) t0[(size_t)i * RIFT_MAX_DET + k] = descs[i].q_t0_gps[k] - descs[i].t_ref_gps;
-    if ((e = cache_dev_alloc((void **)&h->tau0, sizeof(double) * t0.size())) != cudaSuccess ||
-        (e = cudaMemcpy(h->tau0, t0.data(), sizeof(double) * t0.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
-      fprintf(stderr, "rift_ile_create: %s\n", cudaGetErrorString(e));
-      rift_ile_destroy(h);
-      return RIFT_ECUDA;
-    }
   }
   *out = h;
   return RIFT_OK;
@@ -865,7 +983,7 @@ rift_status prepare_learned(rift_ile *h, const rift_mc_opts *o, cudaStream_t st)
   RIFT_CK(h, cudaMemcpyAsync(h->gcst, c.data(), sizeof(float) * c.size(), cudaMemcpyHostToDevice, st));
   if (o->mdn) {
     RIFT_CK(h, launch_summary(h->pts_dev, h->q_arena, h->c_arena, h->tau0, np, h->summ, st));
-    RIFT_CK(h, launch_mdn_gmm(static_cast<const rift_mdn *>(o->mdn), h->summ, h->gcst, np, h->head, h->gmm, st));
+    RIFT_CK(h, launch_mdn_gmm(static_cast<const rift_mdn *>(o->mdn), h->summ, h->gcst, np, h->head, h->gmm, h->flags, st));
   } else {
     RIFT_CK(h, launch_gmm_from_head(h->head, h->gcst, np, h->gmm, st));
   }

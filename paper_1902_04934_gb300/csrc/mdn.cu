@@ -3,9 +3,10 @@
 // per-point summary it is conditioned on.
 //
 // Network: s (64) -> 256 -> 256 (GELU, erf form) -> 88 = 8 logits + 8x5 means + 8x5 log
-// sigmas; weights bfloat16 (rounded from a float32 master copy), activations and
-// accumulation float32.  One CTA per point for forward, loss and backward; weight gradients
-// are accumulated with float32 atomics (order-dependent in the last bits only).
+// sigmas; weights bfloat16 (rounded from a float32 master copy), accumulation float32.  The
+// forward pass runs on the tensor cores (tcgen05, 128 points per CTA, activations split into two
+// bfloat16 terms); loss and backward take one CTA per point; weight gradients are sums over
+// points in point order (the same bits on every run).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -17,6 +18,7 @@
 #include "../../include/rift_ile.h"
 #include "rift_device.cuh"
 #include "rift_internal.h"
+#include "tc.cuh"
 
 namespace {
 
@@ -48,25 +50,205 @@ __device__ __forceinline__ float row_dot(const __nv_bfloat16 *row, const float *
   return acc;
 }
 
-// head[p] = MLP(S[p]); cache[p] = pre-activations (a1, a2) for the backward pass
-__global__ void __launch_bounds__(256) mdn_forward_kernel(const __nv_bfloat16 *__restrict__ W,
-                                                          const float *__restrict__ S, int P,
-                                                          float *__restrict__ head, float *__restrict__ cache) {
-  const int p = blockIdx.x;
-  if (p >= P) return;
-  __shared__ float s[NI], h1[NH], h2[NH];
-  const int t = threadIdx.x;
-  if (t < NI) s[t] = S[(size_t)p * NI + t];
+// ---------------------------------------------------------------------------------------------
+// Forward pass on the tensor cores (tcgen05), 128 points per CTA.  Each layer is D = A W^T: A
+// holds the layer's inputs (rows = points), W the weight rows (neurons), both BF16 in shared
+// memory in the K-major layout of tc.cuh, D is FP32 in tensor memory.  The FP32 inputs are split
+// into two BF16 terms, a = hi + lo with hi = bf16(a) and lo = bf16(a - hi), and both are multiplied
+// by the (exactly BF16) weights, so the inputs keep about 16 significant bits.  Sixteen warps:
+// warp w reads the tensor-memory lanes of rows 32 (w % 4) .. + 31 (the quarter its position in a
+// warpgroup allows) and the columns of group w / 4, applying bias, GELU and the split on the way
+// to the next layer's operand.  The next weights are staged by asynchronous copies while the
+// warps work through the previous layer's results.  Tensor-memory columns: layer 1 [0, 256),
+// layer 2 [0, 128) and [128, 256) (the two halves of W2 staged in turn), the head [0, 96).
+// ---------------------------------------------------------------------------------------------
+constexpr int TC_P = 128;                        // points per CTA (tensor-memory lanes)
+constexpr int TC_THREADS = 512;                  // 4 lane quarters x 4 column groups
+constexpr int NO_PAD = 96;                       // head rows padded to a multiple of 16
+constexpr int TC_OP = TC_P * NH * 2;             // bytes of one activation operand (K up to 256)
+constexpr int TC_WB = 128 * NH * 2;              // weight buffer: W1 (256 x 64), half of W2, W3 padded
+// dynamic shared memory: weight buffer, activation operands (hi, lo), biases; 224 KB are requested,
+// so the block has the SM to itself and the operand reads of any descriptor stay in the allocation
+constexpr int TC_SMEM_USED = TC_WB + 2 * TC_OP + (2 * NH + NO_PAD) * 4;
+constexpr int TC_SMEM = 224 * 1024;
+static_assert(TC_SMEM_USED <= TC_SMEM, "forward operands exceed the shared memory");
+constexpr uint32_t TC_COLS = 256;                // tensor-memory columns held by a CTA
+
+// Rows [n0, n0 + R) of a row-major BF16 weight matrix with Kd columns into the K-major layout with
+// R rows (rows at or past n_end zero-filled), as 16-byte asynchronous copies: consecutive threads
+// take 8 rows of one 16-byte column group, so a warp reads 64 contiguous bytes of each of 8 rows
+// and writes 512 contiguous bytes.  Completed by tc_copies_done.
+__device__ __forceinline__ void tc_load_w(unsigned char *dst, const __nv_bfloat16 *Wm, int n0, int R, int Kd,
+                                          int n_end) {
+  const int KG = Kd / 8;
+  for (int i = threadIdx.x; i < R * KG; i += blockDim.x) {
+    const int n = ((i >> 3) / KG) * 8 + (i & 7), kg = (i >> 3) % KG;
+    const bool in = n0 + n < n_end;
+    const __nv_bfloat16 *src = Wm + (in ? (size_t)(n0 + n) * Kd + 8 * kg : 0);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     tc::smem_u32(dst + tc::kmajor_off((uint32_t)n, 8u * kg, (uint32_t)R))),
+                 "l"(src), "r"(in ? 16 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tc_copies_done() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Row r, columns [c, c + 16) of both activation operands from 16 FP32 values.
+__device__ __forceinline__ void tc_store16(unsigned char *Ahi, unsigned char *Alo, int r, int c, const float (&a)[16]) {
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    __nv_bfloat162 hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float x0 = a[8 * g + 2 * e], x1 = a[8 * g + 2 * e + 1];
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+      hi[e] = __halves2bfloat162(h0, h1);
+      lo[e] = __halves2bfloat162(__float2bfloat16_rn(x0 - __bfloat162float(h0)),
+                                 __float2bfloat16_rn(x1 - __bfloat162float(h1)));
+    }
+    const uint32_t off = tc::kmajor_off((uint32_t)r, (uint32_t)(c + 8 * g), TC_P);
+    *reinterpret_cast<uint4 *>(Ahi + off) = *reinterpret_cast<const uint4 *>(hi);
+    *reinterpret_cast<uint4 *>(Alo + off) = *reinterpret_cast<const uint4 *>(lo);
+  }
+}
+
+// D (+)= A W^T for the 128 x Kd operands (hi, lo) and the N weight rows staged with R = N rows;
+// issued by one thread, K steps of 16, the first product overwriting D.
+__device__ __forceinline__ void tc_layer(uint32_t d, uint32_t ahi, uint32_t alo, uint32_t wb, int Kd, int N) {
+  const uint32_t idesc = tc::idesc_bf16_f32(TC_P, N);
+  const uint32_t lbo_a = TC_P * 16, lbo_w = (uint32_t)N * 16;
+  for (int s = 0; s < Kd / 16; ++s) {
+    const uint64_t bd = tc::desc_kmajor(wb + 2u * s * lbo_w, lbo_w, 128);
+    tc::mma_bf16(d, tc::desc_kmajor(ahi + 2u * s * lbo_a, lbo_a, 128), bd, idesc, s > 0 ? 1u : 0u);
+    tc::mma_bf16(d, tc::desc_kmajor(alo + 2u * s * lbo_a, lbo_a, 128), bd, idesc, 1u);
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) mdn_forward_tc_kernel(const __nv_bfloat16 *__restrict__ W,
+                                                                      const float *__restrict__ S, int P,
+                                                                      float *__restrict__ head,
+                                                                      float *__restrict__ cache,
+                                                                      uint32_t *__restrict__ status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char *Wb = sm, *Ahi = sm + TC_WB, *Alo = sm + TC_WB + TC_OP;
+  float *bias = reinterpret_cast<float *>(sm + TC_WB + 2 * TC_OP);   // b1 [NH], b2 [NH], b3 [NO_PAD]
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int t = threadIdx.x, wq = t >> 5;
+  const int row = 32 * (wq & 3) + (t & 31), cg = wq >> 2;   // the thread's row and column group
+  const int p = blockIdx.x * TC_P + row;
+  const bool valid = p < P;
+  if (wq == 0) {
+    tc::tmem_alloc(&tslot, TC_COLS);
+    tc::tmem_relinquish();
+  }
+  if (t == 0) tc::mbar_init(&bar, 1);
+  tc_load_w(Wb, W + OFF_W1, 0, NH, NI, NH);
+  for (int i = t; i < NH; i += TC_THREADS) {
+    bias[i] = bf(W, OFF_B1 + i);
+    bias[NH + i] = bf(W, OFF_B2 + i);
+  }
+  if (t < NO_PAD) bias[2 * NH + t] = t < NO ? bf(W, OFF_B3 + t) : 0.f;
+  {
+    float a[16];   // the row's summary features [16 cg, 16 cg + 16)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = valid ? S[(size_t)p * NI + 16 * cg + j] : 0.f;
+    tc_store16(Ahi, Alo, row, 16 * cg, a);
+  }
+  tc_copies_done();
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
   __syncthreads();
-  float a = row_dot(W + OFF_W1 + t * NI, s, NI, bf(W, OFF_B1 + t));
-  if (cache) cache[(size_t)p * 2 * NH + t] = a;
-  h1[t] = gelu(a);
+  tc::fence_after_sync();
+  const uint32_t tm = tslot, trow = tm + ((uint32_t)(32 * (wq & 3)) << 16);
+  const uint32_t ahi = tc::smem_u32(Ahi), alo = tc::smem_u32(Alo), wb = tc::smem_u32(Wb);
+  uint32_t phase = 0;
+  // every thread waits for the products in flight; all agree on the outcome
+  auto wait_products = [&]() {
+    const bool ok = __syncthreads_and(tc::mbar_wait(&bar, phase) ? 1 : 0) != 0;
+    if (ok) phase ^= 1u;
+    tc::fence_after_sync();
+    return ok;
+  };
+  // staged weights and operands written by the threads visible to the tensor core, earlier
+  // tensor-memory loads done
+  auto operands_ready = [&]() {
+    tc_copies_done();
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  // the row's hidden-layer columns [64 cg, 64 cg + 64): a = D + b (cached), next operand GELU(a)
+  auto hidden = [&](const float *b, int cache_off) {
+#pragma unroll 1
+    for (int c = 64 * cg; c < 64 * cg + 64; c += 16) {
+      float a[16];
+      tc::ld_row16(trow + (uint32_t)c, a);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) a[j] += b[c + j];
+      if (cache && valid) {
+        float4 *o = reinterpret_cast<float4 *>(cache + (size_t)p * 2 * NH + cache_off + c);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = make_float4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]);
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) a[j] = gelu(a[j]);
+      tc_store16(Ahi, Alo, row, c, a);
+    }
+  };
+  bool ok = true;
+  do {
+    // layer 1: a1 = W1 s + b1, h1 = GELU(a1); the first half of W2 is staged meanwhile
+    if (t == 0) { tc_layer(tm, ahi, alo, wb, NI, NH); tc::commit(&bar); }
+    if (!(ok = wait_products())) break;
+    tc_load_w(Wb, W + OFF_W2, 0, NH / 2, NH, NH);
+    hidden(bias, 0);
+    operands_ready();
+    // layer 2, one half of the neurons at a time: a2 = W2 h1 + b2, h2 = GELU(a2)
+    if (t == 0) { tc_layer(tm, ahi, alo, wb, NH, NH / 2); tc::commit(&bar); }
+    if (!(ok = wait_products())) break;
+    tc_load_w(Wb, W + OFF_W2, NH / 2, NH / 2, NH, NH);
+    operands_ready();
+    if (t == 0) { tc_layer(tm + NH / 2, ahi, alo, wb, NH, NH / 2); tc::commit(&bar); }
+    if (!(ok = wait_products())) break;
+    tc_load_w(Wb, W + OFF_W3, 0, NO_PAD, NH, NO);
+    hidden(bias + NH, NH);
+    operands_ready();
+    // head = W3 h2 + b3 (columns 16 j for j = cg, cg + 4)
+    if (t == 0) { tc_layer(tm, ahi, alo, wb, NH, NO_PAD); tc::commit(&bar); }
+    if (!(ok = wait_products())) break;
+    for (int c = 16 * cg; c < NO_PAD; c += 64) {
+      float a[16];
+      tc::ld_row16(trow + (uint32_t)c, a);
+      if (valid)
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c + j < NO) head[(size_t)p * NO + c + j] = a[j] + bias[2 * NH + c + j];
+    }
+  } while (false);
+  if (!ok) {
+    // an expired wait: flag it, wait (bounded) once more for the products in flight, then free
+    // the tensor memory
+    if (t == 0) atomicOr(status, RIFT_FLAG_TIMEOUT_BIT);
+    tc::mbar_wait(&bar, phase);
+  }
+  tc_copies_done();
+  tc::fence_before_sync();
   __syncthreads();
-  a = row_dot(W + OFF_W2 + t * NH, h1, NH, bf(W, OFF_B2 + t));
-  if (cache) cache[(size_t)p * 2 * NH + NH + t] = a;
-  h2[t] = gelu(a);
-  __syncthreads();
-  if (t < NO) head[(size_t)p * NO + t] = row_dot(W + OFF_W3 + t * NH, h2, NH, bf(W, OFF_B3 + t));
+  if (wq == 0) tc::tmem_dealloc(tm, TC_COLS);
+}
+
+// head[p] = MLP(S[p]) for P points on the tensor cores, cache[p] = (a1, a2) when given; an expired
+// wait sets RIFT_FLAG_TIMEOUT_BIT in *status.
+cudaError_t launch_forward(const __nv_bfloat16 *W, const float *S, int P, float *head, float *cache,
+                           uint32_t *status, cudaStream_t st) {
+  if (P <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(mdn_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  if (e != cudaSuccess) return e;
+  mdn_forward_tc_kernel<<<(P + TC_P - 1) / TC_P, TC_THREADS, TC_SMEM, st>>>(W, S, P, head, cache, status);
+  return cudaGetLastError();
 }
 
 // Weighted NLL of each point's H samples: loss[p] and dL/dhead[p] (scaled by `scale`).
@@ -405,6 +587,7 @@ struct rift_mdn {
   // training scratch
   float *head = nullptr, *cache = nullptr, *gout = nullptr, *loss = nullptr, *ga = nullptr;
   int cap = 0;
+  uint32_t *status = nullptr;   // device word: RIFT_FLAG_TIMEOUT_BIT after an expired wait of the forward pass
 };
 
 namespace {
@@ -419,6 +602,17 @@ rift_status mfail(rift_mdn *m, rift_status s, const std::string &msg) {
     cudaError_t e_ = (call);                                                                \
     if (e_ != cudaSuccess) return mfail(m, RIFT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
+
+thread_local double g_forward_ms = 0.0;   // device time of the last rift_mdn_forward kernel (this thread)
+
+// Reads and clears the forward pass's status word (after the call's work has finished).
+rift_status check_status(rift_mdn *m) {
+  uint32_t f = 0;
+  MCK(m, cudaMemcpy(&f, m->status, sizeof f, cudaMemcpyDeviceToHost));
+  if (!f) return RIFT_OK;
+  MCK(m, cudaMemset(m->status, 0, sizeof f));
+  return mfail(m, RIFT_ETIMEOUT, "a bounded wait of the tensor-core forward pass expired");
+}
 
 rift_status mdn_scratch(rift_mdn *m, int P) {
   if (P <= m->cap) return RIFT_OK;
@@ -476,6 +670,8 @@ rift_status rift_mdn_create(uint64_t seed, rift_mdn **out) {
       (e = cudaMalloc(&m->v, sizeof(float) * NPARAM)) != cudaSuccess ||
       (e = cudaMalloc(&m->grad, sizeof(float) * NPARAM)) != cudaSuccess ||
       (e = cudaMalloc(&m->w, sizeof(__nv_bfloat16) * NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc(&m->status, sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaMemset(m->status, 0, sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaMemcpy(m->master, init.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(m->m, 0, sizeof(float) * NPARAM)) != cudaSuccess ||
       (e = cudaMemset(m->v, 0, sizeof(float) * NPARAM)) != cudaSuccess ||
@@ -493,6 +689,7 @@ void rift_mdn_destroy(rift_mdn *m) {
   if (!m) return;
   cudaFree(m->master); cudaFree(m->m); cudaFree(m->v); cudaFree(m->grad); cudaFree(m->w);
   cudaFree(m->head); cudaFree(m->cache); cudaFree(m->gout); cudaFree(m->loss); cudaFree(m->ga);
+  cudaFree(m->status);
   delete m;
 }
 
@@ -525,11 +722,25 @@ rift_status rift_mdn_get_params(rift_mdn *m, float *host, int which) {
 rift_status rift_mdn_forward(rift_mdn *m, int n, const float *summ_dev, float *head_dev) {
   if (!m || n < 0 || (n && (!summ_dev || !head_dev))) return RIFT_EINVAL;
   if (n == 0) return RIFT_OK;
-  mdn_forward_kernel<<<n, 256>>>(m->w, summ_dev, n, head_dev, nullptr);
-  MCK(m, cudaGetLastError());
-  MCK(m, cudaDeviceSynchronize());
-  return RIFT_OK;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  MCK(m, cudaEventCreate(&ev[0]));
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return mfail(m, RIFT_ECUDA, "cudaEventCreate");
+  }
+  cudaError_t e = cudaEventRecord(ev[0], 0);
+  if (e == cudaSuccess) e = launch_forward(m->w, summ_dev, n, head_dev, nullptr, m->status, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], 0);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+  float ms = 0.f;
+  if (e == cudaSuccess && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) g_forward_ms = ms;
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  MCK(m, e);
+  return check_status(m);
 }
+
+double rift_mdn_forward_ms(void) { return g_forward_ms; }
 
 rift_status rift_mdn_loss_grad(rift_mdn *m, int n, const float *summ_dev, const float *theta_dev, const float *w_dev,
                                int H, const float *box_dev, double *loss_out, float *grad_host) {
@@ -537,7 +748,7 @@ rift_status rift_mdn_loss_grad(rift_mdn *m, int n, const float *summ_dev, const 
   rift_status s = mdn_scratch(m, n);
   if (s != RIFT_OK) return s;
   MCK(m, cudaMemset(m->grad, 0, sizeof(float) * NPARAM));
-  mdn_forward_kernel<<<n, 256>>>(m->w, summ_dev, n, m->head, m->cache);
+  MCK(m, launch_forward(m->w, summ_dev, n, m->head, m->cache, m->status, 0));
   mdn_loss_kernel<<<n, 128>>>(m->head, theta_dev, w_dev, box_dev, H, 1.f / n, m->gout, m->loss);
   mdn_backward_kernel<<<n, 256>>>(m->w, m->cache, m->gout, n, m->ga);
   mdn_wgrad_kernel<<<(NPARAM + 255) / 256, 256>>>(summ_dev, m->cache, m->gout, m->ga, n, m->grad);
@@ -549,7 +760,7 @@ rift_status rift_mdn_loss_grad(rift_mdn *m, int n, const float *summ_dev, const 
   if (loss_out) *loss_out = tot / n;
   if (grad_host) MCK(m, cudaMemcpy(grad_host, m->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
   MCK(m, cudaMemset(m->grad, 0, sizeof(float) * NPARAM));
-  return RIFT_OK;
+  return check_status(m);
 }
 
 rift_status rift_mdn_train(rift_mdn *m, int n, const float *summ_dev, const float *theta_dev, const float *w_dev,
@@ -566,7 +777,7 @@ rift_status rift_mdn_train(rift_mdn *m, int n, const float *summ_dev, const floa
     const float *th = theta_dev + (size_t)p0 * H * ND;
     const float *w = w_dev + (size_t)p0 * H;
     const float *bx = box_dev + (size_t)p0 * 10;
-    mdn_forward_kernel<<<nb, 256>>>(m->w, S, nb, m->head, m->cache);
+    MCK(m, launch_forward(m->w, S, nb, m->head, m->cache, m->status, 0));
     mdn_loss_kernel<<<nb, 128>>>(m->head, th, w, bx, H, 1.f / nb, m->gout, m->loss);
     mdn_backward_kernel<<<nb, 256>>>(m->w, m->cache, m->gout, nb, m->ga);
     mdn_wgrad_kernel<<<(NPARAM + 255) / 256, 256>>>(S, m->cache, m->gout, m->ga, nb, m->grad);
@@ -583,7 +794,7 @@ rift_status rift_mdn_train(rift_mdn *m, int n, const float *summ_dev, const floa
     }
   }
   MCK(m, cudaDeviceSynchronize());
-  return RIFT_OK;
+  return check_status(m);
 }
 
 }  // extern "C"
@@ -596,8 +807,9 @@ cudaError_t launch_summary(const PointC *pts, const float2 *qa, const float4 *ca
 }
 
 cudaError_t launch_mdn_gmm(const rift_mdn *m, const float *summ, const float *cst, int np, float *head_scratch,
-                           float *gmm, cudaStream_t st) {
-  mdn_forward_kernel<<<np, 256, 0, st>>>(m->w, summ, np, head_scratch, nullptr);
+                           float *gmm, uint32_t *flags, cudaStream_t st) {
+  const cudaError_t e = launch_forward(m->w, summ, np, head_scratch, nullptr, flags, st);
+  if (e != cudaSuccess) return e;
   mdn_gmm_kernel<<<(np + 127) / 128, 128, 0, st>>>(head_scratch, cst, np, gmm);
   return cudaGetLastError();
 }

@@ -17,6 +17,8 @@
 
 #include "../../include/rift_ile.h"
 #include "rift_device.cuh"
+#include "rift_internal.h"
+#include "host_par.h"
 
 namespace {
 
@@ -175,9 +177,25 @@ rift_status quv_fail(rift_status s, const std::string &m) {
   return s;
 }
 
+// Device buffer from the process-wide buffer cache, given back when the call returns (the call
+// drains its stream before that, see StreamDrain).
 struct DevBuf {
   void *p = nullptr;
-  ~DevBuf() { if (p) cudaFree(p); }
+  ~DevBuf() { if (p) cache_dev_free(p); }
+};
+
+// Drains the stream at every exit once device work has been queued on it, so buffers go back to
+// the cache only when no work in flight reads them.
+struct StreamDrain {
+  cudaStream_t st = nullptr;
+  bool armed = false;
+  ~StreamDrain() { if (armed) cudaStreamSynchronize(st); }
+};
+
+// Pinned host staging from the buffer cache.
+struct HostBuf {
+  void *p = nullptr;
+  ~HostBuf() { if (p) cache_host_free(p); }
 };
 
 }  // namespace
@@ -215,48 +233,65 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   }
   const int nb = (int)band.size();
   if (nb == 0) return quv_fail(RIFT_EINVAL, "no bin has a nonzero weight");
-  for (int i : band) {
-    for (int a = 0; a < M; ++a)
-      for (int c = 0; c < 2; ++c)
-        if (!std::isfinite(d->hlm[2 * ((size_t)a * nf + i) + c]) || !std::isfinite(d->hlm[2 * ((size_t)a * nf + d->mirror[i]) + c]))
-          return quv_fail(RIFT_EINVAL, "non-finite mode waveform in the band");
-    for (int k = 0; k < K; ++k) {
-      if (!std::isfinite(d->weight[(size_t)k * nf + i]) || d->weight[(size_t)k * nf + i] < 0.0)
-        return quv_fail(RIFT_EINVAL, "weights must be finite and non-negative");
-      for (int c = 0; c < 2; ++c)
-        if (!std::isfinite(d->data[2 * ((size_t)k * nf + i) + c])) return quv_fail(RIFT_EINVAL, "non-finite data in the band");
-    }
-  }
-  // operands rescaled by powers of two so that FP32 holds them whatever the strain units
-  double hmax = 0.0;
-  std::vector<double> bmax(K, 0.0), wmax(K, 0.0);
+  // per band bin, in parallel over bin ranges: validity, the twiddle index nu mod n, the data term
+  // B_k = 2 df w_k d_k exp(2 pi i nu df tau0_k) (FP64), and the largest component magnitudes of
+  // the waveforms, the data terms and the weighted waveforms (for the power-of-two scalings below)
   std::vector<double> Bd(2 * (size_t)K * nb);
   std::vector<int> nuv(nb), run(nb);
-  for (int b = 0; b < nb; ++b) {
-    const int i = band[b];
-    long long v = d->nu[i] % n;
-    if (v < 0) v += n;
-    nuv[b] = (int)v;
-    run[b] = (b == 0 || nuv[b] != (nuv[b - 1] + 1) % n) ? 1 : 0;
-    for (int a = 0; a < M; ++a) {
-      hmax = std::max(hmax, std::hypot(d->hlm[2 * ((size_t)a * nf + i)], d->hlm[2 * ((size_t)a * nf + i) + 1]));
-      const int im = d->mirror[i];
-      hmax = std::max(hmax, std::hypot(d->hlm[2 * ((size_t)a * nf + im)], d->hlm[2 * ((size_t)a * nf + im) + 1]));
+  constexpr int kParts = 8;
+  struct PartMax {
+    double h = 0.0, b[RIFT_MAX_DET] = {}, w[RIFT_MAX_DET] = {};
+    int bad = 0;   // 1 non-finite waveform, 2 bad weight, 3 non-finite data
+  };
+  PartMax pm[kParts];
+  auto cabs = [](const double *z) { return std::max(std::fabs(z[0]), std::fabs(z[1])); };
+  parallel_parts(nb, 2048, kParts, [&](int part, int b0, int b1) {
+    PartMax &r = pm[part];
+    for (int b = b0; b < b1 && !r.bad; ++b) {
+      const int i = band[b], im = d->mirror[i];
+      long long v = d->nu[i] % n;
+      if (v < 0) v += n;
+      nuv[b] = (int)v;
+      double hb = 0.0;   // largest component of the bin's waveforms
+      for (int a = 0; a < M; ++a) {
+        const double *h = d->hlm + 2 * ((size_t)a * nf + i), *hm = d->hlm + 2 * ((size_t)a * nf + im);
+        if (!std::isfinite(h[0]) || !std::isfinite(h[1]) || !std::isfinite(hm[0]) || !std::isfinite(hm[1])) {
+          r.bad = 1;
+          break;
+        }
+        hb = std::max(hb, cabs(h));
+        r.h = std::max(r.h, std::max(cabs(h), cabs(hm)));
+      }
+      for (int k = 0; k < K && !r.bad; ++k) {
+        const double w = d->weight[(size_t)k * nf + i];
+        const double *x = d->data + 2 * ((size_t)k * nf + i);
+        if (!std::isfinite(w) || w < 0.0) { r.bad = 2; break; }
+        if (!std::isfinite(x[0]) || !std::isfinite(x[1])) { r.bad = 3; break; }
+        const double tau0 = d->q_t0_gps[k] - d->t_ref_gps;
+        const double ph = 2.0 * 3.14159265358979323846 * std::fmod((double)d->nu[i] * d->df * tau0, 1.0);
+        const double c = std::cos(ph), sn = std::sin(ph), f = 2.0 * d->df * w;
+        double *bd = &Bd[2 * ((size_t)k * nb + b)];
+        bd[0] = f * (x[0] * c - x[1] * sn);
+        bd[1] = f * (x[0] * sn + x[1] * c);
+        r.b[k] = std::max(r.b[k], cabs(bd));
+        r.w[k] = std::max(r.w[k], w * hb);
+      }
     }
+  });
+  double hmax = 0.0;
+  std::vector<double> bmax(K, 0.0), wmax(K, 0.0);
+  for (int t = 0; t < kParts; ++t) {
+    if (pm[t].bad == 1) return quv_fail(RIFT_EINVAL, "non-finite mode waveform in the band");
+    if (pm[t].bad == 2) return quv_fail(RIFT_EINVAL, "weights must be finite and non-negative");
+    if (pm[t].bad == 3) return quv_fail(RIFT_EINVAL, "non-finite data in the band");
+    hmax = std::max(hmax, pm[t].h);
     for (int k = 0; k < K; ++k) {
-      const double w = d->weight[(size_t)k * nf + i];
-      const double *x = d->data + 2 * ((size_t)k * nf + i);
-      const double tau0 = d->q_t0_gps[k] - d->t_ref_gps;
-      const double ph = 2.0 * 3.14159265358979323846 * std::fmod((double)d->nu[i] * d->df * tau0, 1.0);
-      const double c = std::cos(ph), sn = std::sin(ph), f = 2.0 * d->df * w;
-      double *bd = &Bd[2 * ((size_t)k * nb + b)];
-      bd[0] = f * (x[0] * c - x[1] * sn);
-      bd[1] = f * (x[0] * sn + x[1] * c);
-      bmax[k] = std::max(bmax[k], std::hypot(bd[0], bd[1]));
-      for (int a = 0; a < M; ++a)
-        wmax[k] = std::max(wmax[k], w * std::hypot(d->hlm[2 * ((size_t)a * nf + i)], d->hlm[2 * ((size_t)a * nf + i) + 1]));
+      bmax[k] = std::max(bmax[k], pm[t].b[k]);
+      wmax[k] = std::max(wmax[k], pm[t].w[k]);
     }
   }
+  for (int b = 0; b < nb; ++b) run[b] = (b == 0 || nuv[b] != (nuv[b - 1] + 1) % n) ? 1 : 0;
+  // operands rescaled by powers of two so that FP32 holds them whatever the strain units
   const double sH = unit_scale(hmax);
   std::vector<double> sB(K), sW(K), qscale(K), uvscale(K);
   for (int k = 0; k < K; ++k) {
@@ -265,25 +300,44 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
     qscale[k] = 1.0 / (sH * sB[k]);
     uvscale[k] = 2.0 * d->df / (sH * sW[k]);
   }
-  std::vector<float2> H((size_t)M * nb), Hm((size_t)M * nb), B((size_t)K * nb), Hw((size_t)K * M * nb);
-  for (int b = 0; b < nb; ++b) {
-    const int i = band[b];
-    for (int a = 0; a < M; ++a) {
-      const double *h = d->hlm + 2 * ((size_t)a * nf + i), *hm = d->hlm + 2 * ((size_t)a * nf + d->mirror[i]);
-      H[(size_t)a * nb + b] = make_float2((float)(h[0] * sH), (float)(h[1] * sH));
-      Hm[(size_t)a * nb + b] = make_float2((float)(hm[0] * sH), (float)(hm[1] * sH));
+  // FP32 operands in one pinned staging buffer: H [M][nb], Hm [M][nb], B [K][nb], Hw [K][M][nb],
+  // then the twiddle indices, the run starts and the U/V scales
+  const size_t nH = (size_t)M * nb, nB = (size_t)K * nb, nHw = (size_t)K * M * nb;
+  const size_t o_Hm = nH, o_B = 2 * nH, o_Hw = 2 * nH + nB, n_f2 = 2 * nH + nB + nHw;
+  const size_t stage_bytes = sizeof(float2) * n_f2 + sizeof(int) * 2 * (size_t)nb + sizeof(double) * (K + 1);
+  HostBuf hs;
+  cudaError_t e;
+  if ((e = cache_host_alloc(&hs.p, stage_bytes)) != cudaSuccess)
+    return quv_fail(e == cudaErrorMemoryAllocation ? RIFT_ENOMEM : RIFT_ECUDA, cudaGetErrorString(e));
+  float2 *F2 = static_cast<float2 *>(hs.p);
+  float2 *H = F2, *Hm = F2 + o_Hm, *B = F2 + o_B, *Hw = F2 + o_Hw;
+  int *nu_h = reinterpret_cast<int *>(F2 + n_f2), *run_h = nu_h + nb;
+  double *sc_h = reinterpret_cast<double *>(run_h + nb);   // 8-byte aligned: 2 nb ints follow the float2s
+  std::memcpy(nu_h, nuv.data(), sizeof(int) * nb);
+  std::memcpy(run_h, run.data(), sizeof(int) * nb);
+  for (int k = 0; k < K; ++k) sc_h[k] = uvscale[k];
+  parallel_parts(nb, 2048, kParts, [&](int, int b0, int b1) {
+    for (int b = b0; b < b1; ++b) {
+      const int i = band[b];
+      for (int a = 0; a < M; ++a) {
+        const double *h = d->hlm + 2 * ((size_t)a * nf + i), *hm = d->hlm + 2 * ((size_t)a * nf + d->mirror[i]);
+        H[(size_t)a * nb + b] = make_float2((float)(h[0] * sH), (float)(h[1] * sH));
+        Hm[(size_t)a * nb + b] = make_float2((float)(hm[0] * sH), (float)(hm[1] * sH));
+        for (int k = 0; k < K; ++k) {
+          const double w = d->weight[(size_t)k * nf + i] * sW[k];
+          Hw[((size_t)k * M + a) * nb + b] = make_float2((float)(h[0] * w), (float)(h[1] * w));
+        }
+      }
       for (int k = 0; k < K; ++k) {
-        const double w = d->weight[(size_t)k * nf + i] * sW[k];
-        Hw[((size_t)k * M + a) * nb + b] = make_float2((float)(h[0] * w), (float)(h[1] * w));
+        const double *bd = &Bd[2 * ((size_t)k * nb + b)];
+        B[(size_t)k * nb + b] = make_float2((float)(bd[0] * sB[k]), (float)(bd[1] * sB[k]));
       }
     }
-    for (int k = 0; k < K; ++k) {
-      const double *bd = &Bd[2 * ((size_t)k * nb + b)];
-      B[(size_t)k * nb + b] = make_float2((float)(bd[0] * sB[k]), (float)(bd[1] * sB[k]));
-    }
-  }
+  });
   cudaStream_t st = (cudaStream_t)d->cuda_stream;
-  DevBuf dH, dHm, dB, dHw, dnu, drun, dQ, dU, dV, dsc, dQp;
+  DevBuf dF2, dnu, dsc, dQ, dU, dV, dQp;
+  StreamDrain drain;
+  drain.st = st;
   // bin slices: about four CTAs per SM in all
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
@@ -291,24 +345,21 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   const int ctas = ((nt + kQThreads - 1) / kQThreads) * ((M + kQModes - 1) / kQModes) * K;
   const int nchunk = (nb + kChunk - 1) / kChunk;
   const int slices = std::max(1, std::min(nchunk, (4 * nsm + ctas - 1) / ctas));
-  cudaError_t e;
-  auto up = [&](DevBuf &buf, const void *src, size_t bytes) {
-    cudaError_t r = cudaMalloc(&buf.p, bytes);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, st);
-    return r;
-  };
-  if ((e = up(dH, H.data(), sizeof(float2) * H.size())) != cudaSuccess ||
-      (e = up(dHm, Hm.data(), sizeof(float2) * Hm.size())) != cudaSuccess ||
-      (e = up(dB, B.data(), sizeof(float2) * B.size())) != cudaSuccess ||
-      (e = up(dHw, Hw.data(), sizeof(float2) * Hw.size())) != cudaSuccess ||
-      (e = up(dsc, uvscale.data(), sizeof(double) * K)) != cudaSuccess ||
-      (e = up(dnu, nuv.data(), sizeof(int) * nuv.size())) != cudaSuccess ||
-      (e = up(drun, run.data(), sizeof(int) * run.size())) != cudaSuccess ||
-      (e = cudaMalloc(&dQ.p, sizeof(double2) * (size_t)K * M * nt)) != cudaSuccess ||
-      (e = cudaMalloc(&dQp.p, sizeof(double2) * (size_t)slices * K * M * nt)) != cudaSuccess ||
-      (e = cudaMalloc(&dU.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess ||
-      (e = cudaMalloc(&dV.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess)
+  if ((e = cache_dev_alloc(&dF2.p, sizeof(float2) * n_f2)) != cudaSuccess ||
+      (e = cache_dev_alloc(&dnu.p, sizeof(int) * 2 * (size_t)nb)) != cudaSuccess ||
+      (e = cache_dev_alloc(&dsc.p, sizeof(double) * K)) != cudaSuccess ||
+      (e = cache_dev_alloc(&dQ.p, sizeof(double2) * (size_t)K * M * nt)) != cudaSuccess ||
+      (e = cache_dev_alloc(&dQp.p, sizeof(double2) * (size_t)slices * K * M * nt)) != cudaSuccess ||
+      (e = cache_dev_alloc(&dU.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess ||
+      (e = cache_dev_alloc(&dV.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess)
     return quv_fail(e == cudaErrorMemoryAllocation ? RIFT_ENOMEM : RIFT_ECUDA, cudaGetErrorString(e));
+  drain.armed = true;
+  if ((e = cudaMemcpyAsync(dF2.p, F2, sizeof(float2) * n_f2, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dnu.p, nu_h, sizeof(int) * 2 * (size_t)nb, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dsc.p, sc_h, sizeof(double) * K, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return quv_fail(RIFT_ECUDA, cudaGetErrorString(e));
+  const float2 *dH = static_cast<const float2 *>(dF2.p), *dHm = dH + o_Hm, *dB = dH + o_B, *dHw = dH + o_Hw;
+  const int *dnu_p = static_cast<const int *>(dnu.p), *drun_p = dnu_p + nb;
   // CUDA events around each kernel on the call's stream (rift_quv_kernel_ms)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   for (int i = 0; i < 3; ++i)
@@ -318,15 +369,14 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
     }
   dim3 gq((nt + kQThreads - 1) / kQThreads, (M + kQModes - 1) / kQModes, K * slices);
   cudaEventRecord(ev[0], st);
-  quv_q_kernel<<<gq, kQThreads, 0, st>>>((const float2 *)dH.p, (const float2 *)dB.p, (const int *)dnu.p,
-                                         (const int *)drun.p, nb, M, nt, (int)n, slices, (double2 *)dQp.p);
+  quv_q_kernel<<<gq, kQThreads, 0, st>>>(dH, dB, dnu_p, drun_p, nb, M, nt, (int)n, slices, (double2 *)dQp.p);
   const size_t qcount = (size_t)K * M * nt;
   quv_q_reduce_kernel<<<(unsigned)((qcount + 255) / 256), 256, 0, st>>>((const double2 *)dQp.p, slices, qcount,
                                                                         (double2 *)dQ.p);
   cudaEventRecord(ev[1], st);
   dim3 guv(M * M, K);
-  quv_uv_kernel<<<guv, kUVThreads, 0, st>>>((const float2 *)dH.p, (const float2 *)dHm.p, (const float2 *)dHw.p, nb,
-                                            M, (double2 *)dU.p, (double2 *)dV.p, (const double *)dsc.p);
+  quv_uv_kernel<<<guv, kUVThreads, 0, st>>>(dH, dHm, dHw, nb, M, (double2 *)dU.p, (double2 *)dV.p,
+                                            (const double *)dsc.p);
   cudaEventRecord(ev[2], st);
   if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventSynchronize(ev[2])) == cudaSuccess) {
     float a = 0.f, b = 0.f;

@@ -254,7 +254,7 @@ cudaError_t launch_summary(const PointC *pts, const float2 *qa, const float4 *ca
                            float *out, cudaStream_t st);
 struct rift_mdn;
 cudaError_t launch_mdn_gmm(const rift_mdn *m, const float *summ, const float *cst, int np, float *head_scratch,
-                           float *gmm, cudaStream_t st);
+                           float *gmm, uint32_t *flags, cudaStream_t st);
 cudaError_t launch_gmm_from_head(const float *head, const float *cst, int np, float *gmm, cudaStream_t st);
 // device and pinned host buffers of handles, recycled through a process-wide cache (cache.cu);
 // a buffer is given back only when no work in flight uses it
