@@ -38,17 +38,20 @@ def test_summary_matches_oracle(lib, cuda, pts):
         assert np.allclose(got[p], want, rtol=2e-4, atol=2e-5), (p, np.max(np.abs(got[p] - want)))
 
 
-def test_forward_matches_oracle(lib, cuda):
+@pytest.mark.parametrize("n,scale", [(1, 1.0), (37, 1.0), (128, 3.0), (300, 1.0)])
+def test_forward_matches_oracle(lib, cuda, n, scale):
+    """The tensor-core forward pass (128 points per CTA: one point, a partial CTA, one full CTA,
+    three CTAs with a ragged last one) against the oracle's FP64 network on the BF16 weights."""
     import torch
     m = lib.rift_mdn_create(1)
     prm = _params(2)
     lib.rift_mdn_set_params(m, prm)
     bfw = lib.rift_mdn_get_params(m, 1).astype(np.float64)
     assert np.array_equal(bfw, mdn.bf16_round(prm))              # round-to-nearest-even, bit for bit
-    S = np.random.default_rng(3).normal(0, 1, (37, 64)).astype(np.float32)
+    S = np.random.default_rng(3 + n).normal(0, scale, (n, 64)).astype(np.float32)
     got = lib.rift_mdn_forward(m, torch.as_tensor(S, device="cuda")).cpu().numpy().astype(np.float64)
     want = mdn.forward(mdn.unflatten(bfw), S.astype(np.float64))
-    assert np.allclose(got, want, rtol=1e-4, atol=1e-4)
+    assert np.allclose(got, want, rtol=1e-4, atol=1e-4), float(np.max(np.abs(got - want)))
 
 
 def test_loss_and_gradient_match_oracle(lib, cuda):
