@@ -203,14 +203,16 @@ def _desc(pt, interp=3, stream=None, keep=None):
 
 
 def _fd_desc(pt, interp=3, stream=None, keep=None):
-    """Frequency-domain descriptor of a point dict with freqs, df, hlm, data, weight, mirror, n_t."""
+    """Frequency-domain descriptor of a point dict with freqs, df, hlm, data, weight, mirror, n_t (nu,
+    the integer bins of the grid with freqs = nu df, is taken from the dict when given)."""
     K = int(np.asarray(pt["det_tensor"]).shape[0])
     hlm = np.ascontiguousarray(np.asarray(pt["hlm"], dtype=np.complex128))
     M, nf = hlm.shape
     df = float(pt["df"])
     arrs = dict(det_tensor=_f64(pt["det_tensor"]), det_pos=_f64(pt["det_pos"]),
                 lm=np.ascontiguousarray(np.asarray(pt["lm"], dtype=np.int32).reshape(-1, 2)),
-                nu=np.ascontiguousarray(np.rint(np.asarray(pt["freqs"]) / df).astype(np.int32)),
+                nu=np.ascontiguousarray(pt["nu"], dtype=np.int32) if "nu" in pt
+                else np.ascontiguousarray(np.rint(np.asarray(pt["freqs"]) / df).astype(np.int32)),
                 hlm=hlm.view(np.float64),
                 data=np.ascontiguousarray(np.asarray(pt["data"], dtype=np.complex128)).view(np.float64),
                 weight=_f64(pt["weight"]), mirror=np.ascontiguousarray(np.asarray(pt["mirror"], dtype=np.int32)),

@@ -29,11 +29,15 @@ constexpr int kChunk = 256;      // band bins staged per pass
 __device__ __forceinline__ void df_acc(df &acc, float v) { acc = df_add_f(acc, v); }
 
 // Partial Q of detector blockIdx.z / slices over bin slice blockIdx.z % slices, modes
-// [blockIdx.y * kQModes, +kQModes), times [blockIdx.x * kQThreads, +): the band is cut into slices
-// of whole chunks so that enough CTAs run (one thread per grid time would leave the SMs nearly
-// idle); quv_q_reduce_kernel adds the slices.  X[a][b] = conj(h_a(f_b)) B_k(f_b) is formed per
-// staged chunk; the twiddle index nu_b j mod n advances by j between consecutive bins of the same
-// run and is recomputed at run starts.  Qp: [slices][K][M][nt] complex double.
+// [blockIdx.y * kQModes, +kQModes), grid times [blockIdx.x * kQTimes, +kQTimes): thread t takes the
+// times j = base + t and base + t + kQThreads, so every staged product is used twice.  The band is
+// cut into slices of whole chunks so that enough CTAs run; quv_q_reduce_kernel adds the slices.
+// X[a][b] = conj(h_a(f_b)) B_k(f_b) is formed per staged chunk; each time's twiddle index nu_b j
+// mod n advances by j between consecutive bins of the same run and is recomputed at run starts.
+// Qp: [slices][K][M][nt] complex double.
+constexpr int kQPerThread = 2;
+constexpr int kQTimes = kQThreads * kQPerThread;   // grid times per CTA
+
 __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restrict__ H, const float2 *__restrict__ Bk,
                                                           const int *__restrict__ nu, const int *__restrict__ run_start,
                                                           int nb, int M, int nt, int n, int slices,
@@ -43,15 +47,27 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
   const int k = blockIdx.z / slices, slice = blockIdx.z % slices, a0 = blockIdx.y * kQModes;
   const int nchunk = (nb + kChunk - 1) / kChunk, per = (nchunk + slices - 1) / slices;
   const int b_begin = min(nb, slice * per * kChunk), b_end = min(nb, (slice + 1) * per * kChunk);
-  const int j = blockIdx.x * kQThreads + threadIdx.x;
   const int ma = min(kQModes, M - a0);
-  df accr[kQModes], acci[kQModes];
+  int jt[kQPerThread];
 #pragma unroll
-  for (int a = 0; a < kQModes; ++a) { accr[a] = df{0.f, 0.f}; acci[a] = df{0.f, 0.f}; }
+  for (int q = 0; q < kQPerThread; ++q) jt[q] = blockIdx.x * kQTimes + threadIdx.x + q * kQThreads;
+  df accr[kQPerThread][kQModes], acci[kQPerThread][kQModes];
+#pragma unroll
+  for (int q = 0; q < kQPerThread; ++q)
+#pragma unroll
+    for (int a = 0; a < kQModes; ++a) { accr[q][a] = df{0.f, 0.f}; acci[q][a] = df{0.f, 0.f}; }
   const float inv_n2 = 2.0f / (float)n;
-  float sts, stc;   // exp(2 pi i j / n), the twiddle's step between consecutive bins of a run
-  sincospif((float)(j % n) * inv_n2, &sts, &stc);
-  int idx = 0;
+  // per time: exp(2 pi i j / n), the twiddle's step between consecutive bins of a run; the
+  // twiddle itself and its integer index
+  float sts[kQPerThread], stc[kQPerThread], sn[kQPerThread], cs[kQPerThread];
+  int idx[kQPerThread];
+#pragma unroll
+  for (int q = 0; q < kQPerThread; ++q) {
+    sincospif((float)(jt[q] % n) * inv_n2, &sts[q], &stc[q]);
+    sn[q] = 0.f;
+    cs[q] = 1.f;
+    idx[q] = 0;
+  }
   for (int b0 = b_begin; b0 < b_end; b0 += kChunk) {
     const int cb = min(kChunk, b_end - b0);
     __syncthreads();
@@ -67,46 +83,66 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
     }
     for (int t = threadIdx.x; t < cb; t += blockDim.x) { sNu[t] = nu[b0 + t]; sRun[t] = run_start[b0 + t]; }
     __syncthreads();
-    float pr[kQModes], pi[kQModes];
+    float pr[kQPerThread][kQModes], pi[kQPerThread][kQModes];
 #pragma unroll
-    for (int a = 0; a < kQModes; ++a) { pr[a] = 0.f; pi[a] = 0.f; }
-    float sn = 0.f, cs = 1.f;
+    for (int q = 0; q < kQPerThread; ++q)
+#pragma unroll
+      for (int a = 0; a < kQModes; ++a) { pr[q][a] = 0.f; pi[q][a] = 0.f; }
     for (int b = 0; b < cb; ++b) {
       // the twiddle exp(2 pi i (nu_b j mod n) / n): exact (integer index into sincospi) at the start
-      // of a run of consecutive bins and every 16 bins; in between rotated by the thread's step
+      // of a run of consecutive bins and every 16 bins; in between rotated by the time's step
       // exp(2 pi i j / n), so its error stays within about 16 roundings
-      if (b == 0 || sRun[b]) idx = (int)(((long long)sNu[b] * j) % n);
-      else { idx += j; if (idx >= n) idx -= n; }
-      if (b == 0 || sRun[b] || (b & 15) == 0) {
-        sincospif((float)idx * inv_n2, &sn, &cs);
-      } else {
-        const float c2 = fmaf(cs, stc, -sn * sts);
-        sn = fmaf(sn, stc, cs * sts);
-        cs = c2;
+      const bool restart = b == 0 || sRun[b];
+      const bool exact = restart || (b & 15) == 0;
+#pragma unroll
+      for (int q = 0; q < kQPerThread; ++q) {
+        if (restart) idx[q] = (int)(((long long)sNu[b] * jt[q]) % n);
+        else { idx[q] += jt[q]; if (idx[q] >= n) idx[q] -= n; }
+        if (exact) {
+          sincospif((float)idx[q] * inv_n2, &sn[q], &cs[q]);
+        } else {
+          const float c2 = fmaf(cs[q], stc[q], -sn[q] * sts[q]);
+          sn[q] = fmaf(sn[q], stc[q], cs[q] * sts[q]);
+          cs[q] = c2;
+        }
       }
 #pragma unroll
       for (int a = 0; a < kQModes; ++a) {
         const float2 x = sX[a][b];
-        pr[a] = fmaf(x.x, cs, fmaf(-x.y, sn, pr[a]));
-        pi[a] = fmaf(x.x, sn, fmaf(x.y, cs, pi[a]));
+#pragma unroll
+        for (int q = 0; q < kQPerThread; ++q) {
+          pr[q][a] = fmaf(x.x, cs[q], fmaf(-x.y, sn[q], pr[q][a]));
+          pi[q][a] = fmaf(x.x, sn[q], fmaf(x.y, cs[q], pi[q][a]));
+        }
       }
       if ((b & 31) == 31 || b == cb - 1) {
 #pragma unroll
-        for (int a = 0; a < kQModes; ++a) { df_acc(accr[a], pr[a]); df_acc(acci[a], pi[a]); pr[a] = 0.f; pi[a] = 0.f; }
+        for (int q = 0; q < kQPerThread; ++q)
+#pragma unroll
+          for (int a = 0; a < kQModes; ++a) {
+            df_acc(accr[q][a], pr[q][a]);
+            df_acc(acci[q][a], pi[q][a]);
+            pr[q][a] = 0.f;
+            pi[q][a] = 0.f;
+          }
       }
     }
   }
-  if (j < nt) {
 #pragma unroll
-    for (int a = 0; a < kQModes; ++a)
-      if (a < ma)
-        Qp[(((size_t)slice * (gridDim.z / slices) + k) * M + a0 + a) * nt + j] =
-            make_double2((double)accr[a].hi + (double)accr[a].lo, (double)acci[a].hi + (double)acci[a].lo);
-  }
+  for (int q = 0; q < kQPerThread; ++q)
+    if (jt[q] < nt) {
+#pragma unroll
+      for (int a = 0; a < kQModes; ++a)
+        if (a < ma)
+          Qp[(((size_t)slice * (gridDim.z / slices) + k) * M + a0 + a) * nt + jt[q]] =
+              make_double2((double)accr[q][a].hi + (double)accr[q][a].lo, (double)acci[q][a].hi + (double)acci[q][a].lo);
+    }
 }
 
-// Q[k][m][j] = the sum over the slices of Qp, in slice order (FP64).
-__global__ void quv_q_reduce_kernel(const double2 *__restrict__ Qp, int slices, size_t count, double2 *__restrict__ Q) {
+// Q[k][m][j] = qscale[k] times the sum over the slices of Qp, in slice order (FP64); qscale undoes
+// the power-of-two scalings of the data term and the waveforms.
+__global__ void quv_q_reduce_kernel(const double2 *__restrict__ Qp, int slices, size_t count, size_t per_det,
+                                    const double *__restrict__ qscale, double2 *__restrict__ Q) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   double re = 0.0, im = 0.0;
@@ -115,7 +151,8 @@ __global__ void quv_q_reduce_kernel(const double2 *__restrict__ Qp, int slices, 
     re += v.x;
     im += v.y;
   }
-  Q[i] = make_double2(re, im);
+  const double sc = qscale[i / per_det];
+  Q[i] = make_double2(re * sc, im * sc);
 }
 
 // U and V of detector blockIdx.y, pair (a, b) = blockIdx.x: the block's threads stride over the band
@@ -223,13 +260,24 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   if (n < 2 || std::fabs(nd - (double)n) > 1e-9 * nd || n > (1ll << 30))
     return quv_fail(RIFT_EINVAL, "fs / df must be an integer (the Q grid and the frequency grid share it)");
   if ((long long)nt > n) return quv_fail(RIFT_EINVAL, "n_t exceeds fs / df samples");
-  // band bins: weight nonzero in some detector; their mirrors
+  // band bins: weight nonzero in some detector (in bin order; parts of the bin range on the
+  // worker pool, joined in part order); every mirror index in range
+  constexpr int kParts = 8;
+  std::vector<int> bpart[kParts];
+  int bad_mirror[kParts] = {};
+  parallel_parts(nf, 16384, kParts, [&](int part, int i0, int i1) {
+    std::vector<int> &v = bpart[part];
+    for (int i = i0; i < i1; ++i) {
+      bad_mirror[part] |= (d->mirror[i] < 0) | (d->mirror[i] >= nf);
+      bool in = false;
+      for (int k = 0; k < K; ++k) in = in || d->weight[(size_t)k * nf + i] != 0.0;
+      if (in) v.push_back(i);
+    }
+  });
   std::vector<int> band;
-  for (int i = 0; i < nf; ++i) {
-    if (d->mirror[i] < 0 || d->mirror[i] >= nf) return quv_fail(RIFT_EINVAL, "mirror index out of range");
-    bool in = false;
-    for (int k = 0; k < K; ++k) in = in || d->weight[(size_t)k * nf + i] != 0.0;
-    if (in) band.push_back(i);
+  for (int t = 0; t < kParts; ++t) {
+    if (bad_mirror[t]) return quv_fail(RIFT_EINVAL, "mirror index out of range");
+    band.insert(band.end(), bpart[t].begin(), bpart[t].end());
   }
   const int nb = (int)band.size();
   if (nb == 0) return quv_fail(RIFT_EINVAL, "no bin has a nonzero weight");
@@ -238,16 +286,28 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   // the waveforms, the data terms and the weighted waveforms (for the power-of-two scalings below)
   std::vector<double> Bd(2 * (size_t)K * nb);
   std::vector<int> nuv(nb), run(nb);
-  constexpr int kParts = 8;
   struct PartMax {
     double h = 0.0, b[RIFT_MAX_DET] = {}, w[RIFT_MAX_DET] = {};
     int bad = 0;   // 1 non-finite waveform, 2 bad weight, 3 non-finite data
   };
   PartMax pm[kParts];
   auto cabs = [](const double *z) { return std::max(std::fabs(z[0]), std::fabs(z[1])); };
+  // exp(2 pi i nu df tau0_k) of a bin: exact (fmod, cos, sin) at the start of a part, of a run of
+  // consecutive nu and every 32 bins, otherwise the previous bin's value times exp(2 pi i df tau0_k)
+  constexpr double kTwoPi = 2.0 * 3.14159265358979323846;
+  double wre[RIFT_MAX_DET], wim[RIFT_MAX_DET];
+  for (int k = 0; k < K; ++k) {
+    const double ph = kTwoPi * std::fmod(d->df * (d->q_t0_gps[k] - d->t_ref_gps), 1.0);
+    wre[k] = std::cos(ph);
+    wim[k] = std::sin(ph);
+  }
   parallel_parts(nb, 2048, kParts, [&](int part, int b0, int b1) {
     PartMax &r = pm[part];
+    double cre[RIFT_MAX_DET] = {}, cim[RIFT_MAX_DET] = {};
+    int since = 0;
     for (int b = b0; b < b1 && !r.bad; ++b) {
+      const bool exact = b == b0 || d->nu[band[b]] != d->nu[band[b - 1]] + 1 || ++since == 32;
+      if (exact) since = 0;
       const int i = band[b], im = d->mirror[i];
       long long v = d->nu[i] % n;
       if (v < 0) v += n;
@@ -267,9 +327,17 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
         const double *x = d->data + 2 * ((size_t)k * nf + i);
         if (!std::isfinite(w) || w < 0.0) { r.bad = 2; break; }
         if (!std::isfinite(x[0]) || !std::isfinite(x[1])) { r.bad = 3; break; }
-        const double tau0 = d->q_t0_gps[k] - d->t_ref_gps;
-        const double ph = 2.0 * 3.14159265358979323846 * std::fmod((double)d->nu[i] * d->df * tau0, 1.0);
-        const double c = std::cos(ph), sn = std::sin(ph), f = 2.0 * d->df * w;
+        if (exact) {
+          const double tau0 = d->q_t0_gps[k] - d->t_ref_gps;
+          const double ph = kTwoPi * std::fmod((double)d->nu[i] * d->df * tau0, 1.0);
+          cre[k] = std::cos(ph);
+          cim[k] = std::sin(ph);
+        } else {
+          const double c2 = cre[k] * wre[k] - cim[k] * wim[k];
+          cim[k] = cre[k] * wim[k] + cim[k] * wre[k];
+          cre[k] = c2;
+        }
+        const double c = cre[k], sn = cim[k], f = 2.0 * d->df * w;
         double *bd = &Bd[2 * ((size_t)k * nb + b)];
         bd[0] = f * (x[0] * c - x[1] * sn);
         bd[1] = f * (x[0] * sn + x[1] * c);
@@ -304,7 +372,7 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   // then the twiddle indices, the run starts and the U/V scales
   const size_t nH = (size_t)M * nb, nB = (size_t)K * nb, nHw = (size_t)K * M * nb;
   const size_t o_Hm = nH, o_B = 2 * nH, o_Hw = 2 * nH + nB, n_f2 = 2 * nH + nB + nHw;
-  const size_t stage_bytes = sizeof(float2) * n_f2 + sizeof(int) * 2 * (size_t)nb + sizeof(double) * (K + 1);
+  const size_t stage_bytes = sizeof(float2) * n_f2 + sizeof(int) * 2 * (size_t)nb + sizeof(double) * (2 * K + 1);
   HostBuf hs;
   cudaError_t e;
   if ((e = cache_host_alloc(&hs.p, stage_bytes)) != cudaSuccess)
@@ -315,7 +383,10 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   double *sc_h = reinterpret_cast<double *>(run_h + nb);   // 8-byte aligned: 2 nb ints follow the float2s
   std::memcpy(nu_h, nuv.data(), sizeof(int) * nb);
   std::memcpy(run_h, run.data(), sizeof(int) * nb);
-  for (int k = 0; k < K; ++k) sc_h[k] = uvscale[k];
+  for (int k = 0; k < K; ++k) {
+    sc_h[k] = uvscale[k];
+    sc_h[K + k] = qscale[k];
+  }
   parallel_parts(nb, 2048, kParts, [&](int, int b0, int b1) {
     for (int b = b0; b < b1; ++b) {
       const int i = band[b];
@@ -342,12 +413,12 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int ctas = ((nt + kQThreads - 1) / kQThreads) * ((M + kQModes - 1) / kQModes) * K;
+  const int ctas = ((nt + kQTimes - 1) / kQTimes) * ((M + kQModes - 1) / kQModes) * K;
   const int nchunk = (nb + kChunk - 1) / kChunk;
   const int slices = std::max(1, std::min(nchunk, (4 * nsm + ctas - 1) / ctas));
   if ((e = cache_dev_alloc(&dF2.p, sizeof(float2) * n_f2)) != cudaSuccess ||
       (e = cache_dev_alloc(&dnu.p, sizeof(int) * 2 * (size_t)nb)) != cudaSuccess ||
-      (e = cache_dev_alloc(&dsc.p, sizeof(double) * K)) != cudaSuccess ||
+      (e = cache_dev_alloc(&dsc.p, sizeof(double) * 2 * K)) != cudaSuccess ||
       (e = cache_dev_alloc(&dQ.p, sizeof(double2) * (size_t)K * M * nt)) != cudaSuccess ||
       (e = cache_dev_alloc(&dQp.p, sizeof(double2) * (size_t)slices * K * M * nt)) != cudaSuccess ||
       (e = cache_dev_alloc(&dU.p, sizeof(double2) * (size_t)K * M * M)) != cudaSuccess ||
@@ -356,7 +427,7 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   drain.armed = true;
   if ((e = cudaMemcpyAsync(dF2.p, F2, sizeof(float2) * n_f2, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(dnu.p, nu_h, sizeof(int) * 2 * (size_t)nb, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(dsc.p, sc_h, sizeof(double) * K, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      (e = cudaMemcpyAsync(dsc.p, sc_h, sizeof(double) * 2 * K, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return quv_fail(RIFT_ECUDA, cudaGetErrorString(e));
   const float2 *dH = static_cast<const float2 *>(dF2.p), *dHm = dH + o_Hm, *dB = dH + o_B, *dHw = dH + o_Hw;
   const int *dnu_p = static_cast<const int *>(dnu.p), *drun_p = dnu_p + nb;
@@ -367,12 +438,12 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
       for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
       return quv_fail(RIFT_ECUDA, cudaGetErrorString(e));
     }
-  dim3 gq((nt + kQThreads - 1) / kQThreads, (M + kQModes - 1) / kQModes, K * slices);
+  dim3 gq((nt + kQTimes - 1) / kQTimes, (M + kQModes - 1) / kQModes, K * slices);
   cudaEventRecord(ev[0], st);
   quv_q_kernel<<<gq, kQThreads, 0, st>>>(dH, dB, dnu_p, drun_p, nb, M, nt, (int)n, slices, (double2 *)dQp.p);
   const size_t qcount = (size_t)K * M * nt;
-  quv_q_reduce_kernel<<<(unsigned)((qcount + 255) / 256), 256, 0, st>>>((const double2 *)dQp.p, slices, qcount,
-                                                                        (double2 *)dQ.p);
+  quv_q_reduce_kernel<<<(unsigned)((qcount + 255) / 256), 256, 0, st>>>(
+      (const double2 *)dQp.p, slices, qcount, (size_t)M * nt, (const double *)dsc.p + K, (double2 *)dQ.p);
   cudaEventRecord(ev[1], st);
   dim3 guv(M * M, K);
   quv_uv_kernel<<<guv, kUVThreads, 0, st>>>(dH, dHm, dHw, nb, M, (double2 *)dU.p, (double2 *)dV.p,
@@ -392,8 +463,6 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
       (e = cudaMemcpyAsync(V, dV.p, sizeof(double2) * (size_t)K * M * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return quv_fail(RIFT_ECUDA, cudaGetErrorString(e));
-  for (int k = 0; k < K; ++k)   // undo the scalings of the data term and the waveforms
-    for (size_t o = 2 * (size_t)k * M * nt; o < 2 * (size_t)(k + 1) * M * nt; ++o) Q[o] *= qscale[k];
   return RIFT_OK;
 }
 

@@ -307,7 +307,8 @@ def make_point(spec: PointSpec, seed: int, injection=None):
         Q=Q, q_t0_gps=np.full(K, spec.t_ref_gps - J / spec.fs), fs=float(spec.fs), U=U, V=V,
         t_ref_gps=float(spec.t_ref_gps), d_ref_mpc=float(spec.d_ref), t_lo=-t_half, t_hi=t_half,
         # frequency-domain arrays (oracle brute force only)
-        freqs=freqs, df=df, hlm=hlm, data=data, weight=weight, mirror=mirror,
+        freqs=freqs, df=df, hlm=hlm, data=data, weight=weight, mirror=mirror.astype(np.int32),
+        nu=np.rint(freqs / df).astype(np.int32),   # the grid's integer bins, freqs = nu df
         coef=coef * amp, tk=tk, snr=spec.snr, dmax=dmax, n_t=n_t, J=J,
     )
 
