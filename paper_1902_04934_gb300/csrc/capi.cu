@@ -679,6 +679,7 @@ rift_status create_impl(const rift_ile_desc *descs, int n, rift_ile **out) {
   if (!out) return RIFT_EINVAL;
   *out = nullptr;
   if (!descs || n < 1) return RIFT_EINVAL;
+  host_par::Pool::get().wake();   // the Q conversion below runs on the worker pool
   rift_ile *h = new (std::nothrow) rift_ile();
   if (!h) return RIFT_ENOMEM;
   h->n_points = n;

@@ -1,10 +1,13 @@
 // Host-side helper: a loop over [0, n) cut into parts, run by a process-wide pool of worker
-// threads (started on first use and kept, so a call costs a wake-up rather than a thread start).
+// threads (started on first use and kept).  A worker that finishes a job, or is woken ahead of
+// one (Pool::wake), keeps polling for the next job for a short while before it sleeps, so a call
+// that follows soon after costs no thread wake-up.
 #pragma once
 #include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <functional>
 #include <mutex>
@@ -16,10 +19,21 @@ namespace host_par {
 class Pool {
  public:
   static constexpr int kMaxWorkers = 7;
+  static constexpr std::chrono::microseconds kSpin{300};   // polling time before a worker sleeps
 
   static Pool &get() {
     static Pool *p = new Pool;   // never destroyed: its threads live until the process exits
     return *p;
+  }
+
+  // Wakes the workers ahead of a job that will follow shortly (they poll for kSpin).
+  void wake() {
+    if (getpid() != pid_) return;
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      ++wake_;
+    }
+    cv_work_.notify_all();
   }
 
   // Runs job(part) for part in [0, parts) on the calling thread and the workers; returns false
@@ -34,7 +48,7 @@ class Pool {
       parts_ = parts;
       next_.store(0);
       left_ = parts;
-      ++gen_;
+      gen_.fetch_add(1, std::memory_order_release);
     }
     cv_work_.notify_all();
     work();
@@ -70,19 +84,37 @@ class Pool {
     }
   }
 
+  // Joins the current job if it is still open.
+  void join_job(unsigned long long &seen) {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      seen = gen_.load();
+      if (!job_) return;   // that job has finished
+      ++active_;
+    }
+    work();
+    std::lock_guard<std::mutex> g(mu_);
+    if (--active_ == 0) cv_done_.notify_all();
+  }
+
   void loop() {
-    unsigned long long seen = 0;
+    unsigned long long seen = 0, woken = 0;
     for (;;) {
       {
         std::unique_lock<std::mutex> g(mu_);
-        cv_work_.wait(g, [&] { return gen_ != seen; });
-        seen = gen_;
-        if (!job_) continue;   // woke after that job had finished
-        ++active_;
+        cv_work_.wait(g, [&] { return gen_.load() != seen || wake_ != woken; });
+        woken = wake_;
       }
-      work();
-      std::lock_guard<std::mutex> g(mu_);
-      if (--active_ == 0) cv_done_.notify_all();
+      // jobs as they come, polling up to kSpin after the last one
+      auto last = std::chrono::steady_clock::now();
+      while (std::chrono::steady_clock::now() - last < kSpin) {
+        if (gen_.load(std::memory_order_acquire) != seen) {
+          join_job(seen);
+          last = std::chrono::steady_clock::now();
+        } else {
+          std::this_thread::yield();
+        }
+      }
     }
   }
 
@@ -91,7 +123,8 @@ class Pool {
   const std::function<void(int)> *job_ = nullptr;
   int parts_ = 0, left_ = 0, active_ = 0;
   std::atomic<int> next_{0};
-  unsigned long long gen_ = 0;
+  std::atomic<unsigned long long> gen_{0};
+  unsigned long long wake_ = 0;
   const pid_t pid_;
   std::vector<std::thread> threads_;
 };

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
                                                           int nb, int M, int nt, int n, int slices,
                                                           double2 *__restrict__ Qp) {
   __shared__ float2 sX[kQModes][kChunk];
-  __shared__ int sNu[kChunk], sRun[kChunk];
+  __shared__ int sNu[kChunk], sRun[kChunk], sBlk[kChunk / 16];
   const int k = blockIdx.z / slices, slice = blockIdx.z % slices, a0 = blockIdx.y * kQModes;
   const int nchunk = (nb + kChunk - 1) / kChunk, per = (nchunk + slices - 1) / slices;
   const int b_begin = min(nb, slice * per * kChunk), b_end = min(nb, (slice + 1) * per * kChunk);
@@ -82,16 +82,48 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
       sX[a][b] = x;
     }
     for (int t = threadIdx.x; t < cb; t += blockDim.x) { sNu[t] = nu[b0 + t]; sRun[t] = run_start[b0 + t]; }
+    // blocks of 16 bins inside the chunk with no run starting after their first bin
+    for (int g = threadIdx.x; g < kChunk / 16; g += blockDim.x) {
+      bool whole = 16 * g + 16 <= cb;
+      for (int u = 1; u < 16 && whole; ++u) whole = run_start[b0 + 16 * g + u] == 0;
+      sBlk[g] = whole ? 1 : 0;
+    }
     __syncthreads();
     float pr[kQPerThread][kQModes], pi[kQPerThread][kQModes];
 #pragma unroll
     for (int q = 0; q < kQPerThread; ++q)
 #pragma unroll
       for (int a = 0; a < kQModes; ++a) { pr[q][a] = 0.f; pi[q][a] = 0.f; }
-    for (int b = 0; b < cb; ++b) {
-      // the twiddle exp(2 pi i (nu_b j mod n) / n): exact (integer index into sincospi) at the start
-      // of a run of consecutive bins and every 16 bins; in between rotated by the time's step
-      // exp(2 pi i j / n), so its error stays within about 16 roundings
+    // one bin's products with the current twiddles into the FP32 partial sums; the partial sums
+    // go into the double-float totals every 32 bins and at the end of the chunk
+    auto products = [&](int b) {
+#pragma unroll
+      for (int a = 0; a < kQModes; ++a) {
+        const float2 x = sX[a][b];
+#pragma unroll
+        for (int q = 0; q < kQPerThread; ++q) {
+          pr[q][a] = fmaf(x.x, cs[q], fmaf(-x.y, sn[q], pr[q][a]));
+          pi[q][a] = fmaf(x.x, sn[q], fmaf(x.y, cs[q], pi[q][a]));
+        }
+      }
+    };
+    auto fold = [&](int b) {
+      if ((b & 31) == 31 || b == cb - 1) {
+#pragma unroll
+        for (int q = 0; q < kQPerThread; ++q)
+#pragma unroll
+          for (int a = 0; a < kQModes; ++a) {
+            df_acc(accr[q][a], pr[q][a]);
+            df_acc(acci[q][a], pi[q][a]);
+            pr[q][a] = 0.f;
+            pi[q][a] = 0.f;
+          }
+      }
+    };
+    // the twiddle exp(2 pi i (nu_b j mod n) / n): exact (integer index into sincospi) at the start
+    // of a run of consecutive bins and every 16 bins; in between rotated by the time's step
+    // exp(2 pi i j / n), so its error stays within about 16 roundings
+    auto twiddle = [&](int b) {
       const bool restart = b == 0 || sRun[b];
       const bool exact = restart || (b & 15) == 0;
 #pragma unroll
@@ -106,25 +138,33 @@ __global__ void __launch_bounds__(kQThreads) quv_q_kernel(const float2 *__restri
           cs[q] = c2;
         }
       }
+    };
+    for (int b = 0; b < cb;) {
+      if ((b & 15) == 0 && sBlk[b >> 4]) {
+        // 16 bins of one run (a run may start at the first): the same twiddles as bin by bin,
+        // without the per-bin index and run bookkeeping
+        twiddle(b);
+        products(b);
 #pragma unroll
-      for (int a = 0; a < kQModes; ++a) {
-        const float2 x = sX[a][b];
+        for (int u = 1; u < 16; ++u) {
 #pragma unroll
-        for (int q = 0; q < kQPerThread; ++q) {
-          pr[q][a] = fmaf(x.x, cs[q], fmaf(-x.y, sn[q], pr[q][a]));
-          pi[q][a] = fmaf(x.x, sn[q], fmaf(x.y, cs[q], pi[q][a]));
-        }
-      }
-      if ((b & 31) == 31 || b == cb - 1) {
-#pragma unroll
-        for (int q = 0; q < kQPerThread; ++q)
-#pragma unroll
-          for (int a = 0; a < kQModes; ++a) {
-            df_acc(accr[q][a], pr[q][a]);
-            df_acc(acci[q][a], pi[q][a]);
-            pr[q][a] = 0.f;
-            pi[q][a] = 0.f;
+          for (int q = 0; q < kQPerThread; ++q) {
+            const float c2 = fmaf(cs[q], stc[q], -sn[q] * sts[q]);
+            sn[q] = fmaf(sn[q], stc[q], cs[q] * sts[q]);
+            cs[q] = c2;
           }
+          products(b + u);
+        }
+        fold(b + 15);
+#pragma unroll
+        for (int q = 0; q < kQPerThread; ++q)   // the index of bin b + 15
+          idx[q] = (int)(((long long)idx[q] + 15ll * jt[q]) % n);
+        b += 16;
+      } else {
+        twiddle(b);
+        products(b);
+        fold(b);
+        ++b;
       }
     }
   }
@@ -260,6 +300,7 @@ rift_status rift_quv(const rift_ile_fd_desc *d, double *Q, double *U, double *V)
   if (n < 2 || std::fabs(nd - (double)n) > 1e-9 * nd || n > (1ll << 30))
     return quv_fail(RIFT_EINVAL, "fs / df must be an integer (the Q grid and the frequency grid share it)");
   if ((long long)nt > n) return quv_fail(RIFT_EINVAL, "n_t exceeds fs / df samples");
+  host_par::Pool::get().wake();   // the passes over the bins below run on the worker pool
   // band bins: weight nonzero in some detector (in bin order; parts of the bin range on the
   // worker pool, joined in part order); every mirror index in range
   constexpr int kParts = 8;
