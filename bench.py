@@ -593,6 +593,8 @@ def run_extras(args, rift, W, peak):
         out["mdn"] = run_mdn(rift, peak)
     if "config45" in sel:
         out["config45"] = run_config45(args, rift, W)
+    if "converge" in sel:
+        out["converge"] = run_converge(args, rift, W)
     if "batched" not in sel:
         return out
     pts, gen_s = physical_batch(rift, W, args.batch_points, 5, 1000)
@@ -629,6 +631,34 @@ def run_extras(args, rift, W, peak):
     if "learned" in sel:
         out["learned"] = run_learned(args, rift, W, hb, pts, rt)
     return out
+
+
+def run_converge(args, rift, W):
+    """Points of the batched workload run to the stopping rule (Sec. II.C, n_eff >= 1000): the
+    event time integrated by quadrature, adaptive (ra, sin dec), 1e5-draw rounds, in one batched
+    launch sequence, up to --converge-draws draws per point.  Reports which points converge, the
+    draws they needed, and the batch's wall time to the rule (or the cap)."""
+    import numpy as np
+    pts, gen_s = physical_batch(rift, W, args.converge_points, 7, 3000)
+    hb = rift.rift_ile_batch_create(pts)
+    kt = dict(seed=11, n_per_round=100000, max_evals=args.converge_draws, n_eff_target=1000.0,
+              proposal="adaptive", n_bins=100, time_marg=1)
+    rift.rift_ile_batch_marginalize(hb, **dict(kt, max_evals=100000))   # warm-up (graph, scratch)
+    res, secs = _timed_batch(rift, hb, **kt)
+    rift.rift_ile_destroy(hb)
+    snr = [float(p["snr"]) for p in pts]
+    conv = [i for i, r in enumerate(res) if r["n_eff"] >= 1000]
+    return {"workload": f"{len(pts)} physical injections of the batched workload (SNR U[8,30]); event time "
+                        f"integrated by quadrature, adaptive (ra, sin dec), 1e5-draw rounds until n_eff >= 1000 "
+                        f"or {args.converge_draws:.0e} draws per point",
+            "seconds": secs, "points_per_s_to_rule_or_cap": len(pts) / secs,
+            "draws_per_s": sum(r["n_evals"] for r in res) / secs,
+            "points_reaching_neff_1000": len(conv),
+            "median_draws_to_neff_1000": float(np.median([res[i]["n_evals"] for i in conv])) if conv else None,
+            "points": [{"snr": round(snr[i], 2), "n_eff": round(float(r["n_eff"]), 1), "draws": int(r["n_evals"]),
+                        "lnL_marg": round(float(r["lnL_marg"]), 4), "sigma_lnL": round(float(r["sigma"]), 4)}
+                       for i, r in enumerate(res)],
+            "generation_s": gen_s}
 
 
 def run_config45(args, rift, W):
@@ -912,6 +942,8 @@ def main():
     ap.add_argument("--tmarg-draws", type=int, default=1_000_000,
                     help="draws per point at most in the time-marginalised batched runs")
     ap.add_argument("--heldout-points", type=int, default=128)
+    ap.add_argument("--converge-points", type=int, default=16, help="points of the opt-in 'converge' extra")
+    ap.add_argument("--converge-draws", type=int, default=200_000_000, help="draw cap per point of 'converge'")
     ap.add_argument("--fallback-neff", type=float, default=10.0)
     ap.add_argument("--samples", type=int, default=N_SAMPLES,
                     help="samples per step (profiling captures use a smaller count of the same workload)")
