@@ -650,14 +650,22 @@ __device__ __forceinline__ void tmarg_gemm_item(const CellLaunch &L, const Point
           __syncthreads();   // S is rewritten by the next stage
         }
         if (ok && pv) {
+          // the chunk's log-sum-exp against its own maximum (no per-point branch; four partial
+          // sums), then merged into the draw's running (max, sum)
           const float xx = XX[pslot], cc = CX[pslot];
+          float mc = kNegInf;
 #pragma unroll
           for (int jj = 0; jj < kTgLin; ++jj) {
-            if (jj < nj) {
-              const float l = xx * (lin[jj] + cc);
-              if (l > em) { es = fmaf(es, expf(em - l), 1.f); em = l; }
-              else es += expf(l - em);
-            }
+            lin[jj] = jj < nj ? xx * (lin[jj] + cc) : kNegInf;
+            mc = fmaxf(mc, lin[jj]);
+          }
+          if (mc > kNegInf) {
+            float sc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int jj = 0; jj < kTgLin; ++jj) sc[jj & 3] += expf(lin[jj] - mc);
+            const float sum = (sc[0] + sc[1]) + (sc[2] + sc[3]);
+            if (mc > em) { es = fmaf(es, expf(em - mc), sum); em = mc; }
+            else es = fmaf(sum, expf(mc - em), es);
           }
         }
       }
