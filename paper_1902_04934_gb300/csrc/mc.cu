@@ -647,7 +647,8 @@ __device__ __forceinline__ void tmarg_gemm_item(const CellLaunch &L, const Point
               if (jj < nj) lin[jj] += v;
             }
           }
-          __syncthreads();   // S is rewritten by the next stage
+          // S is rewritten by the next stage's GEMM, which every thread reaches only through that
+          // stage's barrier on the staged rows (and a group's end passes two more barriers)
         }
         if (ok && pv) {
           // the chunk's log-sum-exp against its own maximum (no per-point branch; four partial
