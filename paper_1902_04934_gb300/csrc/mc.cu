@@ -708,6 +708,63 @@ __device__ __forceinline__ void tmarg_gemm_item(const CellLaunch &L, const Point
   }
 }
 
+// Rows of the Q window of each detector for the samples of a stratified cell, from the cell's box
+// alone: the box in (ra, sin dec, t) (its uniforms' bounds through the round's tables when the
+// proposal is adaptive), the time-of-flight term of the index on a 5 x 5 grid over the sky patch
+// (one grid point per lane of the calling warp) and the time range at its ends.  Between grid
+// points the term x_k . n / c (times fs) departs from the grid's range by at most
+// |x_k| fs / c (h_ra^2 + h_dec^2) / 8 (its second derivative along the sky is at most |x_k|), which
+// is added with one row more.  A sample whose taps still fall outside reads them from global
+// memory, so the bounds decide only what is staged.  Called by whole warps; every lane returns the
+// warp's bounds.
+template <int K, int NT>
+__device__ __forceinline__ void cell_window_rows(const PointC &P, const RoundPt &R, uint32_t cell, const float *tab,
+                                                 int (&rmin)[K], int (&rmax)[K]) {
+  constexpr int first = (NT == 4) ? -1 : 0;
+  const int lane = threadIdx.x & 31;
+  const uint32_t ls[3] = {R.ls0, R.ls1, R.ls2};
+  const uint32_t cc[3] = {cell & ((1u << R.ls0) - 1u), (cell >> R.ls0) & ((1u << R.ls1) - 1u), cell >> (R.ls0 + R.ls1)};
+  float xa[3], xb[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float sc = __int_as_float((127 - (int)ls[d]) << 23);   // 2^-ls
+    const float ua = (float)cc[d] * sc, ub = (float)(cc[d] + 1u) * sc;
+    if (R.proposal == 1) {
+      int b;
+      xa[d] = inv_cdf_df(tab + d * (R.nb + 1), R.nb, df{ua, 0.f}, b).hi;
+      xb[d] = inv_cdf_df(tab + d * (R.nb + 1), R.nb, df{ub, 0.f}, b).hi;
+    } else {
+      xa[d] = ua;
+      xb[d] = ub;
+    }
+  }
+  const int g = lane < 25 ? lane : 0;
+  const float fr = 0.25f * (float)(g % 5), fs = 0.25f * (float)(g / 5);
+  const float v = fmaf(xb[0] - xa[0], fr, xa[0]) - P.g_hi;   // ra/2pi - GMST/2pi (turns)
+  float sa, ca;
+  sincospif(2.f * v, &sa, &ca);
+  const float sd = fmaf(2.f, fmaf(xb[1] - xa[1], fs, xa[1]), -1.f);
+  const float cd = sqrtf(fmaxf(0.f, fmaf(-sd, sd, 1.f)));
+  const float nx = cd * ca, ny = cd * sa;
+  const float ta = P.A * xa[2], tb = P.A * xb[2];   // (t - t_lo) fs at the ends of the time range
+  const float half = (NT == 1) ? 0.5f : 0.f;
+  // grid spacings (radians) in ra and dec
+  const float h_ra = 0.25f * kTwoPi * (xb[0] - xa[0]);
+  const float h_dec = 0.25f * (asinf(fminf(1.f, fmaf(2.f, xb[1], -1.f))) - asinf(fmaxf(-1.f, fmaf(2.f, xa[1], -1.f))));
+  const float curv = 0.125f * fmaf(h_ra, h_ra, h_dec * h_dec);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const DetC &D = P.det[k];
+    const float acc = fmaf(D.P[0], nx, fmaf(D.P[1], ny, D.P[2] * sd));
+    const float rk = sqrtf(fmaf(D.P[0], D.P[0], fmaf(D.P[1], D.P[1], D.P[2] * D.P[2])));   // |x_k| fs / c
+    const int margin = (int)ceilf(rk * curv) + 1;
+    const int lo = __reduce_min_sync(0xffffffffu, (int)floorf(D.c0 + ta - acc + half));
+    const int hi = __reduce_max_sync(0xffffffffu, (int)floorf(D.c0 + tb - acc + half));
+    rmin[k] = lo + first - margin;
+    rmax[k] = hi + first + NT - 1 + margin;
+  }
+}
+
 // TMARG: the event time is marginalised by quadrature (Eq. lnL:tmarg) instead of sampled; the
 // sample's t uniform is unused, its Q rows span the whole time window (no staging), and the
 // likelihood is tmarg_term: each point reads its half rows (tgrid_scan_half) when it has them, and
@@ -818,11 +875,14 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
 #pragma unroll
       for (int k = 0; k < K; ++k) { win[k] = nullptr; wlo[k] = 0; whi[k] = -1; }
     } else {
-    // A. window of every detector from the cell's samples
+    // A. window of every detector: from the cell's box for stratified prior and adaptive rounds,
+    // else from the cell's samples
     int rmin[K], rmax[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) { rmin[k] = INT_MAX; rmax[k] = INT_MIN; }
-    for (uint32_t j = j0 + threadIdx.x; j < j_end; j += blockDim.x) {
+    const bool boxed = !LEARNED && R.proposal <= 1 && (R.ls0 + R.ls1 + R.ls2) > 0u;
+    if (boxed) cell_window_rows<K, NT>(P, R, cell, tab, rmin, rmax);
+    for (uint32_t j = j0 + threadIdx.x; j < j_end && !boxed; j += blockDim.x) {
       const Drawn d = draw_any<LEARNED>(L.seed, R, sample_index(R, cell, j), cell, tab, lnw, s_gmm, P.dref, L.d_lo3,
                                         L.d_span3);
       const Sky s = sky_of(P, d);
