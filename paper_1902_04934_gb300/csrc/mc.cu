@@ -987,8 +987,16 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
         const float quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
         lnL = tmarg_term<K, NT, TMARG == 2 ? 1 : -1>(P, Q, g.s, g.F, Ys, ystride, g.x, quad, flags);
       } else {
-        // the quadratic form first: the d_lm it takes from the harmonics are then dead before the
-        // linear term's taps are loaded
+        // merged rows (YR 2): the linear term first, so its tap rows, weights and indices are dead
+        // before the quadratic form (about a third of the register spills of the other order);
+        // otherwise the quadratic form first, so the d_lm it takes from the harmonics are dead
+        // before the linear term's taps are loaded.  The same operations either way.
+        float lin = 0.f;
+        if constexpr (YR == 2) {
+          float2 e[5];
+          eiphi_powers(cphi, sphi, e);
+          lin = linear_term_merged<K, NT>(P, Q + P.qh_rel, g.s, g.F, dj, e, win, wlo, whi, flags);
+        }
         float quad;
         if constexpr (CP == 3)
           quad = quad_mirror_from_d<K>(static_cast<const float2 *>(cpg), g, dj, P.sigma_neg,
@@ -996,16 +1004,11 @@ __device__ __forceinline__ void cells_body(const CellLaunch &L, const void *__re
         else if constexpr (CP != 0)
           quad = quad_canon_from_d<K, CP == 2>(static_cast<const float4 *>(cpg), g, dj, (uint32_t)(d.u_phi * 16777216.f));
         else quad = quad_cell<K, NT, CP>(P, C, cpg, g, Ys, ystride, ch, sh, d.u_phi);
-        float lin;
-        if constexpr (YR == 2) {
-          float2 e[5];
-          eiphi_powers(cphi, sphi, e);
-          lin = linear_term_merged<K, NT>(P, Q + P.qh_rel, g.s, g.F, dj, e, win, wlo, whi, flags);
-        } else if constexpr (YR) {
+        if constexpr (YR == 1) {
           float2 e[5];
           eiphi_powers(cphi, sphi, e);
           lin = linear_term_yreg<K, NT>(P, Q, g.s, g.F, dj, e, win, wlo, whi, flags);
-        } else {
+        } else if constexpr (YR == 0) {
           lin = linear_term_staged<K, NT>(P, Q, g.s, g.F, Ys, ystride, win, wlo, whi, flags);
         }
         lnL = g.x * fmaf(-0.25f * g.x, quad, lin);
