@@ -869,15 +869,20 @@ void fill_result(const AccState &a, rift_mc_result *r, const RefineState *rs = n
   r->sigma = (a.n > 1) ? std::sqrt(std::max(n * r->acc_s2 / (r->acc_s1 * r->acc_s1) - 1.0, 0.0) / (n - 1.0)) : INFINITY;
 }
 
+// Status of a device status word read back from the handle.
+rift_status flags_status(rift_ile *h, uint32_t f) {
+  if (f & RIFT_FLAG_TIMEOUT_BIT) return fail(h, RIFT_ETIMEOUT, "a bounded wait for a shared-memory copy expired");
+  if (f & RIFT_FLAG_WINDOW) return fail(h, RIFT_EWINDOW, "interpolation taps left the Q window");
+  if (f & RIFT_FLAG_NONFINITE) return fail(h, RIFT_ENONFINITE, "non-finite log-likelihood");
+  return RIFT_OK;
+}
+
 rift_status read_flags(rift_ile *h) {
   uint32_t f = 0;
   RIFT_CK(h, cudaMemcpyAsync(&f, h->flags, sizeof(f), cudaMemcpyDeviceToHost, h->stream));
   RIFT_CK(h, cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), h->stream));
   RIFT_CK(h, cudaStreamSynchronize(h->stream));
-  if (f & RIFT_FLAG_TIMEOUT_BIT) return fail(h, RIFT_ETIMEOUT, "a bounded wait for a shared-memory copy expired");
-  if (f & RIFT_FLAG_WINDOW) return fail(h, RIFT_EWINDOW, "interpolation taps left the Q window");
-  if (f & RIFT_FLAG_NONFINITE) return fail(h, RIFT_ENONFINITE, "non-finite log-likelihood");
-  return RIFT_OK;
+  return flags_status(h, f);
 }
 
 int taps_of(int interp) { return interp == 3 ? 4 : (interp == 1 ? 2 : 1); }
@@ -1303,11 +1308,14 @@ rift_status run_mc(rift_ile *h, const rift_mc_opts *o, int np, McScratch &S, rif
     std::memset(o->save, 0, RIFT_MC_STATE_BYTES);
     std::memcpy(o->save, &outb, sizeof(outb));
   }
-  if (refine) {
+  // the refinement's corrections and the status word, read back behind one synchronisation
+  uint32_t fword = 0;
+  if (refine)
     RIFT_CK(h, cudaMemcpyAsync(h->rstate_host, h->rstate, sizeof(RefineState) * np, cudaMemcpyDeviceToHost, st));
-    RIFT_CK(h, cudaStreamSynchronize(st));
-  }
-  rift_status fl = read_flags(h);
+  RIFT_CK(h, cudaMemcpyAsync(&fword, h->flags, sizeof(fword), cudaMemcpyDeviceToHost, st));
+  RIFT_CK(h, cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), st));
+  RIFT_CK(h, cudaStreamSynchronize(st));
+  rift_status fl = flags_status(h, fword);
   for (int p = 0; p < np; ++p) {
     fill_result(S.acc_host[p], &res[p], refine ? &h->rstate_host[p] : nullptr);
     res[p].rounds = rounds[p];

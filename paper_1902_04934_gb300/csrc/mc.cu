@@ -1085,9 +1085,11 @@ __device__ __forceinline__ void neumaier(double &s, double &c, double x) {
 // Pass 1 takes the largest partial maximum M; pass 2 sums s1 e^{m - M} and s2 e^{2(m - M)} in FP64
 // (the factors in FP32: relative 6e-8 on terms that are FP32 sums themselves), both reduced in a
 // fixed order, so the result is deterministic.
-__global__ void __launch_bounds__(256) merge_points_kernel(const Part *__restrict__ part, const RoundPt *__restrict__ rp,
-                                                           AccState *__restrict__ acc) {
-  __shared__ double sm[3][8];
+constexpr int kMergeThreads = 1024;
+__global__ void __launch_bounds__(kMergeThreads) merge_points_kernel(const Part *__restrict__ part,
+                                                                     const RoundPt *__restrict__ rp,
+                                                                     AccState *__restrict__ acc) {
+  __shared__ double sm[3][kMergeThreads / 32];
   __shared__ double sM;
   const RoundPt &R = rp[blockIdx.x];
   AccState &A = acc[blockIdx.x];
@@ -1534,7 +1536,7 @@ int cells_blocks_per_sm(int K, int ntap, size_t smem, int block, int tmarg) {
 
 cudaError_t launch_merge_points(const Part *partials, const RoundPt *rp, int n_points, AccState *acc,
                                 cudaStream_t st) {
-  merge_points_kernel<<<n_points, 256, 0, st>>>(partials, rp, acc);
+  merge_points_kernel<<<n_points, kMergeThreads, 0, st>>>(partials, rp, acc);
   return cudaGetLastError();
 }
 
