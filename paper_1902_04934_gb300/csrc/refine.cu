@@ -190,17 +190,19 @@ __device__ double2 detector_fp64_warp(const PointD &P, const double2 *__restrict
 }
 
 constexpr int kBuckets = 24;
+constexpr int kSelThreads = 1024;   // threads of the one block per point
 
 // Per point (one block): the round's candidates within B nats of the running maximum, in the order
-// (thread t of the block, its items t, t + 256, ..., warp, rank); B as in the header.  Items whose largest log weight lies 24 nats or more
-// below are skipped whole.  Learned and time-marginalised rounds choose none.
-__global__ void __launch_bounds__(256) refine_select_kernel(const RoundPt *__restrict__ rp,
+// (thread t of the block, its items t, t + kSelThreads, ..., warp, rank); B as in the header.  Items
+// whose largest log weight lies 24 nats or more below are skipped whole.  Learned and
+// time-marginalised rounds choose none.
+__global__ void __launch_bounds__(kSelThreads) refine_select_kernel(const RoundPt *__restrict__ rp,
                                                             const AccState *__restrict__ acc,
                                                             const float *__restrict__ cmax,
                                                             const float2 *__restrict__ cand, uint2 *__restrict__ list,
                                                             int *__restrict__ count) {
   __shared__ int hist[kBuckets];
-  __shared__ int scan[256];
+  __shared__ int scan[kSelThreads];
   __shared__ int s_B;
   const int p = blockIdx.x, t = threadIdx.x;
   const RoundPt R = rp[p];
@@ -210,10 +212,10 @@ __global__ void __launch_bounds__(256) refine_select_kernel(const RoundPt *__res
   }
   // the maximum is a float log weight (converted exactly): the distances below it in float
   const float Mx = (float)acc[p].m;
-  const long long ni = (long long)R.nitem;   // thread t takes items t, t + 256, ... (coalesced)
+  const long long ni = (long long)R.nitem;   // thread t takes items t, t + kSelThreads, ... (coalesced)
   if (t < kBuckets) hist[t] = 0;
   __syncthreads();
-  for (long long it = t; it < ni; it += 256) {
+  for (long long it = t; it < ni; it += kSelThreads) {
     const float pm = cmax[R.item0 + it];
     if (!(Mx - pm < (float)kBuckets)) continue;
     const float2 *c = cand + (R.item0 + it) * RIFT_CAND_PER_ITEM;
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(256) refine_select_kernel(const RoundPt *__res
   __syncthreads();
   const float B = (float)s_B;
   int mine = 0;
-  for (long long it = t; it < ni; it += 256) {
+  for (long long it = t; it < ni; it += kSelThreads) {
     const float pm = cmax[R.item0 + it];
     if (!(Mx - pm < B)) continue;
     const float2 *c = cand + (R.item0 + it) * RIFT_CAND_PER_ITEM;
@@ -248,14 +250,14 @@ __global__ void __launch_bounds__(256) refine_select_kernel(const RoundPt *__res
   }
   scan[t] = mine;
   __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
+  for (int o = 1; o < kSelThreads; o <<= 1) {
     const int v = (t >= o) ? scan[t - o] : 0;
     __syncthreads();
     scan[t] += v;
     __syncthreads();
   }
   int off = scan[t] - mine;
-  for (long long it = t; it < ni; it += 256) {
+  for (long long it = t; it < ni; it += kSelThreads) {
     const float pm = cmax[R.item0 + it];
     if (!(Mx - pm < B)) continue;
     const float2 *c = cand + (R.item0 + it) * RIFT_CAND_PER_ITEM;
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(256) refine_select_kernel(const RoundPt *__res
         list[(size_t)p * RIFT_REFINE_CAP + off++] = make_uint2(__float_as_uint(c[q].y), __float_as_uint(l));
     }
   }
-  if (t == 255) count[p] = min(scan[255], RIFT_REFINE_CAP);
+  if (t == kSelThreads - 1) count[p] = min(scan[kSelThreads - 1], RIFT_REFINE_CAP);
 }
 
 // One block per chosen sample, one warp per detector: (l32, l64) with l64 = FP64 lnL + FP64
@@ -357,7 +359,7 @@ cudaError_t launch_refine(const PointC *pts, const PointD *pd, const double2 *uv
   int *count = reinterpret_cast<int *>(b);
   b += ((size_t)np * sizeof(int) + 255) / 256 * 256;
   double2 *out = reinterpret_cast<double2 *>(b);
-  refine_select_kernel<<<np, 256, 0, st>>>(rp, acc, cmax, cand, list, count);
+  refine_select_kernel<<<np, kSelThreads, 0, st>>>(rp, acc, cmax, cand, list, count);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   refine_eval_kernel<<<dim3(RIFT_REFINE_CAP, (unsigned)np), 32 * RIFT_MAXK, 0, st>>>(pd, uv64, qa, rp, list, count, seed,
